@@ -1,0 +1,135 @@
+/*
+ * CPU oracle for dense matrix multiplication over GF(2^e), 2 <= e <= 10.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or constant with the
+ * CUDA path: no slicing schedule, no precomputed multiples, no tables.
+ *
+ * Every function is the plain definition it cites, written for clarity and
+ * not for speed:
+ *
+ *   - Field elements (Section 2, "Notation"): GF(2^e) = F2[x]/<f>, deg f = e,
+ *     an element sum_i a_i x^i is identified with the integer sum_i a_i 2^i.
+ *     f is passed as an integer bitmask that includes the x^e term.
+ *   - Field product: polynomial (carry-less) product of the two
+ *     representatives, then reduction modulo f.
+ *   - Matrix product (Algorithm 1, "Cubic matrix multiplication"): for every
+ *     row r of A and every index t of the inner dimension, row t of B is
+ *     scaled by A[r][t] and added into row r of C.  The printed loop indices
+ *     of Algorithm 1 are garbled; the standard reading C[r][c] =
+ *     sum_t A[r][t] * B[t][c] (A is m x l, B is l x n) is used.
+ *   - Addition in characteristic 2 is XOR (Section 1 and Section 3.1).
+ *   - Slicing (Section 3.2 and Figure 1): slice i of a matrix holds
+ *     coefficient i (bit i of the integer encoding) of every entry.  Slices
+ *     are stored as rows of 64-bit words, column c at bit (c mod 64) of word
+ *     floor(c / 64) (least significant bit first), padding bits zero.
+ *
+ * Parity of every function here is pinned by the tests in tests/ against
+ * values fixed independently of this file (Figure 1, the GF(4) example of
+ * Section 5, brute-force field axioms, logarithm tables, invariants).
+ */
+#include <stdint.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Section 2: product in F2[x]/<f>.  Carry-less multiply, then reduce the
+ * terms of degree 2e-2 down to e by subtracting (XOR) shifted copies of f. */
+uint32_t oracle_gf_mul(int e, uint32_t f, uint32_t a, uint32_t b)
+{
+    uint32_t p = 0;
+    for (int i = 0; i < e; i++)
+        if ((b >> i) & 1u)
+            p ^= a << i;
+    for (int d = 2 * e - 2; d >= e; d--)
+        if ((p >> d) & 1u)
+            p ^= f << (d - e);
+    return p;
+}
+
+/* Full 2^e x 2^e product table built entry by entry from oracle_gf_mul
+ * (used by the tests to compare against independently built tables). */
+void oracle_gf_mul_table(int e, uint32_t f, uint16_t *out)
+{
+    uint32_t q = 1u << e;
+    for (uint32_t a = 0; a < q; a++)
+        for (uint32_t b = 0; b < q; b++)
+            out[(size_t)a * q + b] = (uint16_t)oracle_gf_mul(e, f, a, b);
+}
+
+static int oracle_threads = 0;
+
+/* Number of OpenMP threads the matrix routines use (0 = OpenMP default). */
+void oracle_set_threads(int n) { oracle_threads = n; }
+
+int oracle_get_threads(void)
+{
+#ifdef _OPENMP
+    return oracle_threads > 0 ? oracle_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Algorithm 1: C <- C + A * B when accumulate != 0, C <- A * B otherwise.
+ * A is m x k, B is k x n, C is m x n, all row-major with leading dimensions
+ * k, n and n, entries stored as uint16 integers < 2^e.  Rows of C are
+ * independent, so they are distributed over threads; the per-row work is the
+ * algorithm's own loop order (scale row t of B by A[r][t], add to row r). */
+void oracle_matmul(int e, uint32_t f, int64_t m, int64_t n, int64_t k,
+                   const uint16_t *A, const uint16_t *B, uint16_t *C,
+                   int accumulate)
+{
+    int nt = oracle_get_threads();
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t r = 0; r < m; r++) {
+        uint16_t *crow = C + r * n;
+        if (!accumulate)
+            for (int64_t c = 0; c < n; c++)
+                crow[c] = 0;
+        for (int64_t t = 0; t < k; t++) {
+            uint32_t a = A[r * k + t];
+            const uint16_t *brow = B + t * n;
+            for (int64_t c = 0; c < n; c++)
+                crow[c] ^= (uint16_t)oracle_gf_mul(e, f, a, brow[c]);
+        }
+    }
+}
+
+/* Section 3.2 / Figure 1: slicing.  elems is rows x cols (uint16, row-major);
+ * slices receives e planes, plane i at slices + i * rows * ld_words, row r of
+ * plane i at + r * ld_words; bit (c mod 64) of word floor(c/64) is bit i of
+ * elems[r][c].  Padding bits (c >= cols) are written as zero. */
+void oracle_slice(int e, int64_t rows, int64_t cols, const uint16_t *elems,
+                  uint64_t *slices, int64_t ld_words)
+{
+    for (int i = 0; i < e; i++) {
+        uint64_t *plane = slices + (int64_t)i * rows * ld_words;
+        for (int64_t r = 0; r < rows; r++) {
+            uint64_t *row = plane + r * ld_words;
+            for (int64_t w = 0; w < ld_words; w++)
+                row[w] = 0;
+            for (int64_t c = 0; c < cols; c++)
+                if ((elems[r * cols + c] >> i) & 1u)
+                    row[c / 64] |= (uint64_t)1 << (c % 64);
+        }
+    }
+}
+
+/* Section 3.2: clinging, the inverse of slicing.  Padding bits are ignored. */
+void oracle_cling(int e, int64_t rows, int64_t cols, const uint64_t *slices,
+                  int64_t ld_words, uint16_t *elems)
+{
+    for (int64_t r = 0; r < rows; r++)
+        for (int64_t c = 0; c < cols; c++) {
+            uint32_t v = 0;
+            for (int i = 0; i < e; i++) {
+                const uint64_t *row = slices + (int64_t)i * rows * ld_words + r * ld_words;
+                v |= (uint32_t)((row[c / 64] >> (c % 64)) & 1u) << i;
+            }
+            elems[r * cols + c] = (uint16_t)v;
+        }
+}

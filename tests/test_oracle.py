@@ -1,0 +1,304 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every check compares the oracle with something computed independently of it:
+Figure 1, the GF(4) example of Section 5, textbook field products, logarithm
+tables built from powers of alpha, brute force and matrix identities.  The
+mutation tests at the end plant plausible mistakes into a copy of the
+oracle's C source and check that the pins catch each one.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests import fieldref as fr
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_fig1():
+    lines = [l.split("#")[0].strip() for l in open(os.path.join(GOLDEN, "fig1_gf8.txt"))]
+    lines = [l for l in lines if l]
+    e = int(lines[0].split()[1])
+    assert lines[1] == "elements"
+    elems = np.array([[int(v) for v in lines[2].split()], [int(v) for v in lines[3].split()]])
+    slices = []
+    i = 4
+    while i < len(lines):
+        assert lines[i].startswith("slice")
+        slices.append(np.array([[int(v) for v in lines[i + 1].split()], [int(v) for v in lines[i + 2].split()]]))
+        i += 3
+    return e, elems, slices
+
+
+# ---------------------------------------------------------------- Figure 1
+
+
+def test_fig1_slicing_matches_figure():
+    e, elems, slices = _read_fig1()
+    planes = oracle.slice_(e, elems)
+    assert planes.shape == (3, 2, 1)
+    for i in range(e):
+        got = np.array([[(int(planes[i, r, 0]) >> c) & 1 for c in range(2)] for r in range(2)])
+        np.testing.assert_array_equal(got, slices[i], err_msg=f"slice {i}")
+        # only the two columns may be set: padding bits are zero
+        assert all(int(planes[i, r, 0]) >> 2 == 0 for r in range(2))
+
+
+def test_fig1_clinging_inverts_slicing():
+    e, elems, _ = _read_fig1()
+    np.testing.assert_array_equal(oracle.cling(e, oracle.slice_(e, elems), 2), elems)
+
+
+def test_slice_cling_roundtrip_random_and_padding():
+    rng = np.random.default_rng(5)
+    for e in (2, 5, 8, 10):
+        X = workloads.elements(rng, e, (7, 131))
+        S = oracle.slice_(e, X, ld_words=4)   # wider than the 3 words needed
+        assert S.shape == (e, 7, 4)
+        assert (S[:, :, 3] == 0).all()
+        assert (S[:, :, 2] >> np.uint64(131 - 128) == 0).all()
+        # bit (c mod 64) of word c // 64 is coefficient i of column c
+        for (r, c) in [(0, 0), (3, 63), (6, 64), (2, 130)]:
+            for i in range(e):
+                assert (int(S[i, r, c // 64]) >> (c % 64)) & 1 == (int(X[r, c]) >> i) & 1
+        np.testing.assert_array_equal(oracle.cling(e, S, 131), X)
+
+
+# ---------------------------------------------------------------- the field
+
+
+@pytest.mark.parametrize("e", sorted(workloads.FIELD_POLY))
+def test_field_polynomials_irreducible_and_primitive(e):
+    f = workloads.FIELD_POLY[e]
+    assert fr.poly_deg(f) == e
+    assert fr.is_irreducible(f)
+    assert fr.order_of_x(e, f) == (1 << e) - 1
+
+
+def test_irreducibility_check_rejects_reducible():
+    # x^4 + 1 = (x + 1)^4, x^2 + 1 = (x + 1)^2, x^8+x^4+x^3+x^2 has the root 0,
+    # x^4 + x^2 + 1 = (x^2 + x + 1)^2
+    for f in (0x11, 0x5, 0x11C, 0x15):
+        assert not fr.is_irreducible(f)
+    assert fr.is_irreducible(0x1F)  # x^4+x^3+x^2+x+1: irreducible, x has order 5
+    assert fr.order_of_x(4, 0x1F) == 5
+
+
+def test_aes_worked_products():
+    rows = [l.split("#")[0].split() for l in open(os.path.join(GOLDEN, "aes_gf256.txt"))]
+    rows = [r for r in rows if r]
+    e = int(rows[0][1])
+    f = int(rows[1][1], 16)
+    assert fr.is_irreducible(f) and fr.order_of_x(e, f) == 51
+    for a, b, c in rows[2:]:
+        assert oracle.gf_mul(e, f, int(a, 16), int(b, 16)) == int(c, 16)
+
+
+@pytest.mark.parametrize("e", sorted(workloads.FIELD_POLY))
+def test_product_equals_log_table_exhaustive(e):
+    """All 2^(2e) products equal alpha^(log a + log b)."""
+    f = workloads.FIELD_POLY[e]
+    np.testing.assert_array_equal(oracle.mul_table(e, f).astype(np.int64), fr.log_table_product(e, f))
+
+
+@pytest.mark.parametrize("e", [2, 3, 4])
+def test_field_axioms_brute_force(e):
+    f = workloads.FIELD_POLY[e]
+    T = oracle.mul_table(e, f).astype(np.int64)
+    q = 1 << e
+    a = np.arange(q)
+    assert (T == T.T).all()                       # commutative
+    assert (T[1] == a).all() and (T[:, 0] == 0).all()   # identity, zero
+    # associative: (ab)c == a(bc) for all triples
+    A3, B3, C3 = np.meshgrid(a, a, a, indexing="ij")
+    assert (T[T[A3, B3], C3] == T[A3, T[B3, C3]]).all()
+    # distributive: a(b + c) == ab + ac
+    assert (T[A3, B3 ^ C3] == (T[A3, B3] ^ T[A3, C3])).all()
+    # every nonzero element has exactly one inverse
+    for x in range(1, q):
+        assert (T[x] == 1).sum() == 1
+    assert (T[0] == 1).sum() == 0
+
+
+def test_product_with_merely_irreducible_polynomial():
+    """0x11B is irreducible with x of order 51: the product still follows the
+    field axioms (checked against the xtime construction of b * x^i)."""
+    e, f = 8, 0x11B
+    T = oracle.mul_table(e, f).astype(np.int64)
+    # a * x^i via repeated xtime, for all a and i < 8, and linearity in b
+    for a in range(256):
+        xi = a
+        for i in range(8):
+            assert T[a, 1 << i] == xi
+            xi = fr.xtime(e, f, xi)
+    b = np.arange(256)
+    for a in (0x57, 0x83, 0xFF):
+        expect = np.zeros(256, dtype=np.int64)
+        for i in range(8):
+            expect ^= ((b >> i) & 1) * T[a, 1 << i]
+        assert (T[a] == expect).all()
+
+
+# ---------------------------------------------------------------- matrices
+
+
+def test_section5_gf4_example():
+    """Section 5: over GF(4) with f = x^2+x+1, C = (A1B1 + A1B0 + A0B1) x + A0B0 + A1B1,
+    and the 3-product form ((A1+A0)(B1+B0) + A0B0) x + A0B0 + A1B1."""
+    e, f = 2, 0x7
+    A, B, _ = workloads.random_problem(e, 23, 19, 37, seed=11)
+    C = oracle.matmul(e, f, A, B).astype(np.int64)
+    A0, A1, B0, B1 = fr.bits(A, 0), fr.bits(A, 1), fr.bits(B, 0), fr.bits(B, 1)
+    P = fr.gf2_matmul
+    C1 = P(A1, B1) ^ P(A1, B0) ^ P(A0, B1)
+    C0 = P(A0, B0) ^ P(A1, B1)
+    np.testing.assert_array_equal(C, C1 * 2 + C0)
+    K1 = P(A1 ^ A0, B1 ^ B0) ^ P(A0, B0)
+    np.testing.assert_array_equal(C, K1 * 2 + C0)
+
+
+@pytest.mark.parametrize("e", sorted(workloads.FIELD_POLY))
+def test_slice_decomposition_equals_oracle(e):
+    """Special case reducing to a library routine: the GF(2) slice products via
+    numpy integer matmul, recombined as a polynomial product and reduced mod f."""
+    f = workloads.FIELD_POLY[e]
+    A, B, _ = workloads.random_problem(e, 37, 41, 53, seed=100 + e)
+    np.testing.assert_array_equal(oracle.matmul(e, f, A, B).astype(np.int64), fr.slice_product(e, f, A, B))
+
+
+def test_brute_force_all_2x2x2_over_gf4():
+    """Every pair of 2x2 matrices over GF(4), against the logarithm table."""
+    e, f = 2, 0x7
+    T = fr.log_table_product(e, f)
+    mats = np.array(list(itertools.product(range(4), repeat=4)), dtype=np.int64).reshape(-1, 2, 2)
+    # stack all A as rows of one tall matrix and all B side by side, one oracle call
+    bigA = mats.reshape(-1, 2)                    # (256*2) x 2
+    bigB = mats.transpose(1, 0, 2).reshape(2, -1)  # 2 x (256*2)
+    got = oracle.matmul(e, f, bigA, bigB).astype(np.int64).reshape(256, 2, 256, 2).transpose(0, 2, 1, 3)
+    expect = np.zeros((256, 256, 2, 2), dtype=np.int64)
+    for t in range(2):
+        expect ^= T[mats[:, None, :, t, None], mats[None, :, None, t, :]]
+    np.testing.assert_array_equal(got, expect)
+
+
+def test_one_by_one_products_are_the_table():
+    for e in (3, 9):
+        f = workloads.FIELD_POLY[e]
+        T = fr.log_table_product(e, f)
+        rng = np.random.default_rng(e)
+        for a, b in rng.integers(0, 1 << e, size=(50, 2)):
+            assert int(oracle.matmul(e, f, [[a]], [[b]])[0, 0]) == T[a, b]
+
+
+@pytest.mark.parametrize("e", [2, 3, 8, 10])
+def test_matrix_invariants(e):
+    f = workloads.FIELD_POLY[e]
+    rng = np.random.default_rng(7 * e)
+    A = workloads.elements(rng, e, (9, 12))
+    B = workloads.elements(rng, e, (12, 10))
+    B2 = workloads.elements(rng, e, (12, 10))
+    D = workloads.elements(rng, e, (10, 8))
+    C0 = workloads.elements(rng, e, (9, 10))
+    mm = lambda X, Y: oracle.matmul(e, f, X, Y).astype(np.int64)
+    np.testing.assert_array_equal(mm(A, np.eye(12, dtype=np.int64)), A)
+    np.testing.assert_array_equal(mm(np.eye(9, dtype=np.int64), A), A)
+    assert (mm(A, np.zeros((12, 5), dtype=np.int64)) == 0).all()
+    np.testing.assert_array_equal(mm(A, B ^ B2), mm(A, B) ^ mm(A, B2))
+    np.testing.assert_array_equal(mm(mm(A, B), D), mm(A, mm(B, D)))
+    np.testing.assert_array_equal(mm(A, B).T, mm(B.T, A.T))
+    T = fr.log_table_product(e, f)
+    for j in (1, e - 1, e + 3):
+        aj = fr.x_power_mod(e, f, j)
+        np.testing.assert_array_equal(mm(aj * np.eye(12, dtype=np.int64), B), T[aj, B.astype(np.int64)])
+    C1 = oracle.addmul(e, f, A, B, C0).astype(np.int64)
+    np.testing.assert_array_equal(C1, mm(A, B) ^ C0)
+    np.testing.assert_array_equal(oracle.addmul(e, f, A, B, C1), C0)
+    # k = 0: mul gives zero, addmul leaves C
+    assert (mm(A[:, :0], B[:0]) == 0).all()
+    np.testing.assert_array_equal(oracle.addmul(e, f, A[:, :0], B[:0], C0), C0)
+
+
+def test_oracle_rejects_out_of_range_entries():
+    with pytest.raises(ValueError):
+        oracle.matmul(2, 0x7, [[4]], [[1]])
+
+
+def test_freivalds_accepts_correct_and_rejects_planted_error():
+    e, f = 4, 0x13
+    A, B, _ = workloads.random_problem(e, 40, 30, 50, seed=3)
+    C = oracle.matmul(e, f, A, B)
+    assert oracle.freivalds(e, f, A, B, C, trials=16)
+    bad = C.copy()
+    bad[17, 11] ^= 1
+    assert not oracle.freivalds(e, f, A, B, bad, trials=16)
+
+
+def test_threads_setting():
+    n = oracle.get_threads()
+    assert n >= 1
+    oracle.set_threads(1)
+    assert oracle.get_threads() == 1
+    oracle.set_threads(0)
+    assert oracle.get_threads() == n
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+_MUTANTS = {
+    # reduction subtracts f at the wrong degree
+    "reduce_shift": ("p ^= f << (d - e);", "p ^= f << (d - e + 1);"),
+    # reduction skips the highest product term
+    "reduce_top": ("for (int d = 2 * e - 2; d >= e; d--)", "for (int d = 2 * e - 3; d >= e; d--)"),
+    # carry-less multiply drops the top coefficient of b
+    "clmul_term": ("for (int i = 0; i < e; i++)\n        if ((b >> i) & 1u)", "for (int i = 0; i < e - 1; i++)\n        if ((b >> i) & 1u)"),
+    # matmul drops the last term of the inner sum
+    "dropped_t": ("for (int64_t t = 0; t < k; t++) {", "for (int64_t t = 0; t + 1 < k; t++) {"),
+    # matmul reads A transposed (only visible on non-symmetric inputs)
+    "transposed_a": ("uint32_t a = A[r * k + t];", "uint32_t a = A[(t % m) * k + (r % k)];"),
+    # slicing uses most-significant-bit-first columns
+    "slice_msb": ("row[c / 64] |= (uint64_t)1 << (c % 64);", "row[c / 64] |= (uint64_t)1 << (63 - c % 64);"),
+    # addition as OR instead of XOR
+    "add_or": ("crow[c] ^= (uint16_t)oracle_gf_mul(e, f, a, brow[c]);", "crow[c] |= (uint16_t)oracle_gf_mul(e, f, a, brow[c]);"),
+}
+
+
+def _pins_pass(O: oracle.OracleLib) -> bool:
+    """The cheap pins of this file, run against one compiled copy of the oracle."""
+    try:
+        e, elems, slices = _read_fig1()
+        planes = O.slice_(e, elems)
+        for i in range(e):
+            got = np.array([[(int(planes[i, r, 0]) >> c) & 1 for c in range(2)] for r in range(2)])
+            if not np.array_equal(got, slices[i]):
+                return False
+        for e in (2, 4, 8, 10):
+            f = workloads.FIELD_POLY[e]
+            if not np.array_equal(O.mul_table(e, f).astype(np.int64), fr.log_table_product(e, f)):
+                return False
+        for e in (2, 5):
+            f = workloads.FIELD_POLY[e]
+            A, B, _ = workloads.random_problem(e, 13, 11, 17, seed=9)
+            if not np.array_equal(O.matmul(e, f, A, B).astype(np.int64), fr.slice_product(e, f, A, B)):
+                return False
+        return True
+    except Exception:
+        return False
+
+
+def test_pins_pass_on_the_oracle():
+    assert _pins_pass(oracle.default())
+
+
+@pytest.mark.parametrize("name", sorted(_MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = _MUTANTS[name]
+    src = open(oracle.SOURCE).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mut = tmp_path / f"oracle_{name}.c"
+    mut.write_text(src.replace(old, new))
+    lib = oracle.compile_source(str(mut), str(tmp_path / f"lib_{name}.so"))
+    assert not _pins_pass(oracle.OracleLib(lib)), f"pins did not detect mutant {name}"
