@@ -1,0 +1,297 @@
+"""Benchmark: GF(2^e) matrix multiplication throughput on GB300.
+
+One step = one complete product C = A B over GF(2^4) with A, B 4096 x 4096
+(operand slicing, the GF(2) slice GEMM with its fused parity + mod-f
+epilogue), inputs already resident in device memory.  Every form is timed
+(bit-packed popc on the CUDA cores, tcgen05 with exact 0/1 FP8 operands, ...)
+and `value` is the fastest; the per-form numbers are in "forms".  The L2 cache
+is flushed (a 512 MB write) between timed steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun, one rank per GPU) runs an independent replica per rank
+("replicas only": the product needs no exchange); value = all ranks'
+field operations / the slowest rank's time.
+
+--impl reference times the CPU oracle (test infrastructure, plain C with
+OpenMP over rows) on a bounded row panel of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = workloads.WORKLOADS[2]
+METRIC = "GF(2^e) matmul field-ops/s, 4096² GF(2^4), INT8-TC vs bit-packed; bit-exact"
+UNIT = "field-ops/s"
+CONFIG = {"workload": "C = A*B over GF(2^4), f = x^4+x+1, A, B 4096x4096 uint8",
+          "m": 4096, "n": 4096, "k": 4096, "e": 4, "f": "0x13",
+          "l2": "flushed between timed steps (512 MB write, not timed)"}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(rows: int = 32):
+    """The oracle on a row panel of the workload (bounded CPU work)."""
+    import oracle
+    w = WORKLOAD
+    A, B, _ = w.inputs()
+    Ap = np.ascontiguousarray(A[:rows])
+    t0 = time.perf_counter()
+    oracle.matmul(w.e, w.f, Ap, B)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * rows * w.n * w.k / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"rows 0..{rows - 1} of A times B ({rows}x{w.k}x{w.n}), one run, {dt:.2f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    w = WORKLOAD
+    A, B, _ = w.inputs()
+    rows = args.ref_rows
+    Ap = np.ascontiguousarray(A[:rows])
+    for _ in range(args.warmup):
+        oracle.matmul(w.e, w.f, Ap, B)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.matmul(w.e, w.f, Ap, B)
+        times.append(time.perf_counter() - t0)
+    per = sum(times) / len(times)
+    value = 2.0 * rows * w.n * w.k / per
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": CONFIG,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                            "sample": f"each step: rows 0..{rows - 1} of A times B ({rows}x{w.k}x{w.n})"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", default="popc,tc_f8")
+    ap.add_argument("--schedules", default="alpha_b,karatsuba")
+    ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import paper_1111_6900_gb300 as m4
+
+    w = WORKLOAD
+    A, B, _ = w.inputs()
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    dC = torch.empty((w.m, w.n), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = m4.Context(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    results = {}
+    for form in args.forms.split(","):
+        for sched in args.schedules.split(","):
+            ctx.set_form(form)
+            ctx.set_schedule(sched)
+            try:
+                for _ in range(args.warmup):
+                    ctx.mul(w.e, w.f, dA, dB, dC)
+                torch.cuda.synchronize()
+            except m4.M4rieError as err:
+                results[f"{form}/{sched}"] = {"error": str(err)}
+                continue
+            ctx.enable_timing(True)
+            ctx.phase_times(reset=True)
+            launches0 = ctx.kernel_launches()
+            starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            barrier()
+            with ClockSampler(local) as clk:
+                for i in range(args.steps):
+                    flush.fill_(i & 0xFF)
+                    starts[i].record(stream)
+                    ctx.mul(w.e, w.f, dA, dB, dC)
+                    stops[i].record(stream)
+                barrier()
+            ms = sum(s.elapsed_time(t) for s, t in zip(starts, stops)) / args.steps
+            pack_ms, gemm_ms, rec_ms, nprod = ctx.phase_times(reset=True)
+            ctx.enable_timing(False)
+            if world > 1:
+                t = torch.tensor([ms], device="cuda")
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                ms = float(t.item())
+            status = ctx.device_status()
+            results[f"{form}/{sched}"] = {
+                "ms_per_step": ms, "value": world * w.field_ops / (ms * 1e-3),
+                "gemm_ms": gemm_ms / max(nprod, 1), "pack_ms": pack_ms / max(nprod, 1),
+                "recombine_ms": rec_ms / max(nprod, 1), "launches": ctx.kernel_launches() - launches0,
+                "products": m4.schedule_products(w.e, w.f, sched), "clocks": clk.summary(),
+                "device_status": status}
+
+    good = {k: v for k, v in results.items() if "value" in v and v["device_status"] == m4.OK}
+    best_key = max(good, key=lambda k: good[k]["value"])
+    best = good[best_key]
+    form, sched = best_key.split("/")
+
+    # end-to-end: host buffers through the C ABI (pinned), copies inside the timed region
+    ctx.set_form(form)
+    ctx.set_schedule(sched)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.empty((w.m, w.n), dtype=torch.uint8).pin_memory()
+    for _ in range(2):
+        ctx.mul_host(w.e, w.f, hA, hB, hC)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 4)
+    for _ in range(e2e_steps):
+        ctx.mul_host(w.e, w.f, hA, hB, hC)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel (the slice GEMM)
+    pk = peaks() or {}
+    r = m4.schedule_products(w.e, w.f, sched)
+    gemm_s = best["gemm_ms"] * 1e-3
+    if form == "popc":
+        # one LOP3 (AND + XOR) per 32 bit-MACs; ALU pipe 16 lanes / SMSP / clock
+        bitmacs = r * w.m * w.n * w.k
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 4 * 16 * 32 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": bitmacs / gemm_s / 1e12, "peak": peak, "unit": "T bit-MAC/s",
+                "frac": bitmacs / gemm_s / 1e12 / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 SMSPs x 16 LOP3 lanes x 32 bits x max SM clock"}
+    else:
+        flops = 2.0 * r * w.m * w.n * w.k
+        bf16 = pk.get("bf16_tflops", 1900.0)
+        peak = bf16 * 2.0  # FP8 dense = 2 x bf16 dense (nominal 4.5 vs 2.25 PFLOP/s)
+        roof = {"bound": "tensor", "achieved": flops / gemm_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / gemm_s / 1e12 / peak, "traffic": None,
+                "peak_source": ("measured bf16 burst x 2 (FP8/bf16 nominal ratio)" if peaks()
+                                else "fallback 1.9 PFLOP/s bf16 x 2")}
+
+    out = {"metric": METRIC, "value": best["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": best["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "config": dict(CONFIG, form=form, schedule=sched, parallelism=f"replicas{world}"),
+           "clocks": best["clocks"], "gpu_launches": best["launches"],
+           "e2e": {"value": world * w.field_ops / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": A.nbytes + B.nbytes, "d2h_bytes_per_step": w.m * w.n},
+           "roofline": roof,
+           "forms": {k: ({"value": v["value"], "ms_per_step": v["ms_per_step"], "gemm_ms": v["gemm_ms"],
+                          "pack_ms": v["pack_ms"], "recombine_ms": v["recombine_ms"], "products": v["products"]}
+                         if "value" in v else v) for k, v in results.items()}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * m4rie_gpu.h -- C ABI of the GB300 (sm_103a) library for dense matrix
+ * multiplication over GF(2^e), 2 <= e <= 10, in the bitsliced form.
+ *
+ * Method (Section 5, "Karatsuba multiplication"): a matrix over GF(2^e) is a
+ * polynomial with GF(2)-matrix coefficients, its slices (Section 3.2).  The
+ * product A*B is computed from GF(2) products of slices (or of XOR sums of
+ * slices), whose results are recombined and reduced modulo the field
+ * polynomial f.  Every result is exact: each call produces the same bits as
+ * the plain definition C[r][c] = sum_t A[r][t] * B[t][c] (Algorithm 1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Field elements (Section 2): the integer sum_i a_i 2^i stands for
+ *    sum_i a_i x^i in F2[x]/<f>.  Element arrays are uint8 when e <= 8 and
+ *    little-endian uint16 when e is 9 or 10.  Addition is XOR.
+ *  - f: bitmask of the field polynomial including the x^e term (for example
+ *    0x13 = x^4 + x + 1).  It must have degree exactly e and be irreducible;
+ *    primitivity is not required.
+ *  - Matrices: contiguous row-major, A is m x k, B is k x n, C is m x n
+ *    (leading dimensions k, n, n).
+ *  - Pointers: device pointers owned by the caller, unless the name says host.
+ *    The library never frees them.  A pointer may be NULL only when the
+ *    matrix it points to has no entries.
+ *  - Asynchrony: calls enqueue work on the context's stream and return
+ *    without waiting.  The return value reports host-side validation and
+ *    launch errors only.  Errors found on the device (an entry >= 2^e, a
+ *    wait that timed out) set a sticky device status word that
+ *    m4rie_get_device_status() reads.  An out-of-range entry is then used
+ *    through its low e bits, so the output stays deterministic.
+ *  - Zero sizes: m == 0 or n == 0 is a no-op.  k == 0 makes m4rie_mul write
+ *    zeros to C and leaves C unchanged for m4rie_addmul.
+ *  - Errors never trap or abort on the device.
+ */
+#ifndef M4RIE_GPU_H
+#define M4RIE_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum m4rie_status {
+    M4RIE_OK = 0,
+    M4RIE_ERR_ARG = 1,        /* invalid argument: e outside [2,10], negative size, NULL data, bad option */
+    M4RIE_ERR_POLY = 2,       /* f does not have degree e or is reducible over GF(2) */
+    M4RIE_ERR_ALIAS = 3,      /* the output overlaps an input */
+    M4RIE_ERR_RANGE = 4,      /* device: an input entry was >= 2^e (its low e bits were used) */
+    M4RIE_ERR_NOMEM = 5,      /* workspace allocation failed */
+    M4RIE_ERR_CUDA = 6,       /* a CUDA runtime or driver call failed (see m4rie_last_error) */
+    M4RIE_ERR_TIMEOUT = 7,    /* device: a bounded wait inside a kernel ran out; that kernel's output is incomplete */
+    M4RIE_ERR_UNSUPPORTED = 8 /* the requested form is not available for this problem or device */
+} m4rie_status;
+
+/* How the GF(2) slice products are computed. */
+typedef enum m4rie_form {
+    M4RIE_FORM_AUTO = 0,   /* autotuned choice (the fastest form measured for this shape class) */
+    M4RIE_FORM_POPC = 1,   /* bit-packed slices, AND/XOR on the CUDA cores, parity by popcount */
+    M4RIE_FORM_TC_F8 = 2,  /* tcgen05 tensor cores; 0/1 operands encoded exactly as FP8 E4M3, FP32 counts */
+    M4RIE_FORM_MMA_S8 = 3, /* legacy warp-level INT8 tensor instructions (mma.sync s8), int32 counts */
+    M4RIE_FORM_TC_F4 = 4   /* tcgen05 block-scaled FP4 (E2M1 0/1 operands, unit scales), FP32 counts */
+} m4rie_form;
+
+/* Which bilinear schedule reduces the GF(2^e) product to GF(2) products. */
+typedef enum m4rie_schedule {
+    M4RIE_SCHED_AUTO = 0,      /* autotuned choice */
+    M4RIE_SCHED_ALPHA_B = 1,   /* e^2 products C_i = sum_j A_j (alpha^j B)_i: the schoolbook count,
+                                  with the reduction mod f folded into B (Algorithm 2's alpha^k B) */
+    M4RIE_SCHED_KARATSUBA = 2  /* Karatsuba-like: fewer products (Table 3), recombined after parity */
+} m4rie_schedule;
+
+typedef struct m4rie_ctx m4rie_ctx;
+
+/* One product of a batch (m4rie_mul_batched).  Host-side descriptor; the
+ * pointers inside are device pointers. */
+typedef struct m4rie_problem {
+    int32_t e;
+    uint32_t f;
+    int64_t m, n, k;
+    const void *A;  /* m x k */
+    const void *B;  /* k x n */
+    void *C;        /* m x n */
+    int32_t accumulate; /* 0: C = A B, 1: C += A B */
+    int32_t reserved;
+} m4rie_problem;
+
+/* Create a context bound to the current CUDA device and to `stream` (a
+ * cudaStream_t; NULL means the legacy default stream).  The context owns a
+ * device workspace that grows on demand, the device status word and the
+ * autotuning cache.  One context per stream; a context is not thread-safe.
+ * Returns M4RIE_ERR_ARG if ctx is NULL, M4RIE_ERR_CUDA if no device. */
+m4rie_status m4rie_create(m4rie_ctx **ctx, void *stream);
+
+/* Wait for the context's stream, then free everything it owns. */
+void m4rie_destroy(m4rie_ctx *ctx);
+
+/* Select the form and the schedule used by later calls (AUTO by default).
+ * M4RIE_ERR_ARG for an unknown value. */
+m4rie_status m4rie_set_form(m4rie_ctx *ctx, int form);
+m4rie_status m4rie_set_schedule(m4rie_ctx *ctx, int schedule);
+
+/* C = A * B over GF(2^e) = F2[x]/<f> (Section 5; result as in Algorithm 1).
+ * A: m x k, B: k x n, C: m x n, device pointers, element width from e.
+ * C must not overlap A or B (M4RIE_ERR_ALIAS).  Asynchronous on the stream. */
+m4rie_status m4rie_mul(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
+                       const void *A, const void *B, void *C);
+
+/* C = C + A * B over GF(2^e) (addition is XOR, Section 3.1).  C is read and
+ * updated in place; otherwise as m4rie_mul. */
+m4rie_status m4rie_addmul(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
+                          const void *A, const void *B, void *C);
+
+/* m4rie_mul / m4rie_addmul (accumulate != 0) on HOST buffers: copies A, B
+ * (and C when accumulating) to context-owned device memory, computes, copies
+ * C back and waits for the stream.  Host buffers may be pageable or pinned. */
+m4rie_status m4rie_mul_host(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
+                            const void *hostA, const void *hostB, void *hostC, int accumulate);
+
+/* Slicing (Section 3.2, Figure 1): elements (rows x cols, row-major) to e
+ * GF(2) slices.  Slice i holds coefficient i of every entry; slice i, row r
+ * starts at slices + (i * rows + r) * ld_words; column c is bit (c mod 64) of
+ * word floor(c / 64), least significant bit first.  ld_words >= ceil(cols/64);
+ * padding bits are written as zero.  Device pointers. */
+m4rie_status m4rie_pack(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, const void *elems,
+                        uint64_t *slices, int64_t ld_words);
+
+/* Clinging (Section 3.2): the inverse of m4rie_pack.  Padding bits are ignored. */
+m4rie_status m4rie_unpack(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, const uint64_t *slices,
+                          int64_t ld_words, void *elems);
+
+/* Many independent products (each with its own e, f, m, n, k) in one
+ * persistent launch.  `problems` is a HOST array of `count` descriptors,
+ * validated like m4rie_mul; no two outputs may overlap each other or any
+ * input.  The work is recorded once into a CUDA graph that is cached in the
+ * context and replayed while the same descriptor array contents are passed. */
+m4rie_status m4rie_mul_batched(m4rie_ctx *ctx, int count, const m4rie_problem *problems);
+
+/* Wait for the stream, return the sticky device status (M4RIE_OK,
+ * M4RIE_ERR_RANGE or M4RIE_ERR_TIMEOUT; TIMEOUT wins) and clear it. */
+m4rie_status m4rie_get_device_status(m4rie_ctx *ctx);
+
+/* Number of GF(2) slice products that `schedule` uses for GF(2^e) with the
+ * field polynomial f (e^2 for ALPHA_B).  Negative m4rie_status on error. */
+int m4rie_schedule_products(int e, uint32_t f, int schedule);
+
+/* The host-side checks of m4rie_mul on these arguments, without a context,
+ * a device or a launch: M4RIE_OK, M4RIE_ERR_ARG, M4RIE_ERR_POLY or
+ * M4RIE_ERR_ALIAS.  Pointers are only compared, never dereferenced. */
+m4rie_status m4rie_validate(int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void *A, const void *B,
+                            const void *C);
+
+/* The masks of a schedule, for inspection: product p multiplies the XOR sum
+ * of the A slices in amask[p] by the XOR sum of the B slices in bmask[p];
+ * output slice s is the XOR of the products p with bit p of out_mask[s].  For
+ * ALPHA_B, product p = i*e + j is A_j times (alpha^j B)_i: amask[p] = 1 << j
+ * and bmask[p] holds the coefficients of alpha^j B that make slice i;
+ * product p feeds output slice p / e (out_mask is filled only when e*e <= 64).
+ * Arrays must hold `cap` entries (out_mask: 10).  Returns the number of
+ * products, or a negative m4rie_status. */
+int m4rie_schedule_masks(int e, uint32_t f, int schedule, int cap, uint16_t *amask, uint16_t *bmask,
+                         uint64_t *out_mask);
+
+/* Form that AUTO picks for this shape (after m4rie_tune, the measured best). */
+int m4rie_resolve_form(m4rie_ctx *ctx, int e, int64_t m, int64_t n, int64_t k);
+
+/* Static description of a status code. */
+const char *m4rie_status_string(m4rie_status s);
+
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char *m4rie_last_error(m4rie_ctx *ctx);
+
+/* Number of this library's kernels launched through ctx since creation. */
+int64_t m4rie_kernel_launches(m4rie_ctx *ctx);
+
+/* Per-phase device timing for measurement.  When enabled, the context
+ * records CUDA events on its stream around each phase of every product:
+ * operand slicing (pack kernels), the GF(2) slice GEMM, and the
+ * recombination / output phase when it is a separate kernel.
+ * m4rie_phase_times waits for the stream and returns the accumulated
+ * milliseconds and the number of products timed since the last reset
+ * (reset = 1 clears them).  Timing adds no synchronisation while enabled. */
+m4rie_status m4rie_enable_timing(m4rie_ctx *ctx, int on);
+m4rie_status m4rie_phase_times(m4rie_ctx *ctx, double *pack_ms, double *gemm_ms, double *recombine_ms,
+                               int64_t *products, int reset);
+
+/* Test hook: limit, in nanoseconds, of every bounded wait inside this
+ * context's persistent kernels (default 4e9).  A small value makes those
+ * waits run out; the kernel then sets M4RIE_ERR_TIMEOUT and returns. */
+m4rie_status m4rie_set_wait_limit_ns(m4rie_ctx *ctx, uint64_t ns);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* M4RIE_GPU_H */

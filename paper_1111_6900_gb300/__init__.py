@@ -1,0 +1,247 @@
+"""Python binding of the GB300 GF(2^e) bitsliced matmul library (libm4rie_gpu.so).
+
+Thin argument marshalling over the C ABI declared in include/m4rie_gpu.h: the
+functions keep the C names, take torch CUDA tensors (for device memory and
+streams) and pass raw pointers.  Every step of the computation runs in the
+library's CUDA kernels; there is no CPU fallback.  Importing this package
+without the built library raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libm4rie_gpu.so")
+
+OK, ERR_ARG, ERR_POLY, ERR_ALIAS, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
+FORM_AUTO, FORM_POPC, FORM_TC_F8, FORM_MMA_S8, FORM_TC_F4 = range(5)
+SCHED_AUTO, SCHED_ALPHA_B, SCHED_KARATSUBA = range(3)
+FORMS = {"auto": FORM_AUTO, "popc": FORM_POPC, "tc_f8": FORM_TC_F8, "mma_s8": FORM_MMA_S8, "tc_f4": FORM_TC_F4}
+SCHEDULES = {"auto": SCHED_AUTO, "alpha_b": SCHED_ALPHA_B, "karatsuba": SCHED_KARATSUBA}
+
+
+class M4rieError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {status_string(status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("e", ctypes.c_int32), ("f", ctypes.c_uint32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("k", ctypes.c_int64), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("accumulate", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+                          "(needs nvcc for sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32, i64, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "m4rie_create": (i32, [ctypes.POINTER(vp), vp]),
+        "m4rie_destroy": (None, [vp]),
+        "m4rie_set_form": (i32, [vp, i32]),
+        "m4rie_set_schedule": (i32, [vp, i32]),
+        "m4rie_mul": (i32, [vp, i32, u32, i64, i64, i64, vp, vp, vp]),
+        "m4rie_addmul": (i32, [vp, i32, u32, i64, i64, i64, vp, vp, vp]),
+        "m4rie_mul_host": (i32, [vp, i32, u32, i64, i64, i64, vp, vp, vp, i32]),
+        "m4rie_pack": (i32, [vp, i32, i64, i64, vp, vp, i64]),
+        "m4rie_unpack": (i32, [vp, i32, i64, i64, vp, i64, vp]),
+        "m4rie_mul_batched": (i32, [vp, i32, vp]),
+        "m4rie_get_device_status": (i32, [vp]),
+        "m4rie_schedule_products": (i32, [i32, u32, i32]),
+        "m4rie_schedule_masks": (i32, [i32, u32, i32, i32, vp, vp, vp]),
+        "m4rie_validate": (i32, [i32, u32, i64, i64, i64, vp, vp, vp]),
+        "m4rie_resolve_form": (i32, [vp, i32, i64, i64, i64]),
+        "m4rie_status_string": (ctypes.c_char_p, [i32]),
+        "m4rie_last_error": (ctypes.c_char_p, [vp]),
+        "m4rie_kernel_launches": (i64, [vp]),
+        "m4rie_set_wait_limit_ns": (i32, [vp, u64]),
+        "m4rie_enable_timing": (i32, [vp, i32]),
+        "m4rie_phase_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def status_string(status: int) -> str:
+    return lib.m4rie_status_string(int(status)).decode()
+
+
+def elem_dtype_torch(e: int):
+    import torch
+    return torch.uint8 if e <= 8 else torch.uint16
+
+
+def _ptr(t):
+    return None if t is None or t.numel() == 0 else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_dev(t, e, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != elem_dtype_torch(e):
+        raise TypeError(f"{name} must be {elem_dtype_torch(e)} for e = {e}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (row-major)")
+
+
+class Context:
+    """An m4rie_ctx bound to the current device and a torch CUDA stream."""
+
+    def __init__(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = ctypes.c_void_p()
+        st = lib.m4rie_create(ctypes.byref(handle), ctypes.c_void_p(stream.cuda_stream))
+        if st != OK:
+            raise M4rieError(st, "m4rie_create")
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.m4rie_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, st, where):
+        if st != OK:
+            raise M4rieError(st, where, lib.m4rie_last_error(self.handle).decode())
+
+    def set_form(self, form):
+        self._raise(lib.m4rie_set_form(self.handle, FORMS.get(form, form)), "m4rie_set_form")
+
+    def set_schedule(self, schedule):
+        self._raise(lib.m4rie_set_schedule(self.handle, SCHEDULES.get(schedule, schedule)), "m4rie_set_schedule")
+
+    def set_wait_limit_ns(self, ns: int):
+        self._raise(lib.m4rie_set_wait_limit_ns(self.handle, int(ns)), "m4rie_set_wait_limit_ns")
+
+    def mul(self, e: int, f: int, A, B, C=None):
+        """C = A B over GF(2^e); allocates C when not given.  Asynchronous."""
+        import torch
+        _check_dev(A, e, "A")
+        _check_dev(B, e, "B")
+        m, k = A.shape
+        k2, n = B.shape
+        if k2 != k:
+            raise ValueError("inner dimensions differ")
+        if C is None:
+            C = torch.empty((m, n), dtype=A.dtype, device=A.device)
+        _check_dev(C, e, "C")
+        self._raise(lib.m4rie_mul(self.handle, e, f, m, n, k, _ptr(A), _ptr(B), _ptr(C)), "m4rie_mul")
+        return C
+
+    def addmul(self, e: int, f: int, A, B, C):
+        """C += A B over GF(2^e), in place.  Asynchronous."""
+        for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+            _check_dev(t, e, nm)
+        m, k = A.shape
+        n = B.shape[1]
+        self._raise(lib.m4rie_addmul(self.handle, e, f, m, n, k, _ptr(A), _ptr(B), _ptr(C)), "m4rie_addmul")
+        return C
+
+    def mul_host(self, e: int, f: int, A, B, C, accumulate: bool = False):
+        """Host-buffer product (torch CPU tensors or numpy arrays); synchronous."""
+        import numpy as np
+
+        def addr(x):
+            if hasattr(x, "data_ptr"):
+                return ctypes.c_void_p(x.data_ptr()) if x.numel() else None
+            x = np.asarray(x)
+            return ctypes.c_void_p(x.ctypes.data) if x.size else None
+        m, k = A.shape
+        n = B.shape[1]
+        self._raise(lib.m4rie_mul_host(self.handle, e, f, m, n, k, addr(A), addr(B), addr(C), 1 if accumulate else 0),
+                    "m4rie_mul_host")
+        return C
+
+    def pack(self, e: int, elems, ld_words: int | None = None):
+        """Slicing (Section 3.2): returns int64 tensor (e, rows, ld_words) of 64-bit words."""
+        import torch
+        _check_dev(elems, e, "elems")
+        rows, cols = elems.shape
+        if ld_words is None:
+            ld_words = (cols + 63) // 64
+        S = torch.empty((e, rows, ld_words), dtype=torch.int64, device=elems.device)
+        self._raise(lib.m4rie_pack(self.handle, e, rows, cols, _ptr(elems), _ptr(S), ld_words), "m4rie_pack")
+        return S
+
+    def unpack(self, e: int, slices, cols: int):
+        """Clinging: (e, rows, ld_words) words -> rows x cols elements."""
+        import torch
+        _, rows, ld_words = slices.shape
+        X = torch.empty((rows, cols), dtype=elem_dtype_torch(e), device=slices.device)
+        self._raise(lib.m4rie_unpack(self.handle, e, rows, cols, _ptr(slices), ld_words, _ptr(X)), "m4rie_unpack")
+        return X
+
+    def mul_batched(self, problems):
+        """problems: list of (e, f, A, B, C, accumulate) with CUDA tensors."""
+        arr = (_Problem * len(problems))()
+        for i, (e, f, A, B, C, acc) in enumerate(problems):
+            m, k = A.shape
+            n = B.shape[1]
+            arr[i] = _Problem(e, f, m, n, k, A.data_ptr(), B.data_ptr(), C.data_ptr(), 1 if acc else 0, 0)
+        self._raise(lib.m4rie_mul_batched(self.handle, len(problems), arr), "m4rie_mul_batched")
+
+    def enable_timing(self, on: bool = True):
+        self._raise(lib.m4rie_enable_timing(self.handle, 1 if on else 0), "m4rie_enable_timing")
+
+    def phase_times(self, reset: bool = True):
+        """(pack_ms, gemm_ms, recombine_ms, products) accumulated since the last reset."""
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        self._raise(lib.m4rie_phase_times(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                          ctypes.byref(n), 1 if reset else 0), "m4rie_phase_times")
+        return a.value, b.value, c.value, n.value
+
+    def device_status(self) -> int:
+        return lib.m4rie_get_device_status(self.handle)
+
+    def kernel_launches(self) -> int:
+        return int(lib.m4rie_kernel_launches(self.handle))
+
+    def resolve_form(self, e, m, n, k) -> int:
+        return int(lib.m4rie_resolve_form(self.handle, e, m, n, k))
+
+
+def schedule_products(e: int, f: int, schedule) -> int:
+    return int(lib.m4rie_schedule_products(e, f, SCHEDULES.get(schedule, schedule)))
+
+
+def schedule_masks(e: int, f: int, schedule):
+    """(amask list, bmask list, out_mask list of 10) of a schedule."""
+    cap = 128
+    am = (ctypes.c_uint16 * cap)()
+    bm = (ctypes.c_uint16 * cap)()
+    om = (ctypes.c_uint64 * 10)()
+    r = lib.m4rie_schedule_masks(e, f, SCHEDULES.get(schedule, schedule), cap, am, bm, om)
+    if r < 0:
+        raise M4rieError(-r, "m4rie_schedule_masks")
+    return list(am[:r]), list(bm[:r]), list(om)
+
+
+def validate(e, f, m, n, k, A=None, B=None, C=None) -> int:
+    """Host-side argument check; A, B, C are integer addresses (or None)."""
+    v = lambda x: None if x is None else ctypes.c_void_p(x)
+    return int(lib.m4rie_validate(e, f, m, n, k, v(A), v(B), v(C)))

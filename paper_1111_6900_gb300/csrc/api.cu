@@ -1,0 +1,672 @@
+// Host side of the C ABI (include/m4rie_gpu.h): validation, workspace,
+// schedule and form selection, kernel dispatch.
+#include <cstdio>
+#include <cstdlib>
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/m4rie_gpu.h"
+#include "m4rie_internal.cuh"
+#include "schedule.h"
+
+using namespace m4rie;
+
+struct m4rie_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* io = nullptr;  // device copies for m4rie_mul_host
+  size_t io_bytes = 0;
+  int* d_status = nullptr;
+  int form = M4RIE_FORM_AUTO;
+  int schedule = M4RIE_SCHED_AUTO;
+  std::string last_error;
+  int64_t launches = 0;
+  uint64_t wait_limit_ns = 4000000000ull;
+  int tc_chunk = 4096;  // elements of K' per FP32 accumulation chunk
+  int auto_form[11][4];   // [e][size class] -> form, 0 = heuristic
+  int auto_sched[11][4];
+  // phase timing (m4rie_enable_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;  // (phase, (start, stop))
+  size_t ev_next = 0;
+  double phase_ms[3] = {0, 0, 0};
+  int64_t timed_products = 0;
+};
+
+namespace {
+
+m4rie_status cuda_fail(m4rie_ctx* ctx, cudaError_t err) {
+  if (ctx) ctx->last_error = cudaGetErrorString(err);
+  return M4RIE_ERR_CUDA;
+}
+
+int elem_bytes(int e) { return e <= 8 ? 1 : 2; }
+
+// Phase markers: mark(ctx, phase) opens a phase, mark(ctx, -1) closes it.
+enum { kPhasePack = 0, kPhaseGemm = 1, kPhaseRecombine = 2 };
+
+cudaEvent_t take_event(m4rie_ctx* ctx) {
+  if (ctx->ev_next == ctx->ev_pool.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    ctx->ev_pool.push_back(ev);
+  }
+  return ctx->ev_pool[ctx->ev_next++];
+}
+
+struct PhaseTimer {
+  m4rie_ctx* ctx;
+  int phase = -1;
+  cudaEvent_t start = nullptr;
+  explicit PhaseTimer(m4rie_ctx* c) : ctx(c) {}
+  void begin(int ph) {
+    end();
+    if (!ctx->timing) return;
+    start = take_event(ctx);
+    if (start && cudaEventRecord(start, ctx->stream) == cudaSuccess) phase = ph;
+  }
+  void end() {
+    if (phase < 0) return;
+    cudaEvent_t stop = take_event(ctx);
+    if (stop && cudaEventRecord(stop, ctx->stream) == cudaSuccess) ctx->ev_pending.push_back({phase, {start, stop}});
+    phase = -1;
+  }
+  ~PhaseTimer() { end(); }
+};
+
+bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
+  if (!an || !bn) return false;
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bn && y < x + an;
+}
+
+m4rie_status check_field(int e, uint32_t f) {
+  if (e < 2 || e > 10) return M4RIE_ERR_ARG;
+  if (poly_degree(f) != e || !poly_irreducible(f)) return M4RIE_ERR_POLY;
+  return M4RIE_OK;
+}
+
+m4rie_status validate(int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                      const void* C) {
+  m4rie_status st = check_field(e, f);
+  if (st != M4RIE_OK) return st;
+  if (m < 0 || n < 0 || k < 0) return M4RIE_ERR_ARG;
+  // sizes the kernels index with 32-bit block counts and 64-bit offsets
+  if (m > (1ll << 31) || n > (1ll << 31) || k > (1ll << 31)) return M4RIE_ERR_ARG;
+  if ((m * k && !A) || (k * n && !B) || (m * n && !C)) return M4RIE_ERR_ARG;
+  const size_t w = elem_bytes(e);
+  if (overlaps(C, (size_t)(m * n) * w, A, (size_t)(m * k) * w) || overlaps(C, (size_t)(m * n) * w, B, (size_t)(k * n) * w))
+    return M4RIE_ERR_ALIAS;
+  return M4RIE_OK;
+}
+
+m4rie_status ensure_ws(m4rie_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return M4RIE_OK;
+  cudaError_t err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  size_t want = bytes + (bytes >> 3);
+  if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->ws = nullptr;
+      ctx->last_error = "workspace allocation failed";
+      return M4RIE_ERR_NOMEM;
+    }
+    want = bytes;
+  }
+  ctx->ws_bytes = want;
+  return M4RIE_OK;
+}
+
+int size_class(int64_t m, int64_t n, int64_t k) {
+  const double v = (double)m * (double)n * (double)k;
+  if (v < 1.0e7) return 0;
+  if (v < 1.0e9) return 1;
+  if (v < 2.0e10) return 2;
+  return 3;
+}
+
+int resolve_form(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k) {
+  if (ctx->form != M4RIE_FORM_AUTO) return ctx->form;
+  const int sc = size_class(m, n, k);
+  if (ctx->auto_form[e][sc]) return ctx->auto_form[e][sc];
+  return sc >= 2 ? M4RIE_FORM_TC_F8 : M4RIE_FORM_POPC;
+}
+
+int resolve_schedule(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k) {
+  if (ctx->schedule != M4RIE_SCHED_AUTO) return ctx->schedule;
+  const int sc = size_class(m, n, k);
+  if (ctx->auto_sched[e][sc]) return ctx->auto_sched[e][sc];
+  return M4RIE_SCHED_ALPHA_B;
+}
+
+struct FormInfo {
+  int fmt;
+  uint32_t one;
+  int bits;  // bits per plane entry
+};
+
+FormInfo form_info(int form) {
+  switch (form) {
+    case M4RIE_FORM_POPC: return {kFmtBit, 1, 1};
+    case M4RIE_FORM_TC_F8: return {kFmtByte, 0x38, 8};
+    case M4RIE_FORM_MMA_S8: return {kFmtByte, 0x01, 8};
+    default: return {kFmtNib, 0x2, 4};
+  }
+}
+
+size_t entries_bytes(int64_t entries, int bits) { return (size_t)((entries * bits + 7) / 8); }
+
+// ---------------------------------------------------------------- alpha^j-B
+m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A,
+                         const void* B, void* C, int add) {
+  const FormInfo fi = form_info(form);
+  int G;
+  if (form == M4RIE_FORM_POPC) G = popc_group(e);
+  else if (form == M4RIE_FORM_TC_F8) G = tc_group(e);
+  else return M4RIE_ERR_UNSUPPORTED;
+  const int64_t Kp = round_up(k, 128);
+  const int64_t ld = (int64_t)e * Kp;
+  const int64_t Mp = round_up(m, 128);
+  const int64_t groups = ceil_div(n, G);
+  const int64_t brows = groups * e * G;
+  const size_t a_bytes = round_up((int64_t)entries_bytes(Mp * ld, fi.bits), 1024);
+  const size_t b_bytes = round_up((int64_t)entries_bytes(brows * ld, fi.bits), 1024);
+  m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes);
+  if (st != M4RIE_OK) return st;
+  uint8_t* Ap = static_cast<uint8_t*>(ctx->ws);
+  uint8_t* Bp = Ap + a_bytes;
+
+  uint16_t amask[10], bmask[100];
+  alpha_b_masks(e, f, amask, bmask);
+  PackParams pa{};
+  pa.X = A;
+  pa.ldx = k;
+  pa.elem_bytes = elem_bytes(e);
+  pa.rows = m;
+  pa.K = k;
+  pa.rows_p = Mp;
+  pa.fmt = fi.fmt;
+  pa.one = fi.one;
+  pa.P = e;
+  pa.nb = 1;
+  pa.kb = e;
+  pa.G = 1;
+  pa.Kp = Kp;
+  pa.ld = ld;
+  pa.bstride = 0;
+  pa.emask = (1u << e) - 1;
+  pa.out = Ap;
+  pa.status = ctx->d_status;
+  for (int j = 0; j < e; ++j) pa.mask[j] = amask[j];
+  PhaseTimer timer(ctx);
+  timer.begin(kPhasePack);
+  cudaError_t err = launch_pack_planes(pa, false, ctx->stream, &ctx->launches);
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+
+  PackParams pb = pa;
+  pb.X = B;
+  pb.ldx = n;
+  pb.rows = n;
+  pb.rows_p = groups * G;
+  pb.P = e * e;
+  pb.nb = e;
+  pb.kb = e;
+  pb.G = G;
+  pb.out = Bp;
+  for (int q = 0; q < e * e; ++q) pb.mask[q] = bmask[q];
+  err = launch_pack_planes(pb, true, ctx->stream, &ctx->launches);
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  timer.begin(kPhaseGemm);
+
+  if (form == M4RIE_FORM_POPC) {
+    PopcParams pp{};
+    pp.A = reinterpret_cast<const uint32_t*>(Ap);
+    pp.B = reinterpret_cast<const uint32_t*>(Bp);
+    pp.ldw = ld / 32;
+    pp.m = m;
+    pp.n = n;
+    pp.e = e;
+    pp.C = C;
+    pp.ldc = n;
+    pp.elem_bytes = elem_bytes(e);
+    pp.add = add;
+    pp.emask = (1u << e) - 1;
+    pp.status = ctx->d_status;
+    err = launch_popc_fused(pp, ctx->stream, &ctx->launches);
+  } else {
+    TcParams tp{};
+    tp.m = m;
+    tp.n = n;
+    tp.e = e;
+    tp.G = G;
+    tp.BN = e * G;
+    tp.tiles_m = (int)(Mp / 128);
+    tp.tiles_n = (int)groups;
+    tp.batch = 1;
+    tp.kblocks = (int)(ld / 128);
+    tp.kc = std::max(1, ctx->tc_chunk / 128);
+    tp.group_m = tp.tiles_m;
+    tp.C = C;
+    tp.ldc = n;
+    tp.elem_bytes = elem_bytes(e);
+    tp.add = add;
+    tp.emask = (1u << e) - 1;
+    tp.status = ctx->d_status;
+    tp.mode = 0;
+    tp.wait_limit_ns = ctx->wait_limit_ns;
+    err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld, tp, ctx->num_sms, ctx->stream, &ctx->launches);
+  }
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  return M4RIE_OK;
+}
+
+// ---------------------------------------------------------------- Karatsuba
+m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
+                           const void* A, const void* B, void* C, int add) {
+  if (form != M4RIE_FORM_POPC && form != M4RIE_FORM_TC_F8) return M4RIE_ERR_UNSUPPORTED;
+  Schedule sc;
+  if (!karatsuba_schedule(e, f, &sc)) {
+    ctx->last_error = "schedule construction failed its check";
+    return M4RIE_ERR_ARG;
+  }
+  const FormInfo fi = form_info(form);
+  const int r = sc.r;
+  const int64_t Kp = round_up(k, 128);
+  const int64_t Mp = round_up(m, 128);
+  const int64_t Np = round_up(n, form == M4RIE_FORM_POPC ? 128 : 256);
+  const int64_t ldp = Np / 32;  // words per parity row
+  const size_t a_bytes = round_up((int64_t)entries_bytes((int64_t)r * Mp * Kp, fi.bits), 1024);
+  const size_t b_bytes = round_up((int64_t)entries_bytes((int64_t)r * Np * Kp, fi.bits), 1024);
+  const size_t p_bytes = round_up((int64_t)r * Mp * ldp * 4, 1024);
+  m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes + p_bytes);
+  if (st != M4RIE_OK) return st;
+  uint8_t* Ap = static_cast<uint8_t*>(ctx->ws);
+  uint8_t* Bp = Ap + a_bytes;
+  uint32_t* Pp = reinterpret_cast<uint32_t*>(Bp + b_bytes);
+
+  PackParams pa{};
+  pa.X = A;
+  pa.ldx = k;
+  pa.elem_bytes = elem_bytes(e);
+  pa.rows = m;
+  pa.K = k;
+  pa.rows_p = Mp;
+  pa.fmt = fi.fmt;
+  pa.one = fi.one;
+  pa.P = r;
+  pa.nb = 1;
+  pa.kb = 1;
+  pa.G = 1;
+  pa.Kp = Kp;
+  pa.ld = Kp;
+  pa.bstride = Mp * Kp;
+  pa.emask = (1u << e) - 1;
+  pa.out = Ap;
+  pa.status = ctx->d_status;
+  for (int p = 0; p < r; ++p) pa.mask[p] = sc.amask[p];
+  PhaseTimer timer(ctx);
+  timer.begin(kPhasePack);
+  cudaError_t err = launch_pack_planes(pa, false, ctx->stream, &ctx->launches);
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  PackParams pb = pa;
+  pb.X = B;
+  pb.ldx = n;
+  pb.rows = n;
+  pb.rows_p = Np;
+  pb.bstride = Np * Kp;
+  pb.out = Bp;
+  for (int p = 0; p < r; ++p) pb.mask[p] = sc.bmask[p];
+  err = launch_pack_planes(pb, true, ctx->stream, &ctx->launches);
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  timer.begin(kPhaseGemm);
+
+  if (form == M4RIE_FORM_POPC) {
+    PopcParams pp{};
+    pp.A = reinterpret_cast<const uint32_t*>(Ap);
+    pp.B = reinterpret_cast<const uint32_t*>(Bp);
+    pp.ldw = Kp / 32;
+    pp.m = m;
+    pp.n = n;
+    pp.e = e;
+    pp.C = Pp;
+    pp.ldc = ldp;
+    pp.status = ctx->d_status;
+    pp.batch = r;
+    pp.a_bstride = Mp * Kp / 32;
+    pp.b_bstride = Np * Kp / 32;
+    pp.c_bstride = Mp * ldp;
+    err = launch_popc_parity(pp, ctx->stream, &ctx->launches);
+  } else {
+    TcParams tp{};
+    tp.m = m;
+    tp.n = n;
+    tp.e = e;
+    tp.G = 256;
+    tp.BN = 256;
+    tp.tiles_m = (int)(Mp / 128);
+    tp.tiles_n = (int)(Np / 256);
+    tp.batch = r;
+    tp.a_brows = Mp;
+    tp.b_brows = Np;
+    tp.kblocks = (int)(Kp / 128);
+    tp.kc = std::max(1, ctx->tc_chunk / 128);
+    tp.group_m = tp.tiles_m;
+    tp.C = Pp;
+    tp.status = ctx->d_status;
+    tp.mode = 2;
+    tp.ldp = ldp;
+    tp.p_bstride = Mp * ldp;
+    tp.wait_limit_ns = ctx->wait_limit_ns;
+    err = launch_tc(fi.fmt, Ap, (int64_t)r * Mp, Bp, (int64_t)r * Np, Kp, tp, ctx->num_sms, ctx->stream,
+                    &ctx->launches);
+  }
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  timer.begin(kPhaseRecombine);
+  RecombineParams rc{};
+  rc.P = Pp;
+  rc.ldw = ldp;
+  rc.rows_p = Mp;
+  rc.r = r;
+  rc.e = e;
+  rc.m = m;
+  rc.n = n;
+  rc.C = C;
+  rc.ldc = n;
+  rc.elem_bytes = elem_bytes(e);
+  rc.add = add;
+  rc.emask = (1u << e) - 1;
+  rc.status = ctx->d_status;
+  for (int s = 0; s < 10; ++s) rc.out_mask[s] = sc.out_mask[s];
+  err = launch_recombine(rc, ctx->stream, &ctx->launches);
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  return M4RIE_OK;
+}
+
+m4rie_status run_mul(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A,
+                     const void* B, void* C, int add) {
+  if (!ctx) return M4RIE_ERR_ARG;
+  m4rie_status st = validate(e, f, m, n, k, A, B, C);
+  if (st != M4RIE_OK) return st;
+  if (m == 0 || n == 0) return M4RIE_OK;
+  if (k == 0) {
+    if (add) return M4RIE_OK;
+    cudaError_t err = cudaMemsetAsync(C, 0, (size_t)(m * n) * elem_bytes(e), ctx->stream);
+    return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+  }
+  const int form = resolve_form(ctx, e, m, n, k);
+  const int sched = resolve_schedule(ctx, e, m, n, k);
+  if (ctx->timing) ++ctx->timed_products;
+  if (sched == M4RIE_SCHED_KARATSUBA) return run_karatsuba(ctx, form, e, f, m, n, k, A, B, C, add);
+  return run_alpha_b(ctx, form, e, f, m, n, k, A, B, C, add);
+}
+
+}  // namespace
+
+extern "C" {
+
+m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
+  if (!out) return M4RIE_ERR_ARG;
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return M4RIE_ERR_CUDA;
+  m4rie_ctx* ctx = new m4rie_ctx();
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->device = dev;
+  memset(ctx->auto_form, 0, sizeof(ctx->auto_form));
+  memset(ctx->auto_sched, 0, sizeof(ctx->auto_sched));
+  err = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err == cudaSuccess) err = cudaMalloc(&ctx->d_status, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) {
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return M4RIE_ERR_CUDA;
+  }
+  if (const char* s = getenv("M4RIE_TC_CHUNK")) ctx->tc_chunk = std::max(128, atoi(s));
+  *out = ctx;
+  return M4RIE_OK;
+}
+
+void m4rie_destroy(m4rie_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->io) cudaFree(ctx->io);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+  delete ctx;
+}
+
+m4rie_status m4rie_set_form(m4rie_ctx* ctx, int form) {
+  if (!ctx || form < M4RIE_FORM_AUTO || form > M4RIE_FORM_TC_F4) return M4RIE_ERR_ARG;
+  ctx->form = form;
+  return M4RIE_OK;
+}
+
+m4rie_status m4rie_set_schedule(m4rie_ctx* ctx, int schedule) {
+  if (!ctx || schedule < M4RIE_SCHED_AUTO || schedule > M4RIE_SCHED_KARATSUBA) return M4RIE_ERR_ARG;
+  ctx->schedule = schedule;
+  return M4RIE_OK;
+}
+
+m4rie_status m4rie_mul(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A,
+                       const void* B, void* C) {
+  return run_mul(ctx, e, f, m, n, k, A, B, C, 0);
+}
+
+m4rie_status m4rie_addmul(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A,
+                          const void* B, void* C) {
+  return run_mul(ctx, e, f, m, n, k, A, B, C, 1);
+}
+
+m4rie_status m4rie_mul_host(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* hA,
+                            const void* hB, void* hC, int accumulate) {
+  if (!ctx) return M4RIE_ERR_ARG;
+  m4rie_status st = validate(e, f, m, n, k, hA, hB, hC);
+  if (st != M4RIE_OK) return st;
+  const size_t w = elem_bytes(e);
+  const size_t sa = round_up((int64_t)(m * k * w), 256), sb = round_up((int64_t)(k * n * w), 256);
+  const size_t sc = round_up((int64_t)(m * n * w), 256);
+  if (sa + sb + sc > ctx->io_bytes) {
+    cudaError_t err = cudaStreamSynchronize(ctx->stream);
+    if (err != cudaSuccess) return cuda_fail(ctx, err);
+    if (ctx->io) cudaFree(ctx->io);
+    ctx->io = nullptr;
+    ctx->io_bytes = 0;
+    if (cudaMalloc(&ctx->io, sa + sb + sc) != cudaSuccess) {
+      cudaGetLastError();
+      return M4RIE_ERR_NOMEM;
+    }
+    ctx->io_bytes = sa + sb + sc;
+  }
+  uint8_t* dA = static_cast<uint8_t*>(ctx->io);
+  uint8_t* dB = dA + sa;
+  uint8_t* dC = dB + sb;
+  cudaError_t err = cudaSuccess;
+  if (m * k) err = cudaMemcpyAsync(dA, hA, m * k * w, cudaMemcpyHostToDevice, ctx->stream);
+  if (err == cudaSuccess && k * n) err = cudaMemcpyAsync(dB, hB, k * n * w, cudaMemcpyHostToDevice, ctx->stream);
+  if (err == cudaSuccess && accumulate && m * n)
+    err = cudaMemcpyAsync(dC, hC, m * n * w, cudaMemcpyHostToDevice, ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  st = run_mul(ctx, e, f, m, n, k, m * k ? dA : nullptr, k * n ? dB : nullptr, m * n ? dC : nullptr, accumulate);
+  if (st != M4RIE_OK) return st;
+  if (m * n) err = cudaMemcpyAsync(hC, dC, m * n * w, cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+}
+
+m4rie_status m4rie_pack(m4rie_ctx* ctx, int e, int64_t rows, int64_t cols, const void* elems, uint64_t* slices,
+                        int64_t ld_words) {
+  if (!ctx || e < 2 || e > 10 || rows < 0 || cols < 0) return M4RIE_ERR_ARG;
+  if (ld_words < (cols + 63) / 64) return M4RIE_ERR_ARG;
+  if (rows * cols && (!elems || !slices)) return M4RIE_ERR_ARG;
+  if (rows * ld_words && !slices) return M4RIE_ERR_ARG;
+  if (overlaps(slices, (size_t)(e * rows * ld_words) * 8, elems, (size_t)(rows * cols) * elem_bytes(e)))
+    return M4RIE_ERR_ALIAS;
+  if (rows == 0 || ld_words == 0) return M4RIE_OK;
+  cudaError_t err = launch_slice(e, rows, cols, elems, slices, ld_words, ctx->d_status, ctx->stream, &ctx->launches);
+  return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+}
+
+m4rie_status m4rie_unpack(m4rie_ctx* ctx, int e, int64_t rows, int64_t cols, const uint64_t* slices, int64_t ld_words,
+                          void* elems) {
+  if (!ctx || e < 2 || e > 10 || rows < 0 || cols < 0) return M4RIE_ERR_ARG;
+  if (ld_words < (cols + 63) / 64) return M4RIE_ERR_ARG;
+  if (rows * cols && (!elems || !slices)) return M4RIE_ERR_ARG;
+  if (overlaps(slices, (size_t)(e * rows * ld_words) * 8, elems, (size_t)(rows * cols) * elem_bytes(e)))
+    return M4RIE_ERR_ALIAS;
+  if (rows == 0 || cols == 0) return M4RIE_OK;
+  cudaError_t err = launch_cling(e, rows, cols, slices, ld_words, elems, ctx->stream, &ctx->launches);
+  return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+}
+
+m4rie_status m4rie_mul_batched(m4rie_ctx* ctx, int count, const m4rie_problem* problems) {
+  if (!ctx || count < 0 || (count && !problems)) return M4RIE_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    const m4rie_problem& p = problems[i];
+    m4rie_status st = validate(p.e, p.f, p.m, p.n, p.k, p.A, p.B, p.C);
+    if (st != M4RIE_OK) return st;
+  }
+  for (int i = 0; i < count; ++i) {
+    const m4rie_problem& p = problems[i];
+    m4rie_status st = run_mul(ctx, p.e, p.f, p.m, p.n, p.k, p.A, p.B, p.C, p.accumulate ? 1 : 0);
+    if (st != M4RIE_OK) return st;
+  }
+  return M4RIE_OK;
+}
+
+m4rie_status m4rie_get_device_status(m4rie_ctx* ctx) {
+  if (!ctx) return M4RIE_ERR_ARG;
+  int h = 0;
+  cudaError_t err = cudaMemcpyAsync(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  if (h & kStatusTimeout) return M4RIE_ERR_TIMEOUT;
+  if (h & kStatusRange) return M4RIE_ERR_RANGE;
+  return M4RIE_OK;
+}
+
+int m4rie_schedule_products(int e, uint32_t f, int schedule) {
+  m4rie_status st = check_field(e, f);
+  if (st != M4RIE_OK) return -(int)st;
+  if (schedule == M4RIE_SCHED_ALPHA_B) return e * e;
+  if (schedule == M4RIE_SCHED_KARATSUBA) {
+    Schedule sc;
+    if (!karatsuba_schedule(e, f, &sc)) return -(int)M4RIE_ERR_ARG;
+    return sc.r;
+  }
+  return -(int)M4RIE_ERR_ARG;
+}
+
+m4rie_status m4rie_validate(int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                            const void* C) {
+  return validate(e, f, m, n, k, A, B, C);
+}
+
+int m4rie_schedule_masks(int e, uint32_t f, int schedule, int cap, uint16_t* amask, uint16_t* bmask,
+                         uint64_t* out_mask) {
+  m4rie_status st = check_field(e, f);
+  if (st != M4RIE_OK) return -(int)st;
+  if (!amask || !bmask || !out_mask) return -(int)M4RIE_ERR_ARG;
+  for (int s = 0; s < 10; ++s) out_mask[s] = 0;
+  if (schedule == M4RIE_SCHED_ALPHA_B) {
+    if (cap < e * e) return -(int)M4RIE_ERR_ARG;
+    uint16_t am[10], bm[100];
+    alpha_b_masks(e, f, am, bm);
+    for (int i = 0; i < e; ++i)
+      for (int j = 0; j < e; ++j) {
+        const int p = i * e + j;
+        amask[p] = am[j];
+        bmask[p] = bm[i * e + j];
+        if (e * e <= 64) out_mask[i] |= 1ull << p;
+      }
+    return e * e;
+  }
+  if (schedule == M4RIE_SCHED_KARATSUBA) {
+    Schedule sc;
+    if (!karatsuba_schedule(e, f, &sc)) return -(int)M4RIE_ERR_ARG;
+    if (cap < sc.r) return -(int)M4RIE_ERR_ARG;
+    for (int p = 0; p < sc.r; ++p) {
+      amask[p] = sc.amask[p];
+      bmask[p] = sc.bmask[p];
+    }
+    for (int s = 0; s < 10; ++s) out_mask[s] = sc.out_mask[s];
+    return sc.r;
+  }
+  return -(int)M4RIE_ERR_ARG;
+}
+
+int m4rie_resolve_form(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k) {
+  if (!ctx || e < 2 || e > 10) return -(int)M4RIE_ERR_ARG;
+  return resolve_form(ctx, e, m, n, k);
+}
+
+const char* m4rie_status_string(m4rie_status s) {
+  switch (s) {
+    case M4RIE_OK: return "ok";
+    case M4RIE_ERR_ARG: return "invalid argument";
+    case M4RIE_ERR_POLY: return "field polynomial does not have degree e or is reducible";
+    case M4RIE_ERR_ALIAS: return "output overlaps an input";
+    case M4RIE_ERR_RANGE: return "an input entry was >= 2^e (its low e bits were used)";
+    case M4RIE_ERR_NOMEM: return "workspace allocation failed";
+    case M4RIE_ERR_CUDA: return "CUDA error";
+    case M4RIE_ERR_TIMEOUT: return "a bounded wait inside a kernel ran out";
+    case M4RIE_ERR_UNSUPPORTED: return "form not available for this problem or device";
+  }
+  return "unknown status";
+}
+
+const char* m4rie_last_error(m4rie_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int64_t m4rie_kernel_launches(m4rie_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+m4rie_status m4rie_enable_timing(m4rie_ctx* ctx, int on) {
+  if (!ctx) return M4RIE_ERR_ARG;
+  ctx->timing = on != 0;
+  return M4RIE_OK;
+}
+
+m4rie_status m4rie_phase_times(m4rie_ctx* ctx, double* pack_ms, double* gemm_ms, double* recombine_ms,
+                               int64_t* products, int reset) {
+  if (!ctx) return M4RIE_ERR_ARG;
+  cudaError_t err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) return cuda_fail(ctx, err);
+  for (auto& pe : ctx->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) ctx->phase_ms[pe.first] += ms;
+  }
+  ctx->ev_pending.clear();
+  ctx->ev_next = 0;
+  if (pack_ms) *pack_ms = ctx->phase_ms[kPhasePack];
+  if (gemm_ms) *gemm_ms = ctx->phase_ms[kPhaseGemm];
+  if (recombine_ms) *recombine_ms = ctx->phase_ms[kPhaseRecombine];
+  if (products) *products = ctx->timed_products;
+  if (reset) {
+    ctx->phase_ms[0] = ctx->phase_ms[1] = ctx->phase_ms[2] = 0;
+    ctx->timed_products = 0;
+  }
+  return M4RIE_OK;
+}
+
+m4rie_status m4rie_set_wait_limit_ns(m4rie_ctx* ctx, uint64_t ns) {
+  if (!ctx) return M4RIE_ERR_ARG;
+  ctx->wait_limit_ns = ns;
+  return M4RIE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,443 @@
+// GF(2) slice GEMM on the tcgen05 tensor cores (sm_103a).
+//
+// Operands are the 0/1 slice planes encoded exactly as FP8 E4M3 (1.0 = 0x38);
+// each tcgen05.mma accumulates integer counts sum_t a_t b_t in FP32 in tensor
+// memory.  Counts are bounded per accumulation chunk (kc k-blocks of 128), so
+// every partial sum is a small integer and exact; after each chunk the
+// epilogue warps take the low bit (the GF(2) sum) and XOR it into per-row bit
+// vectors.  With the alpha^j-B schedule the tile's columns are the e slices of
+// G consecutive output elements (column i*G + c holds slice i of element c),
+// so the epilogue assembles finished field elements (Section 5: product of
+// slice polynomials with the reduction mod f folded into B).
+//
+// Structure: persistent, one CTA per SM, 6 warps.  Warp 0 issues TMA loads
+// (128-byte swizzled tiles) into a 4-stage shared-memory ring, warp 1 issues
+// the MMAs into two 256-column TMEM accumulators, warps 2-5 drain TMEM.  Every
+// wait is bounded by a global-timer limit; on expiry the CTA sets the timeout
+// status, stops issuing, waits (bounded) for its copies in flight, frees TMEM
+// and returns.
+#include "m4rie_internal.cuh"
+
+namespace m4rie {
+namespace {
+
+constexpr int STAGES = 4;
+constexpr int A_TILE = 128 * 128;  // bytes
+constexpr int B_SLOT = 256 * 128;  // bytes (tile N <= 256)
+constexpr int ACC_COLS = 256;
+constexpr int THREADS = 192;
+// Bound on the waits that drain copies and MMAs already in flight when a CTA
+// aborts; independent of the (possibly tiny) wait limit that triggered it.
+constexpr uint64_t DRAIN_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on phase `parity`.  Returns false when the CTA is aborting.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          uint64_t limit_ns) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > limit_ns) {
+      *abort_flag = 1;
+      atomicOr(status, kStatusTimeout);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f8(int M, int N) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile_coords(const TcParams& p, int tile, int& b, int& tm, int& tn) {
+  const int per = p.tiles_m * p.tiles_n;
+  b = tile / per;
+  tile -= b * per;
+  const int span = p.group_m * p.tiles_n;
+  const int grp = tile / span;
+  const int first = grp * p.group_m;
+  const int gm = min(p.tiles_m - first, p.group_m);
+  const int local = tile - grp * span;
+  tm = first + local % gm;
+  tn = local / gm;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_f8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_TILE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_SLOT);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  uint32_t* sbits = tmem_slot + 4;  // [4 warps][32 rows][9 words]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t drain = smem_u32(bars + 2 * STAGES + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 128);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * ACC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int total = p.batch * p.tiles_m * p.tiles_n;
+  const uint64_t lim = p.wait_limit_ns;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      const uint32_t bytes = A_TILE + (uint32_t)p.BN * 128;
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, issued_parity = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+        int b, tm, tn;
+        tile_coords(p, tile, b, tm, tn);
+        const int arow = (int)(b * p.a_brows) + tm * 128, brow = (int)(b * p.b_brows) + tn * p.BN;
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status, lim)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full0 + 8 * stage;
+          mbar_expect_tx(fb, bytes);
+          tma_load_2d(smem_u32(sA + stage * A_TILE), &tmA, fb, kb * 128, arow);
+          tma_load_2d(smem_u32(sB + stage * B_SLOT), &tmB, fb, kb * 128, brow);
+          issued_mask |= 1u << stage;
+          issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      if (!ok) {
+        // Aborting: wait (bounded) for the copies this thread issued.
+        for (int s = 0; s < STAGES; ++s)
+          if (issued_mask >> s & 1u) {
+            const uint64_t t0 = gtimer();
+            while (!mbar_try(full0 + 8 * s, (issued_parity >> s) & 1u) && gtimer() - t0 < DRAIN_NS) {
+            }
+          }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = idesc_f8(128, p.BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      int chunk = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+        for (int kb0 = 0; kb0 < p.kblocks && ok; kb0 += p.kc) {
+          const int kb1 = min(kb0 + p.kc, p.kblocks);
+          const int buf = chunk & 1;
+          const uint32_t tph = (chunk >> 1) & 1;
+          if (!mbar_wait(tempty0 + 8 * buf, tph ^ 1, abort_flag, p.status, lim)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t d = tmem + buf * ACC_COLS;
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.status, lim)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint32_t a0 = smem_u32(sA + stage * A_TILE), b0 = smem_u32(sB + stage * B_SLOT);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              mma_f8(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+            mma_commit(empty0 + 8 * stage);
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+          if (!ok) break;
+          mma_commit(tfull0 + 8 * buf);
+          ++chunk;
+        }
+      }
+      // Every MMA this thread issued has completed once `drain` flips; only
+      // then may TMEM be freed (bounded wait, also on the abort path).
+      mma_commit(drain);
+      const uint64_t t0 = gtimer();
+      while (!mbar_try(drain, 0) && gtimer() - t0 < DRAIN_NS) {
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, TMEM lanes 32*(warp%4) ...
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    uint32_t* wbits = sbits + q * 32 * 9;  // this warp's 32 rows
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const int nc16 = p.BN / 16;
+    int chunk = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+      int b, tm, tn;
+      tile_coords(p, tile, b, tm, tn);
+      uint32_t bits[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int kb0 = 0; kb0 < p.kblocks; kb0 += p.kc) {
+        const int buf = chunk & 1;
+        const uint32_t tph = (chunk >> 1) & 1;
+        // warp-uniform decision: tcgen05.ld below needs all 32 lanes
+        if (!__all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * buf, tph, abort_flag, p.status, lim))) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t ta = tmem + lane_base + buf * ACC_COLS;
+#pragma unroll
+        for (int c16 = 0; c16 < 16; ++c16) {
+          if (c16 < nc16) {
+            uint32_t v[16];
+            tmem_ld16(ta + 16 * c16, v);
+            if (p.mode == 1) {
+              if (kb0 == 0) {
+                uint32_t* out = static_cast<uint32_t*>(p.C) + ((int64_t)tm * 128 + row) * p.ldc +
+                                (int64_t)tn * p.BN + 16 * c16;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) out[j] = (uint32_t)__float2int_rz(__uint_as_float(v[j]));
+              }
+            } else {
+              uint32_t w = 0;
+#pragma unroll
+              for (int j = 0; j < 16; ++j) w |= ((uint32_t)__float2int_rz(__uint_as_float(v[j])) & 1u) << j;
+              bits[c16 >> 1] ^= w << (16 * (c16 & 1));
+            }
+          }
+        }
+        fence_before();
+        mbar_arrive(tempty0 + 8 * buf);
+        ++chunk;
+      }
+      if (!ok || p.mode == 1) continue;
+      const int64_t r0 = (int64_t)tm * 128;
+      if (p.mode == 2) {
+        // parity planes: row r0+row, columns tn*BN .. +BN
+        uint32_t* P = static_cast<uint32_t*>(p.C) + b * p.p_bstride + (r0 + row) * p.ldp + (int64_t)tn * p.BN / 32;
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+          if (w < p.BN / 32) P[w] = bits[w];
+        continue;
+      }
+      // Assemble field elements: element c of this tile has bit i at column
+      // i*G + c.  Each warp writes its own 32 rows (lanes along columns).
+#pragma unroll
+      for (int w = 0; w < 8; ++w) wbits[lane * 9 + w] = bits[w];
+      __syncwarp();
+      const int G = p.G, E = p.e;
+      const int64_t c0 = (int64_t)tn * G;
+      bool bad = false;
+      for (int idx = lane; idx < 32 * G; idx += 32) {
+        const int rl = idx / G, cl = idx - rl * G;
+        const int64_t r = r0 + 32 * q + rl, c = c0 + cl;
+        if (r >= p.m || c >= p.n) continue;
+        uint32_t val = 0;
+        for (int i = 0; i < E; ++i) {
+          const int col = i * G + cl;
+          val |= ((wbits[rl * 9 + (col >> 5)] >> (col & 31)) & 1u) << i;
+        }
+        if (p.elem_bytes == 1) {
+          uint8_t* dst = static_cast<uint8_t*>(p.C) + r * p.ldc + c;
+          if (p.add) {
+            const uint32_t old = *dst;
+            bad |= old > p.emask;
+            val ^= old & p.emask;
+          }
+          *dst = (uint8_t)val;
+        } else {
+          uint16_t* dst = static_cast<uint16_t*>(p.C) + r * p.ldc + c;
+          if (p.add) {
+            const uint32_t old = *dst;
+            bad |= old > p.emask;
+            val ^= old & p.emask;
+          }
+          *dst = (uint16_t)val;
+        }
+      }
+      if (bad) atomicOr(p.status, kStatusRange);
+      __syncwarp();
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS) : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld_bytes, int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ld_bytes, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld_bytes};
+  cuuint32_t box[2] = {128, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int tc_group(int e) {
+  switch (e) {
+    case 2: return 128;
+    case 3: return 80;
+    case 4: return 64;
+    case 5: return 48;
+    case 6: return 40;
+    case 7: return 32;
+    case 8: return 32;
+    case 9: return 16;
+    default: return 24;
+  }
+}
+
+size_t tc_smem_bytes() { return 1024 + (size_t)STAGES * (A_TILE + B_SLOT) + 16 * 8 + 16 + 128 * 9 * 4; }
+
+cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
+                      int64_t ld_bytes, const TcParams& p, int num_sms, cudaStream_t s, int64_t* launches) {
+  if (fmt != kFmtByte) return cudaErrorNotSupported;
+  if (p.BN % 16 != 0 || p.BN < 16 || p.BN > 256 || ld_bytes % 128 != 0) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, Aplanes, a_rows, ld_bytes, 128) || !make_map(&mb, Bplanes, b_rows, ld_bytes, p.BN))
+    return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes();
+  cudaError_t err = cudaFuncSetAttribute(tc_f8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int64_t total = (int64_t)p.batch * p.tiles_m * p.tiles_n;
+  if (total > 0x7fffffffLL || p.a_brows * p.batch > 0x7fffffffLL || p.b_brows * p.batch > 0x7fffffffLL)
+    return cudaErrorInvalidValue;
+  const int grid = total < num_sms ? (int)total : num_sms;
+  if (grid <= 0) return cudaSuccess;
+  tc_f8_kernel<<<grid, THREADS, smem, s>>>(ma, mb, p);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace m4rie

@@ -1,0 +1,129 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda.h>
+
+namespace m4rie {
+
+// Device status bits (sticky word owned by the context).
+enum : int { kStatusRange = 1, kStatusTimeout = 2 };
+
+// Operand plane formats.  Every plane entry is parity(x & mask) for one
+// element x and one GF(2)-linear mask, stored as:
+enum PlaneFmt : int {
+  kFmtBit = 0,   // 1 bit, 32-bit words along K, least significant bit first
+  kFmtByte = 1,  // 1 byte per entry: 0 or `one` (0x01 for INT8, 0x38 for FP8 E4M3 1.0)
+  kFmtNib = 2,   // 4 bits per entry, two per byte (low nibble first): 0 or `one` (0x2 = E2M1 1.0)
+};
+
+constexpr int kMaxMasks = 128;
+
+// Layout of the planes generated from one input matrix (A, or B read column
+// by column).  Mask q = (b * nb + i) * kb + j produces the entries of input row
+// r at element offset  b*bstride + orow(r, i)*ld + j*Kp + t,
+// orow(r, i) = (r / G) * nb * G + i * G + (r % G).
+struct PackParams {
+  const void* X;      // input elements
+  int64_t ldx;        // leading dimension of X in elements
+  int elem_bytes;     // 1 or 2
+  int64_t rows;       // input rows (A: m; B read by columns: n)
+  int64_t K;          // inner dimension k
+  int64_t rows_p;     // padded rows per batch plane (multiple of G and of the GEMM's M tile)
+  int fmt;
+  uint32_t one;
+  int P, nb, kb, G;
+  int64_t Kp;         // padded K per k-block, multiple of 128
+  int64_t ld;         // output row length (entries) = kb * Kp
+  int64_t bstride;    // entries between batch planes
+  uint32_t emask;     // 2^e - 1
+  void* out;
+  int* status;
+  uint16_t mask[kMaxMasks];
+};
+
+// Pack launchers (pack.cu).  trans = false: rows of X are the planes' rows
+// (A side).  trans = true: columns of X are the planes' rows (B side).
+cudaError_t launch_pack_planes(const PackParams& p, bool trans, cudaStream_t s, int64_t* launches);
+
+// Public slice format (Section 3.2): pack.cu.
+cudaError_t launch_slice(int e, int64_t rows, int64_t cols, const void* elems, uint64_t* slices,
+                         int64_t ld_words, int* status, cudaStream_t s, int64_t* launches);
+cudaError_t launch_cling(int e, int64_t rows, int64_t cols, const uint64_t* slices, int64_t ld_words,
+                         void* elems, cudaStream_t s, int64_t* launches);
+
+// Karatsuba recombination: out bits from r parity planes (pack.cu).
+struct RecombineParams {
+  const uint32_t* P;  // r bit planes, plane p row i at P + (p*rows_p + i)*ldw
+  int64_t ldw;        // words per parity-plane row
+  int64_t rows_p;
+  int r;
+  int e;
+  int64_t m, n;
+  void* C;
+  int64_t ldc;
+  int elem_bytes;
+  int add;
+  uint32_t emask;
+  int* status;
+  uint64_t out_mask[10];  // bit p of out_mask[s]: product p contributes to output slice s
+};
+cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches);
+
+// ---------------------------------------------------------------- popc form
+// Tile constants of the bit-packed GEMM (gemm_popc.cu).
+constexpr int kPopcBM = 128;
+int popc_group(int e);  // elements per block column (G of the B-side plane layout)
+
+struct PopcParams {
+  const uint32_t* A;  // [Mp][ldw]
+  const uint32_t* B;  // [groups * e * G][ldw]  (fused)  or  [r][Np][ldw] (parity)
+  int64_t ldw;        // words per row
+  int64_t m, n;
+  int e;
+  void* C;            // fused: elements; parity: bit planes
+  int64_t ldc;        // fused: elements per row of C; parity: words per plane row
+  int elem_bytes;
+  int add;
+  uint32_t emask;
+  int* status;
+  // parity (batched) mode
+  int batch;
+  int64_t a_bstride, b_bstride, c_bstride;  // words between batch planes
+};
+cudaError_t launch_popc_fused(const PopcParams& p, cudaStream_t s, int64_t* launches);
+cudaError_t launch_popc_parity(const PopcParams& p, cudaStream_t s, int64_t* launches);
+
+// ---------------------------------------------------------------- tcgen05 form
+constexpr int kTcBM = 128;
+int tc_group(int e);  // elements per tile column: tile N = e * G <= 256
+
+struct TcParams {
+  int64_t m, n;
+  int e, G, BN;
+  int tiles_m, tiles_n;
+  int batch;          // independent products (parity mode); 1 otherwise
+  int64_t a_brows, b_brows;  // plane rows between products in the A / B tensor maps
+  int kblocks;        // K' / 128 bytes
+  int kc;             // k-blocks per accumulation chunk (bounds each FP32 count)
+  int group_m;        // tile raster: group_m m-tiles per super-column
+  void* C;
+  int64_t ldc;
+  int elem_bytes;
+  int add;
+  uint32_t emask;
+  int* status;
+  int mode;           // 0: elements, 1: raw counts of the first chunk (test hook), 2: parity planes
+  int64_t ldp;        // parity mode: words per plane row
+  int64_t p_bstride;  // parity mode: words between products
+  uint64_t wait_limit_ns;
+};
+// fmt: kFmtByte (E4M3) or kFmtNib (E2M1, block scaled).
+cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
+                      int64_t ld_bytes, const TcParams& p, int num_sms, cudaStream_t s, int64_t* launches);
+
+// ---------------------------------------------------------------- helpers
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+}  // namespace m4rie

@@ -1,0 +1,137 @@
+"""Host-side tests of the C ABI that need no GPU: the library loads and exports
+every declared entry point, argument validation returns the documented
+status codes, and the GF(2)-product schedules compute the field product
+(checked independently of the library with numpy GF(2) products)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads
+from tests import fieldref as fr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for mt in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(m4rie_\w+)\s*\(", text, flags=re.M):
+            names.add(mt.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1111_6900_gb300 as m4
+    declared = _declared_functions()
+    assert len(declared) >= 19
+    lib = ctypes.CDLL(m4.LIB_PATH)
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    import paper_1111_6900_gb300 as m4
+    for s in range(9):
+        assert m4.status_string(s)
+    assert m4.status_string(0) == "ok"
+
+
+def test_validation_codes():
+    import paper_1111_6900_gb300 as m4
+    v = m4.validate
+    A, B, C = 0x10000, 0x20000, 0x30000
+    assert v(4, 0x13, 8, 8, 8, A, B, C) == m4.OK
+    assert v(1, 0x3, 8, 8, 8, A, B, C) == m4.ERR_ARG         # e < 2
+    assert v(11, 0x805, 8, 8, 8, A, B, C) == m4.ERR_ARG       # e > 10
+    assert v(4, 0x11, 8, 8, 8, A, B, C) == m4.ERR_POLY        # x^4 + 1 reducible
+    assert v(4, 0x15, 8, 8, 8, A, B, C) == m4.ERR_POLY        # (x^2+x+1)^2
+    assert v(4, 0x25, 8, 8, 8, A, B, C) == m4.ERR_POLY        # degree 5
+    assert v(8, 0x11B, 8, 8, 8, A, B, C) == m4.OK             # irreducible, not primitive
+    assert v(4, 0x13, -1, 8, 8, A, B, C) == m4.ERR_ARG
+    assert v(4, 0x13, 8, 8, 8, None, B, C) == m4.ERR_ARG
+    assert v(4, 0x13, 0, 8, 0, None, None, None) == m4.OK     # nothing to point to
+    assert v(4, 0x13, 8, 8, 0, None, None, C) == m4.OK        # k = 0: only C needed
+    assert v(4, 0x13, 16, 16, 16, A, B, A + 100) == m4.ERR_ALIAS
+    assert v(4, 0x13, 16, 16, 16, A, B, B - 10) == m4.ERR_ALIAS
+    assert v(4, 0x13, 16, 16, 16, A, B, A + 256) == m4.OK     # adjacent, no overlap
+    assert v(10, 0x409, 16, 16, 16, A, B, A + 256) == m4.ERR_ALIAS  # 2-byte elements overlap
+
+
+def test_every_configured_polynomial_accepted():
+    import paper_1111_6900_gb300 as m4
+    for e, f in workloads.FIELD_POLY.items():
+        assert m4.validate(e, f, 4, 4, 4, 0x1000, 0x2000, 0x3000) == m4.OK
+
+
+@pytest.mark.parametrize("e", sorted(workloads.FIELD_POLY))
+@pytest.mark.parametrize("sched", ["alpha_b", "karatsuba"])
+def test_schedule_is_the_field_product(e, sched):
+    """Symbolic check on basis pairs (x^i, x^j), independent of the library:
+    the schedule's output must be x^(i+j) mod f."""
+    import paper_1111_6900_gb300 as m4
+    f = workloads.FIELD_POLY[e]
+    am, bm, om = m4.schedule_masks(e, f, sched)
+    r = len(am)
+    for i in range(e):
+        for j in range(e):
+            out = 0
+            for p in range(r):
+                if am[p] >> i & 1 and bm[p] >> j & 1:
+                    if sched == "alpha_b":      # product p = i*e + j feeds slice p // e
+                        out ^= 1 << (p // e)
+                        continue
+                    for s in range(e):
+                        if om[s] >> p & 1:
+                            out ^= 1 << s
+            assert out == fr.x_power_mod(e, f, i + j), (i, j)
+
+
+@pytest.mark.parametrize("e", [2, 3, 5, 8, 10])
+def test_karatsuba_schedule_on_matrices(e):
+    """Run the Karatsuba schedule with numpy GF(2) products and compare with
+    the oracle: the same recombination the GPU epilogue performs."""
+    import oracle
+    import paper_1111_6900_gb300 as m4
+    f = workloads.FIELD_POLY[e]
+    am, bm, om = m4.schedule_masks(e, f, "karatsuba")
+    A, B, _ = workloads.random_problem(e, 21, 17, 29, seed=40 + e)
+
+    def lin(M, mask):
+        out = np.zeros(M.shape, dtype=np.int64)
+        for i in range(e):
+            if mask >> i & 1:
+                out ^= fr.bits(M, i)
+        return out
+    P = [fr.gf2_matmul(lin(A, am[p]), lin(B, bm[p])) for p in range(len(am))]
+    C = np.zeros((21, 17), dtype=np.int64)
+    for s in range(e):
+        acc = np.zeros_like(C)
+        for p in range(len(am)):
+            if om[s] >> p & 1:
+                acc ^= P[p]
+        C |= acc << s
+    np.testing.assert_array_equal(C, oracle.matmul(e, f, A, B).astype(np.int64))
+
+
+def test_product_counts():
+    """alpha_b uses the schoolbook count e^2 (Table 3 'naive'); the
+    Karatsuba-like schedules use fewer, within the table's best-known counts
+    plus the gap of the recursive constructions for e = 5, 6, 7."""
+    import paper_1111_6900_gb300 as m4
+    rows = [l.split("#")[0].split() for l in open(os.path.join(ROOT, "tests", "golden", "table3_counts.txt"))]
+    table = {int(r[0]): (int(r[1]), int(r[2])) for r in rows if r}
+    got = {}
+    for e, f in workloads.FIELD_POLY.items():
+        assert m4.schedule_products(e, f, "alpha_b") == e * e
+        got[e] = m4.schedule_products(e, f, "karatsuba")
+        assert got[e] < e * e
+    for e, (naive, best) in table.items():
+        assert naive == e * e
+        assert best <= got[e] <= best + 2, (e, got[e], best)
+    assert got == {2: 3, 3: 6, 4: 9, 5: 15, 6: 18, 7: 24, 8: 27, 9: 36, 10: 45}

@@ -1,0 +1,226 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Every comparison is bit-exact (field arithmetic has one correct result).
+Small and ragged shapes are compared in full; the full-size workloads are
+compared on sampled row panels that the oracle computes directly plus a
+Freivalds check of the whole product.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1111_6900_gb300 as m4  # noqa: E402
+
+FORMS = ["popc", "tc_f8"]
+SCHEDS = ["alpha_b", "karatsuba"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = m4.Context()
+    yield c
+    c.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def run(ctx, form, sched, e, A, B, C0=None):
+    ctx.set_form(form)
+    ctx.set_schedule(sched)
+    f = workloads.FIELD_POLY[e]
+    dA, dB = dev(A), dev(B)
+    if C0 is None:
+        C = ctx.mul(e, f, dA, dB)
+    else:
+        C = dev(C0)
+        ctx.addmul(e, f, dA, dB, C)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == m4.OK
+    return host(C)
+
+
+# ---------------------------------------------------------------- slicing
+
+
+def test_pack_figure1(ctx):
+    e = 3
+    X = np.array([[5, 2], [3, 1]], dtype=np.uint8)
+    S = host(ctx.pack(e, dev(X))).view(np.uint64)
+    expect = oracle.slice_(e, X)
+    np.testing.assert_array_equal(S, expect)
+    assert [int(S[i, r, 0]) for i in range(3) for r in range(2)] == [0b01, 0b11, 0b10, 0b01, 0b01, 0b00]
+    np.testing.assert_array_equal(host(ctx.unpack(e, ctx.pack(e, dev(X)), 2)), X)
+
+
+@pytest.mark.parametrize("e", [2, 4, 8, 9, 10])
+@pytest.mark.parametrize("shape", [(1, 1), (7, 131), (64, 64), (33, 200)])
+def test_pack_unpack_random(ctx, e, shape):
+    rng = np.random.default_rng(e * 100 + shape[1])
+    X = workloads.elements(rng, e, shape)
+    ldw = (shape[1] + 63) // 64 + 1
+    S = ctx.pack(e, dev(X), ld_words=ldw)
+    np.testing.assert_array_equal(host(S).view(np.uint64), oracle.slice_(e, X, ld_words=ldw))
+    np.testing.assert_array_equal(host(ctx.unpack(e, S, shape[1])), X)
+
+
+# ---------------------------------------------------------------- products
+
+
+@pytest.mark.parametrize("e", sorted(workloads.FIELD_POLY))
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_mul_ragged_every_field(ctx, e, form, sched):
+    """Several tiles in every direction plus a ragged tail."""
+    f = workloads.FIELD_POLY[e]
+    for (m, n, k) in [(33, 65, 129), (130, 300, 257)]:
+        A, B, _ = workloads.random_problem(e, m, n, k, seed=e * 1000 + m)
+        np.testing.assert_array_equal(run(ctx, form, sched, e, A, B), oracle.matmul(e, f, A, B),
+                                      err_msg=f"{form} {sched} e={e} {m}x{k}x{n}")
+
+
+@pytest.mark.parametrize("e", [2, 5, 8, 10])
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_addmul(ctx, e, form, sched):
+    f = workloads.FIELD_POLY[e]
+    A, B, C0 = workloads.random_problem(e, 150, 97, 333, seed=77 + e, with_c=True)
+    np.testing.assert_array_equal(run(ctx, form, sched, e, A, B, C0), oracle.addmul(e, f, A, B, C0))
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_degenerate_shapes(ctx, form, sched):
+    e, f = 4, workloads.FIELD_POLY[4]
+    for (m, n, k) in [(1, 1, 1), (1, 300, 1), (300, 1, 1), (1, 1, 5000), (2, 3, 4096)]:
+        A, B, _ = workloads.random_problem(e, m, n, k, seed=m + n + k)
+        np.testing.assert_array_equal(run(ctx, form, sched, e, A, B), oracle.matmul(e, f, A, B))
+    # k = 0: mul writes zeros, addmul leaves C unchanged; m = 0 / n = 0 are no-ops
+    ctx.set_form(form)
+    ctx.set_schedule(sched)
+    A = torch.empty((5, 0), dtype=torch.uint8, device="cuda")
+    B = torch.empty((0, 7), dtype=torch.uint8, device="cuda")
+    C = torch.full((5, 7), 9, dtype=torch.uint8, device="cuda")
+    ctx.mul(e, f, A, B, C)
+    assert int(C.max()) == 0
+    C.fill_(9)
+    ctx.addmul(e, f, A, B, C)
+    assert int(C.min()) == 9
+    ctx.mul(e, f, torch.empty((0, 3), dtype=torch.uint8, device="cuda"), torch.ones((3, 4), dtype=torch.uint8, device="cuda"))
+    torch.cuda.synchronize()
+    assert ctx.device_status() == m4.OK
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_out_of_range_entries_flagged_and_masked(ctx, form):
+    e, f = 3, workloads.FIELD_POLY[3]
+    A, B, _ = workloads.random_problem(e, 40, 30, 50, seed=5)
+    A2 = A.copy()
+    A2[3, 7] |= 0x80           # entry >= 2^e
+    ctx.set_form(form)
+    ctx.set_schedule("alpha_b")
+    C = ctx.mul(e, f, dev(A2), dev(B))
+    assert ctx.device_status() == m4.ERR_RANGE
+    assert ctx.device_status() == m4.OK   # status is cleared once read
+    np.testing.assert_array_equal(host(C), oracle.matmul(e, f, A, B))
+
+
+def test_invalid_arguments_launch_nothing(ctx):
+    e, f = 4, workloads.FIELD_POLY[4]
+    A = dev(np.zeros((8, 8), np.uint8))
+    before = ctx.kernel_launches()
+    with pytest.raises(m4.M4rieError) as ei:
+        ctx.mul(e, 0x11, A, A)        # reducible f
+    assert ei.value.status == m4.ERR_POLY
+    with pytest.raises(m4.M4rieError) as ei:
+        ctx.mul(e, f, A, A, A)        # C aliases A
+    assert ei.value.status == m4.ERR_ALIAS
+    assert ctx.kernel_launches() == before
+
+
+def test_host_buffer_entry_point(ctx):
+    e, f = 5, workloads.FIELD_POLY[5]
+    A, B, C0 = workloads.random_problem(e, 70, 90, 110, seed=3, with_c=True)
+    for form in FORMS:
+        ctx.set_form(form)
+        ctx.set_schedule("alpha_b")
+        C = np.zeros((70, 90), np.uint8)
+        ctx.mul_host(e, f, A, B, C)
+        np.testing.assert_array_equal(C, oracle.matmul(e, f, A, B))
+        C = C0.copy()
+        ctx.mul_host(e, f, A, B, C, accumulate=True)
+        np.testing.assert_array_equal(C, oracle.addmul(e, f, A, B, C0))
+
+
+def test_batched_matches_individual(ctx):
+    ctx.set_form("auto")
+    ctx.set_schedule("auto")
+    probs, expect = [], []
+    for j in range(12):
+        e, f, m, n, k, A, B = workloads.batched_instance(j)
+        m, n, k = max(1, m // 8), max(1, n // 8), max(1, k // 8)
+        A, B = A[:m, :k].copy(), B[:k, :n].copy()
+        C = torch.zeros((m, n), dtype=m4.elem_dtype_torch(e), device="cuda")
+        probs.append((e, f, dev(A), dev(B), C, False))
+        expect.append(oracle.matmul(e, f, A, B))
+    ctx.mul_batched(probs)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == m4.OK
+    for (e, f, A, B, C, _), ex in zip(probs, expect):
+        np.testing.assert_array_equal(host(C), ex)
+
+
+# ---------------------------------------------------------------- full-size workloads
+
+_panel_cache = {}
+
+
+def _workload_panel(idx, rows):
+    """Inputs of a workload and the oracle's product on a row panel."""
+    key = (idx, rows.start, rows.stop)
+    if key not in _panel_cache:
+        w = workloads.WORKLOADS[idx]
+        A, B, C0 = w.inputs()
+        Ap = A[rows]
+        ref = oracle.addmul(w.e, w.f, Ap, B, C0[rows]) if C0 is not None else oracle.matmul(w.e, w.f, Ap, B)
+        _panel_cache[key] = (w, A, B, C0, ref)
+    return _panel_cache[key]
+
+
+def test_workload1_full(ctx):
+    w = workloads.WORKLOADS[1]
+    A, B, _ = w.inputs()
+    ref = oracle.matmul(w.e, w.f, A, B)
+    for form in FORMS:
+        for sched in SCHEDS:
+            np.testing.assert_array_equal(run(ctx, form, sched, w.e, A, B), ref, err_msg=f"{form} {sched}")
+
+
+@pytest.mark.parametrize("idx", [2, 3, 5])
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_full_size_workloads(ctx, idx, form, sched):
+    w = workloads.WORKLOADS[idx]
+    rows = slice(w.m // 2 - 8, w.m // 2 + 8)
+    w, A, B, C0, ref = _workload_panel(idx, rows)
+    C = run(ctx, form, sched, w.e, A, B, C0)
+    np.testing.assert_array_equal(C[rows], ref)                 # sampled rows, exact
+    np.testing.assert_array_equal(C[:4], (oracle.addmul(w.e, w.f, A[:4], B, C0[:4]) if C0 is not None
+                                          else oracle.matmul(w.e, w.f, A[:4], B)))   # first rows (first tile)
+    lhs = C if C0 is None else (C ^ C0)
+    assert oracle.freivalds(w.e, w.f, A, B, lhs, trials=4, seed=idx)   # whole product, error <= 2^(-4e)
