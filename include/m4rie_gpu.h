@@ -51,7 +51,8 @@ typedef enum m4rie_status {
     M4RIE_ERR_NOMEM = 5,      /* workspace allocation failed */
     M4RIE_ERR_CUDA = 6,       /* a CUDA runtime or driver call failed (see m4rie_last_error) */
     M4RIE_ERR_TIMEOUT = 7,    /* device: a bounded wait inside a kernel ran out; that kernel's output is incomplete */
-    M4RIE_ERR_UNSUPPORTED = 8 /* the requested form is not available for this problem or device */
+    M4RIE_ERR_UNSUPPORTED = 8, /* the requested form is not available for this problem or device */
+    M4RIE_ERR_SCRATCH = 9      /* m4rie_mul_noalloc: the operand planes exceed its fixed scratch array */
 } m4rie_status;
 
 /* How the GF(2) slice products are computed. */
@@ -189,6 +190,36 @@ m4rie_status m4rie_phase_times(m4rie_ctx *ctx, double *pack_ms, double *gemm_ms,
  * context's persistent kernels (default 4e9).  A small value makes those
  * waits run out; the kernel then sets M4RIE_ERR_TIMEOUT and returns. */
 m4rie_status m4rie_set_wait_limit_ns(m4rie_ctx *ctx, uint64_t ns);
+
+/* C = A*B (accumulate == 0) or C += A*B (accumulate != 0) over GF(2^e), like
+ * m4rie_mul / m4rie_addmul, for callers that may not allocate device memory:
+ * for example a host framework whose own allocator has already reserved the
+ * GPU's memory, code whose memory footprint must be fixed when the library is
+ * loaded, or a latency-critical loop in which cudaMalloc / cudaFree (which can
+ * synchronise the device) are not acceptable.  The paper has no counterpart;
+ * this is a deployment variant of the bit-packed popc form with the alpha^j-B
+ * schedule.
+ *
+ * No context is needed and the call allocates nothing.  Its operand planes
+ * live in one statically allocated device array of 64 MiB that every GPU
+ * loading this library holds until the process exits.  Problems whose planes
+ * do not fit (roughly: Mp*e*Kp/8 + ceil(n/G)*G*e*e*Kp/8 bytes with Kp =
+ * k rounded up to 128, Mp = m rounded up to 128, G = 64, 32 or 16 for
+ * e = 2, 3-4, 5-10; a 4096 x 4096 x 4096 product over GF(2^4) fits) are
+ * rejected with M4RIE_ERR_SCRATCH before anything is launched.
+ *
+ * A, B, C: device pointers as for m4rie_mul.  device_status: optional device
+ * int that receives the status bits (1: an entry was >= 2^e, 2: a wait timed
+ * out) OR-ed in; NULL discards them.  stream: cudaStream_t (NULL = legacy
+ * default stream).  Asynchronous like m4rie_mul.
+ *
+ * The first call on each device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress); make that first call before any stream
+ * capture on that device.  All calls share the scratch array, which keeps the
+ * previous call's contents (each call rewrites every word it reads), so calls
+ * whose GPU work overlaps race on it: serialise them. */
+m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void *A, const void *B,
+                               void *C, int accumulate, int *device_status, void *stream);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libm4rie_gpu.so")
 
-OK, ERR_ARG, ERR_POLY, ERR_ALIAS, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
+OK, ERR_ARG, ERR_POLY, ERR_ALIAS, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH = range(10)
 FORM_AUTO, FORM_POPC, FORM_TC_F8, FORM_MMA_S8, FORM_TC_F4 = range(5)
 SCHED_AUTO, SCHED_ALPHA_B, SCHED_KARATSUBA = range(3)
 FORMS = {"auto": FORM_AUTO, "popc": FORM_POPC, "tc_f8": FORM_TC_F8, "mma_s8": FORM_MMA_S8, "tc_f4": FORM_TC_F4}
@@ -63,6 +63,7 @@ def _load() -> ctypes.CDLL:
         "m4rie_kernel_launches": (i64, [vp]),
         "m4rie_set_wait_limit_ns": (i32, [vp, u64]),
         "m4rie_enable_timing": (i32, [vp, i32]),
+        "m4rie_mul_noalloc": (i32, [i32, u32, i64, i64, i64, vp, vp, vp, i32, vp, vp]),
         "m4rie_phase_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]),
     }
@@ -223,6 +224,17 @@ class Context:
 
     def resolve_form(self, e, m, n, k) -> int:
         return int(lib.m4rie_resolve_form(self.handle, e, m, n, k))
+
+
+def mul_noalloc(e: int, f: int, A, B, C, accumulate: bool = False, device_status=None, stream=None) -> int:
+    """m4rie_mul_noalloc on CUDA tensors; returns the m4rie_status code."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    m, k = A.shape
+    n = B.shape[1]
+    return int(lib.m4rie_mul_noalloc(e, f, m, n, k, _ptr(A), _ptr(B), _ptr(C), 1 if accumulate else 0,
+                                     _ptr(device_status), ctypes.c_void_p(stream.cuda_stream)))
 
 
 def schedule_products(e: int, f: int, schedule) -> int:

@@ -627,6 +627,7 @@ const char* m4rie_status_string(m4rie_status s) {
     case M4RIE_ERR_CUDA: return "CUDA error";
     case M4RIE_ERR_TIMEOUT: return "a bounded wait inside a kernel ran out";
     case M4RIE_ERR_UNSUPPORTED: return "form not available for this problem or device";
+    case M4RIE_ERR_SCRATCH: return "problem too large for the fixed scratch of m4rie_mul_noalloc";
   }
   return "unknown status";
 }
