@@ -58,13 +58,20 @@ class ClockSampler:
 
     def __init__(self, index: int):
         self.index = index
-        self.rows = []
+        self.rows = []   # (host time of arrival, fields)
         self.proc = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -74,7 +81,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
 
     def __exit__(self, *a):
         if self.proc:
@@ -85,15 +92,21 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        """Samples that arrived inside [mark_start, mark_end] (+ the 50 ms sampling
+        interval); if the timed region was shorter than one interval, the sample
+        closest to it."""
+        rows = [(t, r) for t, r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        inside = [r for t, r in rows if self.t0 is not None and self.t0 <= t <= (self.t1 or t) + 0.05]
+        if not inside and rows and self.t0 is not None:
+            inside = [min(rows, key=lambda tr: abs(tr[0] - self.t0))[1]]
+        sm = [float(r[1]) for r in inside]
+        mx = [float(r[2]) for r in inside]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            if len(r) >= 9:
-                for nm, v in zip(names, r[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
+        for r in inside:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
 
@@ -105,7 +118,7 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(rows: int = 32):
+def cpu_baseline(rows: int = 256):
     """The oracle on a row panel of the workload (bounded CPU work)."""
     import oracle
     w = WORKLOAD
@@ -156,6 +169,9 @@ def main():
     ap.add_argument("--schedules", default="alpha_b,karatsuba")
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single", default=None,
+                    help="FORM/SCHEDULE: run the warm-up steps and one more step of that form, print nothing "
+                         "(a fixed launch sequence for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -186,6 +202,17 @@ def main():
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
+    if args.single:
+        form, sched = args.single.split("/")
+        ctx.set_form(form)
+        ctx.set_schedule(sched)
+        for _ in range(args.warmup + 1):
+            ctx.mul(w.e, w.f, dA, dB, dC)
+        torch.cuda.synchronize()
+        status = ctx.device_status()
+        ctx.close()
+        return 0 if status == m4.OK else 1
+
     results = {}
     for form in args.forms.split(","):
         for sched in args.schedules.split(","):
@@ -203,14 +230,18 @@ def main():
             launches0 = ctx.kernel_launches()
             starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
             stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            barrier()
             with ClockSampler(local) as clk:
+                time.sleep(0.3)   # let the sampler start before the timed region
+                barrier()
+                clk.mark_start()
                 for i in range(args.steps):
                     flush.fill_(i & 0xFF)
                     starts[i].record(stream)
                     ctx.mul(w.e, w.f, dA, dB, dC)
                     stops[i].record(stream)
                 barrier()
+                clk.mark_end()
+                time.sleep(0.1)
             ms = sum(s.elapsed_time(t) for s, t in zip(starts, stops)) / args.steps
             pack_ms, gemm_ms, rec_ms, nprod = ctx.phase_times(reset=True)
             ctx.enable_timing(False)

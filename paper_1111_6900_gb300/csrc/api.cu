@@ -48,6 +48,8 @@ m4rie_status cuda_fail(m4rie_ctx* ctx, cudaError_t err) {
 
 int elem_bytes(int e) { return e <= 8 ? 1 : 2; }
 
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 // Phase markers: mark(ctx, phase) opens a phase, mark(ctx, -1) closes it.
 enum { kPhasePack = 0, kPhaseGemm = 1, kPhaseRecombine = 2 };
 
@@ -206,6 +208,8 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   pa.ld = ld;
   pa.bstride = 0;
   pa.emask = (1u << e) - 1;
+  pa.e = e;
+  pa.vec = aligned16(A) && (k * elem_bytes(e)) % 16 == 0;
   pa.out = Ap;
   pa.status = ctx->d_status;
   for (int j = 0; j < e; ++j) pa.mask[j] = amask[j];
@@ -217,6 +221,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   PackParams pb = pa;
   pb.X = B;
   pb.ldx = n;
+  pb.vec = aligned16(B) && (n * elem_bytes(e)) % 16 == 0;
   pb.rows = n;
   pb.rows_p = groups * G;
   pb.P = e * e;
@@ -312,6 +317,8 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   pa.ld = Kp;
   pa.bstride = Mp * Kp;
   pa.emask = (1u << e) - 1;
+  pa.e = e;
+  pa.vec = aligned16(A) && (k * elem_bytes(e)) % 16 == 0;
   pa.out = Ap;
   pa.status = ctx->d_status;
   for (int p = 0; p < r; ++p) pa.mask[p] = sc.amask[p];
@@ -322,6 +329,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   PackParams pb = pa;
   pb.X = B;
   pb.ldx = n;
+  pb.vec = aligned16(B) && (n * elem_bytes(e)) % 16 == 0;
   pb.rows = n;
   pb.rows_p = Np;
   pb.bstride = Np * Kp;

@@ -37,6 +37,8 @@ struct PackParams {
   int64_t ld;         // output row length (entries) = kb * Kp
   int64_t bstride;    // entries between batch planes
   uint32_t emask;     // 2^e - 1
+  int e;              // number of slice bits of an element
+  int vec;            // X and its rows are 16-byte aligned: 128-bit loads allowed
   void* out;
   int* status;
   uint16_t mask[kMaxMasks];

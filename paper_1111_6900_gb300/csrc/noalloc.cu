@@ -100,6 +100,8 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   pa.Kp = Kp;
   pa.ld = ld;
   pa.emask = (1u << e) - 1;
+  pa.e = e;
+  pa.vec = (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && (k * eb) % 16 == 0;
   pa.out = Ap;
   pa.status = status;
   for (int j = 0; j < e; ++j) pa.mask[j] = amask[j];
@@ -108,6 +110,7 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   PackParams pb = pa;
   pb.X = B;
   pb.ldx = n;
+  pb.vec = (reinterpret_cast<uintptr_t>(B) & 15u) == 0 && (n * eb) % 16 == 0;
   pb.rows = n;
   pb.rows_p = groups * G;
   pb.P = e * e;

@@ -32,177 +32,226 @@ __device__ __forceinline__ void flag_range(int* status, bool bad) {
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusRange);
 }
 
+// ---- Slice words.  Bit u of slice word l is coefficient l of element u; an
+// operand plane for mask q is the XOR of the slice words selected by q.
+
+// 16 consecutive elements of row r starting at t0 (zeros past the row end),
+// as 4 words of bytes (u8) or 8 words of halfwords (u16).
+template <typename T>
+__device__ __forceinline__ void load16(const PackParams& p, int64_t r, int64_t t0, uint32_t (&v)[8]) {
+  const T* row = static_cast<const T*>(p.X) + r * p.ldx;
+  constexpr int W = sizeof(T) == 1 ? 4 : 8;
+  if (p.vec && t0 + 16 <= p.K) {
+    const uint4* q = reinterpret_cast<const uint4*>(row + t0);
+    const uint4 a = q[0];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+    if (W == 8) {
+      const uint4 b = q[1];
+      v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; ++k) v[k] = 0;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (t0 + u < p.K) v[u * sizeof(T) / 4] |= (uint32_t)row[t0 + u] << (8 * sizeof(T) * (u % (4 / sizeof(T))));
+  }
+}
+
+// Range check and masking of packed elements; returns true if any was >= 2^e.
+template <typename T>
+__device__ __forceinline__ bool clamp16(uint32_t (&v)[8], uint32_t emask) {
+  constexpr int W = sizeof(T) == 1 ? 4 : 8;
+  const uint32_t rep = sizeof(T) == 1 ? emask * 0x01010101u : emask * 0x00010001u;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    bad |= (v[k] & ~rep) != 0;
+    v[k] &= rep;
+  }
+  return bad;
+}
+
+// Slice words of 16 packed elements: S[l] bit u = bit l of element u.
+template <typename T>
+__device__ __forceinline__ void slices16(const uint32_t (&v)[8], int e, uint32_t (&S)[10]) {
+#pragma unroll
+  for (int l = 0; l < 10; ++l) {
+    uint32_t w = 0;
+    if (l < e) {
+      if (sizeof(T) == 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w |= ((((v[k] >> l) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w |= (((((v[k] >> l) & 0x00010001u) * 0x00008001u) >> 15) & 3u) << (2 * k);
+      }
+    }
+    S[l] = w;
+  }
+}
+
+__device__ __forceinline__ uint32_t combine(const uint32_t (&S)[10], int e, uint32_t mask) {
+  uint32_t w = 0;
+#pragma unroll
+  for (int l = 0; l < 10; ++l)
+    if (l < e && (mask >> l & 1u)) w ^= S[l];
+  return w;
+}
+
+// 16 plane bits -> 16 bytes (0 or `one`) or 16 nibbles.
+__device__ __forceinline__ void store_bytes16(uint8_t* dst, uint32_t bits, uint32_t one) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) w[k] = (((bits >> (4 * k)) & 0xFu) * 0x00204081u & 0x01010101u) * one;
+  *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ void store_nibs16(uint8_t* dst, uint32_t bits, uint32_t one) {
+  uint32_t w[2] = {0, 0};
+#pragma unroll
+  for (int u = 0; u < 16; ++u) w[u >> 3] |= ((bits >> u) & 1u) * one << (4 * (u & 7));
+  *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+}
+
 // ---- A side, byte / nibble planes: one thread per (row, 16 consecutive t).
 template <typename T, bool NIB>
-__global__ void pack_rows_bytes(const __grid_constant__ PackParams p) {
+__global__ void __launch_bounds__(256) pack_rows_bytes(const __grid_constant__ PackParams p) {
   const int64_t nch = p.Kp / 16;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = idx < p.rows_p * nch;
   const int64_t r = live ? idx / nch : 0;
   const int64_t t0 = live ? (idx % nch) * 16 : 0;
-  uint32_t x[16];
-  bool bad = false;
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int64_t t = t0 + u;
-    x[u] = (live && r < p.rows && t < p.K) ? load_elem<T>(p, r, t) : 0u;
-    bad |= x[u] > p.emask;
-    x[u] &= p.emask;
-  }
-  flag_range(p.status, bad);
+  uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (live && r < p.rows) load16<T>(p, r, t0, v);
+  flag_range(p.status, clamp16<T>(v, p.emask));
   if (!live) return;
+  uint32_t S[10];
+  slices16<T>(v, p.e, S);
+  uint8_t* out = static_cast<uint8_t*>(p.out);
   for (int q = 0; q < p.P; ++q) {
-    const uint32_t mk = p.mask[q];
+    const uint32_t bits = combine(S, p.e, p.mask[q]);
     const int64_t o = plane_index(p, q, r, t0);
-    if (!NIB) {
-      uint32_t w[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        w[k] = 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) w[k] |= (par(x[4 * k + u] & mk) * p.one) << (8 * u);
-      }
-      *reinterpret_cast<uint4*>(static_cast<uint8_t*>(p.out) + o) = make_uint4(w[0], w[1], w[2], w[3]);
-    } else {
-      uint32_t w[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        w[k] = 0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) w[k] |= (par(x[8 * k + u] & mk) * p.one) << (4 * u);
-      }
-      *reinterpret_cast<uint2*>(static_cast<uint8_t*>(p.out) + o / 2) = make_uint2(w[0], w[1]);
-    }
+    if (NIB) store_nibs16(out + o / 2, bits, p.one);
+    else store_bytes16(out + o, bits, p.one);
   }
 }
 
-// ---- A side, bit planes: one warp per (row, 512 consecutive t).  Lanes load
-// 16 consecutive elements each, stage them in shared memory, and every
-// output word is one ballot over 32 consecutive elements.
+// ---- A side, bit planes: one warp per (row, 512 consecutive t).  Lane l
+// holds t = 16 l .. 16 l + 15; lane pairs form 32-bit words.
 template <typename T>
 __global__ void __launch_bounds__(256) pack_rows_bits(const __grid_constant__ PackParams p) {
-  __shared__ uint32_t sx[8][512];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int64_t nch = (p.Kp + 511) / 512;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const bool live = wid < p.rows_p * nch;  // warp-uniform
   const int64_t r = live ? wid / nch : 0;
   const int64_t tb = live ? (wid % nch) * 512 : 0;
-  bool bad = false;
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int64_t t = tb + 16 * lane + u;
-    uint32_t v = (live && r < p.rows && t < p.K) ? load_elem<T>(p, r, t) : 0u;
-    bad |= v > p.emask;
-    sx[wib][16 * lane + u] = v & p.emask;
-  }
-  flag_range(p.status, bad);
-  __syncwarp();
+  uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (live && r < p.rows) load16<T>(p, r, tb + 16 * lane, v);
+  flag_range(p.status, clamp16<T>(v, p.emask));
   if (!live) return;
-  uint32_t x[16];
+  uint32_t S[10];
+  slices16<T>(v, p.e, S);
 #pragma unroll
-  for (int w = 0; w < 16; ++w) x[w] = sx[wib][32 * w + lane];
-  const bool store = tb + 32 * lane < p.Kp && lane < 16;
+  for (int l = 0; l < 10; ++l) S[l] |= __shfl_down_sync(0xffffffffu, S[l], 1) << 16;
+  const bool store = (lane & 1) == 0 && tb + 16 * lane < p.Kp;
+  uint32_t* out = static_cast<uint32_t*>(p.out);
   for (int q = 0; q < p.P; ++q) {
-    const uint32_t mk = p.mask[q];
-    uint32_t my = 0;
-#pragma unroll
-    for (int w = 0; w < 16; ++w) {
-      const uint32_t wd = __ballot_sync(0xffffffffu, par(x[w] & mk));
-      my = (lane == w) ? wd : my;
-    }
-    if (store) static_cast<uint32_t*>(p.out)[plane_index(p, q, r, tb) / 32 + lane] = my;
+    const uint32_t w = combine(S, p.e, p.mask[q]);
+    if (store) out[plane_index(p, q, r, tb) / 32 + (lane >> 1)] = w;
   }
 }
 
-// ---- B side (columns of X become plane rows), byte / nibble planes.
-// Tile of 64 t x 64 columns staged in shared memory (one 32-bit word per
-// element, conflict-free column reads); one thread per (column, 16 t).
-template <typename T, bool NIB>
-__global__ void __launch_bounds__(256) pack_cols_bytes(const __grid_constant__ PackParams p) {
-  __shared__ uint32_t tile[64][65];
-  const int64_t c0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 64;
+// Stage a tile of TT rows (t) x 64 columns of X into shared memory, one
+// 32-bit word per element; masks the elements and reports out-of-range ones.
+template <typename T, int TT>
+__device__ __forceinline__ void stage_tile(const PackParams& p, int64_t t0, int64_t c0, uint32_t (*tile)[65]) {
   bool bad = false;
-  for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
-    const int tt = idx >> 6, cc = idx & 63;
-    const int64_t t = t0 + tt, c = c0 + cc;
-    uint32_t v = (t < p.K && c < p.rows) ? (uint32_t) static_cast<const T*>(p.X)[t * p.ldx + c] : 0u;
-    bad |= v > p.emask;
-    tile[tt][cc] = v & p.emask;
+  const T* X = static_cast<const T*>(p.X);
+  constexpr int CH = 64 * sizeof(T) / 16;  // 16-byte chunks per tile row
+  if (p.vec && c0 + 64 <= p.rows && t0 + TT <= p.K) {
+    for (int idx = threadIdx.x; idx < TT * CH; idx += blockDim.x) {
+      const int tt = idx / CH, ch = idx % CH;
+      const uint4 a = *reinterpret_cast<const uint4*>(X + (t0 + tt) * p.ldx + c0 + ch * (16 / sizeof(T)));
+      const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int k = 0; k < 16 / (int)sizeof(T); ++k) {
+        const uint32_t x = sizeof(T) == 1 ? (w[k >> 2] >> (8 * (k & 3))) & 0xFFu : (w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+        bad |= x > p.emask;
+        tile[tt][ch * (16 / sizeof(T)) + k] = x & p.emask;
+      }
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < TT * 64; idx += blockDim.x) {
+      const int tt = idx >> 6, cc = idx & 63;
+      const int64_t t = t0 + tt, c = c0 + cc;
+      const uint32_t x = (t < p.K && c < p.rows) ? (uint32_t)X[t * p.ldx + c] : 0u;
+      bad |= x > p.emask;
+      tile[tt][cc] = x & p.emask;
+    }
   }
   flag_range(p.status, bad);
-  __syncthreads();
-  const int cl = threadIdx.x >> 2, ch = threadIdx.x & 3;
-  const int64_t c = c0 + cl;
-  if (c >= p.rows_p) return;
-  uint32_t x[16];
-#pragma unroll
-  for (int u = 0; u < 16; ++u) x[u] = tile[ch * 16 + u][cl];
-  const int64_t tt0 = t0 + ch * 16;
-  for (int q = 0; q < p.P; ++q) {
-    const uint32_t mk = p.mask[q];
-    const int64_t o = plane_index(p, q, c, tt0);
-    if (!NIB) {
-      uint32_t w[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        w[k] = 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) w[k] |= (par(x[4 * k + u] & mk) * p.one) << (8 * u);
-      }
-      *reinterpret_cast<uint4*>(static_cast<uint8_t*>(p.out) + o) = make_uint4(w[0], w[1], w[2], w[3]);
-    } else {
-      uint32_t w[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        w[k] = 0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) w[k] |= (par(x[8 * k + u] & mk) * p.one) << (4 * u);
-      }
-      *reinterpret_cast<uint2*>(static_cast<uint8_t*>(p.out) + o / 2) = make_uint2(w[0], w[1]);
-    }
-  }
 }
 
-// ---- B side, bit planes: tile of 128 t x 64 columns; each warp owns 8
-// columns; lane l reads t = 32 s + l, one ballot per (mask, s) gives a word.
+// ---- B side (columns of X become plane rows), bit planes.  Tile of 128 t x
+// 64 columns; each warp owns 8 columns; lane l reads t = 32 s + l; e ballots
+// per 32 elements give the slice words, lane q forms plane q by XORs.
 template <typename T>
 __global__ void __launch_bounds__(256) pack_cols_bits(const __grid_constant__ PackParams p) {
   __shared__ uint32_t tile[128][65];
   const int64_t c0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 128;
-  bool bad = false;
-  for (int idx = threadIdx.x; idx < 128 * 64; idx += 256) {
-    const int tt = idx >> 6, cc = idx & 63;
-    const int64_t t = t0 + tt, c = c0 + cc;
-    uint32_t v = (t < p.K && c < p.rows) ? (uint32_t) static_cast<const T*>(p.X)[t * p.ldx + c] : 0u;
-    bad |= v > p.emask;
-    tile[tt][cc] = v & p.emask;
-  }
-  flag_range(p.status, bad);
+  stage_tile<T, 128>(p, t0, c0, tile);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* out = static_cast<uint32_t*>(p.out);
   for (int cc = 0; cc < 8; ++cc) {
     const int cl = w * 8 + cc;
     const int64_t c = c0 + cl;
     if (c >= p.rows_p) break;  // warp-uniform
-    uint32_t x[4];
+    uint32_t S[4][10];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) x[s] = tile[32 * s + lane][cl];
-    for (int q0 = 0; q0 < p.P; q0 += 32) {
-      const int cnt = min(32, p.P - q0);
-      uint32_t my[4] = {0, 0, 0, 0};
-      for (int qq = 0; qq < cnt; ++qq) {
-        const uint32_t mk = p.mask[q0 + qq];
+    for (int s = 0; s < 4; ++s) {
+      const uint32_t x = tile[32 * s + lane][cl];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const uint32_t wd = __ballot_sync(0xffffffffu, par(x[s] & mk));
-          my[s] = (lane == qq) ? wd : my[s];
-        }
-      }
-      if (lane < cnt) {
-        uint32_t* o = static_cast<uint32_t*>(p.out) + plane_index(p, q0 + lane, c, t0) / 32;
-        *reinterpret_cast<uint4*>(o) = make_uint4(my[0], my[1], my[2], my[3]);
-      }
+      for (int l = 0; l < 10; ++l) S[s][l] = l < p.e ? __ballot_sync(0xffffffffu, (x >> l) & 1u) : 0u;
+    }
+    for (int q = lane; q < p.P; q += 32) {
+      const uint32_t mk = p.mask[q];
+      uint4 o;
+      o.x = combine(S[0], p.e, mk);
+      o.y = combine(S[1], p.e, mk);
+      o.z = combine(S[2], p.e, mk);
+      o.w = combine(S[3], p.e, mk);
+      *reinterpret_cast<uint4*>(out + plane_index(p, q, c, t0) / 32) = o;
+    }
+  }
+}
+
+// ---- B side, byte / nibble planes.  Tile of 32 t x 64 columns; each warp
+// owns 8 columns with lane = t; e ballots give the slice words; the 2P
+// (plane, 16-t half) outputs of a column are spread over the lanes.
+template <typename T, bool NIB>
+__global__ void __launch_bounds__(256) pack_cols_bytes(const __grid_constant__ PackParams p) {
+  __shared__ uint32_t tile[32][65];
+  const int64_t c0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 32;
+  stage_tile<T, 32>(p, t0, c0, tile);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint8_t* out = static_cast<uint8_t*>(p.out);
+  for (int cc = 0; cc < 8; ++cc) {
+    const int cl = w * 8 + cc;
+    const int64_t c = c0 + cl;
+    if (c >= p.rows_p) break;  // warp-uniform
+    const uint32_t x = tile[lane][cl];
+    uint32_t S[10];
+#pragma unroll
+    for (int l = 0; l < 10; ++l) S[l] = l < p.e ? __ballot_sync(0xffffffffu, (x >> l) & 1u) : 0u;
+    for (int it = lane; it < 2 * p.P; it += 32) {
+      const int q = it >> 1, h = it & 1;
+      const uint32_t bits = (combine(S, p.e, p.mask[q]) >> (16 * h)) & 0xFFFFu;
+      const int64_t o = plane_index(p, q, c, t0 + 16 * h);
+      if (NIB) store_nibs16(out + o / 2, bits, p.one);
+      else store_bytes16(out + o, bits, p.one);
     }
   }
 }
@@ -251,29 +300,74 @@ __global__ void __launch_bounds__(256) cling_kernel(int e, int64_t rows, int64_t
 }
 
 // ---- Karatsuba recombination: bit s of C[r][c] is the parity of the
-// products selected by out_mask[s] (reduction mod f folded in).
+// products selected by out_mask[s] (reduction mod f folded in).  One thread
+// per (row, 32 columns): XOR the r parity words into e output slice words,
+// then transpose bits into 32 elements.
 template <typename T>
 __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecombineParams p) {
+  const int64_t nw = (p.n + 31) / 32;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = idx < p.m * p.n;
-  const int64_t r = live ? idx / p.n : 0, c = live ? idx % p.n : 0;
-  uint64_t v = 0;
+  const bool live = idx < p.m * nw;
+  const int64_t r = live ? idx / nw : 0, w = live ? idx % nw : 0;
+  uint32_t out[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (live)
     for (int q = 0; q < p.r; ++q) {
-      const uint32_t w = p.P[((int64_t)q * p.rows_p + r) * p.ldw + (c >> 5)];
-      v |= (uint64_t)((w >> (c & 31)) & 1u) << q;
+      const uint32_t pw = p.P[((int64_t)q * p.rows_p + r) * p.ldw + w];
+#pragma unroll
+      for (int s = 0; s < 10; ++s)
+        if (s < p.e && (p.out_mask[s] >> q & 1ull)) out[s] ^= pw;
     }
-  uint32_t out = 0;
-  for (int s = 0; s < p.e; ++s) out |= (uint32_t)(__popcll(v & p.out_mask[s]) & 1) << s;
-  bool bad = false;
+  // elements c = 32 w + b, packed 4 (u8) or 2 (u16) per 32-bit word
+  constexpr int PER = 4 / sizeof(T);
+  constexpr int NW = 32 / PER;
+  uint32_t vals[NW];
+#pragma unroll
+  for (int g = 0; g < NW; ++g) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int s = 0; s < 10; ++s) {
+      if (s >= p.e) break;
+      const uint32_t bits = (out[s] >> (PER * g)) & ((1u << PER) - 1);
+      const uint32_t spread = sizeof(T) == 1 ? (bits * 0x00204081u) & 0x01010101u : (bits & 1u) | ((bits >> 1) << 16);
+      v |= spread << s;
+    }
+    vals[g] = v;
+  }
   T* C = static_cast<T*>(p.C);
-  if (live && p.add) {
-    uint32_t old = (uint32_t)C[r * p.ldc + c];
-    bad = old > p.emask;
-    out ^= old & p.emask;
+  T* dst = C + r * p.ldc + 32 * w;
+  const bool full = 32 * w + 32 <= p.n;
+  const bool vec = full && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
+  bool bad = false;
+  if (live) {
+    if (vec) {
+      uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+      for (int h = 0; h < NW / 4; ++h) {
+        uint4 o = make_uint4(vals[4 * h], vals[4 * h + 1], vals[4 * h + 2], vals[4 * h + 3]);
+        if (p.add) {
+          const uint4 old = d4[h];
+          const uint32_t rep = sizeof(T) == 1 ? p.emask * 0x01010101u : p.emask * 0x00010001u;
+          bad |= ((old.x | old.y | old.z | old.w) & ~rep) != 0;
+          o.x ^= old.x & rep, o.y ^= old.y & rep, o.z ^= old.z & rep, o.w ^= old.w & rep;
+        }
+        d4[h] = o;
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < 32; ++b) {
+        if (32 * w + b < p.n) {
+          uint32_t v = (vals[b / PER] >> (8 * sizeof(T) * (b % PER))) & (sizeof(T) == 1 ? 0xFFu : 0xFFFFu);
+          if (p.add) {
+            const uint32_t old = dst[b];
+            bad |= old > p.emask;
+            v ^= old & p.emask;
+          }
+          dst[b] = (T)v;
+        }
+      }
+    }
   }
   flag_range(p.status, bad);
-  if (live) C[r * p.ldc + c] = (T)out;
 }
 
 template <typename K, typename... Args>
@@ -311,7 +405,7 @@ cudaError_t launch_pack_planes(const PackParams& p, bool trans, cudaStream_t s, 
     if (u16) pack_cols_bits<uint16_t><<<grid, 256, 0, s>>>(p);
     else pack_cols_bits<uint8_t><<<grid, 256, 0, s>>>(p);
   } else {
-    const int64_t gy = p.Kp / 64;
+    const int64_t gy = p.Kp / 32;
     if (gy > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)gx, (unsigned)gy);
     if (p.fmt == kFmtByte) {
@@ -347,7 +441,7 @@ cudaError_t launch_cling(int e, int64_t rows, int64_t cols, const uint64_t* slic
 }
 
 cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches) {
-  const int64_t n = p.m * p.n;
+  const int64_t n = p.m * ((p.n + 31) / 32);
   if (p.elem_bytes == 2) return launch(recombine_kernel<uint16_t>, ceil_div(n, 256), 256, s, launches, p);
   return launch(recombine_kernel<uint8_t>, ceil_div(n, 256), 256, s, launches, p);
 }
