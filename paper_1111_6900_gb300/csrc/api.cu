@@ -175,7 +175,8 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   const FormInfo fi = form_info(form);
   int G;
   if (form == M4RIE_FORM_POPC) G = popc_group(e);
-  else if (form == M4RIE_FORM_TC_F8) G = tc_group(e);
+  else if (form == M4RIE_FORM_TC_F8 || form == M4RIE_FORM_TC_F4) G = tc_group(e, fi.fmt);
+  else if (form == M4RIE_FORM_MMA_S8) G = mma_group(e);
   else return M4RIE_ERR_UNSUPPORTED;
   const int64_t Kp = round_up(k, 128);
   const int64_t ld = (int64_t)e * Kp;
@@ -259,7 +260,8 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.tiles_m = (int)(Mp / 128);
     tp.tiles_n = (int)groups;
     tp.batch = 1;
-    tp.kblocks = (int)(ld / 128);
+    const int64_t ld_bytes = (int64_t)entries_bytes(ld, fi.bits);
+    tp.kblocks = (int)ceil_div(ld_bytes, 128);
     tp.kc = std::max(1, ctx->tc_chunk / 128);
     tp.group_m = tp.tiles_m;
     tp.C = C;
@@ -270,7 +272,8 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.status = ctx->d_status;
     tp.mode = 0;
     tp.wait_limit_ns = ctx->wait_limit_ns;
-    err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld, tp, ctx->num_sms, ctx->stream, &ctx->launches);
+    if (form == M4RIE_FORM_MMA_S8) err = launch_mma_s8(Ap, Bp, ld_bytes, tp, ctx->stream, &ctx->launches);
+    else err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld_bytes, tp, ctx->num_sms, ctx->stream, &ctx->launches);
   }
   if (err != cudaSuccess) return cuda_fail(ctx, err);
   return M4RIE_OK;
@@ -279,7 +282,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
 // ---------------------------------------------------------------- Karatsuba
 m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
                            const void* A, const void* B, void* C, int add) {
-  if (form != M4RIE_FORM_POPC && form != M4RIE_FORM_TC_F8) return M4RIE_ERR_UNSUPPORTED;
+  if (form != M4RIE_FORM_POPC && form != M4RIE_FORM_TC_F8 && form != M4RIE_FORM_TC_F4) return M4RIE_ERR_UNSUPPORTED;
   Schedule sc;
   if (!karatsuba_schedule(e, f, &sc)) {
     ctx->last_error = "schedule construction failed its check";
@@ -289,7 +292,10 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   const int r = sc.r;
   const int64_t Kp = round_up(k, 128);
   const int64_t Mp = round_up(m, 128);
-  const int64_t Np = round_up(n, form == M4RIE_FORM_POPC ? 128 : 256);
+  // popc parity tiles are 128 columns; tcgen05 tiles 256 (FP8) or 224 (FP4, which
+  // keeps its scale factors in TMEM next to each accumulator)
+  const int ntile = form == M4RIE_FORM_POPC ? 128 : (form == M4RIE_FORM_TC_F8 ? 256 : 224);
+  const int64_t Np = round_up(n, ntile);
   const int64_t ldp = Np / 32;  // words per parity row
   const size_t a_bytes = round_up((int64_t)entries_bytes((int64_t)r * Mp * Kp, fi.bits), 1024);
   const size_t b_bytes = round_up((int64_t)entries_bytes((int64_t)r * Np * Kp, fi.bits), 1024);
@@ -360,14 +366,15 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     tp.m = m;
     tp.n = n;
     tp.e = e;
-    tp.G = 256;
-    tp.BN = 256;
+    tp.G = ntile;
+    tp.BN = ntile;
     tp.tiles_m = (int)(Mp / 128);
-    tp.tiles_n = (int)(Np / 256);
+    tp.tiles_n = (int)(Np / ntile);
     tp.batch = r;
     tp.a_brows = Mp;
     tp.b_brows = Np;
-    tp.kblocks = (int)(Kp / 128);
+    const int64_t ld_bytes = (int64_t)entries_bytes(Kp, fi.bits);
+    tp.kblocks = (int)ceil_div(ld_bytes, 128);
     tp.kc = std::max(1, ctx->tc_chunk / 128);
     tp.group_m = tp.tiles_m;
     tp.C = Pp;
@@ -376,7 +383,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     tp.ldp = ldp;
     tp.p_bstride = Mp * ldp;
     tp.wait_limit_ns = ctx->wait_limit_ns;
-    err = launch_tc(fi.fmt, Ap, (int64_t)r * Mp, Bp, (int64_t)r * Np, Kp, tp, ctx->num_sms, ctx->stream,
+    err = launch_tc(fi.fmt, Ap, (int64_t)r * Mp, Bp, (int64_t)r * Np, ld_bytes, tp, ctx->num_sms, ctx->stream,
                     &ctx->launches);
   }
   if (err != cudaSuccess) return cuda_fail(ctx, err);

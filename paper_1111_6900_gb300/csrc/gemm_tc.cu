@@ -101,11 +101,28 @@ __host__ __device__ constexpr uint32_t idesc_f8(int M, int N) {
   return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::mxf4 (block scaled): A = B = E2M1, both
+// K-major, UE8M0 scale factors (scale-factor ids 0), dense K = 64, D = F32.
+__host__ __device__ constexpr uint32_t idesc_f4(int M, int N) {
+  return (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | (1u << 23) | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
           d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// D (+)= A * B with per-32-element block scales read from tensor memory
+// (all scales are 2^0 here, so the products are the plain 0/1 counts).
+__device__ __forceinline__ void mma_f4(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t sf,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %5, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%4], p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(sf), "r"(acc)
       : "memory");
 }
 
@@ -135,9 +152,13 @@ __device__ __forceinline__ void tile_coords(const TcParams& p, int tile, int& b,
   tn = local / gm;
 }
 
+// FP4 only: TMEM columns [SF_COL, SF_COL + 16) hold the unit scale factors.
+constexpr int SF_COL = 240;
+
+template <int FMT>
 __global__ void __launch_bounds__(THREADS, 1)
-    tc_f8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const __grid_constant__ TcParams p) {
+    tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -178,6 +199,22 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
+  if (FMT == kFmtNib) {
+    // Unit block-scale factors (UE8M0 0x7F = 2^0) for every lane, written by
+    // the four epilogue warps (each owns 32 TMEM lanes).
+    if (warp >= 2) {
+      uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + SF_COL;
+      const uint32_t v = 0x7F7F7F7Fu;
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+          "r"(v)
+          : "memory");
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
   const int total = p.batch * p.tiles_m * p.tiles_n;
   const uint64_t lim = p.wait_limit_ns;
 
@@ -223,7 +260,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      const uint32_t idesc = idesc_f8(128, p.BN);
+      const uint32_t idesc = FMT == kFmtNib ? idesc_f4(128, p.BN) : idesc_f8(128, p.BN);
+      const uint32_t sf = tmem + SF_COL;
       int stage = 0;
       uint32_t phase = 0;
       int chunk = 0;
@@ -247,8 +285,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             fence_after();
             const uint32_t a0 = smem_u32(sA + stage * A_TILE), b0 = smem_u32(sB + stage * B_SLOT);
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              mma_f8(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA: 32 FP8 or 64 FP4 entries
+              const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
+              if (FMT == kFmtNib) mma_f4(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, sf, acc);
+              else mma_f8(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, acc);
+            }
             mma_commit(empty0 + 8 * stage);
             if (++stage == STAGES) {
               stage = 0;
@@ -404,38 +445,36 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld_bytes
 
 }  // namespace
 
-int tc_group(int e) {
-  switch (e) {
-    case 2: return 128;
-    case 3: return 80;
-    case 4: return 64;
-    case 5: return 48;
-    case 6: return 40;
-    case 7: return 32;
-    case 8: return 32;
-    case 9: return 16;
-    default: return 24;
-  }
+int tc_group(int e, int fmt) {
+  // tile N = e * G: a multiple of 16, at most 256 (FP8) or 240 (FP4, whose
+  // TMEM also holds the scale factors next to each accumulator)
+  const int cap = fmt == kFmtNib ? 240 : 256;
+  int best = 16;
+  for (int g = 1; e * g <= cap; ++g)
+    if ((e * g) % 16 == 0) best = g;
+  return best;
 }
 
 size_t tc_smem_bytes() { return 1024 + (size_t)STAGES * (A_TILE + B_SLOT) + 16 * 8 + 16 + 128 * 9 * 4; }
 
 cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
                       int64_t ld_bytes, const TcParams& p, int num_sms, cudaStream_t s, int64_t* launches) {
-  if (fmt != kFmtByte) return cudaErrorNotSupported;
-  if (p.BN % 16 != 0 || p.BN < 16 || p.BN > 256 || ld_bytes % 128 != 0) return cudaErrorInvalidValue;
+  if (fmt != kFmtByte && fmt != kFmtNib) return cudaErrorNotSupported;
+  if (p.BN % 16 != 0 || p.BN < 16 || p.BN > (fmt == kFmtNib ? SF_COL : 256) || ld_bytes % 16 != 0)
+    return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   if (!make_map(&ma, Aplanes, a_rows, ld_bytes, 128) || !make_map(&mb, Bplanes, b_rows, ld_bytes, p.BN))
     return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes();
-  cudaError_t err = cudaFuncSetAttribute(tc_f8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kernel = fmt == kFmtNib ? tc_kernel<kFmtNib> : tc_kernel<kFmtByte>;
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int64_t total = (int64_t)p.batch * p.tiles_m * p.tiles_n;
   if (total > 0x7fffffffLL || p.a_brows * p.batch > 0x7fffffffLL || p.b_brows * p.batch > 0x7fffffffLL)
     return cudaErrorInvalidValue;
   const int grid = total < num_sms ? (int)total : num_sms;
   if (grid <= 0) return cudaSuccess;
-  tc_f8_kernel<<<grid, THREADS, smem, s>>>(ma, mb, p);
+  kernel<<<grid, THREADS, smem, s>>>(ma, mb, p);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

@@ -98,7 +98,7 @@ cudaError_t launch_popc_parity(const PopcParams& p, cudaStream_t s, int64_t* lau
 
 // ---------------------------------------------------------------- tcgen05 form
 constexpr int kTcBM = 128;
-int tc_group(int e);  // elements per tile column: tile N = e * G <= 256
+int tc_group(int e, int fmt);  // elements per tile column: tile N = e * G
 
 struct TcParams {
   int64_t m, n;
@@ -123,6 +123,11 @@ struct TcParams {
 // fmt: kFmtByte (E4M3) or kFmtNib (E2M1, block scaled).
 cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
                       int64_t ld_bytes, const TcParams& p, int num_sms, cudaStream_t s, int64_t* launches);
+
+// ---------------------------------------------------------------- INT8 mma.sync form
+int mma_group(int e);  // elements per block column: block N = e * G <= 160
+cudaError_t launch_mma_s8(const void* Aplanes, const void* Bplanes, int64_t ld_bytes, const TcParams& p,
+                          cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------- helpers
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }

@@ -13,14 +13,19 @@ namespace {
 
 __device__ __forceinline__ uint32_t par(uint32_t x) { return __popc(x) & 1u; }
 
-__device__ __forceinline__ int64_t plane_index(const PackParams& p, int q, int64_t r, int64_t t) {
-  const int per_b = p.nb * p.kb;
-  const int b = q / per_b;
-  const int i = (q / p.kb) % p.nb;
-  const int j = q % p.kb;
+// Plane addressing: entry (q, r, t) is at qoff[q] + row_offset(r) + t with
+// qoff[q] = b*bstride + i*G*ld + j*Kp  (q = (b*nb + i)*kb + j) and
+// row_offset(r) = ((r / G) * nb * G + r % G) * ld.  qoff is computed once per
+// block into shared memory so the per-entry work has no divisions.
+__device__ __forceinline__ void fill_qoff(const PackParams& p, int64_t* qoff) {
+  for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
+    const int b = q / (p.nb * p.kb), i = (q / p.kb) % p.nb, j = q % p.kb;
+    qoff[q] = (int64_t)b * p.bstride + (int64_t)i * p.G * p.ld + (int64_t)j * p.Kp;
+  }
+}
+__device__ __forceinline__ int64_t row_offset(const PackParams& p, int64_t r) {
   const int64_t G = p.G;
-  const int64_t orow = (r / G) * p.nb * G + (int64_t)i * G + (r % G);
-  return (int64_t)b * p.bstride + orow * p.ld + (int64_t)j * p.Kp + t;
+  return ((r / G) * p.nb * G + r % G) * p.ld;
 }
 
 template <typename T>
@@ -116,6 +121,9 @@ __device__ __forceinline__ void store_nibs16(uint8_t* dst, uint32_t bits, uint32
 // ---- A side, byte / nibble planes: one thread per (row, 16 consecutive t).
 template <typename T, bool NIB>
 __global__ void __launch_bounds__(256) pack_rows_bytes(const __grid_constant__ PackParams p) {
+  __shared__ int64_t qoff[kMaxMasks];
+  fill_qoff(p, qoff);
+  __syncthreads();
   const int64_t nch = p.Kp / 16;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = idx < p.rows_p * nch;
@@ -128,9 +136,10 @@ __global__ void __launch_bounds__(256) pack_rows_bytes(const __grid_constant__ P
   uint32_t S[10];
   slices16<T>(v, p.e, S);
   uint8_t* out = static_cast<uint8_t*>(p.out);
+  const int64_t base = row_offset(p, r) + t0;
   for (int q = 0; q < p.P; ++q) {
     const uint32_t bits = combine(S, p.e, p.mask[q]);
-    const int64_t o = plane_index(p, q, r, t0);
+    const int64_t o = qoff[q] + base;
     if (NIB) store_nibs16(out + o / 2, bits, p.one);
     else store_bytes16(out + o, bits, p.one);
   }
@@ -140,6 +149,9 @@ __global__ void __launch_bounds__(256) pack_rows_bytes(const __grid_constant__ P
 // holds t = 16 l .. 16 l + 15; lane pairs form 32-bit words.
 template <typename T>
 __global__ void __launch_bounds__(256) pack_rows_bits(const __grid_constant__ PackParams p) {
+  __shared__ int64_t qoff[kMaxMasks];
+  fill_qoff(p, qoff);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t nch = (p.Kp + 511) / 512;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -156,9 +168,10 @@ __global__ void __launch_bounds__(256) pack_rows_bits(const __grid_constant__ Pa
   for (int l = 0; l < 10; ++l) S[l] |= __shfl_down_sync(0xffffffffu, S[l], 1) << 16;
   const bool store = (lane & 1) == 0 && tb + 16 * lane < p.Kp;
   uint32_t* out = static_cast<uint32_t*>(p.out);
+  const int64_t base = row_offset(p, r) + tb;
   for (int q = 0; q < p.P; ++q) {
     const uint32_t w = combine(S, p.e, p.mask[q]);
-    if (store) out[plane_index(p, q, r, tb) / 32 + (lane >> 1)] = w;
+    if (store) out[(qoff[q] + base) / 32 + (lane >> 1)] = w;
   }
 }
 
@@ -199,7 +212,9 @@ __device__ __forceinline__ void stage_tile(const PackParams& p, int64_t t0, int6
 template <typename T>
 __global__ void __launch_bounds__(256) pack_cols_bits(const __grid_constant__ PackParams p) {
   __shared__ uint32_t tile[128][65];
+  __shared__ int64_t qoff[kMaxMasks];
   const int64_t c0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 128;
+  fill_qoff(p, qoff);
   stage_tile<T, 128>(p, t0, c0, tile);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -215,6 +230,7 @@ __global__ void __launch_bounds__(256) pack_cols_bits(const __grid_constant__ Pa
 #pragma unroll
       for (int l = 0; l < 10; ++l) S[s][l] = l < p.e ? __ballot_sync(0xffffffffu, (x >> l) & 1u) : 0u;
     }
+    const int64_t base = row_offset(p, c) + t0;
     for (int q = lane; q < p.P; q += 32) {
       const uint32_t mk = p.mask[q];
       uint4 o;
@@ -222,7 +238,7 @@ __global__ void __launch_bounds__(256) pack_cols_bits(const __grid_constant__ Pa
       o.y = combine(S[1], p.e, mk);
       o.z = combine(S[2], p.e, mk);
       o.w = combine(S[3], p.e, mk);
-      *reinterpret_cast<uint4*>(out + plane_index(p, q, c, t0) / 32) = o;
+      *reinterpret_cast<uint4*>(out + (qoff[q] + base) / 32) = o;
     }
   }
 }
@@ -233,7 +249,9 @@ __global__ void __launch_bounds__(256) pack_cols_bits(const __grid_constant__ Pa
 template <typename T, bool NIB>
 __global__ void __launch_bounds__(256) pack_cols_bytes(const __grid_constant__ PackParams p) {
   __shared__ uint32_t tile[32][65];
+  __shared__ int64_t qoff[kMaxMasks];
   const int64_t c0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 32;
+  fill_qoff(p, qoff);
   stage_tile<T, 32>(p, t0, c0, tile);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -246,10 +264,11 @@ __global__ void __launch_bounds__(256) pack_cols_bytes(const __grid_constant__ P
     uint32_t S[10];
 #pragma unroll
     for (int l = 0; l < 10; ++l) S[l] = l < p.e ? __ballot_sync(0xffffffffu, (x >> l) & 1u) : 0u;
+    const int64_t base = row_offset(p, c) + t0;
     for (int it = lane; it < 2 * p.P; it += 32) {
       const int q = it >> 1, h = it & 1;
       const uint32_t bits = (combine(S, p.e, p.mask[q]) >> (16 * h)) & 0xFFFFu;
-      const int64_t o = plane_index(p, q, c, t0 + 16 * h);
+      const int64_t o = qoff[q] + base + 16 * h;
       if (NIB) store_nibs16(out + o / 2, bits, p.one);
       else store_bytes16(out + o, bits, p.one);
     }

@@ -21,8 +21,10 @@ if not torch.cuda.is_available():
 
 import paper_1111_6900_gb300 as m4  # noqa: E402
 
-FORMS = ["popc", "tc_f8"]
-SCHEDS = ["alpha_b", "karatsuba"]
+FORMS = ["popc", "tc_f8", "tc_f4", "mma_s8"]
+# (form, schedule) pairs the library implements; the INT8 mma.sync form runs
+# the alpha^j-B schedule only
+FORM_SCHEDS = [(f, s) for f in FORMS for s in ("alpha_b", "karatsuba") if not (f == "mma_s8" and s == "karatsuba")]
 
 
 @pytest.fixture(scope="module")
@@ -83,8 +85,7 @@ def test_pack_unpack_random(ctx, e, shape):
 
 
 @pytest.mark.parametrize("e", sorted(workloads.FIELD_POLY))
-@pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("form,sched", FORM_SCHEDS)
 def test_mul_ragged_every_field(ctx, e, form, sched):
     """Several tiles in every direction plus a ragged tail."""
     f = workloads.FIELD_POLY[e]
@@ -95,16 +96,14 @@ def test_mul_ragged_every_field(ctx, e, form, sched):
 
 
 @pytest.mark.parametrize("e", [2, 5, 8, 10])
-@pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("form,sched", FORM_SCHEDS)
 def test_addmul(ctx, e, form, sched):
     f = workloads.FIELD_POLY[e]
     A, B, C0 = workloads.random_problem(e, 150, 97, 333, seed=77 + e, with_c=True)
     np.testing.assert_array_equal(run(ctx, form, sched, e, A, B, C0), oracle.addmul(e, f, A, B, C0))
 
 
-@pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("form,sched", FORM_SCHEDS)
 def test_degenerate_shapes(ctx, form, sched):
     e, f = 4, workloads.FIELD_POLY[4]
     for (m, n, k) in [(1, 1, 1), (1, 300, 1), (300, 1, 1), (1, 1, 5000), (2, 3, 4096)]:
@@ -138,6 +137,16 @@ def test_out_of_range_entries_flagged_and_masked(ctx, form):
     assert ctx.device_status() == m4.ERR_RANGE
     assert ctx.device_status() == m4.OK   # status is cleared once read
     np.testing.assert_array_equal(host(C), oracle.matmul(e, f, A, B))
+
+
+def test_int8_form_has_no_karatsuba_schedule(ctx):
+    e, f = 4, workloads.FIELD_POLY[4]
+    ctx.set_form("mma_s8")
+    ctx.set_schedule("karatsuba")
+    A = dev(np.ones((8, 8), np.uint8))
+    with pytest.raises(m4.M4rieError) as ei:
+        ctx.mul(e, f, A, A)
+    assert ei.value.status == m4.ERR_UNSUPPORTED
 
 
 def test_invalid_arguments_launch_nothing(ctx):
@@ -206,14 +215,12 @@ def test_workload1_full(ctx):
     w = workloads.WORKLOADS[1]
     A, B, _ = w.inputs()
     ref = oracle.matmul(w.e, w.f, A, B)
-    for form in FORMS:
-        for sched in SCHEDS:
-            np.testing.assert_array_equal(run(ctx, form, sched, w.e, A, B), ref, err_msg=f"{form} {sched}")
+    for form, sched in FORM_SCHEDS:
+        np.testing.assert_array_equal(run(ctx, form, sched, w.e, A, B), ref, err_msg=f"{form} {sched}")
 
 
 @pytest.mark.parametrize("idx", [2, 3, 5])
-@pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("form,sched", FORM_SCHEDS)
 def test_full_size_workloads(ctx, idx, form, sched):
     w = workloads.WORKLOADS[idx]
     rows = slice(w.m // 2 - 8, w.m // 2 + 8)
