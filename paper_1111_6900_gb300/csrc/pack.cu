@@ -6,6 +6,8 @@
 // the mask whose bit l is coefficient i of x^(j+l) mod f.  So one kernel per
 // layout serves every schedule.  All kernels are HBM-bound; loads are
 // coalesced along rows and bits are gathered with warp ballots.
+#include <algorithm>
+
 #include "m4rie_internal.cuh"
 
 namespace m4rie {
@@ -24,8 +26,32 @@ __device__ __forceinline__ void fill_qoff(const PackParams& p, int64_t* qoff) {
   }
 }
 __device__ __forceinline__ int64_t row_offset(const PackParams& p, int64_t r) {
-  const int64_t G = p.G;
-  return ((r / G) * p.nb * G + r % G) * p.ld;
+  // r < 2^31 and G < 2^16 (validated on the host): 32-bit division
+  const uint32_t rr = (uint32_t)r, G = (uint32_t)p.G;
+  const uint32_t g = rr / G;
+  return ((int64_t)g * p.nb * G + (rr - g * G)) * p.ld;
+}
+
+// Warp-wide lookup of XOR combinations of the slice words: after
+// build_xor_table, lane l holds lo = XOR of S[b] over the bits b < 5 of l and
+// hi = XOR of S[5 + b] over the bits b of l; the combination for any mask is
+// then two shuffles and one XOR.
+struct XorTable {
+  uint32_t lo, hi;
+};
+__device__ __forceinline__ XorTable build_xor_table(const uint32_t (&S)[10], int e, int lane) {
+  XorTable t{0, 0};
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if (b < e && (lane >> b & 1)) t.lo ^= S[b];
+    if (b + 5 < e && (lane >> b & 1)) t.hi ^= S[b + 5];
+  }
+  return t;
+}
+__device__ __forceinline__ uint32_t xor_lookup(const XorTable& t, uint32_t mask, int e) {
+  uint32_t w = __shfl_sync(0xffffffffu, t.lo, mask & 31u);
+  if (e > 5) w ^= __shfl_sync(0xffffffffu, t.hi, (mask >> 5) & 31u);
+  return w;
 }
 
 template <typename T>
@@ -119,59 +145,60 @@ __device__ __forceinline__ void store_nibs16(uint8_t* dst, uint32_t bits, uint32
 }
 
 // ---- A side, byte / nibble planes: one thread per (row, 16 consecutive t).
+// grid.x covers the 16-element chunks of a row, grid.y strides over rows.
 template <typename T, bool NIB>
 __global__ void __launch_bounds__(256) pack_rows_bytes(const __grid_constant__ PackParams p) {
   __shared__ int64_t qoff[kMaxMasks];
   fill_qoff(p, qoff);
   __syncthreads();
-  const int64_t nch = p.Kp / 16;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = idx < p.rows_p * nch;
-  const int64_t r = live ? idx / nch : 0;
-  const int64_t t0 = live ? (idx % nch) * 16 : 0;
-  uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (live && r < p.rows) load16<T>(p, r, t0, v);
-  flag_range(p.status, clamp16<T>(v, p.emask));
-  if (!live) return;
-  uint32_t S[10];
-  slices16<T>(v, p.e, S);
+  const int64_t t0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
+  const bool live_t = t0 < p.Kp;
   uint8_t* out = static_cast<uint8_t*>(p.out);
-  const int64_t base = row_offset(p, r) + t0;
-  for (int q = 0; q < p.P; ++q) {
-    const uint32_t bits = combine(S, p.e, p.mask[q]);
-    const int64_t o = qoff[q] + base;
-    if (NIB) store_nibs16(out + o / 2, bits, p.one);
-    else store_bytes16(out + o, bits, p.one);
+  for (int64_t r = blockIdx.y; r < p.rows_p; r += gridDim.y) {
+    uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (live_t && r < p.rows) load16<T>(p, r, t0, v);
+    flag_range(p.status, clamp16<T>(v, p.emask));
+    if (!live_t) continue;
+    uint32_t S[10];
+    slices16<T>(v, p.e, S);
+    const int64_t base = row_offset(p, r) + t0;
+    for (int q = 0; q < p.P; ++q) {
+      const uint32_t bits = combine(S, p.e, p.mask[q]);
+      const int64_t o = qoff[q] + base;
+      if (NIB) store_nibs16(out + o / 2, bits, p.one);
+      else store_bytes16(out + o, bits, p.one);
+    }
   }
 }
 
 // ---- A side, bit planes: one warp per (row, 512 consecutive t).  Lane l
 // holds t = 16 l .. 16 l + 15; lane pairs form 32-bit words.
+// grid.x * 8 warps cover the 512-element chunks of a row, grid.y strides over rows.
 template <typename T>
 __global__ void __launch_bounds__(256) pack_rows_bits(const __grid_constant__ PackParams p) {
   __shared__ int64_t qoff[kMaxMasks];
   fill_qoff(p, qoff);
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t nch = (p.Kp + 511) / 512;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const bool live = wid < p.rows_p * nch;  // warp-uniform
-  const int64_t r = live ? wid / nch : 0;
-  const int64_t tb = live ? (wid % nch) * 512 : 0;
-  uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (live && r < p.rows) load16<T>(p, r, tb + 16 * lane, v);
-  flag_range(p.status, clamp16<T>(v, p.emask));
-  if (!live) return;
-  uint32_t S[10];
-  slices16<T>(v, p.e, S);
-#pragma unroll
-  for (int l = 0; l < 10; ++l) S[l] |= __shfl_down_sync(0xffffffffu, S[l], 1) << 16;
-  const bool store = (lane & 1) == 0 && tb + 16 * lane < p.Kp;
+  const int64_t tb = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 512;
+  const bool live_t = tb < p.Kp;  // warp-uniform
   uint32_t* out = static_cast<uint32_t*>(p.out);
-  const int64_t base = row_offset(p, r) + tb;
-  for (int q = 0; q < p.P; ++q) {
-    const uint32_t w = combine(S, p.e, p.mask[q]);
-    if (store) out[(qoff[q] + base) / 32 + (lane >> 1)] = w;
+  for (int64_t r = blockIdx.y; r < p.rows_p; r += gridDim.y) {
+    uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (live_t && r < p.rows) load16<T>(p, r, tb + 16 * lane, v);
+    flag_range(p.status, clamp16<T>(v, p.emask));
+    if (!live_t) continue;
+    uint32_t S[10];
+    slices16<T>(v, p.e, S);
+#pragma unroll
+    for (int l = 0; l < 10; ++l) S[l] |= __shfl_down_sync(0xffffffffu, S[l], 1) << 16;
+    // lanes 2w now hold word w of every slice; share the XOR table of those words
+    const bool store = (lane & 1) == 0 && tb + 16 * lane < p.Kp;
+    const int64_t base = (row_offset(p, r) + tb) / 32 + (lane >> 1);
+    for (int q = 0; q < p.P; ++q) {
+      const uint32_t w = combine(S, p.e, p.mask[q]);
+      if (store) out[qoff[q] / 32 + base] = w;
+    }
   }
 }
 
@@ -223,22 +250,25 @@ __global__ void __launch_bounds__(256) pack_cols_bits(const __grid_constant__ Pa
     const int cl = w * 8 + cc;
     const int64_t c = c0 + cl;
     if (c >= p.rows_p) break;  // warp-uniform
-    uint32_t S[4][10];
+    XorTable tab[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       const uint32_t x = tile[32 * s + lane][cl];
+      uint32_t S[10];
 #pragma unroll
-      for (int l = 0; l < 10; ++l) S[s][l] = l < p.e ? __ballot_sync(0xffffffffu, (x >> l) & 1u) : 0u;
+      for (int l = 0; l < 10; ++l) S[l] = l < p.e ? __ballot_sync(0xffffffffu, (x >> l) & 1u) : 0u;
+      tab[s] = build_xor_table(S, p.e, lane);
     }
-    const int64_t base = row_offset(p, c) + t0;
-    for (int q = lane; q < p.P; q += 32) {
-      const uint32_t mk = p.mask[q];
+    const int64_t base = (row_offset(p, c) + t0) / 32;
+    for (int q0 = 0; q0 < p.P; q0 += 32) {
+      const int q = q0 + lane;
+      const uint32_t mk = q < p.P ? p.mask[q] : 0u;
       uint4 o;
-      o.x = combine(S[0], p.e, mk);
-      o.y = combine(S[1], p.e, mk);
-      o.z = combine(S[2], p.e, mk);
-      o.w = combine(S[3], p.e, mk);
-      *reinterpret_cast<uint4*>(out + (qoff[q] + base) / 32) = o;
+      o.x = xor_lookup(tab[0], mk, p.e);
+      o.y = xor_lookup(tab[1], mk, p.e);
+      o.z = xor_lookup(tab[2], mk, p.e);
+      o.w = xor_lookup(tab[3], mk, p.e);
+      if (q < p.P) *reinterpret_cast<uint4*>(out + qoff[q] / 32 + base) = o;
     }
   }
 }
@@ -264,13 +294,18 @@ __global__ void __launch_bounds__(256) pack_cols_bytes(const __grid_constant__ P
     uint32_t S[10];
 #pragma unroll
     for (int l = 0; l < 10; ++l) S[l] = l < p.e ? __ballot_sync(0xffffffffu, (x >> l) & 1u) : 0u;
+    const XorTable tab = build_xor_table(S, p.e, lane);
     const int64_t base = row_offset(p, c) + t0;
-    for (int it = lane; it < 2 * p.P; it += 32) {
+    for (int it0 = 0; it0 < 2 * p.P; it0 += 32) {  // warp-uniform trip count (shuffles inside)
+      const int it = it0 + lane;
       const int q = it >> 1, h = it & 1;
-      const uint32_t bits = (combine(S, p.e, p.mask[q]) >> (16 * h)) & 0xFFFFu;
-      const int64_t o = qoff[q] + base + 16 * h;
-      if (NIB) store_nibs16(out + o / 2, bits, p.one);
-      else store_bytes16(out + o, bits, p.one);
+      const uint32_t mk = it < 2 * p.P ? p.mask[q] : 0u;
+      const uint32_t bits = (xor_lookup(tab, mk, p.e) >> (16 * h)) & 0xFFFFu;
+      if (it < 2 * p.P) {
+        const int64_t o = qoff[q] + base + 16 * h;
+        if (NIB) store_nibs16(out + o / 2, bits, p.one);
+        else store_bytes16(out + o, bits, p.one);
+      }
     }
   }
 }
@@ -403,17 +438,23 @@ cudaError_t launch(K kernel, int64_t blocks, int threads, cudaStream_t s, int64_
 cudaError_t launch_pack_planes(const PackParams& p, bool trans, cudaStream_t s, int64_t* launches) {
   const bool u16 = p.elem_bytes == 2;
   if (!trans) {
+    const int64_t gx = p.fmt == kFmtBit ? ceil_div(p.Kp, 512 * 8) : ceil_div(p.Kp / 16, 256);
+    const int64_t gy = std::min<int64_t>(p.rows_p, 65535);
+    if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (gx <= 0 || gy <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)gx, (unsigned)gy);
     if (p.fmt == kFmtBit) {
-      const int64_t warps = p.rows_p * ((p.Kp + 511) / 512);
-      return u16 ? launch(pack_rows_bits<uint16_t>, ceil_div(warps, 8), 256, s, launches, p)
-                 : launch(pack_rows_bits<uint8_t>, ceil_div(warps, 8), 256, s, launches, p);
+      if (u16) pack_rows_bits<uint16_t><<<grid, 256, 0, s>>>(p);
+      else pack_rows_bits<uint8_t><<<grid, 256, 0, s>>>(p);
+    } else if (p.fmt == kFmtByte) {
+      if (u16) pack_rows_bytes<uint16_t, false><<<grid, 256, 0, s>>>(p);
+      else pack_rows_bytes<uint8_t, false><<<grid, 256, 0, s>>>(p);
+    } else {
+      if (u16) pack_rows_bytes<uint16_t, true><<<grid, 256, 0, s>>>(p);
+      else pack_rows_bytes<uint8_t, true><<<grid, 256, 0, s>>>(p);
     }
-    const int64_t threads = p.rows_p * (p.Kp / 16);
-    if (p.fmt == kFmtByte)
-      return u16 ? launch(pack_rows_bytes<uint16_t, false>, ceil_div(threads, 256), 256, s, launches, p)
-                 : launch(pack_rows_bytes<uint8_t, false>, ceil_div(threads, 256), 256, s, launches, p);
-    return u16 ? launch(pack_rows_bytes<uint16_t, true>, ceil_div(threads, 256), 256, s, launches, p)
-               : launch(pack_rows_bytes<uint8_t, true>, ceil_div(threads, 256), 256, s, launches, p);
+    if (launches) ++*launches;
+    return cudaGetLastError();
   }
   const int64_t gx = ceil_div(p.rows_p, 64);
   if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
