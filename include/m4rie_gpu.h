@@ -203,10 +203,11 @@ m4rie_status m4rie_set_wait_limit_ns(m4rie_ctx *ctx, uint64_t ns);
  * No context is needed and the call allocates nothing.  Its operand planes
  * live in one statically allocated device array of 64 MiB that every GPU
  * loading this library holds until the process exits.  Problems whose planes
- * do not fit (roughly: Mp*e*Kp/8 + ceil(n/G)*G*e*e*Kp/8 bytes with Kp =
- * k rounded up to 128, Mp = m rounded up to 128, G = 64, 32 or 16 for
- * e = 2, 3-4, 5-10; a 4096 x 4096 x 4096 product over GF(2^4) fits) are
- * rejected with M4RIE_ERR_SCRATCH before anything is launched.
+ * do not fit (roughly: Mp*e*Kp/8 + ceil(n/G)*G*e*e*Kp/8 + n*k*w bytes with
+ * Kp = k rounded up to 128, Mp = m rounded up to 128, G = 64, 32 or 16 for
+ * e = 2, 3-4, 5-10, w = element bytes; a 4096 x 4096 x 4096 product over
+ * GF(2^4) fits) are rejected with M4RIE_ERR_SCRATCH before anything is
+ * launched.
  *
  * A, B, C: device pointers as for m4rie_mul.  device_status: optional device
  * int that receives the status bits (1: an entry was >= 2^e, 2: a wait timed

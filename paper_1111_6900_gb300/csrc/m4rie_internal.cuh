@@ -44,9 +44,11 @@ struct PackParams {
   uint16_t mask[kMaxMasks];
 };
 
-// Pack launchers (pack.cu).  trans = false: rows of X are the planes' rows
-// (A side).  trans = true: columns of X are the planes' rows (B side).
-cudaError_t launch_pack_planes(const PackParams& p, bool trans, cudaStream_t s, int64_t* launches);
+// Pack launcher (pack.cu): rows of X are the planes' rows.  The B side is
+// first transposed with launch_transpose (K x rows -> rows x K elements).
+cudaError_t launch_pack_planes(const PackParams& p, cudaStream_t s, int64_t* launches);
+cudaError_t launch_transpose(const void* X, int64_t ldx, int64_t K, int64_t rows, int elem_bytes, void* Xt,
+                             cudaStream_t s, int64_t* launches);
 
 // Public slice format (Section 3.2): pack.cu.
 cudaError_t launch_slice(int e, int64_t rows, int64_t cols, const void* elems, uint64_t* slices,

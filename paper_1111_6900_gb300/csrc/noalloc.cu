@@ -70,9 +70,10 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   const int64_t Mp = round_up(m, 128);
   const int64_t groups = ceil_div(n, G);
   const int64_t brows = groups * e * G;
-  const double a_bytes_d = (double)Mp * ld / 8, b_bytes_d = (double)brows * ld / 8;
-  if (a_bytes_d + b_bytes_d + 1024.0 > (double)kStatusSlot) return M4RIE_ERR_SCRATCH;
+  const double a_bytes_d = (double)Mp * ld / 8, b_bytes_d = (double)brows * ld / 8, t_bytes_d = (double)n * k * eb;
+  if (a_bytes_d + b_bytes_d + t_bytes_d + 2048.0 > (double)kStatusSlot) return M4RIE_ERR_SCRATCH;
   const size_t a_bytes = (size_t)round_up(Mp * ld / 8, 1024);
+  const size_t b_bytes = (size_t)round_up(brows * ld / 8, 1024);
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return M4RIE_ERR_CUDA;
@@ -80,6 +81,7 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   if (scratch_address(dev, &base) != cudaSuccess) return M4RIE_ERR_CUDA;
   uint8_t* Ap = static_cast<uint8_t*>(base);
   uint8_t* Bp = Ap + a_bytes;
+  uint8_t* Bt = Bp + b_bytes;  // B transposed (elements)
   int* status = device_status ? device_status : reinterpret_cast<int*>(static_cast<uint8_t*>(base) + kStatusSlot);
 
   uint16_t amask[10], bmask[100];
@@ -105,12 +107,13 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   pa.out = Ap;
   pa.status = status;
   for (int j = 0; j < e; ++j) pa.mask[j] = amask[j];
-  if (launch_pack_planes(pa, false, stream, nullptr) != cudaSuccess) return M4RIE_ERR_CUDA;
+  if (launch_pack_planes(pa, stream, nullptr) != cudaSuccess) return M4RIE_ERR_CUDA;
+  if (launch_transpose(B, n, k, n, eb, Bt, stream, nullptr) != cudaSuccess) return M4RIE_ERR_CUDA;
 
   PackParams pb = pa;
-  pb.X = B;
-  pb.ldx = n;
-  pb.vec = (reinterpret_cast<uintptr_t>(B) & 15u) == 0 && (n * eb) % 16 == 0;
+  pb.X = Bt;
+  pb.ldx = k;
+  pb.vec = (k * eb) % 16 == 0;
   pb.rows = n;
   pb.rows_p = groups * G;
   pb.P = e * e;
@@ -119,7 +122,7 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   pb.G = G;
   pb.out = Bp;
   for (int q = 0; q < e * e; ++q) pb.mask[q] = bmask[q];
-  if (launch_pack_planes(pb, true, stream, nullptr) != cudaSuccess) return M4RIE_ERR_CUDA;
+  if (launch_pack_planes(pb, stream, nullptr) != cudaSuccess) return M4RIE_ERR_CUDA;
 
   PopcParams pp{};
   pp.A = reinterpret_cast<const uint32_t*>(Ap);

@@ -13,300 +13,198 @@
 namespace m4rie {
 namespace {
 
-__device__ __forceinline__ uint32_t par(uint32_t x) { return __popc(x) & 1u; }
-
-// Plane addressing: entry (q, r, t) is at qoff[q] + row_offset(r) + t with
-// qoff[q] = b*bstride + i*G*ld + j*Kp  (q = (b*nb + i)*kb + j) and
-// row_offset(r) = ((r / G) * nb * G + r % G) * ld.  qoff is computed once per
-// block into shared memory so the per-entry work has no divisions.
-__device__ __forceinline__ void fill_qoff(const PackParams& p, int64_t* qoff) {
-  for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
-    const int b = q / (p.nb * p.kb), i = (q / p.kb) % p.nb, j = q % p.kb;
-    qoff[q] = (int64_t)b * p.bstride + (int64_t)i * p.G * p.ld + (int64_t)j * p.Kp;
-  }
-}
-__device__ __forceinline__ int64_t row_offset(const PackParams& p, int64_t r) {
-  // r < 2^31 and G < 2^16 (validated on the host): 32-bit division
-  const uint32_t rr = (uint32_t)r, G = (uint32_t)p.G;
-  const uint32_t g = rr / G;
-  return ((int64_t)g * p.nb * G + (rr - g * G)) * p.ld;
-}
-
-// Warp-wide lookup of XOR combinations of the slice words: after
-// build_xor_table, lane l holds lo = XOR of S[b] over the bits b < 5 of l and
-// hi = XOR of S[5 + b] over the bits b of l; the combination for any mask is
-// then two shuffles and one XOR.
-struct XorTable {
-  uint32_t lo, hi;
-};
-__device__ __forceinline__ XorTable build_xor_table(const uint32_t (&S)[10], int e, int lane) {
-  XorTable t{0, 0};
-#pragma unroll
-  for (int b = 0; b < 5; ++b) {
-    if (b < e && (lane >> b & 1)) t.lo ^= S[b];
-    if (b + 5 < e && (lane >> b & 1)) t.hi ^= S[b + 5];
-  }
-  return t;
-}
-__device__ __forceinline__ uint32_t xor_lookup(const XorTable& t, uint32_t mask, int e) {
-  uint32_t w = __shfl_sync(0xffffffffu, t.lo, mask & 31u);
-  if (e > 5) w ^= __shfl_sync(0xffffffffu, t.hi, (mask >> 5) & 31u);
-  return w;
-}
-
-template <typename T>
-__device__ __forceinline__ uint32_t load_elem(const PackParams& p, int64_t r, int64_t c) {
-  return (uint32_t)static_cast<const T*>(p.X)[r * p.ldx + c];
-}
-
 __device__ __forceinline__ void flag_range(int* status, bool bad) {
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusRange);
 }
 
-// ---- Slice words.  Bit u of slice word l is coefficient l of element u; an
-// operand plane for mask q is the XOR of the slice words selected by q.
+// ---- Operand planes with SWAR parities.  A thread takes 16 (32 for bit
+// planes) consecutive elements of one row as packed 32-bit words (4 bytes or 2
+// halfwords per word) and, for every mask q, computes parity(x & mask_q) of
+// all of them at once: AND with the mask replicated per element, then fold the
+// element's bits onto its lowest bit (x ^= x >> 4, 2, 1 for bytes; 8, 4, 2, 1
+// for halfwords).  The 0/1 results are then laid out as bytes (0 / one),
+// nibbles or bits.  B is transposed first, so both sides read rows.
 
-// 16 consecutive elements of row r starting at t0 (zeros past the row end),
-// as 4 words of bytes (u8) or 8 words of halfwords (u16).
 template <typename T>
-__device__ __forceinline__ void load16(const PackParams& p, int64_t r, int64_t t0, uint32_t (&v)[8]) {
+struct Swar;
+template <>
+struct Swar<uint8_t> {
+  static constexpr int PER = 4;  // elements per word
+  static __device__ __forceinline__ uint32_t rep(uint32_t m) { return m * 0x01010101u; }
+  static __device__ __forceinline__ uint32_t parity(uint32_t y) {
+    y ^= y >> 4;
+    y ^= y >> 2;
+    y ^= y >> 1;
+    return y & 0x01010101u;  // element u's parity at bit 8u
+  }
+  // 4 parities -> 4 bytes (0 or one)
+  static __device__ __forceinline__ uint32_t bytes(uint32_t p, uint32_t one) { return p * one; }
+  // 4 parities -> 4 nibbles (16 bits, 0 or one)
+  static __device__ __forceinline__ uint32_t nibs(uint32_t p, uint32_t one) {
+    return ((p & 1u) | ((p >> 4) & 0x10u) | ((p >> 8) & 0x100u) | ((p >> 12) & 0x1000u)) * one;
+  }
+  // 4 parities -> 4 bits
+  static __device__ __forceinline__ uint32_t bits(uint32_t p) { return (p * 0x01020408u) >> 24; }
+};
+template <>
+struct Swar<uint16_t> {
+  static constexpr int PER = 2;
+  static __device__ __forceinline__ uint32_t rep(uint32_t m) { return m * 0x00010001u; }
+  static __device__ __forceinline__ uint32_t parity(uint32_t y) {
+    y ^= y >> 8;
+    y ^= y >> 4;
+    y ^= y >> 2;
+    y ^= y >> 1;
+    return y & 0x00010001u;  // element u's parity at bit 16u
+  }
+  static __device__ __forceinline__ uint32_t bytes(uint32_t p, uint32_t one) {  // 2 parities -> 2 bytes
+    return ((p & 1u) | ((p >> 8) & 0x100u)) * one;
+  }
+  static __device__ __forceinline__ uint32_t nibs(uint32_t p, uint32_t one) {  // 2 parities -> 8 bits
+    return ((p & 1u) | ((p >> 12) & 0x10u)) * one;
+  }
+  static __device__ __forceinline__ uint32_t bits(uint32_t p) { return (p & 1u) | ((p >> 15) & 2u); }
+};
+
+// NE consecutive elements of row r from t0 (zeros past the row end), packed.
+template <typename T, int NE>
+__device__ __forceinline__ void load_row(const PackParams& p, int64_t r, int64_t t0, uint32_t (&v)[NE * sizeof(T) / 4]) {
+  constexpr int W = NE * (int)sizeof(T) / 4;
   const T* row = static_cast<const T*>(p.X) + r * p.ldx;
-  constexpr int W = sizeof(T) == 1 ? 4 : 8;
-  if (p.vec && t0 + 16 <= p.K) {
+  if (p.vec && t0 + NE <= p.K) {
     const uint4* q = reinterpret_cast<const uint4*>(row + t0);
-    const uint4 a = q[0];
-    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
-    if (W == 8) {
-      const uint4 b = q[1];
-      v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+#pragma unroll
+    for (int k = 0; k < W / 4; ++k) {
+      const uint4 a = q[k];
+      v[4 * k] = a.x, v[4 * k + 1] = a.y, v[4 * k + 2] = a.z, v[4 * k + 3] = a.w;
     }
   } else {
 #pragma unroll
     for (int k = 0; k < W; ++k) v[k] = 0;
 #pragma unroll
-    for (int u = 0; u < 16; ++u)
-      if (t0 + u < p.K) v[u * sizeof(T) / 4] |= (uint32_t)row[t0 + u] << (8 * sizeof(T) * (u % (4 / sizeof(T))));
+    for (int u = 0; u < NE; ++u)
+      if (t0 + u < p.K) v[u / Swar<T>::PER] |= (uint32_t)row[t0 + u] << (8 * sizeof(T) * (u % Swar<T>::PER));
   }
 }
 
-// Range check and masking of packed elements; returns true if any was >= 2^e.
-template <typename T>
-__device__ __forceinline__ bool clamp16(uint32_t (&v)[8], uint32_t emask) {
-  constexpr int W = sizeof(T) == 1 ? 4 : 8;
-  const uint32_t rep = sizeof(T) == 1 ? emask * 0x01010101u : emask * 0x00010001u;
-  bool bad = false;
-#pragma unroll
-  for (int k = 0; k < W; ++k) {
-    bad |= (v[k] & ~rep) != 0;
-    v[k] &= rep;
-  }
-  return bad;
-}
-
-// Slice words of 16 packed elements: S[l] bit u = bit l of element u.
-template <typename T>
-__device__ __forceinline__ void slices16(const uint32_t (&v)[8], int e, uint32_t (&S)[10]) {
-#pragma unroll
-  for (int l = 0; l < 10; ++l) {
-    uint32_t w = 0;
-    if (l < e) {
-      if (sizeof(T) == 1) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) w |= ((((v[k] >> l) & 0x01010101u) * 0x01020408u) >> 24) << (4 * k);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) w |= (((((v[k] >> l) & 0x00010001u) * 0x00008001u) >> 15) & 3u) << (2 * k);
-      }
-    }
-    S[l] = w;
-  }
-}
-
-__device__ __forceinline__ uint32_t combine(const uint32_t (&S)[10], int e, uint32_t mask) {
-  uint32_t w = 0;
-#pragma unroll
-  for (int l = 0; l < 10; ++l)
-    if (l < e && (mask >> l & 1u)) w ^= S[l];
-  return w;
-}
-
-// 16 plane bits -> 16 bytes (0 or `one`) or 16 nibbles.
-__device__ __forceinline__ void store_bytes16(uint8_t* dst, uint32_t bits, uint32_t one) {
-  uint32_t w[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) w[k] = (((bits >> (4 * k)) & 0xFu) * 0x00204081u & 0x01010101u) * one;
-  *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-}
-__device__ __forceinline__ void store_nibs16(uint8_t* dst, uint32_t bits, uint32_t one) {
-  uint32_t w[2] = {0, 0};
-#pragma unroll
-  for (int u = 0; u < 16; ++u) w[u >> 3] |= ((bits >> u) & 1u) * one << (4 * (u & 7));
-  *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
-}
-
-// ---- A side, byte / nibble planes: one thread per (row, 16 consecutive t).
-// grid.x covers the 16-element chunks of a row, grid.y strides over rows.
-template <typename T, bool NIB>
-__global__ void __launch_bounds__(256) pack_rows_bytes(const __grid_constant__ PackParams p) {
+// grid.x covers a row in chunks of 256 threads x NE elements, grid.y strides over rows.
+template <typename T, int FMT>
+__global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant__ PackParams p) {
+  constexpr int NE = FMT == kFmtBit ? 32 : 16;  // elements per thread
+  constexpr int W = NE * (int)sizeof(T) / 4;    // packed input words per thread
   __shared__ int64_t qoff[kMaxMasks];
-  fill_qoff(p, qoff);
+  __shared__ uint32_t mrep[kMaxMasks];
+  for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
+    const int b = q / (p.nb * p.kb), i = (q / p.kb) % p.nb, j = q % p.kb;
+    qoff[q] = (int64_t)b * p.bstride + (int64_t)i * p.G * p.ld + (int64_t)j * p.Kp;
+    mrep[q] = Swar<T>::rep(p.mask[q]);
+  }
   __syncthreads();
-  const int64_t t0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
+  const int64_t t0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * NE;
   const bool live_t = t0 < p.Kp;
-  uint8_t* out = static_cast<uint8_t*>(p.out);
+  const uint32_t erep = Swar<T>::rep(p.emask);
   for (int64_t r = blockIdx.y; r < p.rows_p; r += gridDim.y) {
-    uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (live_t && r < p.rows) load16<T>(p, r, t0, v);
-    flag_range(p.status, clamp16<T>(v, p.emask));
+    uint32_t v[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) v[k] = 0;
+    if (live_t && r < p.rows) load_row<T, NE>(p, r, t0, v);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      bad |= (v[k] & ~erep) != 0;
+      v[k] &= erep;
+    }
+    flag_range(p.status, bad);
     if (!live_t) continue;
-    uint32_t S[10];
-    slices16<T>(v, p.e, S);
-    const int64_t base = row_offset(p, r) + t0;
+    // row offset of input row r in the plane layout (32-bit division: r < 2^31, G < 2^16)
+    const uint32_t rr = (uint32_t)r, G = (uint32_t)p.G, g = rr / G;
+    const int64_t base = ((int64_t)g * p.nb * G + (rr - g * G)) * p.ld + t0;
     for (int q = 0; q < p.P; ++q) {
-      const uint32_t bits = combine(S, p.e, p.mask[q]);
+      const uint32_t m = mrep[q];
       const int64_t o = qoff[q] + base;
-      if (NIB) store_nibs16(out + o / 2, bits, p.one);
-      else store_bytes16(out + o, bits, p.one);
-    }
-  }
-}
-
-// ---- A side, bit planes: one warp per (row, 512 consecutive t).  Lane l
-// holds t = 16 l .. 16 l + 15; lane pairs form 32-bit words.
-// grid.x * 8 warps cover the 512-element chunks of a row, grid.y strides over rows.
-template <typename T>
-__global__ void __launch_bounds__(256) pack_rows_bits(const __grid_constant__ PackParams p) {
-  __shared__ int64_t qoff[kMaxMasks];
-  fill_qoff(p, qoff);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t tb = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 512;
-  const bool live_t = tb < p.Kp;  // warp-uniform
-  uint32_t* out = static_cast<uint32_t*>(p.out);
-  for (int64_t r = blockIdx.y; r < p.rows_p; r += gridDim.y) {
-    uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (live_t && r < p.rows) load16<T>(p, r, tb + 16 * lane, v);
-    flag_range(p.status, clamp16<T>(v, p.emask));
-    if (!live_t) continue;
-    uint32_t S[10];
-    slices16<T>(v, p.e, S);
+      if (FMT == kFmtBit) {
+        uint32_t word = 0;
 #pragma unroll
-    for (int l = 0; l < 10; ++l) S[l] |= __shfl_down_sync(0xffffffffu, S[l], 1) << 16;
-    // lanes 2w now hold word w of every slice; share the XOR table of those words
-    const bool store = (lane & 1) == 0 && tb + 16 * lane < p.Kp;
-    const int64_t base = (row_offset(p, r) + tb) / 32 + (lane >> 1);
-    for (int q = 0; q < p.P; ++q) {
-      const uint32_t w = combine(S, p.e, p.mask[q]);
-      if (store) out[qoff[q] / 32 + base] = w;
-    }
-  }
-}
-
-// Stage a tile of TT rows (t) x 64 columns of X into shared memory, one
-// 32-bit word per element; masks the elements and reports out-of-range ones.
-template <typename T, int TT>
-__device__ __forceinline__ void stage_tile(const PackParams& p, int64_t t0, int64_t c0, uint32_t (*tile)[65]) {
-  bool bad = false;
-  const T* X = static_cast<const T*>(p.X);
-  constexpr int CH = 64 * sizeof(T) / 16;  // 16-byte chunks per tile row
-  if (p.vec && c0 + 64 <= p.rows && t0 + TT <= p.K) {
-    for (int idx = threadIdx.x; idx < TT * CH; idx += blockDim.x) {
-      const int tt = idx / CH, ch = idx % CH;
-      const uint4 a = *reinterpret_cast<const uint4*>(X + (t0 + tt) * p.ldx + c0 + ch * (16 / sizeof(T)));
-      const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+        for (int k = 0; k < W; ++k) word |= Swar<T>::bits(Swar<T>::parity(v[k] & m)) << (Swar<T>::PER * k);
+        static_cast<uint32_t*>(p.out)[o / 32] = word;
+      } else if (FMT == kFmtByte) {
+        uint32_t w[4];
+        if (sizeof(T) == 1) {
 #pragma unroll
-      for (int k = 0; k < 16 / (int)sizeof(T); ++k) {
-        const uint32_t x = sizeof(T) == 1 ? (w[k >> 2] >> (8 * (k & 3))) & 0xFFu : (w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
-        bad |= x > p.emask;
-        tile[tt][ch * (16 / sizeof(T)) + k] = x & p.emask;
+          for (int k = 0; k < 4; ++k) w[k] = Swar<T>::bytes(Swar<T>::parity(v[k] & m), p.one);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            w[k] = Swar<T>::bytes(Swar<T>::parity(v[2 * k] & m), p.one) |
+                   (Swar<T>::bytes(Swar<T>::parity(v[2 * k + 1] & m), p.one) << 16);
+        }
+        *reinterpret_cast<uint4*>(static_cast<uint8_t*>(p.out) + o) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        uint32_t w[2] = {0, 0};
+        if (sizeof(T) == 1) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) w[k >> 1] |= Swar<T>::nibs(Swar<T>::parity(v[k] & m), p.one) << (16 * (k & 1));
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) w[k >> 2] |= Swar<T>::nibs(Swar<T>::parity(v[k] & m), p.one) << (8 * (k & 3));
+        }
+        *reinterpret_cast<uint2*>(static_cast<uint8_t*>(p.out) + o / 2) = make_uint2(w[0], w[1]);
       }
     }
-  } else {
-    for (int idx = threadIdx.x; idx < TT * 64; idx += blockDim.x) {
-      const int tt = idx >> 6, cc = idx & 63;
-      const int64_t t = t0 + tt, c = c0 + cc;
-      const uint32_t x = (t < p.K && c < p.rows) ? (uint32_t)X[t * p.ldx + c] : 0u;
-      bad |= x > p.emask;
-      tile[tt][cc] = x & p.emask;
-    }
   }
-  flag_range(p.status, bad);
 }
 
-// ---- B side (columns of X become plane rows), bit planes.  Tile of 128 t x
-// 64 columns; each warp owns 8 columns; lane l reads t = 32 s + l; e ballots
-// per 32 elements give the slice words, lane q forms plane q by XORs.
+// ---- Element transpose X (K x rows, row-major) -> Xt (rows x K), tiles of
+// 64 x 64 elements through shared memory (one 32-bit word per element).
 template <typename T>
-__global__ void __launch_bounds__(256) pack_cols_bits(const __grid_constant__ PackParams p) {
-  __shared__ uint32_t tile[128][65];
-  __shared__ int64_t qoff[kMaxMasks];
-  const int64_t c0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 128;
-  fill_qoff(p, qoff);
-  stage_tile<T, 128>(p, t0, c0, tile);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t* out = static_cast<uint32_t*>(p.out);
-  for (int cc = 0; cc < 8; ++cc) {
-    const int cl = w * 8 + cc;
-    const int64_t c = c0 + cl;
-    if (c >= p.rows_p) break;  // warp-uniform
-    XorTable tab[4];
+__global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ X, int64_t ldx, int64_t K, int64_t rows,
+                                                        T* __restrict__ Xt, int vec) {
+  __shared__ uint32_t tile[64][65];
+  const int64_t c0 = (int64_t)blockIdx.x * 64;
+  for (int64_t t0 = (int64_t)blockIdx.y * 64; t0 < K; t0 += (int64_t)gridDim.y * 64) {
+    constexpr int CH = 64 * sizeof(T) / 16;  // 16-byte chunks per tile row
+    if (vec && c0 + 64 <= rows && t0 + 64 <= K) {
+      for (int idx = threadIdx.x; idx < 64 * CH; idx += 256) {
+        const int tt = idx / CH, ch = idx % CH;
+        const uint4 a = *reinterpret_cast<const uint4*>(X + (t0 + tt) * ldx + c0 + ch * (16 / sizeof(T)));
+        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const uint32_t x = tile[32 * s + lane][cl];
-      uint32_t S[10];
-#pragma unroll
-      for (int l = 0; l < 10; ++l) S[l] = l < p.e ? __ballot_sync(0xffffffffu, (x >> l) & 1u) : 0u;
-      tab[s] = build_xor_table(S, p.e, lane);
-    }
-    const int64_t base = (row_offset(p, c) + t0) / 32;
-    for (int q0 = 0; q0 < p.P; q0 += 32) {
-      const int q = q0 + lane;
-      const uint32_t mk = q < p.P ? p.mask[q] : 0u;
-      uint4 o;
-      o.x = xor_lookup(tab[0], mk, p.e);
-      o.y = xor_lookup(tab[1], mk, p.e);
-      o.z = xor_lookup(tab[2], mk, p.e);
-      o.w = xor_lookup(tab[3], mk, p.e);
-      if (q < p.P) *reinterpret_cast<uint4*>(out + qoff[q] / 32 + base) = o;
-    }
-  }
-}
-
-// ---- B side, byte / nibble planes.  Tile of 32 t x 64 columns; each warp
-// owns 8 columns with lane = t; e ballots give the slice words; the 2P
-// (plane, 16-t half) outputs of a column are spread over the lanes.
-template <typename T, bool NIB>
-__global__ void __launch_bounds__(256) pack_cols_bytes(const __grid_constant__ PackParams p) {
-  __shared__ uint32_t tile[32][65];
-  __shared__ int64_t qoff[kMaxMasks];
-  const int64_t c0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 32;
-  fill_qoff(p, qoff);
-  stage_tile<T, 32>(p, t0, c0, tile);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint8_t* out = static_cast<uint8_t*>(p.out);
-  for (int cc = 0; cc < 8; ++cc) {
-    const int cl = w * 8 + cc;
-    const int64_t c = c0 + cl;
-    if (c >= p.rows_p) break;  // warp-uniform
-    const uint32_t x = tile[lane][cl];
-    uint32_t S[10];
-#pragma unroll
-    for (int l = 0; l < 10; ++l) S[l] = l < p.e ? __ballot_sync(0xffffffffu, (x >> l) & 1u) : 0u;
-    const XorTable tab = build_xor_table(S, p.e, lane);
-    const int64_t base = row_offset(p, c) + t0;
-    for (int it0 = 0; it0 < 2 * p.P; it0 += 32) {  // warp-uniform trip count (shuffles inside)
-      const int it = it0 + lane;
-      const int q = it >> 1, h = it & 1;
-      const uint32_t mk = it < 2 * p.P ? p.mask[q] : 0u;
-      const uint32_t bits = (xor_lookup(tab, mk, p.e) >> (16 * h)) & 0xFFFFu;
-      if (it < 2 * p.P) {
-        const int64_t o = qoff[q] + base + 16 * h;
-        if (NIB) store_nibs16(out + o / 2, bits, p.one);
-        else store_bytes16(out + o, bits, p.one);
+        for (int k = 0; k < 16 / (int)sizeof(T); ++k)
+          tile[tt][ch * (16 / sizeof(T)) + k] =
+              sizeof(T) == 1 ? (w[k >> 2] >> (8 * (k & 3))) & 0xFFu : (w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
+        const int tt = idx >> 6, cc = idx & 63;
+        const int64_t t = t0 + tt, c = c0 + cc;
+        tile[tt][cc] = (t < K && c < rows) ? (uint32_t)X[t * ldx + c] : 0u;
       }
     }
+    __syncthreads();
+    // thread -> (column cl, 16 consecutive t)
+    const int cl = threadIdx.x >> 2, tq = (threadIdx.x & 3) * 16;
+    const int64_t c = c0 + cl;
+    if (c < rows) {
+      T* dst = Xt + c * K + t0 + tq;
+      if (vec && t0 + tq + 16 <= K) {
+        uint32_t w[16 * sizeof(T) / 4];
+#pragma unroll
+        for (int k = 0; k < 16 * (int)sizeof(T) / 4; ++k) {
+          if (sizeof(T) == 1)
+            w[k] = tile[tq + 4 * k][cl] | (tile[tq + 4 * k + 1][cl] << 8) | (tile[tq + 4 * k + 2][cl] << 16) |
+                   (tile[tq + 4 * k + 3][cl] << 24);
+          else
+            w[k] = tile[tq + 2 * k][cl] | (tile[tq + 2 * k + 1][cl] << 16);
+        }
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+        for (int k = 0; k < (int)sizeof(T); ++k) d4[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+      } else {
+        for (int u = 0; u < 16; ++u)
+          if (t0 + tq + u < K) dst[u] = (T)tile[tq + u][cl];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -435,47 +333,42 @@ cudaError_t launch(K kernel, int64_t blocks, int threads, cudaStream_t s, int64_
 
 }  // namespace
 
-cudaError_t launch_pack_planes(const PackParams& p, bool trans, cudaStream_t s, int64_t* launches) {
-  const bool u16 = p.elem_bytes == 2;
-  if (!trans) {
-    const int64_t gx = p.fmt == kFmtBit ? ceil_div(p.Kp, 512 * 8) : ceil_div(p.Kp / 16, 256);
-    const int64_t gy = std::min<int64_t>(p.rows_p, 65535);
-    if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (gx <= 0 || gy <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)gx, (unsigned)gy);
-    if (p.fmt == kFmtBit) {
-      if (u16) pack_rows_bits<uint16_t><<<grid, 256, 0, s>>>(p);
-      else pack_rows_bits<uint8_t><<<grid, 256, 0, s>>>(p);
-    } else if (p.fmt == kFmtByte) {
-      if (u16) pack_rows_bytes<uint16_t, false><<<grid, 256, 0, s>>>(p);
-      else pack_rows_bytes<uint8_t, false><<<grid, 256, 0, s>>>(p);
-    } else {
-      if (u16) pack_rows_bytes<uint16_t, true><<<grid, 256, 0, s>>>(p);
-      else pack_rows_bytes<uint8_t, true><<<grid, 256, 0, s>>>(p);
-    }
-    if (launches) ++*launches;
-    return cudaGetLastError();
-  }
-  const int64_t gx = ceil_div(p.rows_p, 64);
+cudaError_t launch_pack_planes(const PackParams& p, cudaStream_t s, int64_t* launches) {
+  const int ne = p.fmt == kFmtBit ? 32 : 16;
+  const int64_t gx = ceil_div(ceil_div(p.Kp, ne), 256);
+  const int64_t gy = std::min<int64_t>(p.rows_p, 65535);
   if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (gx <= 0 || gy <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)gx, (unsigned)gy);
+  const bool u16 = p.elem_bytes == 2;
   if (p.fmt == kFmtBit) {
-    const int64_t gy = p.Kp / 128;
-    if (gy > 65535) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)gx, (unsigned)gy);
-    if (u16) pack_cols_bits<uint16_t><<<grid, 256, 0, s>>>(p);
-    else pack_cols_bits<uint8_t><<<grid, 256, 0, s>>>(p);
+    if (u16) pack_planes_kernel<uint16_t, kFmtBit><<<grid, 256, 0, s>>>(p);
+    else pack_planes_kernel<uint8_t, kFmtBit><<<grid, 256, 0, s>>>(p);
+  } else if (p.fmt == kFmtByte) {
+    if (u16) pack_planes_kernel<uint16_t, kFmtByte><<<grid, 256, 0, s>>>(p);
+    else pack_planes_kernel<uint8_t, kFmtByte><<<grid, 256, 0, s>>>(p);
   } else {
-    const int64_t gy = p.Kp / 32;
-    if (gy > 65535) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)gx, (unsigned)gy);
-    if (p.fmt == kFmtByte) {
-      if (u16) pack_cols_bytes<uint16_t, false><<<grid, 256, 0, s>>>(p);
-      else pack_cols_bytes<uint8_t, false><<<grid, 256, 0, s>>>(p);
-    } else {
-      if (u16) pack_cols_bytes<uint16_t, true><<<grid, 256, 0, s>>>(p);
-      else pack_cols_bytes<uint8_t, true><<<grid, 256, 0, s>>>(p);
-    }
+    if (u16) pack_planes_kernel<uint16_t, kFmtNib><<<grid, 256, 0, s>>>(p);
+    else pack_planes_kernel<uint8_t, kFmtNib><<<grid, 256, 0, s>>>(p);
   }
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const void* X, int64_t ldx, int64_t K, int64_t rows, int elem_bytes, void* Xt,
+                             cudaStream_t s, int64_t* launches) {
+  if (K <= 0 || rows <= 0) return cudaSuccess;
+  const int64_t gx = ceil_div(rows, 64), gy = std::min<int64_t>(ceil_div(K, 64), 65535);
+  if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const int vec = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Xt)) & 15u) == 0 &&
+                  (ldx * elem_bytes) % 16 == 0 && (K * elem_bytes) % 16 == 0;
+  const dim3 grid((unsigned)gx, (unsigned)gy);
+  if (elem_bytes == 2)
+    transpose_kernel<uint16_t><<<grid, 256, 0, s>>>(static_cast<const uint16_t*>(X), ldx, K, rows,
+                                                    static_cast<uint16_t*>(Xt), vec);
+  else
+    transpose_kernel<uint8_t><<<grid, 256, 0, s>>>(static_cast<const uint8_t*>(X), ldx, K, rows,
+                                                   static_cast<uint8_t*>(Xt), vec);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
