@@ -131,11 +131,17 @@ m4rie_status m4rie_pack(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, const
 m4rie_status m4rie_unpack(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, const uint64_t *slices,
                           int64_t ld_words, void *elems);
 
-/* Many independent products (each with its own e, f, m, n, k) in one
- * persistent launch.  `problems` is a HOST array of `count` descriptors,
- * validated like m4rie_mul; no two outputs may overlap each other or any
- * input.  The work is recorded once into a CUDA graph that is cached in the
- * context and replayed while the same descriptor array contents are passed. */
+/* Many independent products (each with its own e, f, m, n, k and
+ * accumulate flag) in one persistent launch.  `problems` is a HOST array of
+ * `count` descriptors (reserved fields zero), validated like m4rie_mul; no
+ * output may overlap another output or any input (M4RIE_ERR_ALIAS).
+ * With the AUTO, TC_F4 or TC_F8 form the products use the alpha^j-B schedule
+ * on the tcgen05 tensor cores: one batched transpose, one batched operand-plane
+ * kernel per side and one persistent GEMM over the tiles of all products.
+ * That work is recorded once into a CUDA graph, cached in the context with
+ * its own device memory, and replayed while the same descriptor array contents
+ * are passed (a different array rebuilds it; the first call synchronises the
+ * stream).  With the POPC or MMA_S8 form the products run one by one. */
 m4rie_status m4rie_mul_batched(m4rie_ctx *ctx, int count, const m4rie_problem *problems);
 
 /* Wait for the stream, return the sticky device status (M4RIE_OK,

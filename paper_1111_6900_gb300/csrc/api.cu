@@ -7,37 +7,10 @@
 #include <string>
 #include <vector>
 
-#include "../../include/m4rie_gpu.h"
-#include "m4rie_internal.cuh"
+#include "context.h"
 #include "schedule.h"
 
 using namespace m4rie;
-
-struct m4rie_ctx {
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  int num_sms = 0;
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  void* io = nullptr;  // device copies for m4rie_mul_host
-  size_t io_bytes = 0;
-  int* d_status = nullptr;
-  int form = M4RIE_FORM_AUTO;
-  int schedule = M4RIE_SCHED_AUTO;
-  std::string last_error;
-  int64_t launches = 0;
-  uint64_t wait_limit_ns = 4000000000ull;
-  int tc_chunk = 4096;  // elements of K' per FP32 accumulation chunk
-  int auto_form[11][4];   // [e][size class] -> form, 0 = heuristic
-  int auto_sched[11][4];
-  // phase timing (m4rie_enable_timing)
-  bool timing = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;  // (phase, (start, stop))
-  size_t ev_next = 0;
-  double phase_ms[3] = {0, 0, 0};
-  int64_t timed_products = 0;
-};
 
 namespace {
 
@@ -470,6 +443,7 @@ void m4rie_destroy(m4rie_ctx* ctx) {
   if (ctx->io) cudaFree(ctx->io);
   if (ctx->d_status) cudaFree(ctx->d_status);
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+  destroy_plan(ctx->plan);
   delete ctx;
 }
 
@@ -563,12 +537,18 @@ m4rie_status m4rie_mul_batched(m4rie_ctx* ctx, int count, const m4rie_problem* p
     m4rie_status st = validate(p.e, p.f, p.m, p.n, p.k, p.A, p.B, p.C);
     if (st != M4RIE_OK) return st;
   }
-  for (int i = 0; i < count; ++i) {
-    const m4rie_problem& p = problems[i];
-    m4rie_status st = run_mul(ctx, p.e, p.f, p.m, p.n, p.k, p.A, p.B, p.C, p.accumulate ? 1 : 0);
-    if (st != M4RIE_OK) return st;
+  if (count == 0) return M4RIE_OK;
+  // The persistent batched launch uses the tcgen05 forms (FP4 unless FP8 is
+  // requested); the CUDA-core and INT8 forms run the products one by one.
+  if (ctx->form == M4RIE_FORM_POPC || ctx->form == M4RIE_FORM_MMA_S8) {
+    for (int i = 0; i < count; ++i) {
+      const m4rie_problem& p = problems[i];
+      m4rie_status st = run_mul(ctx, p.e, p.f, p.m, p.n, p.k, p.A, p.B, p.C, p.accumulate ? 1 : 0);
+      if (st != M4RIE_OK) return st;
+    }
+    return M4RIE_OK;
   }
-  return M4RIE_OK;
+  return run_batched(ctx, count, problems, ctx->form == M4RIE_FORM_TC_F8 ? kFmtByte : kFmtNib);
 }
 
 m4rie_status m4rie_get_device_status(m4rie_ctx* ctx) {

@@ -16,6 +16,8 @@
 // wait is bounded by a global-timer limit; on expiry the CTA sets the timeout
 // status, stops issuing, waits (bounded) for its copies in flight, frees TMEM
 // and returns.
+#include <cstring>
+
 #include "m4rie_internal.cuh"
 
 namespace m4rie {
@@ -155,10 +157,77 @@ __device__ __forceinline__ void tile_coords(const TcParams& p, int tile, int& b,
 // FP4 only: TMEM columns [SF_COL, SF_COL + 16) hold the unit scale factors.
 constexpr int SF_COL = 240;
 
-template <int FMT>
+// Everything a role needs to know about one output tile.
+struct TileV {
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  int arow, brow;       // TMA row coordinates of the A and B tiles
+  int BN, kblocks, kc;  // tile N, k-blocks, k-blocks per accumulation chunk
+  int b, tm, tn;
+  // epilogue
+  void* C;
+  int64_t m, n, ldc;
+  int G, e, elem_bytes, add;
+  uint32_t emask;
+};
+
+// Non-batched: one problem (or a batch of equally shaped parity products) in p.
+// Batched: the tile's job is found by scanning forward from the previous one
+// (each CTA visits tiles in increasing order).
+template <bool BATCHED>
+__device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restrict__ jobs, const CUtensorMap* tmA,
+                                         const CUtensorMap* tmB, int tile, int& jc, TileV& t) {
+  if (!BATCHED) {
+    tile_coords(p, tile, t.b, t.tm, t.tn);
+    t.ma = tmA;
+    t.mb = tmB;
+    t.arow = (int)(t.b * p.a_brows) + t.tm * 128;
+    t.brow = (int)(t.b * p.b_brows) + t.tn * p.BN;
+    t.BN = p.BN;
+    t.kblocks = p.kblocks;
+    t.kc = p.kc;
+    t.C = p.C;
+    t.m = p.m;
+    t.n = p.n;
+    t.ldc = p.ldc;
+    t.G = p.G;
+    t.e = p.e;
+    t.elem_bytes = p.elem_bytes;
+    t.add = p.add;
+    t.emask = p.emask;
+  } else {
+    const int njobs = p.batch;
+    while (jc + 1 < njobs && jobs[jc + 1].tile_start <= tile) ++jc;
+    const TcJob& j = jobs[jc];
+    const int local = (int)(tile - j.tile_start);
+    t.b = 0;
+    t.tm = local % j.tiles_m;
+    t.tn = local / j.tiles_m;
+    t.ma = &j.ma;
+    t.mb = &j.mb;
+    t.arow = t.tm * 128;
+    t.brow = t.tn * j.BN;
+    t.BN = j.BN;
+    t.kblocks = j.kblocks;
+    t.kc = j.kc;
+    t.C = j.C;
+    t.m = j.m;
+    t.n = j.n;
+    t.ldc = j.ldc;
+    t.G = j.G;
+    t.e = j.e;
+    t.elem_bytes = j.elem_bytes;
+    t.add = j.add;
+    t.emask = j.emask;
+  }
+}
+
+// BATCHED: p.batch = number of jobs, p.tiles_m = total tiles, p.tiles_n = 1;
+// per-tile parameters come from jobs[].
+template <int FMT, bool BATCHED>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const __grid_constant__ TcParams p) {
+              const __grid_constant__ TcParams p, const TcJob* __restrict__ jobs) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -186,8 +255,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    if (!BATCHED) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -215,30 +286,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     fence_after();
   }
-  const int total = p.batch * p.tiles_m * p.tiles_n;
+  const int total = BATCHED ? p.tiles_m : p.batch * p.tiles_m * p.tiles_n;
   const uint64_t lim = p.wait_limit_ns;
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      const uint32_t bytes = A_TILE + (uint32_t)p.BN * 128;
-      int stage = 0;
+      int stage = 0, jc = 0;
       uint32_t phase = 0;
       uint32_t issued_mask = 0, issued_parity = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-        int b, tm, tn;
-        tile_coords(p, tile, b, tm, tn);
-        const int arow = (int)(b * p.a_brows) + tm * 128, brow = (int)(b * p.b_brows) + tn * p.BN;
-        for (int kb = 0; kb < p.kblocks; ++kb) {
+        TileV t;
+        get_tile<BATCHED>(p, jobs, &tmA, &tmB, tile, jc, t);
+        const uint32_t bytes = A_TILE + (uint32_t)t.BN * 128;
+        for (int kb = 0; kb < t.kblocks; ++kb) {
           if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status, lim)) {
             ok = false;
             break;
           }
           const uint32_t fb = full0 + 8 * stage;
           mbar_expect_tx(fb, bytes);
-          tma_load_2d(smem_u32(sA + stage * A_TILE), &tmA, fb, kb * 128, arow);
-          tma_load_2d(smem_u32(sB + stage * B_SLOT), &tmB, fb, kb * 128, brow);
+          tma_load_2d(smem_u32(sA + stage * A_TILE), t.ma, fb, kb * 128, t.arow);
+          tma_load_2d(smem_u32(sB + stage * B_SLOT), t.mb, fb, kb * 128, t.brow);
           issued_mask |= 1u << stage;
           issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) {
@@ -260,15 +330,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      const uint32_t idesc = FMT == kFmtNib ? idesc_f4(128, p.BN) : idesc_f8(128, p.BN);
       const uint32_t sf = tmem + SF_COL;
-      int stage = 0;
+      int stage = 0, jc = 0;
       uint32_t phase = 0;
       int chunk = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-        for (int kb0 = 0; kb0 < p.kblocks && ok; kb0 += p.kc) {
-          const int kb1 = min(kb0 + p.kc, p.kblocks);
+        TileV t;
+        get_tile<BATCHED>(p, jobs, &tmA, &tmB, tile, jc, t);
+        const uint32_t idesc = FMT == kFmtNib ? idesc_f4(128, t.BN) : idesc_f8(128, t.BN);
+        for (int kb0 = 0; kb0 < t.kblocks && ok; kb0 += t.kc) {
+          const int kb1 = min(kb0 + t.kc, t.kblocks);
           const int buf = chunk & 1;
           const uint32_t tph = (chunk >> 1) & 1;
           if (!mbar_wait(tempty0 + 8 * buf, tph ^ 1, abort_flag, p.status, lim)) {
@@ -314,14 +386,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int row = 32 * q + lane;
     uint32_t* wbits = sbits + q * 32 * 9;  // this warp's 32 rows
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    const int nc16 = p.BN / 16;
-    int chunk = 0;
+    int chunk = 0, jc = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-      int b, tm, tn;
-      tile_coords(p, tile, b, tm, tn);
+      TileV t;
+      get_tile<BATCHED>(p, jobs, &tmA, &tmB, tile, jc, t);
+      const int b = t.b, tm = t.tm, tn = t.tn;
+      const int nc16 = t.BN / 16;
       uint32_t bits[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int kb0 = 0; kb0 < p.kblocks; kb0 += p.kc) {
+      for (int kb0 = 0; kb0 < t.kblocks; kb0 += t.kc) {
         const int buf = chunk & 1;
         const uint32_t tph = (chunk >> 1) & 1;
         // warp-uniform decision: tcgen05.ld below needs all 32 lanes
@@ -338,8 +411,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             tmem_ld16(ta + 16 * c16, v);
             if (p.mode == 1) {
               if (kb0 == 0) {
-                uint32_t* out = static_cast<uint32_t*>(p.C) + ((int64_t)tm * 128 + row) * p.ldc +
-                                (int64_t)tn * p.BN + 16 * c16;
+                uint32_t* out = static_cast<uint32_t*>(t.C) + ((int64_t)tm * 128 + row) * t.ldc +
+                                (int64_t)tn * t.BN + 16 * c16;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) out[j] = (uint32_t)__float2int_rz(__uint_as_float(v[j]));
               }
@@ -359,10 +432,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int64_t r0 = (int64_t)tm * 128;
       if (p.mode == 2) {
         // parity planes: row r0+row, columns tn*BN .. +BN
-        uint32_t* P = static_cast<uint32_t*>(p.C) + b * p.p_bstride + (r0 + row) * p.ldp + (int64_t)tn * p.BN / 32;
+        uint32_t* P = static_cast<uint32_t*>(t.C) + b * p.p_bstride + (r0 + row) * p.ldp + (int64_t)tn * t.BN / 32;
 #pragma unroll
         for (int w = 0; w < 8; ++w)
-          if (w < p.BN / 32) P[w] = bits[w];
+          if (w < t.BN / 32) P[w] = bits[w];
         continue;
       }
       // Assemble field elements: element c of this tile has bit i at column
@@ -370,32 +443,32 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int w = 0; w < 8; ++w) wbits[lane * 9 + w] = bits[w];
       __syncwarp();
-      const int G = p.G, E = p.e;
+      const int G = t.G, E = t.e;
       const int64_t c0 = (int64_t)tn * G;
       bool bad = false;
       for (int idx = lane; idx < 32 * G; idx += 32) {
         const int rl = idx / G, cl = idx - rl * G;
         const int64_t r = r0 + 32 * q + rl, c = c0 + cl;
-        if (r >= p.m || c >= p.n) continue;
+        if (r >= t.m || c >= t.n) continue;
         uint32_t val = 0;
         for (int i = 0; i < E; ++i) {
           const int col = i * G + cl;
           val |= ((wbits[rl * 9 + (col >> 5)] >> (col & 31)) & 1u) << i;
         }
-        if (p.elem_bytes == 1) {
-          uint8_t* dst = static_cast<uint8_t*>(p.C) + r * p.ldc + c;
-          if (p.add) {
+        if (t.elem_bytes == 1) {
+          uint8_t* dst = static_cast<uint8_t*>(t.C) + r * t.ldc + c;
+          if (t.add) {
             const uint32_t old = *dst;
-            bad |= old > p.emask;
-            val ^= old & p.emask;
+            bad |= old > t.emask;
+            val ^= old & t.emask;
           }
           *dst = (uint8_t)val;
         } else {
-          uint16_t* dst = static_cast<uint16_t*>(p.C) + r * p.ldc + c;
-          if (p.add) {
+          uint16_t* dst = static_cast<uint16_t*>(t.C) + r * t.ldc + c;
+          if (t.add) {
             const uint32_t old = *dst;
-            bad |= old > p.emask;
-            val ^= old & p.emask;
+            bad |= old > t.emask;
+            val ^= old & t.emask;
           }
           *dst = (uint16_t)val;
         }
@@ -430,7 +503,9 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld_bytes, int box_rows) {
+}  // namespace
+
+bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld_bytes, int box_rows) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)ld_bytes, (cuuint64_t)rows};
@@ -442,8 +517,6 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld_bytes
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
-
-}  // namespace
 
 int tc_group(int e, int fmt) {
   // tile N = e * G: a multiple of 16, at most 256 (FP8) or 240 (FP4, whose
@@ -463,10 +536,10 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
   if (p.BN % 16 != 0 || p.BN < 16 || p.BN > (fmt == kFmtNib ? SF_COL : 256) || ld_bytes % 16 != 0)
     return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, Aplanes, a_rows, ld_bytes, 128) || !make_map(&mb, Bplanes, b_rows, ld_bytes, p.BN))
+  if (!tc_make_map(&ma, Aplanes, a_rows, ld_bytes, 128) || !tc_make_map(&mb, Bplanes, b_rows, ld_bytes, p.BN))
     return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes();
-  auto kernel = fmt == kFmtNib ? tc_kernel<kFmtNib> : tc_kernel<kFmtByte>;
+  auto kernel = fmt == kFmtNib ? tc_kernel<kFmtNib, false> : tc_kernel<kFmtByte, false>;
   cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int64_t total = (int64_t)p.batch * p.tiles_m * p.tiles_n;
@@ -474,7 +547,31 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
     return cudaErrorInvalidValue;
   const int grid = total < num_sms ? (int)total : num_sms;
   if (grid <= 0) return cudaSuccess;
-  kernel<<<grid, THREADS, smem, s>>>(ma, mb, p);
+  kernel<<<grid, THREADS, smem, s>>>(ma, mb, p, nullptr);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, int njobs, int64_t total_tiles, int* status,
+                              uint64_t wait_limit_ns, int num_sms, cudaStream_t s, int64_t* launches) {
+  if (fmt != kFmtByte && fmt != kFmtNib) return cudaErrorNotSupported;
+  if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+  if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  TcParams p{};
+  p.batch = njobs;
+  p.tiles_m = (int)total_tiles;
+  p.tiles_n = 1;
+  p.group_m = 1;
+  p.status = status;
+  p.wait_limit_ns = wait_limit_ns;
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  const size_t smem = tc_smem_bytes();
+  auto kernel = fmt == kFmtNib ? tc_kernel<kFmtNib, true> : tc_kernel<kFmtByte, true>;
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int grid = total_tiles < num_sms ? (int)total_tiles : num_sms;
+  kernel<<<grid, THREADS, smem, s>>>(dummy, dummy, p, d_jobs);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

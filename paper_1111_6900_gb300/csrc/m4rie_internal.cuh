@@ -50,6 +50,21 @@ cudaError_t launch_pack_planes(const PackParams& p, cudaStream_t s, int64_t* lau
 cudaError_t launch_transpose(const void* X, int64_t ldx, int64_t K, int64_t rows, int elem_bytes, void* Xt,
                              cudaStream_t s, int64_t* launches);
 
+// Batched forms: job j owns blocks [start[j], start[j+1]) of one launch (all
+// jobs of a launch share the element width and the plane format).
+struct TransposeJob {
+  const void* X;
+  int64_t ldx, K, rows;
+  void* Xt;
+  int vec;
+};
+int64_t pack_job_blocks(const PackParams& p);
+int64_t transpose_job_blocks(const TransposeJob& j);
+cudaError_t launch_pack_batched(const PackParams* d_jobs, const int64_t* d_start, int njobs, int64_t blocks, int fmt,
+                                int elem_bytes, cudaStream_t s, int64_t* launches);
+cudaError_t launch_transpose_batched(const TransposeJob* d_jobs, const int64_t* d_start, int njobs, int64_t blocks,
+                                     int elem_bytes, cudaStream_t s, int64_t* launches);
+
 // Public slice format (Section 3.2): pack.cu.
 cudaError_t launch_slice(int e, int64_t rows, int64_t cols, const void* elems, uint64_t* slices,
                          int64_t ld_words, int* status, cudaStream_t s, int64_t* launches);
@@ -125,6 +140,21 @@ struct TcParams {
 // fmt: kFmtByte (E4M3) or kFmtNib (E2M1, block scaled).
 cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
                       int64_t ld_bytes, const TcParams& p, int num_sms, cudaStream_t s, int64_t* launches);
+
+// One product of a batched persistent launch (element epilogue, alpha^j-B
+// layout).  Its tiles are global tiles [tile_start, tile_start + tiles_m *
+// tiles_n), m-fastest.  Tensor maps live in device memory with the job.
+struct alignas(64) TcJob {
+  CUtensorMap ma, mb;
+  void* C;
+  int64_t m, n, ldc;
+  int e, G, BN, kblocks, kc, tiles_m, tiles_n, elem_bytes, add;
+  uint32_t emask;
+  int64_t tile_start;
+};
+bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld_bytes, int box_rows);
+cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, int njobs, int64_t total_tiles, int* status,
+                              uint64_t wait_limit_ns, int num_sms, cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------- INT8 mma.sync form
 int mma_group(int e);  // elements per block column: block N = e * G <= 160

@@ -87,23 +87,27 @@ __device__ __forceinline__ void load_row(const PackParams& p, int64_t r, int64_t
   }
 }
 
-// grid.x covers a row in chunks of 256 threads x NE elements, grid.y strides over rows.
-template <typename T, int FMT>
-__global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant__ PackParams p) {
-  constexpr int NE = FMT == kFmtBit ? 32 : 16;  // elements per thread
-  constexpr int W = NE * (int)sizeof(T) / 4;    // packed input words per thread
-  __shared__ int64_t qoff[kMaxMasks];
-  __shared__ uint32_t mrep[kMaxMasks];
+// Per-block tables: plane offsets qoff[q] = b*bstride + i*G*ld + j*Kp for
+// q = (b*nb + i)*kb + j, and the masks replicated per packed element.
+template <typename T>
+__device__ __forceinline__ void plane_tables(const PackParams& p, int64_t* qoff, uint32_t* mrep) {
   for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
     const int b = q / (p.nb * p.kb), i = (q / p.kb) % p.nb, j = q % p.kb;
     qoff[q] = (int64_t)b * p.bstride + (int64_t)i * p.G * p.ld + (int64_t)j * p.Kp;
     mrep[q] = Swar<T>::rep(p.mask[q]);
   }
-  __syncthreads();
-  const int64_t t0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * NE;
+}
+
+// Rows r0, r0 + rstep, ... of one plane job, elements bx*256*NE + ...
+template <typename T, int FMT>
+__device__ __forceinline__ void pack_planes_rows(const PackParams& p, const int64_t* qoff, const uint32_t* mrep,
+                                                 int64_t bx, int64_t r0, int64_t rstep) {
+  constexpr int NE = FMT == kFmtBit ? 32 : 16;  // elements per thread
+  constexpr int W = NE * (int)sizeof(T) / 4;    // packed input words per thread
+  const int64_t t0 = (bx * blockDim.x + threadIdx.x) * NE;
   const bool live_t = t0 < p.Kp;
   const uint32_t erep = Swar<T>::rep(p.emask);
-  for (int64_t r = blockIdx.y; r < p.rows_p; r += gridDim.y) {
+  for (int64_t r = r0; r < p.rows_p; r += rstep) {
     uint32_t v[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) v[k] = 0;
@@ -154,14 +158,54 @@ __global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant_
   }
 }
 
+// grid.x covers a row in chunks of 256 threads x NE elements, grid.y strides over rows.
+template <typename T, int FMT>
+__global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant__ PackParams p) {
+  __shared__ int64_t qoff[kMaxMasks];
+  __shared__ uint32_t mrep[kMaxMasks];
+  plane_tables<T>(p, qoff, mrep);
+  __syncthreads();
+  pack_planes_rows<T, FMT>(p, qoff, mrep, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
+// Index of the job whose block range [start[j], start[j+1]) holds block b.
+__device__ __forceinline__ int find_job(const int64_t* __restrict__ start, int njobs, int64_t b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Many plane jobs in one launch: block b belongs to job j with
+// start[j] <= b < start[j+1]; within the job, local block l covers row
+// l / gx and chunk l % gx (gx = chunks of 256 threads per row).
+template <typename T, int FMT>
+__global__ void __launch_bounds__(256) pack_planes_batched(const PackParams* __restrict__ jobs,
+                                                           const int64_t* __restrict__ start, int njobs) {
+  __shared__ int64_t qoff[kMaxMasks];
+  __shared__ uint32_t mrep[kMaxMasks];
+  __shared__ int sj;
+  if (threadIdx.x == 0) sj = find_job(start, njobs, blockIdx.x);
+  __syncthreads();
+  const PackParams& p = jobs[sj];
+  plane_tables<T>(p, qoff, mrep);
+  __syncthreads();
+  constexpr int NE = FMT == kFmtBit ? 32 : 16;
+  const int64_t gx = (p.Kp + 256 * NE - 1) / (256 * NE);
+  const int64_t l = (int64_t)blockIdx.x - start[sj];
+  pack_planes_rows<T, FMT>(p, qoff, mrep, l % gx, l / gx, p.rows_p);  // one row per block
+}
+
 // ---- Element transpose X (K x rows, row-major) -> Xt (rows x K), tiles of
 // 64 x 64 elements through shared memory (one 32-bit word per element).
 template <typename T>
-__global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ X, int64_t ldx, int64_t K, int64_t rows,
-                                                        T* __restrict__ Xt, int vec) {
-  __shared__ uint32_t tile[64][65];
-  const int64_t c0 = (int64_t)blockIdx.x * 64;
-  for (int64_t t0 = (int64_t)blockIdx.y * 64; t0 < K; t0 += (int64_t)gridDim.y * 64) {
+__device__ __forceinline__ void transpose_tiles(const T* __restrict__ X, int64_t ldx, int64_t K, int64_t rows,
+                                                T* __restrict__ Xt, int vec, int64_t c0, int64_t ty0, int64_t tystep,
+                                                uint32_t (*tile)[65]) {
+  for (int64_t t0 = ty0 * 64; t0 < K; t0 += tystep * 64) {
     constexpr int CH = 64 * sizeof(T) / 16;  // 16-byte chunks per tile row
     if (vec && c0 + 64 <= rows && t0 + 64 <= K) {
       for (int idx = threadIdx.x; idx < 64 * CH; idx += 256) {
@@ -206,6 +250,28 @@ __global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ X,
     }
     __syncthreads();
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ X, int64_t ldx, int64_t K, int64_t rows,
+                                                        T* __restrict__ Xt, int vec) {
+  __shared__ uint32_t tile[64][65];
+  transpose_tiles<T>(X, ldx, K, rows, Xt, vec, (int64_t)blockIdx.x * 64, blockIdx.y, gridDim.y, tile);
+}
+
+// Many transposes in one launch (block ranges per job as in pack_planes_batched).
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_batched(const TransposeJob* __restrict__ jobs,
+                                                         const int64_t* __restrict__ start, int njobs) {
+  __shared__ uint32_t tile[64][65];
+  __shared__ int sj;
+  if (threadIdx.x == 0) sj = find_job(start, njobs, blockIdx.x);
+  __syncthreads();
+  const TransposeJob& j = jobs[sj];
+  const int64_t gx = (j.rows + 63) / 64;
+  const int64_t l = (int64_t)blockIdx.x - start[sj];
+  transpose_tiles<T>(static_cast<const T*>(j.X), j.ldx, j.K, j.rows, static_cast<T*>(j.Xt), j.vec, (l % gx) * 64,
+                     l / gx, (j.K + 63) / 64, tile);
 }
 
 // ---- Public slice format: one warp per (row, 64-bit word).
@@ -369,6 +435,43 @@ cudaError_t launch_transpose(const void* X, int64_t ldx, int64_t K, int64_t rows
   else
     transpose_kernel<uint8_t><<<grid, 256, 0, s>>>(static_cast<const uint8_t*>(X), ldx, K, rows,
                                                    static_cast<uint8_t*>(Xt), vec);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_batched(const PackParams* d_jobs, const int64_t* d_start, int njobs, int64_t blocks, int fmt,
+                                int elem_bytes, cudaStream_t s, int64_t* launches) {
+  if (njobs <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const unsigned g = (unsigned)blocks;
+  const bool u16 = elem_bytes == 2;
+  if (fmt == kFmtBit) {
+    if (u16) pack_planes_batched<uint16_t, kFmtBit><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+    else pack_planes_batched<uint8_t, kFmtBit><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+  } else if (fmt == kFmtByte) {
+    if (u16) pack_planes_batched<uint16_t, kFmtByte><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+    else pack_planes_batched<uint8_t, kFmtByte><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+  } else {
+    if (u16) pack_planes_batched<uint16_t, kFmtNib><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+    else pack_planes_batched<uint8_t, kFmtNib><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+  }
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+int64_t pack_job_blocks(const PackParams& p) {
+  const int ne = p.fmt == kFmtBit ? 32 : 16;
+  return ceil_div(ceil_div(p.Kp, ne), 256) * p.rows_p;
+}
+
+int64_t transpose_job_blocks(const TransposeJob& j) { return ceil_div(j.rows, 64) * ceil_div(j.K, 64); }
+
+cudaError_t launch_transpose_batched(const TransposeJob* d_jobs, const int64_t* d_start, int njobs, int64_t blocks,
+                                     int elem_bytes, cudaStream_t s, int64_t* launches) {
+  if (njobs <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (elem_bytes == 2) transpose_batched<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(d_jobs, d_start, njobs);
+  else transpose_batched<uint8_t><<<(unsigned)blocks, 256, 0, s>>>(d_jobs, d_start, njobs);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

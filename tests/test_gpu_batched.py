@@ -1,0 +1,113 @@
+"""Batched products (one persistent launch replayed from a CUDA graph) against
+the oracle, including the full 4096-instance workload on sampled rows."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1111_6900_gb300 as m4  # noqa: E402
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _problems(specs, seed0):
+    probs, ref = [], []
+    for j, (e, m, n, k, acc) in enumerate(specs):
+        f = workloads.FIELD_POLY[e]
+        A, B, C0 = workloads.random_problem(e, m, n, k, seed=seed0 + j, with_c=True)
+        C = dev(C0)
+        probs.append((e, f, dev(A), dev(B), C, acc))
+        ref.append(oracle.addmul(e, f, A, B, C0) if acc else oracle.matmul(e, f, A, B))
+    return probs, ref
+
+
+SPECS = [(2, 33, 65, 129, False), (3, 130, 70, 300, True), (4, 1, 1, 1, False), (5, 200, 257, 64, False),
+         (6, 64, 64, 64, True), (7, 17, 300, 90, False), (8, 129, 31, 1000, False), (9, 40, 50, 60, False),
+         (10, 70, 33, 130, True), (4, 0, 5, 5, False), (4, 5, 5, 0, False), (8, 6, 7, 0, True)]
+
+
+@pytest.mark.parametrize("form", ["auto", "tc_f8", "popc"])
+def test_batched_mixed_fields_and_shapes(form):
+    ctx = m4.Context()
+    ctx.set_form(form)
+    probs, ref = _problems(SPECS, 5000)
+    ctx.mul_batched(probs)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == m4.OK
+    for (e, f, A, B, C, acc), r, spec in zip(probs, ref, SPECS):
+        np.testing.assert_array_equal(C.cpu().numpy(), r, err_msg=str(spec))
+    ctx.close()
+
+
+def test_batched_graph_replay_sees_new_inputs():
+    ctx = m4.Context()
+    specs = [(4, 100, 90, 80, False), (8, 50, 60, 70, False)]
+    probs, _ = _problems(specs, 6000)
+    ctx.mul_batched(probs)           # records the graph
+    launches = ctx.kernel_launches()
+    # new input values in the same buffers: the replay must compute them
+    refs = []
+    for (e, f, A, B, C, acc), (_, m, n, k, _) in zip(probs, specs):
+        A2, B2, _ = workloads.random_problem(e, m, n, k, seed=77 + e)
+        A.copy_(dev(A2))
+        B.copy_(dev(B2))
+        refs.append(oracle.matmul(e, f, A2, B2))
+    ctx.mul_batched(probs)           # replays
+    torch.cuda.synchronize()
+    assert ctx.kernel_launches() > launches
+    for (e, f, A, B, C, acc), r in zip(probs, refs):
+        np.testing.assert_array_equal(C.cpu().numpy(), r)
+    assert ctx.device_status() == m4.OK
+    ctx.close()
+
+
+def test_batched_rejects_overlapping_outputs():
+    ctx = m4.Context()
+    e, f = 4, workloads.FIELD_POLY[4]
+    A = dev(np.ones((8, 8), np.uint8))
+    C = torch.zeros((16, 8), dtype=torch.uint8, device="cuda")
+    with pytest.raises(m4.M4rieError) as ei:
+        ctx.mul_batched([(e, f, A, A, C[:8], False), (e, f, A, A, C[4:12], False)])
+    assert ei.value.status == m4.ERR_ALIAS
+    with pytest.raises(m4.M4rieError) as ei:   # an output over another product's input
+        ctx.mul_batched([(e, f, A, A, C[:8], False), (e, f, C[:8], A, C[8:], False)])
+    assert ei.value.status == m4.ERR_ALIAS
+    ctx.close()
+
+
+def test_batched_workload_4096_instances():
+    """The batched workload: 4096 instances, e in 2..8, m, n, k in 32..1024.
+    Every instance is checked on its first and last rows against the oracle;
+    64 instances are checked in full against the single-product popc form."""
+    ctx = m4.Context()
+    probs, host = [], []
+    for j in range(workloads.BATCHED_COUNT):
+        e, f, m, n, k, A, B = workloads.batched_instance(j)
+        C = torch.empty((m, n), dtype=m4.elem_dtype_torch(e), device="cuda")
+        probs.append((e, f, dev(A), dev(B), C, False))
+        host.append((A, B))
+    ctx.mul_batched(probs)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == m4.OK
+    rng = np.random.default_rng(4)
+    full = set(rng.choice(len(probs), size=64, replace=False).tolist())
+    chk = m4.Context()
+    chk.set_form("popc")
+    chk.set_schedule("alpha_b")
+    for j, ((e, f, dA, dB, C, _), (A, B)) in enumerate(zip(probs, host)):
+        got = C.cpu().numpy()
+        rows = [0, A.shape[0] - 1]
+        np.testing.assert_array_equal(got[rows], oracle.matmul(e, f, A[rows], B), err_msg=f"instance {j}")
+        if j in full:
+            np.testing.assert_array_equal(got, chk.mul(e, f, dA, dB).cpu().numpy(), err_msg=f"instance {j}")
+    chk.close()
+    ctx.close()
