@@ -163,7 +163,7 @@ def run_batched_workload(args, m4, torch, world, rank, local):
     """4096 independent products (e in 2..8, m, n, k in 32..1024) replayed from
     the CUDA graph of one persistent launch; value = sum of 2mnk / step time."""
     probs, ops = [], 0.0
-    for j in range(workloads.BATCHED_COUNT):
+    for j in range(args.batched_count):
         e, f, m, n, k, A, B = workloads.batched_instance(j)
         C = torch.empty((m, n), dtype=m4.elem_dtype_torch(e), device="cuda")
         probs.append((e, f, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, False))
@@ -191,10 +191,12 @@ def run_batched_workload(args, m4, torch, world, rank, local):
         clk.mark_end()
         time.sleep(0.1)
     ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops)) / args.steps
+    if args.single:
+        return 0
     out = {"metric": "GF(2^e) batched matmul field-ops/s (sum of 2mnk)", "value": world * ops / (ms * 1e-3),
            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-           "config": {"workload": "4096 independent products, e uniform in 2..8, m, n, k uniform in {32, ..., 1024}",
+           "config": {"workload": f"{args.batched_count} independent products, e uniform in 2..8, m, n, k uniform in {{32, ..., 1024}}",
                       "form": "tcgen05 persistent batched launch replayed from a CUDA graph",
                       "l2": "flushed between timed steps (512 MB write, not timed)"},
            "clocks": clk.summary(), "gpu_launches": (ctx.kernel_launches() - launches0) // max(args.steps, 1),
@@ -217,6 +219,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="gf16_4096", choices=["gf16_4096", "batched"],
                     help="gf16_4096: the 4096^3 GF(2^4) product (default); batched: the 4096-instance batch")
+    ap.add_argument("--batched-count", type=int, default=workloads.BATCHED_COUNT,
+                    help="instances of the batched workload (a prefix of it; the default is the whole batch)")
     ap.add_argument("--single", default=None,
                     help="FORM/SCHEDULE: run the warm-up steps and one more step of that form, print nothing "
                          "(a fixed launch sequence for profilers)")

@@ -153,7 +153,11 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
   const size_t off_pstart = off_pjobs + round_up(sizeof(PackParams) * 2 * (size_t)std::max(nl, 1), 256);
   const size_t off_xjobs = off_pstart + round_up(sizeof(int64_t) * (2 * (size_t)nl + 4), 256);
   const size_t off_xstart = off_xjobs + round_up(sizeof(TransposeJob) * (size_t)std::max(nl, 1), 256);
-  const size_t off_ws = off_xstart + round_up(sizeof(int64_t) * ((size_t)nl + 2), 1024);
+  // tile -> job table (upper bound on the tile count: every job's tiles)
+  int64_t tiles_ub = 0;
+  for (int i : live) tiles_ub += (lay[i].Mp / 128) * lay[i].groups;
+  const size_t off_tilejob = off_xstart + round_up(sizeof(int64_t) * ((size_t)nl + 2), 256);
+  const size_t off_ws = off_tilejob + round_up(sizeof(int) * (size_t)std::max<int64_t>(tiles_ub, 1), 1024);
   err = cudaMalloc(&plan->dmem, off_ws + ws);
   if (err != cudaSuccess) {
     cudaGetLastError();
@@ -199,6 +203,9 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
     j.tile_start = tiles;
     tiles += (int64_t)j.tiles_m * j.tiles_n;
   }
+  std::vector<int> tile_job((size_t)tiles);
+  for (int t = 0; t < nl; ++t)
+    for (int64_t x = 0; x < (int64_t)tjobs[t].tiles_m * tjobs[t].tiles_n; ++x) tile_job[tjobs[t].tile_start + x] = t;
 
   // plane and transpose jobs, grouped by side and element width
   for (int grp = 0; grp < 4; ++grp) {
@@ -281,6 +288,8 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
       err = cudaMemcpy(dbase + off_xjobs, xjobs.data(), sizeof(TransposeJob) * xjobs.size(), cudaMemcpyHostToDevice);
     if (err == cudaSuccess)
       err = cudaMemcpy(dbase + off_xstart, xstart.data(), sizeof(int64_t) * xstart.size(), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+      err = cudaMemcpy(dbase + off_tilejob, tile_job.data(), sizeof(int) * tile_job.size(), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return fail(ctx, err, plan);
   }
 
@@ -314,7 +323,8 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
     }
   }
   if (rec == cudaSuccess)
-    rec = launch_tc_batched(fmt, reinterpret_cast<const TcJob*>(dbase + off_tjobs), nl, tiles, ctx->d_status,
+    rec = launch_tc_batched(fmt, reinterpret_cast<const TcJob*>(dbase + off_tjobs),
+                            reinterpret_cast<const int*>(dbase + off_tilejob), nl, tiles, ctx->d_status,
                             ctx->wait_limit_ns, ctx->num_sms, plan->cap, &launches);
   cudaGraph_t graph = nullptr;
   err = cudaStreamEndCapture(plan->cap, &graph);

@@ -172,8 +172,7 @@ struct TileV {
 };
 
 // Non-batched: one problem (or a batch of equally shaped parity products) in p.
-// Batched: the tile's job is found by scanning forward from the previous one
-// (each CTA visits tiles in increasing order).
+// Batched: the tile's job comes from the tile -> job table.
 template <bool BATCHED>
 __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restrict__ jobs, const CUtensorMap* tmA,
                                          const CUtensorMap* tmB, int tile, int& jc, TileV& t) {
@@ -196,8 +195,7 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
     t.add = p.add;
     t.emask = p.emask;
   } else {
-    const int njobs = p.batch;
-    while (jc + 1 < njobs && jobs[jc + 1].tile_start <= tile) ++jc;
+    jc = __ldg(p.tile_job + tile);
     const TcJob& j = jobs[jc];
     const int local = (int)(tile - j.tile_start);
     t.b = 0;
@@ -299,6 +297,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
         TileV t;
         get_tile<BATCHED>(p, jobs, &tmA, &tmB, tile, jc, t);
+        if (BATCHED && tile + (int)gridDim.x < total) {
+          // fetch the next tile's tensor maps into the TMA descriptor cache early
+          const TcJob& nj = jobs[__ldg(p.tile_job + tile + gridDim.x)];
+          asm volatile("prefetch.tensormap [%0];" ::"l"(&nj.ma) : "memory");
+          asm volatile("prefetch.tensormap [%0];" ::"l"(&nj.mb) : "memory");
+        }
         const uint32_t bytes = A_TILE + (uint32_t)t.BN * 128;
         for (int kb = 0; kb < t.kblocks; ++kb) {
           if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status, lim)) {
@@ -552,8 +556,8 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, int njobs, int64_t total_tiles, int* status,
-                              uint64_t wait_limit_ns, int num_sms, cudaStream_t s, int64_t* launches) {
+cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, const int* d_tile_job, int njobs, int64_t total_tiles,
+                              int* status, uint64_t wait_limit_ns, int num_sms, cudaStream_t s, int64_t* launches) {
   if (fmt != kFmtByte && fmt != kFmtNib) return cudaErrorNotSupported;
   if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
   if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -564,6 +568,7 @@ cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, int njobs, int64_t t
   p.group_m = 1;
   p.status = status;
   p.wait_limit_ns = wait_limit_ns;
+  p.tile_job = d_tile_job;
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof(dummy));
   const size_t smem = tc_smem_bytes();

@@ -136,6 +136,7 @@ struct TcParams {
   int64_t ldp;        // parity mode: words per plane row
   int64_t p_bstride;  // parity mode: words between products
   uint64_t wait_limit_ns;
+  const int* tile_job;  // batched launches: job of every global tile
 };
 // fmt: kFmtByte (E4M3) or kFmtNib (E2M1, block scaled).
 cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
@@ -153,8 +154,8 @@ struct alignas(64) TcJob {
   int64_t tile_start;
 };
 bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld_bytes, int box_rows);
-cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, int njobs, int64_t total_tiles, int* status,
-                              uint64_t wait_limit_ns, int num_sms, cudaStream_t s, int64_t* launches);
+cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, const int* d_tile_job, int njobs, int64_t total_tiles,
+                              int* status, uint64_t wait_limit_ns, int num_sms, cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------- INT8 mma.sync form
 int mma_group(int e);  // elements per block column: block N = e * G <= 160

@@ -98,13 +98,14 @@ __device__ __forceinline__ void plane_tables(const PackParams& p, int64_t* qoff,
   }
 }
 
-// Rows r0, r0 + rstep, ... of one plane job, elements bx*256*NE + ...
+// Rows r0, r0 + rstep, ... of one plane job; this thread's elements start at
+// t0 = tchunk * NE (threads with t0 >= Kp only join the warp-wide votes).
 template <typename T, int FMT>
 __device__ __forceinline__ void pack_planes_rows(const PackParams& p, const int64_t* qoff, const uint32_t* mrep,
-                                                 int64_t bx, int64_t r0, int64_t rstep) {
+                                                 int64_t tchunk, int64_t r0, int64_t rstep) {
   constexpr int NE = FMT == kFmtBit ? 32 : 16;  // elements per thread
   constexpr int W = NE * (int)sizeof(T) / 4;    // packed input words per thread
-  const int64_t t0 = (bx * blockDim.x + threadIdx.x) * NE;
+  const int64_t t0 = tchunk * NE;
   const bool live_t = t0 < p.Kp;
   const uint32_t erep = Swar<T>::rep(p.emask);
   for (int64_t r = r0; r < p.rows_p; r += rstep) {
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant_
   __shared__ uint32_t mrep[kMaxMasks];
   plane_tables<T>(p, qoff, mrep);
   __syncthreads();
-  pack_planes_rows<T, FMT>(p, qoff, mrep, blockIdx.x, blockIdx.y, gridDim.y);
+  pack_planes_rows<T, FMT>(p, qoff, mrep, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, gridDim.y);
 }
 
 // Index of the job whose block range [start[j], start[j+1]) holds block b.
@@ -179,9 +180,20 @@ __device__ __forceinline__ int find_job(const int64_t* __restrict__ start, int n
   return lo;
 }
 
+// Threads per row and rows per 256-thread block of a plane job: a row of Kp
+// entries needs ceil(Kp / NE) threads, rounded up to a power of two (at least
+// a warp, at most the block); short rows share a block.
+__host__ __device__ inline void job_shape(int64_t Kp, int ne, int64_t& tpr, int64_t& rpb, int64_t& gx) {
+  const int64_t need = (Kp + ne - 1) / ne;
+  tpr = 32;
+  while (tpr < need && tpr < 256) tpr *= 2;
+  rpb = 256 / tpr;
+  gx = (need + 255) / 256;  // blocks per row when a row needs more than 256 threads
+}
+
 // Many plane jobs in one launch: block b belongs to job j with
-// start[j] <= b < start[j+1]; within the job, local block l covers row
-// l / gx and chunk l % gx (gx = chunks of 256 threads per row).
+// start[j] <= b < start[j+1]; within the job, local block l covers rows
+// (l / gx) * rpb + threadIdx.x / tpr and chunk (l % gx) * 256 + threadIdx.x % tpr.
 template <typename T, int FMT>
 __global__ void __launch_bounds__(256) pack_planes_batched(const PackParams* __restrict__ jobs,
                                                            const int64_t* __restrict__ start, int njobs) {
@@ -194,9 +206,14 @@ __global__ void __launch_bounds__(256) pack_planes_batched(const PackParams* __r
   plane_tables<T>(p, qoff, mrep);
   __syncthreads();
   constexpr int NE = FMT == kFmtBit ? 32 : 16;
-  const int64_t gx = (p.Kp + 256 * NE - 1) / (256 * NE);
+  int64_t tpr, rpb, gx;
+  job_shape(p.Kp, NE, tpr, rpb, gx);
   const int64_t l = (int64_t)blockIdx.x - start[sj];
-  pack_planes_rows<T, FMT>(p, qoff, mrep, l % gx, l / gx, p.rows_p);  // one row per block
+  const int64_t r = (l / gx) * rpb + threadIdx.x / tpr;
+  const int64_t chunk = (l % gx) * 256 + threadIdx.x % tpr;
+  // rows past the job's end still run the loop body's warp votes (zero data)
+  pack_planes_rows<T, FMT>(p, qoff, mrep, r < p.rows_p ? chunk : (p.Kp + NE - 1) / NE, r < p.rows_p ? r : 0,
+                           p.rows_p);
 }
 
 // ---- Element transpose X (K x rows, row-major) -> Xt (rows x K), tiles of
@@ -460,8 +477,9 @@ cudaError_t launch_pack_batched(const PackParams* d_jobs, const int64_t* d_start
 }
 
 int64_t pack_job_blocks(const PackParams& p) {
-  const int ne = p.fmt == kFmtBit ? 32 : 16;
-  return ceil_div(ceil_div(p.Kp, ne), 256) * p.rows_p;
+  int64_t tpr, rpb, gx;
+  job_shape(p.Kp, p.fmt == kFmtBit ? 32 : 16, tpr, rpb, gx);
+  return gx * ceil_div(p.rows_p, rpb);
 }
 
 int64_t transpose_job_blocks(const TransposeJob& j) { return ceil_div(j.rows, 64) * ceil_div(j.K, 64); }
