@@ -206,6 +206,8 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   pb.nb = e;
   pb.kb = e;
   pb.G = G;
+  // the tcgen05 epilogue wants the e slices of an element in adjacent columns
+  pb.emajor = (form == M4RIE_FORM_TC_F8 || form == M4RIE_FORM_TC_F4) ? 1 : 0;
   pb.out = Bp;
   for (int q = 0; q < e * e; ++q) pb.mask[q] = bmask[q];
   err = launch_pack_planes(pb, ctx->stream, &ctx->launches);

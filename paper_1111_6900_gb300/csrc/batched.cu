@@ -248,6 +248,7 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
         q.P = p.e * p.e;
         q.nb = p.e;
         q.G = L.G;
+        q.emajor = 1;  // tcgen05 epilogue: slices of an element in adjacent columns
         q.out = wbase + L.b_off;
         for (int jj = 0; jj < p.e * p.e; ++jj) q.mask[jj] = bmask[jj];
       }

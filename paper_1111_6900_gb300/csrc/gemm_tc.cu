@@ -6,7 +6,7 @@
 // every partial sum is a small integer and exact; after each chunk the
 // epilogue warps take the low bit (the GF(2) sum) and XOR it into per-row bit
 // vectors.  With the alpha^j-B schedule the tile's columns are the e slices of
-// G consecutive output elements (column i*G + c holds slice i of element c),
+// G consecutive output elements (column c*e + i holds slice i of element c),
 // so the epilogue assembles finished field elements (Section 5: product of
 // slice polynomials with the reduction mod f folded into B).
 //
@@ -64,13 +64,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
                                           uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
-  while (true) {
-    if (mbar_try(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtimer() - t0 > limit_ns) {
-      *abort_flag = 1;
-      atomicOr(status, kStatusTimeout);
-      return false;
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;  // try_wait itself suspends for a while
+    if ((it & 15u) == 0) {                   // check abort and the clock every 16 tries
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > limit_ns) {
+        *abort_flag = 1;
+        atomicOr(status, kStatusTimeout);
+        return false;
+      }
     }
   }
 }
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  uint32_t* sbits = tmem_slot + 4;  // [4 warps][32 rows][9 words]
+  uint32_t* sbits = tmem_slot + 4;  // [4 warps][32 rows][9 words] (8 bit words + a zero sentinel)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
@@ -442,39 +444,44 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (w < t.BN / 32) P[w] = bits[w];
         continue;
       }
-      // Assemble field elements: element c of this tile has bit i at column
-      // i*G + c.  Each warp writes its own 32 rows (lanes along columns).
+      // Assemble field elements.  The B planes are element-major: column
+      // c*E + i holds slice i of element c of this tile, so element c is the
+      // E-bit field at bit c*E of the row's bit vector.  Each warp writes its
+      // own 32 rows, lanes along the elements (coalesced stores).
 #pragma unroll
       for (int w = 0; w < 8; ++w) wbits[lane * 9 + w] = bits[w];
+      wbits[lane * 9 + 8] = 0;  // sentinel word for the funnel shift
       __syncwarp();
       const int G = t.G, E = t.e;
       const int64_t c0 = (int64_t)tn * G;
       bool bad = false;
-      for (int idx = lane; idx < 32 * G; idx += 32) {
-        const int rl = idx / G, cl = idx - rl * G;
-        const int64_t r = r0 + 32 * q + rl, c = c0 + cl;
-        if (r >= t.m || c >= t.n) continue;
-        uint32_t val = 0;
-        for (int i = 0; i < E; ++i) {
-          const int col = i * G + cl;
-          val |= ((wbits[rl * 9 + (col >> 5)] >> (col & 31)) & 1u) << i;
-        }
-        if (t.elem_bytes == 1) {
-          uint8_t* dst = static_cast<uint8_t*>(t.C) + r * t.ldc + c;
-          if (t.add) {
-            const uint32_t old = *dst;
-            bad |= old > t.emask;
-            val ^= old & t.emask;
+      for (int rl = 0; rl < 32; ++rl) {
+        const int64_t r = r0 + 32 * q + rl;
+        if (r >= t.m) break;
+        const uint32_t* rb = wbits + rl * 9;
+        for (int cl = lane; cl < G; cl += 32) {
+          const int64_t c = c0 + cl;
+          if (c >= t.n) break;
+          const int pos = cl * E;
+          const uint64_t pair = rb[pos >> 5] | ((uint64_t)rb[(pos >> 5) + 1] << 32);
+          uint32_t val = (uint32_t)(pair >> (pos & 31)) & t.emask;
+          if (t.elem_bytes == 1) {
+            uint8_t* dst = static_cast<uint8_t*>(t.C) + r * t.ldc + c;
+            if (t.add) {
+              const uint32_t old = *dst;
+              bad |= old > t.emask;
+              val ^= old & t.emask;
+            }
+            *dst = (uint8_t)val;
+          } else {
+            uint16_t* dst = static_cast<uint16_t*>(t.C) + r * t.ldc + c;
+            if (t.add) {
+              const uint32_t old = *dst;
+              bad |= old > t.emask;
+              val ^= old & t.emask;
+            }
+            *dst = (uint16_t)val;
           }
-          *dst = (uint8_t)val;
-        } else {
-          uint16_t* dst = static_cast<uint16_t*>(t.C) + r * t.ldc + c;
-          if (t.add) {
-            const uint32_t old = *dst;
-            bad |= old > t.emask;
-            val ^= old & t.emask;
-          }
-          *dst = (uint16_t)val;
         }
       }
       if (bad) atomicOr(p.status, kStatusRange);

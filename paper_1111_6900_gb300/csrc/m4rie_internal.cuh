@@ -19,10 +19,12 @@ enum PlaneFmt : int {
 
 constexpr int kMaxMasks = 128;
 
-// Layout of the planes generated from one input matrix (A, or B read column
-// by column).  Mask q = (b * nb + i) * kb + j produces the entries of input row
-// r at element offset  b*bstride + orow(r, i)*ld + j*Kp + t,
-// orow(r, i) = (r / G) * nb * G + i * G + (r % G).
+// Layout of the planes generated from one input matrix (A, or B transposed).
+// Mask q = (b * nb + i) * kb + j produces the entries of input row r at
+// element offset  b*bstride + orow(r, i)*ld + j*Kp + t, with
+//   slice-major:   orow(r, i) = (r / G) * nb * G + i * G + (r % G)
+//   element-major: orow(r, i) = (r / G) * nb * G + (r % G) * nb + i   (emajor)
+// so a group of nb*G rows holds the nb slices of G consecutive inputs.
 struct PackParams {
   const void* X;      // input elements
   int64_t ldx;        // leading dimension of X in elements
@@ -39,6 +41,7 @@ struct PackParams {
   uint32_t emask;     // 2^e - 1
   int e;              // number of slice bits of an element
   int vec;            // X and its rows are 16-byte aligned: 128-bit loads allowed
+  int emajor;         // element-major row order inside a group (see above)
   void* out;
   int* status;
   uint16_t mask[kMaxMasks];

@@ -22,8 +22,15 @@ __device__ __forceinline__ void flag_range(int* status, bool bad) {
 // halfwords per word) and, for every mask q, computes parity(x & mask_q) of
 // all of them at once: AND with the mask replicated per element, then fold the
 // element's bits onto its lowest bit (x ^= x >> 4, 2, 1 for bytes; 8, 4, 2, 1
-// for halfwords).  The 0/1 results are then laid out as bytes (0 / one),
-// nibbles or bits.  B is transposed first, so both sides read rows.
+// for halfwords; folds above the element width e are skipped).  The 0/1
+// results are laid out as bytes (0 / one), nibbles or bits.  B is transposed
+// first, so both sides read rows.
+//
+// Nibble and bit planes store the entries of each group of 8 (nibbles) or 32
+// (bits) consecutive t in a fixed permuted order within the output word, the
+// order that falls out of the SWAR words without shuffling bits around.  Both
+// operands of a product go through this kernel, so the permutation is the
+// same on both sides of every inner product and sum_t a_t b_t is unchanged.
 
 template <typename T>
 struct Swar;
@@ -31,27 +38,21 @@ template <>
 struct Swar<uint8_t> {
   static constexpr int PER = 4;  // elements per word
   static __device__ __forceinline__ uint32_t rep(uint32_t m) { return m * 0x01010101u; }
-  static __device__ __forceinline__ uint32_t parity(uint32_t y) {
-    y ^= y >> 4;
-    y ^= y >> 2;
+  static __device__ __forceinline__ uint32_t parity(uint32_t y, int e) {
+    if (e > 4) y ^= y >> 4;
+    if (e > 2) y ^= y >> 2;
     y ^= y >> 1;
     return y & 0x01010101u;  // element u's parity at bit 8u
   }
   // 4 parities -> 4 bytes (0 or one)
   static __device__ __forceinline__ uint32_t bytes(uint32_t p, uint32_t one) { return p * one; }
-  // 4 parities -> 4 nibbles (16 bits, 0 or one)
-  static __device__ __forceinline__ uint32_t nibs(uint32_t p, uint32_t one) {
-    return ((p & 1u) | ((p >> 4) & 0x10u) | ((p >> 8) & 0x100u) | ((p >> 12) & 0x1000u)) * one;
-  }
-  // 4 parities -> 4 bits
-  static __device__ __forceinline__ uint32_t bits(uint32_t p) { return (p * 0x01020408u) >> 24; }
 };
 template <>
 struct Swar<uint16_t> {
   static constexpr int PER = 2;
   static __device__ __forceinline__ uint32_t rep(uint32_t m) { return m * 0x00010001u; }
-  static __device__ __forceinline__ uint32_t parity(uint32_t y) {
-    y ^= y >> 8;
+  static __device__ __forceinline__ uint32_t parity(uint32_t y, int e) {
+    if (e > 8) y ^= y >> 8;
     y ^= y >> 4;
     y ^= y >> 2;
     y ^= y >> 1;
@@ -60,10 +61,6 @@ struct Swar<uint16_t> {
   static __device__ __forceinline__ uint32_t bytes(uint32_t p, uint32_t one) {  // 2 parities -> 2 bytes
     return ((p & 1u) | ((p >> 8) & 0x100u)) * one;
   }
-  static __device__ __forceinline__ uint32_t nibs(uint32_t p, uint32_t one) {  // 2 parities -> 8 bits
-    return ((p & 1u) | ((p >> 12) & 0x10u)) * one;
-  }
-  static __device__ __forceinline__ uint32_t bits(uint32_t p) { return (p & 1u) | ((p >> 15) & 2u); }
 };
 
 // NE consecutive elements of row r from t0 (zeros past the row end), packed.
@@ -93,7 +90,7 @@ template <typename T>
 __device__ __forceinline__ void plane_tables(const PackParams& p, int64_t* qoff, uint32_t* mrep) {
   for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
     const int b = q / (p.nb * p.kb), i = (q / p.kb) % p.nb, j = q % p.kb;
-    qoff[q] = (int64_t)b * p.bstride + (int64_t)i * p.G * p.ld + (int64_t)j * p.Kp;
+    qoff[q] = (int64_t)b * p.bstride + (int64_t)i * (p.emajor ? 1 : p.G) * p.ld + (int64_t)j * p.Kp;
     mrep[q] = Swar<T>::rep(p.mask[q]);
   }
 }
@@ -108,6 +105,7 @@ __device__ __forceinline__ void pack_planes_rows(const PackParams& p, const int6
   const int64_t t0 = tchunk * NE;
   const bool live_t = t0 < p.Kp;
   const uint32_t erep = Swar<T>::rep(p.emask);
+  const int e = p.e;
   for (int64_t r = r0; r < p.rows_p; r += rstep) {
     uint32_t v[W];
 #pragma unroll
@@ -123,37 +121,41 @@ __device__ __forceinline__ void pack_planes_rows(const PackParams& p, const int6
     if (!live_t) continue;
     // row offset of input row r in the plane layout (32-bit division: r < 2^31, G < 2^16)
     const uint32_t rr = (uint32_t)r, G = (uint32_t)p.G, g = rr / G;
-    const int64_t base = ((int64_t)g * p.nb * G + (rr - g * G)) * p.ld + t0;
+    const int64_t base = ((int64_t)g * p.nb * G + (int64_t)(rr - g * G) * (p.emajor ? p.nb : 1)) * p.ld + t0;
     for (int q = 0; q < p.P; ++q) {
       const uint32_t m = mrep[q];
       const int64_t o = qoff[q] + base;
       if (FMT == kFmtBit) {
+        // parity words of 4 (u8) or 2 (u16) elements at bits 8u / 16u: word k
+        // shifted by k interleaves them into 32 distinct bits (permuted order)
         uint32_t word = 0;
 #pragma unroll
-        for (int k = 0; k < W; ++k) word |= Swar<T>::bits(Swar<T>::parity(v[k] & m)) << (Swar<T>::PER * k);
+        for (int k = 0; k < W; ++k) word |= Swar<T>::parity(v[k] & m, e) << k;
         static_cast<uint32_t*>(p.out)[o / 32] = word;
       } else if (FMT == kFmtByte) {
         uint32_t w[4];
         if (sizeof(T) == 1) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) w[k] = Swar<T>::bytes(Swar<T>::parity(v[k] & m), p.one);
+          for (int k = 0; k < 4; ++k) w[k] = Swar<T>::bytes(Swar<T>::parity(v[k] & m, e), p.one);
         } else {
 #pragma unroll
           for (int k = 0; k < 4; ++k)
-            w[k] = Swar<T>::bytes(Swar<T>::parity(v[2 * k] & m), p.one) |
-                   (Swar<T>::bytes(Swar<T>::parity(v[2 * k + 1] & m), p.one) << 16);
+            w[k] = Swar<T>::bytes(Swar<T>::parity(v[2 * k] & m, e), p.one) |
+                   (Swar<T>::bytes(Swar<T>::parity(v[2 * k + 1] & m, e), p.one) << 16);
         }
         *reinterpret_cast<uint4*>(static_cast<uint8_t*>(p.out) + o) = make_uint4(w[0], w[1], w[2], w[3]);
       } else {
+        // 16 entries -> 16 nibbles: parity words (at bits 8u or 16u) shifted by
+        // 4 k interleave into distinct nibbles (permuted order), times `one`
         uint32_t w[2] = {0, 0};
         if (sizeof(T) == 1) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) w[k >> 1] |= Swar<T>::nibs(Swar<T>::parity(v[k] & m), p.one) << (16 * (k & 1));
+          for (int k = 0; k < 4; ++k) w[k >> 1] |= Swar<T>::parity(v[k] & m, e) << (4 * (k & 1));
         } else {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) w[k >> 2] |= Swar<T>::nibs(Swar<T>::parity(v[k] & m), p.one) << (8 * (k & 3));
+          for (int k = 0; k < 8; ++k) w[k >> 2] |= Swar<T>::parity(v[k] & m, e) << (4 * (k & 3));
         }
-        *reinterpret_cast<uint2*>(static_cast<uint8_t*>(p.out) + o / 2) = make_uint2(w[0], w[1]);
+        *reinterpret_cast<uint2*>(static_cast<uint8_t*>(p.out) + o / 2) = make_uint2(w[0] * p.one, w[1] * p.one);
       }
     }
   }
