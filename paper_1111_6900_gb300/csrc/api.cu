@@ -251,6 +251,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.status = ctx->d_status;
     tp.mode = 0;
     tp.wait_limit_ns = ctx->wait_limit_ns;
+    tp.f4nv = ctx->f4nv;
     if (form == M4RIE_FORM_MMA_S8) err = launch_mma_s8(Ap, Bp, ld_bytes, tp, ctx->stream, &ctx->launches);
     else err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld_bytes, tp, ctx->num_sms, ctx->stream, &ctx->launches);
   }
@@ -366,6 +367,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     tp.ldp = ldp;
     tp.p_bstride = Mp * ldp;
     tp.wait_limit_ns = ctx->wait_limit_ns;
+    tp.f4nv = ctx->f4nv;
     err = launch_tc(fi.fmt, Ap, (int64_t)r * Mp, Bp, (int64_t)r * Np, ld_bytes, tp, ctx->num_sms, ctx->stream,
                     &ctx->launches);
   }
@@ -434,6 +436,7 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
     return M4RIE_ERR_CUDA;
   }
   if (const char* s = getenv("M4RIE_TC_CHUNK")) ctx->tc_chunk = std::max(128, atoi(s));
+  if (const char* s = getenv("M4RIE_F4_KIND")) ctx->f4nv = strcmp(s, "nvf4") == 0 ? 1 : 0;
   *out = ctx;
   return M4RIE_OK;
 }

@@ -27,6 +27,7 @@ struct m4rie_ctx {
   int64_t launches = 0;
   uint64_t wait_limit_ns = 4000000000ull;
   int tc_chunk = 4096;  // elements of K' per FP32 accumulation chunk
+  int f4nv = 0;         // FP4 form: kind::mxf4nvf4 instead of kind::mxf4
   int auto_form[11][4];   // [e][size class] -> form, 0 = heuristic
   int auto_sched[11][4];
   // phase timing (m4rie_enable_timing)

@@ -105,10 +105,11 @@ __host__ __device__ constexpr uint32_t idesc_f8(int M, int N) {
   return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Instruction descriptor, kind::mxf4 (block scaled): A = B = E2M1, both
-// K-major, UE8M0 scale factors (scale-factor ids 0), dense K = 64, D = F32.
-__host__ __device__ constexpr uint32_t idesc_f4(int M, int N) {
-  return (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | (1u << 23) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor, kind::mxf4 / kind::mxf4nvf4 (block scaled): A = B
+// = E2M1, both K-major, scale factors UE8M0 (mxf4) or UE4M3 (nvf4), scale-factor
+// ids 0, dense K = 64, D = F32.
+__host__ __device__ constexpr uint32_t idesc_f4(int M, int N, bool nv) {
+  return (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | (nv ? 0u : (1u << 23)) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -121,13 +122,22 @@ __device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint3
 
 // D (+)= A * B with per-32-element block scales read from tensor memory
 // (all scales are 2^0 here, so the products are the plain 0/1 counts).
+template <bool NV>
 __device__ __forceinline__ void mma_f4(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t sf,
                                        uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %5, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%4], p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(sf), "r"(acc)
-      : "memory");
+  if (NV)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %5, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::mxf4nvf4.block_scale.scale_vec::4X [%0], %1, %2, %3, [%4], [%4], p;\n}\n" ::
+            "r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(sf), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %5, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%4], p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(sf), "r"(acc)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -223,8 +233,9 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
 }
 
 // BATCHED: p.batch = number of jobs, p.tiles_m = total tiles, p.tiles_n = 1;
-// per-tile parameters come from jobs[].
-template <int FMT, bool BATCHED>
+// per-tile parameters come from jobs[].  NV (FP4 only): kind::mxf4nvf4 with
+// UE4M3 scales per 16 entries instead of kind::mxf4 with UE8M0 per 32.
+template <int FMT, bool BATCHED, bool NV = false>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ TcParams p, const TcJob* __restrict__ jobs) {
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // the four epilogue warps (each owns 32 TMEM lanes).
     if (warp >= 2) {
       uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + SF_COL;
-      const uint32_t v = 0x7F7F7F7Fu;
+      const uint32_t v = NV ? 0x38383838u : 0x7F7F7F7Fu;  // 1.0 as UE4M3 / UE8M0
       asm volatile(
           "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
           "r"(v)
@@ -344,7 +355,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
         TileV t;
         get_tile<BATCHED>(p, jobs, &tmA, &tmB, tile, jc, t);
-        const uint32_t idesc = FMT == kFmtNib ? idesc_f4(128, t.BN) : idesc_f8(128, t.BN);
+        const uint32_t idesc = FMT == kFmtNib ? idesc_f4(128, t.BN, NV) : idesc_f8(128, t.BN);
         for (int kb0 = 0; kb0 < t.kblocks && ok; kb0 += t.kc) {
           const int kb1 = min(kb0 + t.kc, t.kblocks);
           const int buf = chunk & 1;
@@ -365,7 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA: 32 FP8 or 64 FP4 entries
               const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
-              if (FMT == kFmtNib) mma_f4(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, sf, acc);
+              if (FMT == kFmtNib) mma_f4<NV>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, sf, acc);
               else mma_f8(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, acc);
             }
             mma_commit(empty0 + 8 * stage);
@@ -550,7 +561,8 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
   if (!tc_make_map(&ma, Aplanes, a_rows, ld_bytes, 128) || !tc_make_map(&mb, Bplanes, b_rows, ld_bytes, p.BN))
     return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes();
-  auto kernel = fmt == kFmtNib ? tc_kernel<kFmtNib, false> : tc_kernel<kFmtByte, false>;
+  auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true> : tc_kernel<kFmtNib, false, false>)
+                               : tc_kernel<kFmtByte, false>;
   cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int64_t total = (int64_t)p.batch * p.tiles_m * p.tiles_n;
