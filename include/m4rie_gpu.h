@@ -169,6 +169,25 @@ m4rie_status m4rie_validate(int e, uint32_t f, int64_t m, int64_t n, int64_t k, 
 int m4rie_schedule_masks(int e, uint32_t f, int schedule, int cap, uint16_t *amask, uint16_t *bmask,
                          uint64_t *out_mask);
 
+/* Autotuner: run every form x schedule x tile raster on synthetic inputs of
+ * shape (e, m, n, k) (device memory is allocated for the run and freed), drop
+ * any candidate whose output differs from the first candidate's, time the
+ * rest with CUDA events on the context's stream, and make the fastest the
+ * AUTO choice for the shape class (e, floor(log2(m*n*k))).  Synchronous.
+ * The context's explicit form and schedule settings are left unchanged. */
+m4rie_status m4rie_tune(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k);
+
+/* The autotuned choice for the shape class of (e, m, n, k): form and
+ * schedule (0 when the class was not tuned) and its measured milliseconds. */
+m4rie_status m4rie_tuned_choice(m4rie_ctx *ctx, int e, int64_t m, int64_t n, int64_t k, int *form, int *schedule,
+                                double *ms);
+
+/* Save / load the tuned choices as a text file (one line per shape class).
+ * m4rie_create loads the file named by the environment variable
+ * M4RIE_TUNE_CACHE when it exists. */
+m4rie_status m4rie_tune_save(m4rie_ctx *ctx, const char *path);
+m4rie_status m4rie_tune_load(m4rie_ctx *ctx, const char *path);
+
 /* Form that AUTO picks for this shape (after m4rie_tune, the measured best). */
 int m4rie_resolve_form(m4rie_ctx *ctx, int e, int64_t m, int64_t n, int64_t k);
 

@@ -64,6 +64,11 @@ def _load() -> ctypes.CDLL:
         "m4rie_set_wait_limit_ns": (i32, [vp, u64]),
         "m4rie_enable_timing": (i32, [vp, i32]),
         "m4rie_mul_noalloc": (i32, [i32, u32, i64, i64, i64, vp, vp, vp, i32, vp, vp]),
+        "m4rie_tune": (i32, [vp, i32, u32, i64, i64, i64]),
+        "m4rie_tuned_choice": (i32, [vp, i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(ctypes.c_double)]),
+        "m4rie_tune_save": (i32, [vp, ctypes.c_char_p]),
+        "m4rie_tune_load": (i32, [vp, ctypes.c_char_p]),
         "m4rie_phase_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]),
     }
@@ -215,6 +220,25 @@ class Context:
         self._raise(lib.m4rie_phase_times(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                           ctypes.byref(n), 1 if reset else 0), "m4rie_phase_times")
         return a.value, b.value, c.value, n.value
+
+    def tune(self, e: int, f: int, m: int, n: int, k: int):
+        """Autotune the shape class of (e, m, n, k); returns (form, schedule, ms)."""
+        self._raise(lib.m4rie_tune(self.handle, e, f, m, n, k), "m4rie_tune")
+        return self.tuned_choice(e, m, n, k)
+
+    def tuned_choice(self, e: int, m: int, n: int, k: int):
+        fo, sc, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._raise(lib.m4rie_tuned_choice(self.handle, e, m, n, k, ctypes.byref(fo), ctypes.byref(sc),
+                                           ctypes.byref(ms)), "m4rie_tuned_choice")
+        inv_f = {v: k for k, v in FORMS.items()}
+        inv_s = {v: k for k, v in SCHEDULES.items()}
+        return inv_f.get(fo.value, fo.value), inv_s.get(sc.value, sc.value), ms.value
+
+    def tune_save(self, path: str):
+        self._raise(lib.m4rie_tune_save(self.handle, path.encode()), "m4rie_tune_save")
+
+    def tune_load(self, path: str):
+        self._raise(lib.m4rie_tune_load(self.handle, path.encode()), "m4rie_tune_load")
 
     def device_status(self) -> int:
         return lib.m4rie_get_device_status(self.handle)

@@ -103,26 +103,30 @@ m4rie_status ensure_ws(m4rie_ctx* ctx, size_t bytes) {
   return M4RIE_OK;
 }
 
-int size_class(int64_t m, int64_t n, int64_t k) {
-  const double v = (double)m * (double)n * (double)k;
-  if (v < 1.0e7) return 0;
-  if (v < 1.0e9) return 1;
-  if (v < 2.0e10) return 2;
-  return 3;
-}
-
+// AUTO choices: the autotuned entry of the shape class if there is one, else a
+// fixed rule from the measurements on GB300 (tcgen05 FP4 above ~2^21 field
+// multiply-adds, Karatsuba above ~2^27; the bit-packed form for small shapes).
 int resolve_form(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k) {
   if (ctx->form != M4RIE_FORM_AUTO) return ctx->form;
-  const int sc = size_class(m, n, k);
-  if (ctx->auto_form[e][sc]) return ctx->auto_form[e][sc];
-  return sc >= 2 ? M4RIE_FORM_TC_F8 : M4RIE_FORM_POPC;
+  const TuneEntry& t = ctx->tuned[e][shape_class(m, n, k)];
+  if (t.form) return t.form;
+  return shape_class(m, n, k) >= 21 ? M4RIE_FORM_TC_F4 : M4RIE_FORM_POPC;
 }
 
 int resolve_schedule(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k) {
   if (ctx->schedule != M4RIE_SCHED_AUTO) return ctx->schedule;
-  const int sc = size_class(m, n, k);
-  if (ctx->auto_sched[e][sc]) return ctx->auto_sched[e][sc];
-  return M4RIE_SCHED_ALPHA_B;
+  const TuneEntry& t = ctx->tuned[e][shape_class(m, n, k)];
+  if (t.form) return t.sched;
+  return shape_class(m, n, k) >= 27 ? M4RIE_SCHED_KARATSUBA : M4RIE_SCHED_ALPHA_B;
+}
+
+int resolve_group_m(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k, int tiles_m) {
+  int g = ctx->group_m;
+  if (ctx->form == M4RIE_FORM_AUTO) {
+    const TuneEntry& t = ctx->tuned[e][shape_class(m, n, k)];
+    if (t.form) g = t.group_m;
+  }
+  return g > 0 ? std::min(g, tiles_m) : tiles_m;
 }
 
 struct FormInfo {
@@ -242,7 +246,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     const int64_t ld_bytes = (int64_t)entries_bytes(ld, fi.bits);
     tp.kblocks = (int)ceil_div(ld_bytes, 128);
     tp.kc = std::max(1, ctx->tc_chunk / 128);
-    tp.group_m = tp.tiles_m;
+    tp.group_m = resolve_group_m(ctx, e, m, n, k, tp.tiles_m);
     tp.C = C;
     tp.ldc = n;
     tp.elem_bytes = elem_bytes(e);
@@ -360,7 +364,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     const int64_t ld_bytes = (int64_t)entries_bytes(Kp, fi.bits);
     tp.kblocks = (int)ceil_div(ld_bytes, 128);
     tp.kc = std::max(1, ctx->tc_chunk / 128);
-    tp.group_m = tp.tiles_m;
+    tp.group_m = resolve_group_m(ctx, e, m, n, k, tp.tiles_m);
     tp.C = Pp;
     tp.status = ctx->d_status;
     tp.mode = 2;
@@ -424,8 +428,6 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
   m4rie_ctx* ctx = new m4rie_ctx();
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->device = dev;
-  memset(ctx->auto_form, 0, sizeof(ctx->auto_form));
-  memset(ctx->auto_sched, 0, sizeof(ctx->auto_sched));
   err = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (err == cudaSuccess) err = cudaMalloc(&ctx->d_status, sizeof(int));
   if (err == cudaSuccess) err = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
@@ -437,6 +439,7 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
   }
   if (const char* s = getenv("M4RIE_TC_CHUNK")) ctx->tc_chunk = std::max(128, atoi(s));
   if (const char* s = getenv("M4RIE_F4_KIND")) ctx->f4nv = strcmp(s, "nvf4") == 0 ? 1 : 0;
+  if (const char* s = getenv("M4RIE_TUNE_CACHE")) m4rie_tune_load(ctx, s);  // a missing file is not an error
   *out = ctx;
   return M4RIE_OK;
 }

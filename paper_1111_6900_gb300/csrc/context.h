@@ -10,6 +10,11 @@
 namespace m4rie {
 struct BatchedPlan;
 void destroy_plan(BatchedPlan* plan);
+struct TuneEntry {
+  int form = 0, sched = 0, group_m = 0;
+  double ms = 0;
+};
+int shape_class(int64_t m, int64_t n, int64_t k);  // floor(log2(m*n*k)), tune.cu
 }  // namespace m4rie
 
 struct m4rie_ctx {
@@ -28,8 +33,8 @@ struct m4rie_ctx {
   uint64_t wait_limit_ns = 4000000000ull;
   int tc_chunk = 4096;  // elements of K' per FP32 accumulation chunk
   int f4nv = 0;         // FP4 form: kind::mxf4nvf4 instead of kind::mxf4
-  int auto_form[11][4];   // [e][size class] -> form, 0 = heuristic
-  int auto_sched[11][4];
+  int group_m = 0;      // tcgen05 tile raster: m-tiles per column group (0: all m-tiles)
+  m4rie::TuneEntry tuned[11][64];  // [e][floor(log2(m*n*k))] -> autotuned choice (form 0: none)
   // phase timing (m4rie_enable_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
