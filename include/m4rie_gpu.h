@@ -247,6 +247,14 @@ m4rie_status m4rie_set_wait_limit_ns(m4rie_ctx *ctx, uint64_t ns);
 m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void *A, const void *B,
                                void *C, int accumulate, int *device_status, void *stream);
 
+/* Test hook for failure detection: flags & 1 makes every later tcgen05 GEMM
+ * launch of this context first wait on a barrier that nothing signals, so that
+ * its bounded wait runs out (after the m4rie_set_wait_limit_ns limit), the
+ * kernel sets M4RIE_ERR_TIMEOUT, stops and returns; its output is then
+ * incomplete.  flags = 0 restores normal operation.  M4RIE_ERR_ARG for
+ * unknown flags. */
+m4rie_status m4rie_set_test_hook(m4rie_ctx *ctx, int flags);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,7 @@ def _load() -> ctypes.CDLL:
         "m4rie_enable_timing": (i32, [vp, i32]),
         "m4rie_mul_noalloc": (i32, [i32, u32, i64, i64, i64, vp, vp, vp, i32, vp, vp]),
         "m4rie_tune": (i32, [vp, i32, u32, i64, i64, i64]),
+        "m4rie_set_test_hook": (i32, [vp, i32]),
         "m4rie_tuned_choice": (i32, [vp, i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(ctypes.c_double)]),
         "m4rie_tune_save": (i32, [vp, ctypes.c_char_p]),
@@ -139,6 +140,9 @@ class Context:
 
     def set_schedule(self, schedule):
         self._raise(lib.m4rie_set_schedule(self.handle, SCHEDULES.get(schedule, schedule)), "m4rie_set_schedule")
+
+    def set_test_hook(self, flags: int):
+        self._raise(lib.m4rie_set_test_hook(self.handle, int(flags)), "m4rie_set_test_hook")
 
     def set_wait_limit_ns(self, ns: int):
         self._raise(lib.m4rie_set_wait_limit_ns(self.handle, int(ns)), "m4rie_set_wait_limit_ns")
@@ -230,6 +234,8 @@ class Context:
         fo, sc, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         self._raise(lib.m4rie_tuned_choice(self.handle, e, m, n, k, ctypes.byref(fo), ctypes.byref(sc),
                                            ctypes.byref(ms)), "m4rie_tuned_choice")
+        if fo.value == 0:
+            return None, None, 0.0          # shape class not tuned
         inv_f = {v: k for k, v in FORMS.items()}
         inv_s = {v: k for k, v in SCHEDULES.items()}
         return inv_f.get(fo.value, fo.value), inv_s.get(sc.value, sc.value), ms.value

@@ -256,6 +256,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.mode = 0;
     tp.wait_limit_ns = ctx->wait_limit_ns;
     tp.f4nv = ctx->f4nv;
+    tp.stall_test = ctx->stall_test;
     if (form == M4RIE_FORM_MMA_S8) err = launch_mma_s8(Ap, Bp, ld_bytes, tp, ctx->stream, &ctx->launches);
     else err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld_bytes, tp, ctx->num_sms, ctx->stream, &ctx->launches);
   }
@@ -372,6 +373,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     tp.p_bstride = Mp * ldp;
     tp.wait_limit_ns = ctx->wait_limit_ns;
     tp.f4nv = ctx->f4nv;
+    tp.stall_test = ctx->stall_test;
     err = launch_tc(fi.fmt, Ap, (int64_t)r * Mp, Bp, (int64_t)r * Np, ld_bytes, tp, ctx->num_sms, ctx->stream,
                     &ctx->launches);
   }
@@ -672,6 +674,12 @@ m4rie_status m4rie_phase_times(m4rie_ctx* ctx, double* pack_ms, double* gemm_ms,
     ctx->phase_ms[0] = ctx->phase_ms[1] = ctx->phase_ms[2] = 0;
     ctx->timed_products = 0;
   }
+  return M4RIE_OK;
+}
+
+m4rie_status m4rie_set_test_hook(m4rie_ctx* ctx, int flags) {
+  if (!ctx || (flags & ~1)) return M4RIE_ERR_ARG;
+  ctx->stall_test = flags & 1;
   return M4RIE_OK;
 }
 

@@ -33,6 +33,7 @@ struct m4rie_ctx {
   uint64_t wait_limit_ns = 4000000000ull;
   int tc_chunk = 4096;  // elements of K' per FP32 accumulation chunk
   int f4nv = 0;         // FP4 form: kind::mxf4nvf4 instead of kind::mxf4
+  int stall_test = 0;   // m4rie_set_test_hook flag 1
   int group_m = 0;      // tcgen05 tile raster: m-tiles per column group (0: all m-tiles)
   m4rie::TuneEntry tuned[11][64];  // [e][floor(log2(m*n*k))] -> autotuned choice (form 0: none)
   // phase timing (m4rie_enable_timing)

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_TILE;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_SLOT);
-  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain, never
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint32_t* sbits = tmem_slot + 4;  // [4 warps][32 rows][9 words] (8 bit words + a zero sentinel)
@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
   const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 2);
   const uint32_t drain = smem_u32(bars + 2 * STAGES + 4);
+  const uint32_t never = smem_u32(bars + 2 * STAGES + 5);  // test hook: nothing arrives on it
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -264,6 +265,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(tempty0 + 8 * b, 128);
     }
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (!BATCHED) {
@@ -404,7 +406,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t* wbits = sbits + q * 32 * 9;  // this warp's 32 rows
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     int chunk = 0, jc = 0;
-    bool ok = true;
+    // failure-detection test: a wait that can only run out
+    bool ok = !p.stall_test || __all_sync(0xffffffffu, mbar_wait(never, 0, abort_flag, p.status, lim));
     for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
       TileV t;
       get_tile<BATCHED>(p, jobs, &tmA, &tmB, tile, jc, t);

@@ -41,7 +41,7 @@ def test_autotuner_picks_a_correct_candidate_and_auto_uses_it(tmp_path):
     with open(path, "a") as fh:
         fh.write("garbage line\n4 3 99 1 0 1.0\n")   # ignored: not a valid entry
     other = m4.Context()
-    assert other.tuned_choice(e, m, n, k)[0] == 0
+    assert other.tuned_choice(e, m, n, k)[0] is None
     other.tune_load(path)
     assert other.tuned_choice(e, m, n, k)[:2] == (form, sched)
     other.close()
@@ -63,14 +63,18 @@ def test_bounded_wait_timeout_is_reported_and_context_recovers(form):
     ctx = m4.Context()
     ctx.set_form(form)
     ctx.set_schedule("alpha_b")
-    ctx.set_wait_limit_ns(0)                   # every wait that is not ready at once gives up
+    ctx.set_test_hook(1)                       # the epilogue waits on a barrier nothing signals
+    ctx.set_wait_limit_ns(200_000_000)         # 0.2 s
     ctx.mul(e, f, dA, dB)
     torch.cuda.synchronize()
     assert ctx.device_status() == m4.ERR_TIMEOUT
+    ctx.set_test_hook(0)
     ctx.set_wait_limit_ns(4_000_000_000)
     C = ctx.mul(e, f, dA, dB)
     torch.cuda.synchronize()
     assert ctx.device_status() == m4.OK
     rows = slice(0, 8)
     np.testing.assert_array_equal(C.cpu().numpy()[rows], oracle.matmul(e, f, A[rows], B))
+    with pytest.raises(m4.M4rieError):
+        ctx.set_test_hook(2)
     ctx.close()
