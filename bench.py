@@ -37,21 +37,29 @@ import workloads  # noqa: E402
 WORKLOAD = workloads.WORKLOADS[2]
 METRIC = "GF(2^e) matmul field-ops/s, 4096² GF(2^4), INT8-TC vs bit-packed; bit-exact"
 UNIT = "field-ops/s"
-CONFIG = {"workload": "C = A*B over GF(2^4), f = x^4+x+1, A, B 4096x4096 uint8",
-          "m": 4096, "n": 4096, "k": 4096, "e": 4, "f": "0x13",
-          "l2": "flushed between timed steps (512 MB write, not timed)"}
+
+
+def config_of(w):
+    op = "C = A*B" if w.op == "mul" else "C += A*B"
+    ty = "uint8" if w.e <= 8 else "uint16"
+    return {"workload": f"{op} over GF(2^{w.e}), f = {hex(w.f)}, A {w.m}x{w.k}, B {w.k}x{w.n} {ty}",
+            "m": w.m, "n": w.n, "k": w.k, "e": w.e, "f": hex(w.f), "op": w.op,
+            "l2": "flushed between timed steps (512 MB write, not timed)"}
+
+
+CONFIG = config_of(WORKLOAD)
 
 
 # DRAM traffic per launch of the dominant kernel, from the committed ncu
 # summaries (dram__bytes_read.sum + dram__bytes_write.sum).  It is reported only
 # while the kernel source is the one that was profiled (sha256 below).
 TRAFFIC = {
-    "tc_f4/karatsuba": {"bytes": 154.013952e6 + 14.110208e6, "source": "profiles/tc_f4_karatsuba_gf16_4096.md"},
-    "tc_f8/karatsuba": {"bytes": 302.068480e6 + 17.802752e6, "source": "profiles/tc_f8_karatsuba_gf16_4096.md"},
+    "tc_f4/karatsuba": {"bytes": 1.540147e+08 + 1.418368e+07, "source": "profiles/tc_f4_karatsuba_gf16_4096.md"},
+    "tc_f8/karatsuba": {"bytes": 3.021770e+08 + 1.822080e+07, "source": "profiles/tc_f8_karatsuba_gf16_4096.md"},
     "popc/alpha_b": {"bytes": 41.965824e6 + 0.164864e6, "source": "profiles/popc_alpha_b_gf16_4096.md"},
 }
-PROFILED_SOURCES = {"tc_f4/karatsuba": ("gemm_tc.cu", "a2b2b25168aa9d4b418165bd6fce5cc403dd70299ed57fbbaebd871733189b93"),
-                    "tc_f8/karatsuba": ("gemm_tc.cu", "a2b2b25168aa9d4b418165bd6fce5cc403dd70299ed57fbbaebd871733189b93"),
+PROFILED_SOURCES = {"tc_f4/karatsuba": ("gemm_tc.cu", "7b2fd2fc93bf9e2259876e4832b4b6807df96f0a6d9152e82c431b60434de01a"),
+                    "tc_f8/karatsuba": ("gemm_tc.cu", "7b2fd2fc93bf9e2259876e4832b4b6807df96f0a6d9152e82c431b60434de01a"),
                     "popc/alpha_b": ("gemm_popc.cu", "6fc3d0a61765ce47396627acb19770a9ddecc498caad76ea310bae7c899f3a1b")}
 
 
@@ -162,10 +170,11 @@ def cpu_baseline(rows: int = 256):
     """The oracle on a row panel of the workload (bounded CPU work)."""
     import oracle
     w = WORKLOAD
-    A, B, _ = w.inputs()
+    rows = max(8, min(rows, int(256 * 4096 * 4096 / (w.k * w.n))))   # about a second of 16 cores
+    A, B, C0 = w.inputs()
     Ap = np.ascontiguousarray(A[:rows])
     t0 = time.perf_counter()
-    ref = oracle.matmul(w.e, w.f, Ap, B)
+    ref = oracle.addmul(w.e, w.f, Ap, B, C0[:rows]) if C0 is not None else oracle.matmul(w.e, w.f, Ap, B)
     dt = time.perf_counter() - t0
     return ({"value": 2.0 * rows * w.n * w.k / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
              "sample": f"rows 0..{rows - 1} of A times B ({rows}x{w.k}x{w.n}), one run, {dt:.2f} s"}, ref)
@@ -257,8 +266,9 @@ def main():
     ap.add_argument("--schedules", default="alpha_b,karatsuba")
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="gf16_4096", choices=["gf16_4096", "batched"],
-                    help="gf16_4096: the 4096^3 GF(2^4) product (default); batched: the 4096-instance batch")
+    names = {w.name: i for i, w in workloads.WORKLOADS.items()}
+    ap.add_argument("--workload", default="gf16_4096_mul", choices=sorted(names) + ["batched"],
+                    help="gf16_4096_mul (default, the headline), another single-product workload, or batched")
     ap.add_argument("--batched-count", type=int, default=workloads.BATCHED_COUNT,
                     help="instances of the batched workload (a prefix of it; the default is the whole batch)")
     ap.add_argument("--single", default=None,
@@ -282,11 +292,19 @@ def main():
     if args.workload == "batched":
         return run_batched_workload(args, m4, torch, world, rank, local)
 
+    global WORKLOAD, CONFIG
+    WORKLOAD = workloads.WORKLOADS[names[args.workload]]
+    CONFIG = config_of(WORKLOAD)
+    metric = METRIC if WORKLOAD.name == "gf16_4096_mul" else f"GF(2^e) matmul field-ops/s, {WORKLOAD.name}; bit-exact"
     w = WORKLOAD
-    A, B, _ = w.inputs()
+    A, B, C0 = w.inputs()
     dA = torch.from_numpy(A).cuda()
     dB = torch.from_numpy(B).cuda()
-    dC = torch.empty((w.m, w.n), dtype=torch.uint8, device="cuda")
+    dC = torch.from_numpy(C0).cuda() if C0 is not None else torch.empty((w.m, w.n), dtype=dA.dtype, device="cuda")
+    add = w.op == "addmul"
+
+    def step(C):
+        return ctx.addmul(w.e, w.f, dA, dB, C) if add else ctx.mul(w.e, w.f, dA, dB, C)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     ctx = m4.Context(stream)
@@ -302,16 +320,18 @@ def main():
         ctx.set_form(form)
         ctx.set_schedule(sched)
         for _ in range(args.warmup + 1):
-            ctx.mul(w.e, w.f, dA, dB, dC)
+            step(dC)
         torch.cuda.synchronize()
         status = ctx.device_status()
         ctx.close()
         return 0 if status == m4.OK else 1
 
     # reference result on the device: every form must reproduce it bit for bit
+    # (for addmul: one application to the preloaded C)
     ctx.set_form("popc")
     ctx.set_schedule("alpha_b")
-    C_ref = ctx.mul(w.e, w.f, dA, dB)
+    C_ref = dC.clone() if add else torch.empty_like(dC)
+    step(C_ref)
     torch.cuda.synchronize()
 
     results = {}
@@ -322,8 +342,14 @@ def main():
             ctx.set_form(form)
             ctx.set_schedule(sched)
             try:
+                check = dC.clone() if add else dC
+                if add:
+                    check.copy_(torch.from_numpy(C0))
+                step(check)
+                torch.cuda.synchronize()
+                verified = bool(torch.equal(check, C_ref))
                 for _ in range(args.warmup):
-                    ctx.mul(w.e, w.f, dA, dB, dC)
+                    step(dC)
                 torch.cuda.synchronize()
             except m4.M4rieError as err:
                 results[f"{form}/{sched}"] = {"error": str(err)}
@@ -340,7 +366,7 @@ def main():
                 for i in range(args.steps):
                     flush.fill_(i & 0xFF)
                     starts[i].record(stream)
-                    ctx.mul(w.e, w.f, dA, dB, dC)
+                    step(dC)
                     stops[i].record(stream)
                 barrier()
                 clk.mark_end()
@@ -351,7 +377,6 @@ def main():
             _, sec = replica_throughput(w.field_ops, ms * 1e-3, "cuda")
             ms = sec * 1e3
             status = ctx.device_status()
-            verified = bool(torch.equal(dC, C_ref))
             results[f"{form}/{sched}"] = {
                 "verified": verified,
                 "ms_per_step": ms, "value": world * w.field_ops / (ms * 1e-3),
@@ -373,14 +398,14 @@ def main():
     # end-to-end: host buffers through the C ABI (pinned), copies inside the timed region
     hA = torch.from_numpy(A).pin_memory()
     hB = torch.from_numpy(B).pin_memory()
-    hC = torch.empty((w.m, w.n), dtype=torch.uint8).pin_memory()
+    hC = (torch.from_numpy(C0) if add else torch.empty((w.m, w.n), dtype=dA.dtype)).pin_memory()
     for _ in range(2):
-        ctx.mul_host(w.e, w.f, hA, hB, hC)
+        ctx.mul_host(w.e, w.f, hA, hB, hC, accumulate=add)
     barrier()
     t0 = time.perf_counter()
     e2e_steps = max(3, args.steps // 4)
     for _ in range(e2e_steps):
-        ctx.mul_host(w.e, w.f, hA, hB, hC)
+        ctx.mul_host(w.e, w.f, hA, hB, hC, accumulate=add)
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     _, e2e_s = replica_throughput(w.field_ops, e2e_s, "cuda")
@@ -411,14 +436,15 @@ def main():
                 "frac": flops / gemm_s / 1e12 / peak, "traffic": kernel_traffic(f"{form}/{sched}"),
                 "peak_source": src}
 
-    out = {"metric": METRIC, "value": best["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    out = {"metric": metric, "value": best["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": best["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
            "config": dict(CONFIG, form=form, schedule=sched, parallelism=f"replicas{world}"),
            "clocks": best["clocks"], "gpu_launches": best["launches"],
            "autotuned": {"form": tuned[0], "schedule": tuned[1], "ms": tuned[2]},
            "e2e": {"value": world * w.field_ops / e2e_s, "unit": UNIT,
-                   "h2d_bytes_per_step": A.nbytes + B.nbytes, "d2h_bytes_per_step": w.m * w.n},
+                   "h2d_bytes_per_step": A.nbytes + B.nbytes + (hC.numel() * hC.element_size() if add else 0),
+                   "d2h_bytes_per_step": hC.numel() * hC.element_size()},
            "roofline": roof,
            "forms": {k: ({"value": v["value"], "verified": v["verified"], "ms_per_step": v["ms_per_step"],
                           "gemm_ms": v["gemm_ms"],
