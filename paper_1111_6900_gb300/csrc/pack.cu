@@ -38,33 +38,36 @@ template <>
 struct Swar<uint8_t> {
   static constexpr int PER = 4;  // elements per word
   static __device__ __forceinline__ uint32_t rep(uint32_t m) { return m * 0x01010101u; }
-  static __device__ __forceinline__ uint32_t parity(uint32_t y, int e) {
-    if (e > 4) y ^= y >> 4;
-    if (e > 2) y ^= y >> 2;
+  // FOLD = 1, 2, 3 folds cover elements of <= 2, 4, 8 bits
+  template <int FOLD>
+  static __device__ __forceinline__ uint32_t parity(uint32_t y) {
+    if (FOLD >= 3) y ^= y >> 4;
+    if (FOLD >= 2) y ^= y >> 2;
     y ^= y >> 1;
     return y & 0x01010101u;  // element u's parity at bit 8u
   }
-  // 4 parities -> 4 bytes (0 or one)
-  static __device__ __forceinline__ uint32_t bytes(uint32_t p, uint32_t one) { return p * one; }
 };
 template <>
 struct Swar<uint16_t> {
   static constexpr int PER = 2;
   static __device__ __forceinline__ uint32_t rep(uint32_t m) { return m * 0x00010001u; }
-  static __device__ __forceinline__ uint32_t parity(uint32_t y, int e) {
-    if (e > 8) y ^= y >> 8;
+  template <int FOLD>
+  static __device__ __forceinline__ uint32_t parity(uint32_t y) {
+    y ^= y >> 8;
     y ^= y >> 4;
     y ^= y >> 2;
     y ^= y >> 1;
     return y & 0x00010001u;  // element u's parity at bit 16u
   }
-  static __device__ __forceinline__ uint32_t bytes(uint32_t p, uint32_t one) {  // 2 parities -> 2 bytes
-    return ((p & 1u) | ((p >> 8) & 0x100u)) * one;
-  }
 };
 
+// Parity-fold depth for e-bit elements in T.
+inline int fold_of(int e) { return e <= 2 ? 1 : e <= 4 ? 2 : 3; }
+
+constexpr int NE = 32;  // elements per thread
+
 // NE consecutive elements of row r from t0 (zeros past the row end), packed.
-template <typename T, int NE>
+template <typename T>
 __device__ __forceinline__ void load_row(const PackParams& p, int64_t r, int64_t t0, uint32_t (&v)[NE * sizeof(T) / 4]) {
   constexpr int W = NE * (int)sizeof(T) / 4;
   const T* row = static_cast<const T*>(p.X) + r * p.ldx;
@@ -97,20 +100,18 @@ __device__ __forceinline__ void plane_tables(const PackParams& p, int64_t* qoff,
 
 // Rows r0, r0 + rstep, ... of one plane job; this thread's elements start at
 // t0 = tchunk * NE (threads with t0 >= Kp only join the warp-wide votes).
-template <typename T, int FMT>
+template <typename T, int FMT, int FOLD>
 __device__ __forceinline__ void pack_planes_rows(const PackParams& p, const int64_t* qoff, const uint32_t* mrep,
                                                  int64_t tchunk, int64_t r0, int64_t rstep) {
-  constexpr int NE = FMT == kFmtBit ? 32 : 16;  // elements per thread
-  constexpr int W = NE * (int)sizeof(T) / 4;    // packed input words per thread
+  constexpr int W = NE * (int)sizeof(T) / 4;  // packed input words per thread
   const int64_t t0 = tchunk * NE;
   const bool live_t = t0 < p.Kp;
   const uint32_t erep = Swar<T>::rep(p.emask);
-  const int e = p.e;
   for (int64_t r = r0; r < p.rows_p; r += rstep) {
     uint32_t v[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) v[k] = 0;
-    if (live_t && r < p.rows) load_row<T, NE>(p, r, t0, v);
+    if (live_t && r < p.rows) load_row<T>(p, r, t0, v);
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
@@ -122,53 +123,58 @@ __device__ __forceinline__ void pack_planes_rows(const PackParams& p, const int6
     // row offset of input row r in the plane layout (32-bit division: r < 2^31, G < 2^16)
     const uint32_t rr = (uint32_t)r, G = (uint32_t)p.G, g = rr / G;
     const int64_t base = ((int64_t)g * p.nb * G + (int64_t)(rr - g * G) * (p.emajor ? p.nb : 1)) * p.ld + t0;
+    uint8_t* out = static_cast<uint8_t*>(p.out);
+#pragma unroll 1
     for (int q = 0; q < p.P; ++q) {
       const uint32_t m = mrep[q];
       const int64_t o = qoff[q] + base;
+      uint32_t par[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) par[k] = Swar<T>::template parity<FOLD>(v[k] & m);
       if (FMT == kFmtBit) {
-        // parity words of 4 (u8) or 2 (u16) elements at bits 8u / 16u: word k
-        // shifted by k interleaves them into 32 distinct bits (permuted order)
+        // parity words (element u at bit 8u or 16u) shifted by k interleave
+        // into 32 distinct bits (permuted order)
         uint32_t word = 0;
 #pragma unroll
-        for (int k = 0; k < W; ++k) word |= Swar<T>::parity(v[k] & m, e) << k;
-        static_cast<uint32_t*>(p.out)[o / 32] = word;
+        for (int k = 0; k < W; ++k) word |= par[k] << k;
+        reinterpret_cast<uint32_t*>(out)[o / 32] = word;
       } else if (FMT == kFmtByte) {
-        uint32_t w[4];
+        uint32_t w[8];
         if (sizeof(T) == 1) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) w[k] = Swar<T>::bytes(Swar<T>::parity(v[k] & m, e), p.one);
+          for (int k = 0; k < 8; ++k) w[k] = par[k] * p.one;
         } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            w[k] = Swar<T>::bytes(Swar<T>::parity(v[2 * k] & m, e), p.one) |
-                   (Swar<T>::bytes(Swar<T>::parity(v[2 * k + 1] & m, e), p.one) << 16);
+          for (int k = 0; k < 8; ++k)
+            // two elements per parity word, at bits 0 and 16 -> bytes 4k .. 4k+3
+            w[k] = ((par[2 * k] & 1u) | ((par[2 * k] >> 8) & 0x100u) | ((par[2 * k + 1] & 1u) << 16) |
+                    ((par[2 * k + 1] >> 16) << 24)) * p.one;
         }
-        *reinterpret_cast<uint4*>(static_cast<uint8_t*>(p.out) + o) = make_uint4(w[0], w[1], w[2], w[3]);
+        uint4* d = reinterpret_cast<uint4*>(out + o);
+        d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        d[1] = make_uint4(w[4], w[5], w[6], w[7]);
       } else {
-        // 16 entries -> 16 nibbles: parity words (at bits 8u or 16u) shifted by
-        // 4 k interleave into distinct nibbles (permuted order), times `one`
-        uint32_t w[2] = {0, 0};
-        if (sizeof(T) == 1) {
+        // 32 entries -> 32 nibbles: parity words shifted by 4 j interleave
+        // into distinct nibbles (permuted order), times `one`
+        uint32_t w[4] = {0, 0, 0, 0};
+        constexpr int PW = W / 4;  // parity words per output word
 #pragma unroll
-          for (int k = 0; k < 4; ++k) w[k >> 1] |= Swar<T>::parity(v[k] & m, e) << (4 * (k & 1));
-        } else {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) w[k >> 2] |= Swar<T>::parity(v[k] & m, e) << (4 * (k & 3));
-        }
-        *reinterpret_cast<uint2*>(static_cast<uint8_t*>(p.out) + o / 2) = make_uint2(w[0] * p.one, w[1] * p.one);
+        for (int k = 0; k < W; ++k) w[k / PW] |= par[k] << (4 * (k % PW));
+        *reinterpret_cast<uint4*>(out + o / 2) = make_uint4(w[0] * p.one, w[1] * p.one, w[2] * p.one, w[3] * p.one);
       }
     }
   }
 }
 
 // grid.x covers a row in chunks of 256 threads x NE elements, grid.y strides over rows.
-template <typename T, int FMT>
+template <typename T, int FMT, int FOLD>
 __global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant__ PackParams p) {
   __shared__ int64_t qoff[kMaxMasks];
   __shared__ uint32_t mrep[kMaxMasks];
   plane_tables<T>(p, qoff, mrep);
   __syncthreads();
-  pack_planes_rows<T, FMT>(p, qoff, mrep, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, gridDim.y);
+  pack_planes_rows<T, FMT, FOLD>(p, qoff, mrep, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y,
+                                 gridDim.y);
 }
 
 // Index of the job whose block range [start[j], start[j+1]) holds block b.
@@ -196,6 +202,8 @@ __host__ __device__ inline void job_shape(int64_t Kp, int ne, int64_t& tpr, int6
 // Many plane jobs in one launch: block b belongs to job j with
 // start[j] <= b < start[j+1]; within the job, local block l covers rows
 // (l / gx) * rpb + threadIdx.x / tpr and chunk (l % gx) * 256 + threadIdx.x % tpr.
+// Jobs of one launch may have different e: the fold covers the widest (8 bits
+// for uint8, 16 for uint16); extra folds over zero bits change nothing.
 template <typename T, int FMT>
 __global__ void __launch_bounds__(256) pack_planes_batched(const PackParams* __restrict__ jobs,
                                                            const int64_t* __restrict__ start, int njobs) {
@@ -207,15 +215,14 @@ __global__ void __launch_bounds__(256) pack_planes_batched(const PackParams* __r
   const PackParams& p = jobs[sj];
   plane_tables<T>(p, qoff, mrep);
   __syncthreads();
-  constexpr int NE = FMT == kFmtBit ? 32 : 16;
   int64_t tpr, rpb, gx;
   job_shape(p.Kp, NE, tpr, rpb, gx);
   const int64_t l = (int64_t)blockIdx.x - start[sj];
   const int64_t r = (l / gx) * rpb + threadIdx.x / tpr;
   const int64_t chunk = (l % gx) * 256 + threadIdx.x % tpr;
   // rows past the job's end still run the loop body's warp votes (zero data)
-  pack_planes_rows<T, FMT>(p, qoff, mrep, r < p.rows_p ? chunk : (p.Kp + NE - 1) / NE, r < p.rows_p ? r : 0,
-                           p.rows_p);
+  pack_planes_rows<T, FMT, sizeof(T) == 1 ? 3 : 4>(p, qoff, mrep, r < p.rows_p ? chunk : (p.Kp + NE - 1) / NE,
+                                                  r < p.rows_p ? r : 0, p.rows_p);
 }
 
 // ---- Element transpose X (K x rows, row-major) -> Xt (rows x K), tiles of
@@ -338,22 +345,37 @@ __global__ void __launch_bounds__(256) cling_kernel(int e, int64_t rows, int64_t
 
 // ---- Karatsuba recombination: bit s of C[r][c] is the parity of the
 // products selected by out_mask[s] (reduction mod f folded in).  One thread
-// per (row, 32 columns): XOR the r parity words into e output slice words,
-// then transpose bits into 32 elements.
-template <typename T>
+// per (row, 32 columns): XOR the r parity words into E output slice words
+// (which products feed which slices comes from a per-block table), then
+// transpose the bits into 32 elements.
+template <typename T, int E>
 __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecombineParams p) {
+  __shared__ uint32_t qmask[64];  // bit s: product q feeds output slice s
+  for (int q = threadIdx.x; q < p.r; q += blockDim.x) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int s = 0; s < E; ++s) m |= (uint32_t)((p.out_mask[s] >> q) & 1ull) << s;
+    qmask[q] = m;
+  }
+  __syncthreads();
   const int64_t nw = (p.n + 31) / 32;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = idx < p.m * nw;
   const int64_t r = live ? idx / nw : 0, w = live ? idx % nw : 0;
-  uint32_t out[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  if (live)
-    for (int q = 0; q < p.r; ++q) {
-      const uint32_t pw = p.P[((int64_t)q * p.rows_p + r) * p.ldw + w];
+  uint32_t out[E];
 #pragma unroll
-      for (int s = 0; s < 10; ++s)
-        if (s < p.e && (p.out_mask[s] >> q & 1ull)) out[s] ^= pw;
+  for (int s = 0; s < E; ++s) out[s] = 0;
+  if (live) {
+    const uint32_t* src = p.P + r * p.ldw + w;
+    const int64_t pstride = p.rows_p * p.ldw;
+#pragma unroll 4
+    for (int q = 0; q < p.r; ++q) {
+      const uint32_t pw = __ldg(src + q * pstride);
+      const uint32_t m = qmask[q];
+#pragma unroll
+      for (int s = 0; s < E; ++s) out[s] ^= (m >> s & 1u) ? pw : 0u;
     }
+  }
   // elements c = 32 w + b, packed 4 (u8) or 2 (u16) per 32-bit word
   constexpr int PER = 4 / sizeof(T);
   constexpr int NW = 32 / PER;
@@ -362,8 +384,7 @@ __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ 
   for (int g = 0; g < NW; ++g) {
     uint32_t v = 0;
 #pragma unroll
-    for (int s = 0; s < 10; ++s) {
-      if (s >= p.e) break;
+    for (int s = 0; s < E; ++s) {
       const uint32_t bits = (out[s] >> (PER * g)) & ((1u << PER) - 1);
       const uint32_t spread = sizeof(T) == 1 ? (bits * 0x00204081u) & 0x01010101u : (bits & 1u) | ((bits >> 1) << 16);
       v |= spread << s;
@@ -418,24 +439,28 @@ cudaError_t launch(K kernel, int64_t blocks, int threads, cudaStream_t s, int64_
 
 }  // namespace
 
+template <int FMT>
+void launch_planes_fmt(const PackParams& p, dim3 grid, cudaStream_t s) {
+  if (p.elem_bytes == 2) {
+    pack_planes_kernel<uint16_t, FMT, 4><<<grid, 256, 0, s>>>(p);
+    return;
+  }
+  switch (fold_of(p.e)) {
+    case 1: pack_planes_kernel<uint8_t, FMT, 1><<<grid, 256, 0, s>>>(p); break;
+    case 2: pack_planes_kernel<uint8_t, FMT, 2><<<grid, 256, 0, s>>>(p); break;
+    default: pack_planes_kernel<uint8_t, FMT, 3><<<grid, 256, 0, s>>>(p); break;
+  }
+}
+
 cudaError_t launch_pack_planes(const PackParams& p, cudaStream_t s, int64_t* launches) {
-  const int ne = p.fmt == kFmtBit ? 32 : 16;
-  const int64_t gx = ceil_div(ceil_div(p.Kp, ne), 256);
+  const int64_t gx = ceil_div(ceil_div(p.Kp, NE), 256);
   const int64_t gy = std::min<int64_t>(p.rows_p, 65535);
   if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   if (gx <= 0 || gy <= 0) return cudaSuccess;
   const dim3 grid((unsigned)gx, (unsigned)gy);
-  const bool u16 = p.elem_bytes == 2;
-  if (p.fmt == kFmtBit) {
-    if (u16) pack_planes_kernel<uint16_t, kFmtBit><<<grid, 256, 0, s>>>(p);
-    else pack_planes_kernel<uint8_t, kFmtBit><<<grid, 256, 0, s>>>(p);
-  } else if (p.fmt == kFmtByte) {
-    if (u16) pack_planes_kernel<uint16_t, kFmtByte><<<grid, 256, 0, s>>>(p);
-    else pack_planes_kernel<uint8_t, kFmtByte><<<grid, 256, 0, s>>>(p);
-  } else {
-    if (u16) pack_planes_kernel<uint16_t, kFmtNib><<<grid, 256, 0, s>>>(p);
-    else pack_planes_kernel<uint8_t, kFmtNib><<<grid, 256, 0, s>>>(p);
-  }
+  if (p.fmt == kFmtBit) launch_planes_fmt<kFmtBit>(p, grid, s);
+  else if (p.fmt == kFmtByte) launch_planes_fmt<kFmtByte>(p, grid, s);
+  else launch_planes_fmt<kFmtNib>(p, grid, s);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -480,7 +505,7 @@ cudaError_t launch_pack_batched(const PackParams* d_jobs, const int64_t* d_start
 
 int64_t pack_job_blocks(const PackParams& p) {
   int64_t tpr, rpb, gx;
-  job_shape(p.Kp, p.fmt == kFmtBit ? 32 : 16, tpr, rpb, gx);
+  job_shape(p.Kp, NE, tpr, rpb, gx);
   return gx * ceil_div(p.rows_p, rpb);
 }
 
@@ -518,8 +543,20 @@ cudaError_t launch_cling(int e, int64_t rows, int64_t cols, const uint64_t* slic
 
 cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches) {
   const int64_t n = p.m * ((p.n + 31) / 32);
-  if (p.elem_bytes == 2) return launch(recombine_kernel<uint16_t>, ceil_div(n, 256), 256, s, launches, p);
-  return launch(recombine_kernel<uint8_t>, ceil_div(n, 256), 256, s, launches, p);
+  const int64_t g = ceil_div(n, 256);
+  if (p.r > 64) return cudaErrorInvalidValue;
+  switch (p.e) {
+    case 2: return launch(recombine_kernel<uint8_t, 2>, g, 256, s, launches, p);
+    case 3: return launch(recombine_kernel<uint8_t, 3>, g, 256, s, launches, p);
+    case 4: return launch(recombine_kernel<uint8_t, 4>, g, 256, s, launches, p);
+    case 5: return launch(recombine_kernel<uint8_t, 5>, g, 256, s, launches, p);
+    case 6: return launch(recombine_kernel<uint8_t, 6>, g, 256, s, launches, p);
+    case 7: return launch(recombine_kernel<uint8_t, 7>, g, 256, s, launches, p);
+    case 8: return launch(recombine_kernel<uint8_t, 8>, g, 256, s, launches, p);
+    case 9: return launch(recombine_kernel<uint16_t, 9>, g, 256, s, launches, p);
+    case 10: return launch(recombine_kernel<uint16_t, 10>, g, 256, s, launches, p);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace m4rie
