@@ -155,9 +155,10 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   else if (form == M4RIE_FORM_TC_F8 || form == M4RIE_FORM_TC_F4) G = tc_group(e, fi.fmt);
   else if (form == M4RIE_FORM_MMA_S8) G = mma_group(e);
   else return M4RIE_ERR_UNSUPPORTED;
+  const bool tc = form == M4RIE_FORM_TC_F8 || form == M4RIE_FORM_TC_F4;
   const int64_t Kp = round_up(k, 128);
   const int64_t ld = (int64_t)e * Kp;
-  const int64_t Mp = round_up(m, 128);
+  const int64_t Mp = round_up(m, tc && ctx->cluster == 2 ? 256 : 128);  // CTA pairs take m-tile pairs
   const int64_t groups = ceil_div(n, G);
   const int64_t brows = groups * e * G;
   const size_t a_bytes = round_up((int64_t)entries_bytes(Mp * ld, fi.bits), 1024);
@@ -257,6 +258,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.wait_limit_ns = ctx->wait_limit_ns;
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
+    tp.cluster = ctx->cluster;
     if (form == M4RIE_FORM_MMA_S8) err = launch_mma_s8(Ap, Bp, ld_bytes, tp, ctx->stream, &ctx->launches);
     else err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld_bytes, tp, ctx->num_sms, ctx->stream, &ctx->launches);
   }
@@ -276,7 +278,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   const FormInfo fi = form_info(form);
   const int r = sc.r;
   const int64_t Kp = round_up(k, 128);
-  const int64_t Mp = round_up(m, 128);
+  const int64_t Mp = round_up(m, form != M4RIE_FORM_POPC && ctx->cluster == 2 ? 256 : 128);
   // popc parity tiles are 128 columns; tcgen05 tiles 256 (FP8) or 224 (FP4, which
   // keeps its scale factors in TMEM next to each accumulator)
   const int ntile = form == M4RIE_FORM_POPC ? 128 : (form == M4RIE_FORM_TC_F8 ? 256 : 224);
@@ -374,6 +376,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     tp.wait_limit_ns = ctx->wait_limit_ns;
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
+    tp.cluster = ctx->cluster;
     err = launch_tc(fi.fmt, Ap, (int64_t)r * Mp, Bp, (int64_t)r * Np, ld_bytes, tp, ctx->num_sms, ctx->stream,
                     &ctx->launches);
   }
@@ -441,6 +444,7 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
   }
   if (const char* s = getenv("M4RIE_TC_CHUNK")) ctx->tc_chunk = std::max(128, atoi(s));
   if (const char* s = getenv("M4RIE_F4_KIND")) ctx->f4nv = strcmp(s, "nvf4") == 0 ? 1 : 0;
+  if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) == 2 ? 2 : 1;
   if (const char* s = getenv("M4RIE_TUNE_CACHE")) m4rie_tune_load(ctx, s);  // a missing file is not an error
   *out = ctx;
   return M4RIE_OK;

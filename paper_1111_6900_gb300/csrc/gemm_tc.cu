@@ -16,6 +16,7 @@
 // wait is bounded by a global-timer limit; on expiry the CTA sets the timeout
 // status, stops issuing, waits (bounded) for its copies in flight, frees TMEM
 // and returns.
+#include <algorithm>
 #include <cstring>
 
 #include "m4rie_internal.cuh"
@@ -144,6 +145,35 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// Arrive on the barrier at the same shared-memory offset in both CTAs of a
+// 2-CTA cluster once this thread's MMAs have completed.
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"((uint16_t)3)
+      : "memory");
+}
+
+// TMA load whose data and transaction count land at the same shared-memory
+// offsets in both CTAs of a 2-CTA cluster.
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%3, "
+      "%4}], [%2], %5;" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1), "h"((uint16_t)3)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -185,11 +215,14 @@ struct TileV {
 
 // Non-batched: one problem (or a batch of equally shaped parity products) in p.
 // Batched: the tile's job comes from the tile -> job table.
-template <bool BATCHED>
+// CL = 2: tile indices count pairs of m-tiles (2 tm, 2 tm + 1) handled by the
+// two CTAs of a cluster, which share the B tile; `rank` picks this CTA's m-tile.
+template <bool BATCHED, int CL = 1>
 __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restrict__ jobs, const CUtensorMap* tmA,
-                                         const CUtensorMap* tmB, int tile, int& jc, TileV& t) {
+                                         const CUtensorMap* tmB, int tile, int& jc, TileV& t, int rank = 0) {
   if (!BATCHED) {
     tile_coords(p, tile, t.b, t.tm, t.tn);
+    if (CL == 2) t.tm = 2 * t.tm + rank;
     t.ma = tmA;
     t.mb = tmB;
     t.arow = (int)(t.b * p.a_brows) + t.tm * 128;
@@ -235,7 +268,11 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
 // BATCHED: p.batch = number of jobs, p.tiles_m = total tiles, p.tiles_n = 1;
 // per-tile parameters come from jobs[].  NV (FP4 only): kind::mxf4nvf4 with
 // UE4M3 scales per 16 entries instead of kind::mxf4 with UE8M0 per 32.
-template <int FMT, bool BATCHED, bool NV = false>
+// CL = 2 (non-batched): clusters of two CTAs computing adjacent m-tiles of the
+// same n-tile; each CTA loads half of the B tile and multicasts it to both,
+// and each CTA's MMA commits release a stage in both CTAs (p.tiles_m counts
+// m-tile pairs, the B tensor map's box is half a tile).
+template <int FMT, bool BATCHED, bool NV = false, int CL = 1>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ TcParams p, const TcJob* __restrict__ jobs) {
@@ -258,7 +295,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, CL);  // released by the MMA commits of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
@@ -282,6 +319,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_before();
   __syncthreads();
   fence_after();
+  const uint32_t crank = CL == 2 ? cluster_rank() : 0;
+  if (CL == 2) cluster_sync();  // the peer's barriers are initialised before anything lands in them
   const uint32_t tmem = *tmem_slot;
   if (FMT == kFmtNib) {
     // Unit block-scale factors (UE8M0 0x7F = 2^0) for every lane, written by
@@ -301,6 +340,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   const int total = BATCHED ? p.tiles_m : p.batch * p.tiles_m * p.tiles_n;
   const uint64_t lim = p.wait_limit_ns;
+  // tile loop: every CTA (CL = 1) or every cluster (CL = 2) takes every
+  // (gridDim.x / CL)-th tile
+  const int tfirst = blockIdx.x / CL, tstep = gridDim.x / CL;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -309,9 +351,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t phase = 0;
       uint32_t issued_mask = 0, issued_parity = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+      for (int tile = tfirst; tile < total && ok; tile += tstep) {
         TileV t;
-        get_tile<BATCHED>(p, jobs, &tmA, &tmB, tile, jc, t);
+        get_tile<BATCHED, CL>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
         if (BATCHED && tile + (int)gridDim.x < total) {
           // fetch the next tile's tensor maps into the TMA descriptor cache early
           const TcJob& nj = jobs[__ldg(p.tile_job + tile + gridDim.x)];
@@ -327,7 +369,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t fb = full0 + 8 * stage;
           mbar_expect_tx(fb, bytes);
           tma_load_2d(smem_u32(sA + stage * A_TILE), t.ma, fb, kb * 128, t.arow);
-          tma_load_2d(smem_u32(sB + stage * B_SLOT), t.mb, fb, kb * 128, t.brow);
+          if (CL == 2) {
+            // this CTA's half of the B tile, into both CTAs (the peer sends the other half)
+            const int half = t.BN / 2;
+            tma_load_2d_pair(smem_u32(sB + stage * B_SLOT + crank * half * 128), t.mb, fb, kb * 128,
+                             t.brow + (int)crank * half);
+          } else {
+            tma_load_2d(smem_u32(sB + stage * B_SLOT), t.mb, fb, kb * 128, t.brow);
+          }
           issued_mask |= 1u << stage;
           issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) {
@@ -354,9 +403,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t phase = 0;
       int chunk = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+      for (int tile = tfirst; tile < total && ok; tile += tstep) {
         TileV t;
-        get_tile<BATCHED>(p, jobs, &tmA, &tmB, tile, jc, t);
+        get_tile<BATCHED, CL>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
         const uint32_t idesc = FMT == kFmtNib ? idesc_f4(128, t.BN, NV) : idesc_f8(128, t.BN);
         for (int kb0 = 0; kb0 < t.kblocks && ok; kb0 += t.kc) {
           const int kb1 = min(kb0 + t.kc, t.kblocks);
@@ -381,7 +430,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (FMT == kFmtNib) mma_f4<NV>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, sf, acc);
               else mma_f8(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, acc);
             }
-            mma_commit(empty0 + 8 * stage);
+            if (CL == 2) mma_commit_pair(empty0 + 8 * stage);
+            else mma_commit(empty0 + 8 * stage);
             if (++stage == STAGES) {
               stage = 0;
               phase ^= 1;
@@ -408,9 +458,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     int chunk = 0, jc = 0;
     // failure-detection test: a wait that can only run out
     bool ok = !p.stall_test || __all_sync(0xffffffffu, mbar_wait(never, 0, abort_flag, p.status, lim));
-    for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+    for (int tile = tfirst; tile < total && ok; tile += tstep) {
       TileV t;
-      get_tile<BATCHED>(p, jobs, &tmA, &tmB, tile, jc, t);
+      get_tile<BATCHED, CL>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
       const int b = t.b, tm = t.tm, tn = t.tn;
       const int nc16 = t.BN / 16;
       uint32_t bits[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -505,6 +555,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_before();
   __syncthreads();
   fence_after();
+  // no CTA of a cluster leaves while the peer may still write into its shared memory
+  if (CL == 2) cluster_sync();
   if (warp == 1) {
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS) : "memory");
@@ -561,9 +613,41 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
   if (p.BN % 16 != 0 || p.BN < 16 || p.BN > (fmt == kFmtNib ? SF_COL : 256) || ld_bytes % 16 != 0)
     return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
-  if (!tc_make_map(&ma, Aplanes, a_rows, ld_bytes, 128) || !tc_make_map(&mb, Bplanes, b_rows, ld_bytes, p.BN))
+  // 2-CTA clusters share B tiles when the m-tiles pair up (the caller pads the
+  // planes' rows to a multiple of 256 for that)
+  const bool pair = p.cluster == 2 && p.tiles_m % 2 == 0 && num_sms >= 2;
+  if (!tc_make_map(&ma, Aplanes, a_rows, ld_bytes, 128) ||
+      !tc_make_map(&mb, Bplanes, b_rows, ld_bytes, pair ? p.BN / 2 : p.BN))
     return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes();
+  if (pair) {
+    auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 2> : tc_kernel<kFmtNib, false, false, 2>)
+                                 : tc_kernel<kFmtByte, false, false, 2>;
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    TcParams q = p;
+    q.tiles_m = p.tiles_m / 2;  // tiles count m-tile pairs
+    q.group_m = std::max(1, std::min(q.tiles_m, p.group_m / 2));
+    const int64_t pairs = (int64_t)q.batch * q.tiles_m * q.tiles_n;
+    if (pairs > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const int clusters = (int)std::min<int64_t>(pairs, num_sms / 2);
+    if (clusters <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    err = cudaLaunchKernelEx(&cfg, kernel, ma, mb, q, (const TcJob*)nullptr);
+    if (launches) ++*launches;
+    return err != cudaSuccess ? err : cudaGetLastError();
+  }
   auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true> : tc_kernel<kFmtNib, false, false>)
                                : tc_kernel<kFmtByte, false>;
   cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -142,6 +142,7 @@ struct TcParams {
   const int* tile_job;  // batched launches: job of every global tile
   int f4nv;             // FP4: 1 = kind::mxf4nvf4 (UE4M3 scales per 16), 0 = kind::mxf4 (UE8M0 per 32)
   int stall_test;       // test hook: the epilogue first waits on a barrier that is never signalled
+  int cluster;          // 2: pairs of CTAs share B tiles (tiles_m must be even), 1: single CTAs
 };
 // fmt: kFmtByte (E4M3) or kFmtNib (E2M1, block scaled).
 cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
