@@ -163,12 +163,10 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   const int64_t brows = groups * e * G;
   const size_t a_bytes = round_up((int64_t)entries_bytes(Mp * ld, fi.bits), 1024);
   const size_t b_bytes = round_up((int64_t)entries_bytes(brows * ld, fi.bits), 1024);
-  const size_t t_bytes = round_up(n * k * elem_bytes(e), 1024);  // B transposed (elements)
-  m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes + t_bytes);
+  m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes);
   if (st != M4RIE_OK) return st;
   uint8_t* Ap = static_cast<uint8_t*>(ctx->ws);
   uint8_t* Bp = Ap + a_bytes;
-  uint8_t* Bt = Bp + b_bytes;
 
   uint16_t amask[10], bmask[100];
   alpha_b_masks(e, f, amask, bmask);
@@ -198,13 +196,10 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   timer.begin(kPhasePack);
   cudaError_t err = launch_pack_planes(pa, ctx->stream, &ctx->launches);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
-  err = launch_transpose(B, n, k, n, elem_bytes(e), Bt, ctx->stream, &ctx->launches);
-  if (err != cudaSuccess) return cuda_fail(ctx, err);
 
-  PackParams pb = pa;
-  pb.X = Bt;
-  pb.ldx = k;
-  pb.vec = (k * elem_bytes(e)) % 16 == 0;
+  PackParams pb = pa;  // columns of B (k x n) are the planes' rows
+  pb.X = B;
+  pb.ldx = n;
   pb.rows = n;
   pb.rows_p = groups * G;
   pb.P = e * e;
@@ -215,7 +210,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   pb.emajor = (form == M4RIE_FORM_TC_F8 || form == M4RIE_FORM_TC_F4) ? 1 : 0;
   pb.out = Bp;
   for (int q = 0; q < e * e; ++q) pb.mask[q] = bmask[q];
-  err = launch_pack_planes(pb, ctx->stream, &ctx->launches);
+  err = launch_pack_cols(pb, ctx->stream, &ctx->launches);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
   timer.begin(kPhaseGemm);
 
@@ -287,13 +282,11 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   const size_t a_bytes = round_up((int64_t)entries_bytes((int64_t)r * Mp * Kp, fi.bits), 1024);
   const size_t b_bytes = round_up((int64_t)entries_bytes((int64_t)r * Np * Kp, fi.bits), 1024);
   const size_t p_bytes = round_up((int64_t)r * Mp * ldp * 4, 1024);
-  const size_t t_bytes = round_up(n * k * elem_bytes(e), 1024);  // B transposed (elements)
-  m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes + p_bytes + t_bytes);
+  m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes + p_bytes);
   if (st != M4RIE_OK) return st;
   uint8_t* Ap = static_cast<uint8_t*>(ctx->ws);
   uint8_t* Bp = Ap + a_bytes;
   uint32_t* Pp = reinterpret_cast<uint32_t*>(Bp + b_bytes);
-  uint8_t* Bt = Bp + b_bytes + p_bytes;
 
   PackParams pa{};
   pa.X = A;
@@ -321,18 +314,15 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   timer.begin(kPhasePack);
   cudaError_t err = launch_pack_planes(pa, ctx->stream, &ctx->launches);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
-  err = launch_transpose(B, n, k, n, elem_bytes(e), Bt, ctx->stream, &ctx->launches);
-  if (err != cudaSuccess) return cuda_fail(ctx, err);
-  PackParams pb = pa;
-  pb.X = Bt;
-  pb.ldx = k;
-  pb.vec = (k * elem_bytes(e)) % 16 == 0;
+  PackParams pb = pa;  // columns of B (k x n) are the planes' rows
+  pb.X = B;
+  pb.ldx = n;
   pb.rows = n;
   pb.rows_p = Np;
   pb.bstride = Np * Kp;
   pb.out = Bp;
   for (int p = 0; p < r; ++p) pb.mask[p] = sc.bmask[p];
-  err = launch_pack_planes(pb, ctx->stream, &ctx->launches);
+  err = launch_pack_cols(pb, ctx->stream, &ctx->launches);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
   timer.begin(kPhaseGemm);
 

@@ -252,6 +252,10 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
         q.out = wbase + L.b_off;
         for (int jj = 0; jj < p.e * p.e; ++jj) q.mask[jj] = bmask[jj];
       }
+      if (!plane_offsets(q)) {
+        destroy_plan(plan);
+        return M4RIE_ERR_UNSUPPORTED;
+      }
       pstart.push_back(pblocks[grp]);
       pblocks[grp] += pack_job_blocks(q);
       pjobs.push_back(q);

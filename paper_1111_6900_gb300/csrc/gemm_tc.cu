@@ -27,6 +27,9 @@ namespace {
 constexpr int STAGES = 4;
 constexpr int A_TILE = 128 * 128;  // bytes
 constexpr int B_SLOT = 256 * 128;  // bytes (tile N <= 256)
+// Ring depth and B slot size: 4 stages of 256-row B slots, or 5 stages of
+// 224-row slots (tile N <= 224), which still fit in 227 KB of shared memory.
+__host__ __device__ constexpr int b_slot(int stages) { return stages > 4 ? 224 * 128 : B_SLOT; }
 constexpr int ACC_COLS = 256;
 constexpr int THREADS = 192;
 // Bound on the waits that drain copies and MMAs already in flight when a CTA
@@ -272,10 +275,12 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
 // same n-tile; each CTA loads half of the B tile and multicasts it to both,
 // and each CTA's MMA commits release a stage in both CTAs (p.tiles_m counts
 // m-tile pairs, the B tensor map's box is half a tile).
-template <int FMT, bool BATCHED, bool NV = false, int CL = 1>
+template <int FMT, bool BATCHED, bool NV = false, int CL = 1, int STAGES = 4>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ TcParams p, const TcJob* __restrict__ jobs) {
+  constexpr int B_SLOT = b_slot(STAGES);
+  static_assert(2 * STAGES + 6 <= 16, "barrier block holds 16 words");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -605,7 +610,9 @@ int tc_group(int e, int fmt) {
   return best;
 }
 
-size_t tc_smem_bytes() { return 1024 + (size_t)STAGES * (A_TILE + B_SLOT) + 16 * 8 + 16 + 128 * 9 * 4; }
+size_t tc_smem_bytes(int stages = STAGES) {
+  return 1024 + (size_t)stages * (A_TILE + b_slot(stages)) + 16 * 8 + 16 + 128 * 9 * 4;
+}
 
 cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
                       int64_t ld_bytes, const TcParams& p, int num_sms, cudaStream_t s, int64_t* launches) {
@@ -619,9 +626,13 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
   if (!tc_make_map(&ma, Aplanes, a_rows, ld_bytes, 128) ||
       !tc_make_map(&mb, Bplanes, b_rows, ld_bytes, pair ? p.BN / 2 : p.BN))
     return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes();
+  // FP4 tiles of N <= 224 take the 5-stage ring
+  const bool deep = fmt == kFmtNib && p.BN <= 224;
+  const size_t smem = tc_smem_bytes(deep ? 5 : 4);
   if (pair) {
-    auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 2> : tc_kernel<kFmtNib, false, false, 2>)
+    auto kernel = fmt == kFmtNib ? (deep ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 2, 5>
+                                                   : tc_kernel<kFmtNib, false, false, 2, 5>)
+                                         : (p.f4nv ? tc_kernel<kFmtNib, false, true, 2> : tc_kernel<kFmtNib, false, false, 2>))
                                  : tc_kernel<kFmtByte, false, false, 2>;
     cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -648,7 +659,9 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
     if (launches) ++*launches;
     return err != cudaSuccess ? err : cudaGetLastError();
   }
-  auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true> : tc_kernel<kFmtNib, false, false>)
+  auto kernel = fmt == kFmtNib ? (deep ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 1, 5>
+                                                 : tc_kernel<kFmtNib, false, false, 1, 5>)
+                                       : (p.f4nv ? tc_kernel<kFmtNib, false, true> : tc_kernel<kFmtNib, false, false>))
                                : tc_kernel<kFmtByte, false>;
   cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;

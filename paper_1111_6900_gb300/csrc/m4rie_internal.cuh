@@ -45,11 +45,22 @@ struct PackParams {
   void* out;
   int* status;
   uint16_t mask[kMaxMasks];
+  // Filled by plane_offsets() (the launchers call it on their copy): byte
+  // offset of plane q's row 0, entry 0 from out, and ceil(2^40 / G) so that
+  // r / G = (r * gmul) >> 40 for r < 2^31, G < 512.
+  int64_t qoff[kMaxMasks];
+  uint64_t gmul;
 };
 
-// Pack launcher (pack.cu): rows of X are the planes' rows.  The B side is
-// first transposed with launch_transpose (K x rows -> rows x K elements).
+// Fill qoff and gmul of p from its layout fields; false if G is out of range.
+bool plane_offsets(PackParams& p);
+
+// Pack launchers (pack.cu).  launch_pack_planes: rows of X (rows x K, row
+// stride ldx) are the planes' rows.  launch_pack_cols: columns of X (K x rows,
+// row stride ldx) are the planes' rows, transposed on the way through shared
+// memory.  launch_transpose serves the batched path, which transposes first.
 cudaError_t launch_pack_planes(const PackParams& p, cudaStream_t s, int64_t* launches);
+cudaError_t launch_pack_cols(const PackParams& p, cudaStream_t s, int64_t* launches);
 cudaError_t launch_transpose(const void* X, int64_t ldx, int64_t K, int64_t rows, int elem_bytes, void* Xt,
                              cudaStream_t s, int64_t* launches);
 

@@ -17,20 +17,22 @@ __device__ __forceinline__ void flag_range(int* status, bool bad) {
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusRange);
 }
 
-// ---- Operand planes with SWAR parities.  A thread takes 16 (32 for bit
-// planes) consecutive elements of one row as packed 32-bit words (4 bytes or 2
-// halfwords per word) and, for every mask q, computes parity(x & mask_q) of
-// all of them at once: AND with the mask replicated per element, then fold the
-// element's bits onto its lowest bit (x ^= x >> 4, 2, 1 for bytes; 8, 4, 2, 1
-// for halfwords; folds above the element width e are skipped).  The 0/1
-// results are laid out as bytes (0 / one), nibbles or bits.  B is transposed
-// first, so both sides read rows.
+// ---- Operand planes from bit slices.  Every plane entry parity(x & mask) is
+// a GF(2)-linear function of the bits of x: it is the XOR, over the bits i set
+// in the mask, of bit i of x.  A thread takes NE = 32 consecutive elements of
+// one row as packed 32-bit words (4 bytes or 2 halfwords per word), turns
+// them into bit slices (slice i = bit i of all 32 elements, one word) with a
+// SWAR bit-matrix transpose, and then forms each plane word as the XOR of the
+// slices its mask selects (one LOP3 per bit).  The 0/1 results are laid out as
+// bits, bytes (0 / one) or nibbles (0 / one).  A side's plane rows may be the
+// rows of X (pack_planes_rows) or its columns (pack_planes_cols).
 //
-// Nibble and bit planes store the entries of each group of 8 (nibbles) or 32
-// (bits) consecutive t in a fixed permuted order within the output word, the
-// order that falls out of the SWAR words without shuffling bits around.  Both
-// operands of a product go through this kernel, so the permutation is the
-// same on both sides of every inner product and sum_t a_t b_t is unchanged.
+// The 32 entries of a plane word come out in a fixed permuted order of t
+// (slice bit 8u + k, or 16u + k for halfwords, is element u of packed word
+// k), and the byte and nibble layouts spread the bits in their own fixed
+// order.  Both operands of a product go through these kernels, so the
+// permutation is the same on both sides of every inner product and
+// sum_t a_t b_t is unchanged.
 
 template <typename T>
 struct Swar;
@@ -38,33 +40,76 @@ template <>
 struct Swar<uint8_t> {
   static constexpr int PER = 4;  // elements per word
   static __device__ __forceinline__ uint32_t rep(uint32_t m) { return m * 0x01010101u; }
-  // FOLD = 1, 2, 3 folds cover elements of <= 2, 4, 8 bits
-  template <int FOLD>
-  static __device__ __forceinline__ uint32_t parity(uint32_t y) {
-    if (FOLD >= 3) y ^= y >> 4;
-    if (FOLD >= 2) y ^= y >> 2;
-    y ^= y >> 1;
-    return y & 0x01010101u;  // element u's parity at bit 8u
-  }
 };
 template <>
 struct Swar<uint16_t> {
   static constexpr int PER = 2;
   static __device__ __forceinline__ uint32_t rep(uint32_t m) { return m * 0x00010001u; }
-  template <int FOLD>
-  static __device__ __forceinline__ uint32_t parity(uint32_t y) {
-    y ^= y >> 8;
-    y ^= y >> 4;
-    y ^= y >> 2;
-    y ^= y >> 1;
-    return y & 0x00010001u;  // element u's parity at bit 16u
-  }
 };
 
-// Parity-fold depth for e-bit elements in T.
-inline int fold_of(int e) { return e <= 2 ? 1 : e <= 4 ? 2 : 3; }
-
 constexpr int NE = 32;  // elements per thread
+
+// Exchange bit i + D of a with bit i of b for the bit positions i in M (the
+// lower half of every 2D-bit block): one step of the recursive transpose.
+template <int D, uint32_t M>
+__device__ __forceinline__ void delta_swap(uint32_t& a, uint32_t& b) {
+  const uint32_t t = ((a >> D) ^ b) & M;
+  b ^= t;
+  a ^= t << D;
+}
+// The same step when bits i + D of a and all bits of b outside M are known to
+// be zero: only a receives data (b is not needed afterwards).
+template <int D>
+__device__ __forceinline__ void delta_merge(uint32_t& a, uint32_t b) {
+  a |= b << D;
+}
+
+// In place: v[k] holds elements PER k .. PER k + PER - 1 of E bits; afterwards
+// v[i] (i < E) is bit slice i, its bit 8u + k (bytes) or 16u + k (halfwords)
+// taken from element u of the input word k.  This transposes the (word k,
+// bit i) bit matrix of every element lane at once.  Bits at and above E are
+// zero on input, so for E <= 4 (E <= 2) the first one (two) steps only merge
+// words and the upper words are dropped.
+template <typename T, int E>
+__device__ __forceinline__ void bit_slices(uint32_t (&v)[NE * sizeof(T) / 4]) {
+  if constexpr (sizeof(T) == 1) {
+    if constexpr (E > 4) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) delta_swap<4, 0x0F0F0F0Fu>(v[k], v[k + 4]);
+#pragma unroll
+      for (int k : {0, 1, 4, 5}) delta_swap<2, 0x33333333u>(v[k], v[k + 2]);
+#pragma unroll
+      for (int k : {0, 2, 4, 6}) delta_swap<1, 0x55555555u>(v[k], v[k + 1]);
+    } else if constexpr (E > 2) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) delta_merge<4>(v[k], v[k + 4]);
+      delta_swap<2, 0x33333333u>(v[0], v[2]);
+      delta_swap<2, 0x33333333u>(v[1], v[3]);
+      delta_swap<1, 0x55555555u>(v[0], v[1]);
+      delta_swap<1, 0x55555555u>(v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) delta_merge<4>(v[k], v[k + 4]);
+      delta_merge<2>(v[0], v[2]);
+      delta_merge<2>(v[1], v[3]);
+      delta_swap<1, 0x55555555u>(v[0], v[1]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) delta_swap<8, 0x00FF00FFu>(v[k], v[k + 8]);
+#pragma unroll
+    for (int k : {0, 1, 2, 3, 8, 9, 10, 11}) delta_swap<4, 0x0F0F0F0Fu>(v[k], v[k + 4]);
+#pragma unroll
+    for (int k : {0, 1, 4, 5, 8, 9, 12, 13}) delta_swap<2, 0x33333333u>(v[k], v[k + 2]);
+#pragma unroll
+    for (int k : {0, 2, 4, 6, 8, 10, 12, 14}) delta_swap<1, 0x55555555u>(v[k], v[k + 1]);
+  }
+}
+
+// Mask words per plane in the shared table: bit i of the mask as 0 / ~0,
+// padded to whole 128-bit loads.
+template <int E>
+__host__ __device__ constexpr int mask_words() { return (E + 3) & ~3; }
 
 // NE consecutive elements of row r from t0 (zeros past the row end), packed.
 template <typename T>
@@ -87,22 +132,66 @@ __device__ __forceinline__ void load_row(const PackParams& p, int64_t r, int64_t
   }
 }
 
-// Per-block tables: plane offsets qoff[q] = b*bstride + i*G*ld + j*Kp for
-// q = (b*nb + i)*kb + j, and the masks replicated per packed element.
-template <typename T>
-__device__ __forceinline__ void plane_tables(const PackParams& p, int64_t* qoff, uint32_t* mrep) {
-  for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
-    const int b = q / (p.nb * p.kb), i = (q / p.kb) % p.nb, j = q % p.kb;
-    qoff[q] = (int64_t)b * p.bstride + (int64_t)i * (p.emajor ? 1 : p.G) * p.ld + (int64_t)j * p.Kp;
-    mrep[q] = Swar<T>::rep(p.mask[q]);
+// Per-block table: the masks expanded to one 0 / ~0 word per bit.
+template <int E>
+__device__ __forceinline__ void plane_tables(const PackParams& p, uint32_t* mexp) {
+  constexpr int MW = mask_words<E>();
+  for (int x = threadIdx.x; x < p.P * MW; x += blockDim.x) {
+    const int q = x / MW, i = x % MW;
+    mexp[x] = (i < E && ((p.mask[q] >> i) & 1u)) ? ~0u : 0u;
+  }
+}
+
+// All planes of NE consecutive entries (from t0) of input row r, given its
+// packed elements v (bits at and above E zero); v is turned into bit slices.
+template <typename T, int FMT, int E>
+__device__ __forceinline__ void plane_out(const PackParams& p, const uint32_t* mexp, int64_t r, int64_t t0,
+                                          uint32_t (&v)[NE * sizeof(T) / 4]) {
+  constexpr int MW = mask_words<E>();
+  constexpr int BITS = FMT == kFmtBit ? 1 : FMT == kFmtByte ? 8 : 4;  // per entry
+  bit_slices<T, E>(v);
+  // entry offset of input row r, entry t0 in the plane layout (r < 2^31, G < 512)
+  const uint32_t rr = (uint32_t)r, G = (uint32_t)p.G, g = (uint32_t)(((uint64_t)rr * p.gmul) >> 40);
+  const uint64_t base =
+      ((uint64_t)g * p.nb * G + (uint64_t)(rr - g * G) * (p.emajor ? p.nb : 1)) * p.ld + (uint64_t)t0;
+  uint8_t* const rowp = static_cast<uint8_t*>(p.out) + base * BITS / 8;
+#pragma unroll 1
+  for (int q = 0; q < p.P; ++q) {
+    const uint4* mq = reinterpret_cast<const uint4*>(mexp + q * MW);
+    uint32_t x = 0;
+#pragma unroll
+    for (int i4 = 0; i4 < MW; i4 += 4) {
+      const uint4 mb = mq[i4 / 4];
+      const uint32_t mw[4] = {mb.x, mb.y, mb.z, mb.w};
+#pragma unroll
+      for (int i = i4; i < i4 + 4 && i < E; ++i) x ^= v[i] & mw[i - i4];
+    }
+    uint8_t* const dst = rowp + p.qoff[q];
+    if (FMT == kFmtBit) {
+      *reinterpret_cast<uint32_t*>(dst) = x;
+    } else if (FMT == kFmtByte) {
+      // byte j of word k <- bit 8j + k
+      uint32_t w[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) w[k] = ((x >> k) & 0x01010101u) * p.one;
+      uint4* d = reinterpret_cast<uint4*>(dst);
+      d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+      // nibble j of word k <- bit 4j + k
+      uint32_t w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[k] = ((x >> k) & 0x11111111u) * p.one;
+      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
   }
 }
 
 // Rows r0, r0 + rstep, ... of one plane job; this thread's elements start at
 // t0 = tchunk * NE (threads with t0 >= Kp only join the warp-wide votes).
-template <typename T, int FMT, int FOLD>
-__device__ __forceinline__ void pack_planes_rows(const PackParams& p, const int64_t* qoff, const uint32_t* mrep,
-                                                 int64_t tchunk, int64_t r0, int64_t rstep) {
+template <typename T, int FMT, int E>
+__device__ __forceinline__ void pack_planes_rows(const PackParams& p, const uint32_t* mexp, int64_t tchunk, int64_t r0,
+                                                 int64_t rstep) {
   constexpr int W = NE * (int)sizeof(T) / 4;  // packed input words per thread
   const int64_t t0 = tchunk * NE;
   const bool live_t = t0 < p.Kp;
@@ -120,61 +209,122 @@ __device__ __forceinline__ void pack_planes_rows(const PackParams& p, const int6
     }
     flag_range(p.status, bad);
     if (!live_t) continue;
-    // row offset of input row r in the plane layout (32-bit division: r < 2^31, G < 2^16)
-    const uint32_t rr = (uint32_t)r, G = (uint32_t)p.G, g = rr / G;
-    const int64_t base = ((int64_t)g * p.nb * G + (int64_t)(rr - g * G) * (p.emajor ? p.nb : 1)) * p.ld + t0;
-    uint8_t* out = static_cast<uint8_t*>(p.out);
-#pragma unroll 1
-    for (int q = 0; q < p.P; ++q) {
-      const uint32_t m = mrep[q];
-      const int64_t o = qoff[q] + base;
-      uint32_t par[W];
-#pragma unroll
-      for (int k = 0; k < W; ++k) par[k] = Swar<T>::template parity<FOLD>(v[k] & m);
-      if (FMT == kFmtBit) {
-        // parity words (element u at bit 8u or 16u) shifted by k interleave
-        // into 32 distinct bits (permuted order)
-        uint32_t word = 0;
-#pragma unroll
-        for (int k = 0; k < W; ++k) word |= par[k] << k;
-        reinterpret_cast<uint32_t*>(out)[o / 32] = word;
-      } else if (FMT == kFmtByte) {
-        uint32_t w[8];
-        if (sizeof(T) == 1) {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) w[k] = par[k] * p.one;
-        } else {
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            // two elements per parity word, at bits 0 and 16 -> bytes 4k .. 4k+3
-            w[k] = ((par[2 * k] & 1u) | ((par[2 * k] >> 8) & 0x100u) | ((par[2 * k + 1] & 1u) << 16) |
-                    ((par[2 * k + 1] >> 16) << 24)) * p.one;
-        }
-        uint4* d = reinterpret_cast<uint4*>(out + o);
-        d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        d[1] = make_uint4(w[4], w[5], w[6], w[7]);
-      } else {
-        // 32 entries -> 32 nibbles: parity words shifted by 4 j interleave
-        // into distinct nibbles (permuted order), times `one`
-        uint32_t w[4] = {0, 0, 0, 0};
-        constexpr int PW = W / 4;  // parity words per output word
-#pragma unroll
-        for (int k = 0; k < W; ++k) w[k / PW] |= par[k] << (4 * (k % PW));
-        *reinterpret_cast<uint4*>(out + o / 2) = make_uint4(w[0] * p.one, w[1] * p.one, w[2] * p.one, w[3] * p.one);
-      }
-    }
+    plane_out<T, FMT, E>(p, mexp, r, t0, v);
   }
 }
 
-// grid.x covers a row in chunks of 256 threads x NE elements, grid.y strides over rows.
-template <typename T, int FMT, int FOLD>
-__global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant__ PackParams p) {
-  __shared__ int64_t qoff[kMaxMasks];
-  __shared__ uint32_t mrep[kMaxMasks];
-  plane_tables<T>(p, qoff, mrep);
+// Shared mask table of a plane kernel (room for the largest E, 10).
+struct PlaneSmem {
+  uint32_t mexp[kMaxMasks * 12];
+};
+
+// A block holds 256 / tpr rows of tpr threads (tpr a power of two in
+// [32, 256], at least ceil(Kp / NE) when a row fits in one block); grid.x
+// covers longer rows in chunks of 256 threads x NE elements, grid.y strides
+// over row groups.
+template <typename T, int FMT, int E>
+__global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant__ PackParams p, int tpr) {
+  __shared__ PlaneSmem sm;
+  plane_tables<E>(p, sm.mexp);
   __syncthreads();
-  pack_planes_rows<T, FMT, FOLD>(p, qoff, mrep, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y,
-                                 gridDim.y);
+  const int rpb = 256 / tpr;
+  pack_planes_rows<T, FMT, E>(p, sm.mexp, (int64_t)blockIdx.x * 256 + threadIdx.x % tpr,
+                              (int64_t)blockIdx.y * rpb + threadIdx.x / tpr, (int64_t)gridDim.y * rpb);
+}
+
+// ---- Operand planes of the columns of X (X is K x rows, row-major; plane
+// row c holds column c, so B needs no separate transpose).  A tile of 128 t x
+// 64 columns passes through shared memory: each thread loads 8 bytes from each
+// of 4 (u8) or 2 (u16) consecutive rows and turns them, by byte (halfword)
+// permutes, into words that hold consecutive t of one column, stored column by
+// column.  Then each thread takes 32 consecutive t of one column and builds
+// their planes exactly as pack_planes_rows does for a row.
+template <typename T>
+__device__ __forceinline__ void transpose_words(const uint32_t (&r)[4 / sizeof(T)], uint32_t (&o)[4 / sizeof(T)]) {
+  if constexpr (sizeof(T) == 1) {
+    // 4 x 4 bytes: byte i of o[j] = byte j of r[i]
+    const uint32_t a = __byte_perm(r[0], r[1], 0x5140), b = __byte_perm(r[2], r[3], 0x5140);
+    const uint32_t c = __byte_perm(r[0], r[1], 0x7362), d = __byte_perm(r[2], r[3], 0x7362);
+    o[0] = __byte_perm(a, b, 0x5410);
+    o[1] = __byte_perm(a, b, 0x7632);
+    o[2] = __byte_perm(c, d, 0x5410);
+    o[3] = __byte_perm(c, d, 0x7632);
+  } else {
+    // 2 x 2 halfwords: halfword i of o[j] = halfword j of r[i]
+    o[0] = __byte_perm(r[0], r[1], 0x5410);
+    o[1] = __byte_perm(r[0], r[1], 0x7632);
+  }
+}
+
+template <typename T, int FMT, int E>
+__global__ void __launch_bounds__(256) pack_planes_cols(const __grid_constant__ PackParams p) {
+  constexpr int PER = 4 / sizeof(T);       // elements per word
+  constexpr int TT = 128, TC = 64;         // tile: t x columns
+  constexpr int WPC = TT / PER;            // words per tile column
+  constexpr int PITCH = WPC + 1;           // odd pitch: conflict-free column stores and reads
+  constexpr int CPT = 8 / sizeof(T);       // columns per load task (8 bytes of a row)
+  constexpr int CG = TC / CPT;             // column groups: 8 (u8), 16 (u16)
+  constexpr int PASSES = WPC * CG / 256;   // 1 (u8), 4 (u16)
+  constexpr int W = NE * (int)sizeof(T) / 4;
+  __shared__ PlaneSmem sm;
+  __shared__ uint32_t tile[TC * PITCH];
+  plane_tables<E>(p, sm.mexp);
+  const T* X = static_cast<const T*>(p.X);
+  const int64_t c0 = (int64_t)blockIdx.x * TC;
+  const bool aligned8 = ((reinterpret_cast<uintptr_t>(X) | (uintptr_t)(p.ldx * sizeof(T))) & 7u) == 0;
+  const uint32_t erep = Swar<T>::rep(p.emask);
+  for (int64_t tt0 = (int64_t)blockIdx.y * TT; tt0 < p.Kp; tt0 += (int64_t)gridDim.y * TT) {
+    const bool fast = aligned8 && c0 + TC <= p.rows && tt0 + TT <= p.K;
+#pragma unroll
+    for (int pass = 0; pass < PASSES; ++pass) {
+      // a warp takes 8 column groups x 4 row groups
+      const int cg = (threadIdx.x & 7) + 8 * (pass % (CG / 8));
+      const int rg = (threadIdx.x >> 3) + 32 * (pass / (CG / 8));
+      uint32_t lo[PER], hi[PER];
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int64_t t = tt0 + (int64_t)rg * PER + i, c = c0 + (int64_t)cg * CPT;
+        if (fast) {
+          const uint2 a = *reinterpret_cast<const uint2*>(X + t * p.ldx + c);
+          lo[i] = a.x, hi[i] = a.y;
+        } else {
+          lo[i] = hi[i] = 0;
+          if (t < p.K) {
+#pragma unroll
+            for (int u = 0; u < CPT; ++u)
+              if (c + u < p.rows) {
+                const uint32_t x = (uint32_t)X[t * p.ldx + c + u] << (8 * sizeof(T) * (u % PER));
+                if (u < PER) lo[i] |= x;
+                else hi[i] |= x;
+              }
+          }
+        }
+      }
+      uint32_t o[PER];
+      transpose_words<T>(lo, o);
+#pragma unroll
+      for (int j = 0; j < PER; ++j) tile[(cg * CPT + j) * PITCH + rg] = o[j];
+      transpose_words<T>(hi, o);
+#pragma unroll
+      for (int j = 0; j < PER; ++j) tile[(cg * CPT + PER + j) * PITCH + rg] = o[j];
+    }
+    __syncthreads();
+    // thread -> (column cl, 32 consecutive t from t0)
+    const int cl = threadIdx.x >> 2, ch = threadIdx.x & 3;
+    uint32_t v[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) v[k] = tile[cl * PITCH + ch * W + k];
+    __syncthreads();
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      bad |= (v[k] & ~erep) != 0;
+      v[k] &= erep;
+    }
+    flag_range(p.status, bad);
+    const int64_t r = c0 + cl, t0 = tt0 + (int64_t)ch * NE;
+    if (r < p.rows_p && t0 < p.Kp) plane_out<T, FMT, E>(p, sm.mexp, r, t0, v);
+  }
 }
 
 // Index of the job whose block range [start[j], start[j+1]) holds block b.
@@ -202,18 +352,19 @@ __host__ __device__ inline void job_shape(int64_t Kp, int ne, int64_t& tpr, int6
 // Many plane jobs in one launch: block b belongs to job j with
 // start[j] <= b < start[j+1]; within the job, local block l covers rows
 // (l / gx) * rpb + threadIdx.x / tpr and chunk (l % gx) * 256 + threadIdx.x % tpr.
-// Jobs of one launch may have different e: the fold covers the widest (8 bits
-// for uint8, 16 for uint16); extra folds over zero bits change nothing.
+// Jobs of one launch may have different e: the bit slices cover the widest (8
+// bits for uint8, 10 for uint16); slices of bits above a job's e are zero and
+// its masks never select them.
 template <typename T, int FMT>
 __global__ void __launch_bounds__(256) pack_planes_batched(const PackParams* __restrict__ jobs,
                                                            const int64_t* __restrict__ start, int njobs) {
-  __shared__ int64_t qoff[kMaxMasks];
-  __shared__ uint32_t mrep[kMaxMasks];
+  constexpr int E = sizeof(T) == 1 ? 8 : 10;
+  __shared__ PlaneSmem sm;
   __shared__ int sj;
   if (threadIdx.x == 0) sj = find_job(start, njobs, blockIdx.x);
   __syncthreads();
   const PackParams& p = jobs[sj];
-  plane_tables<T>(p, qoff, mrep);
+  plane_tables<E>(p, sm.mexp);
   __syncthreads();
   int64_t tpr, rpb, gx;
   job_shape(p.Kp, NE, tpr, rpb, gx);
@@ -221,8 +372,8 @@ __global__ void __launch_bounds__(256) pack_planes_batched(const PackParams* __r
   const int64_t r = (l / gx) * rpb + threadIdx.x / tpr;
   const int64_t chunk = (l % gx) * 256 + threadIdx.x % tpr;
   // rows past the job's end still run the loop body's warp votes (zero data)
-  pack_planes_rows<T, FMT, sizeof(T) == 1 ? 3 : 4>(p, qoff, mrep, r < p.rows_p ? chunk : (p.Kp + NE - 1) / NE,
-                                                  r < p.rows_p ? r : 0, p.rows_p);
+  pack_planes_rows<T, FMT, E>(p, sm.mexp, r < p.rows_p ? chunk : (p.Kp + NE - 1) / NE,
+                              r < p.rows_p ? r : 0, p.rows_p);
 }
 
 // ---- Element transpose X (K x rows, row-major) -> Xt (rows x K), tiles of
@@ -439,28 +590,63 @@ cudaError_t launch(K kernel, int64_t blocks, int threads, cudaStream_t s, int64_
 
 }  // namespace
 
+// Slice counts the plane kernels are built for: e = 2, 3..4, 5..8 (bytes),
+// 9..10 (halfwords).  A kernel built for more slices than e computes zero
+// slices that no mask selects.
 template <int FMT>
-void launch_planes_fmt(const PackParams& p, dim3 grid, cudaStream_t s) {
-  if (p.elem_bytes == 2) {
-    pack_planes_kernel<uint16_t, FMT, 4><<<grid, 256, 0, s>>>(p);
-    return;
-  }
-  switch (fold_of(p.e)) {
-    case 1: pack_planes_kernel<uint8_t, FMT, 1><<<grid, 256, 0, s>>>(p); break;
-    case 2: pack_planes_kernel<uint8_t, FMT, 2><<<grid, 256, 0, s>>>(p); break;
-    default: pack_planes_kernel<uint8_t, FMT, 3><<<grid, 256, 0, s>>>(p); break;
-  }
+void launch_planes_fmt(const PackParams& p, dim3 grid, int tpr, cudaStream_t s) {
+  if (p.elem_bytes == 2) pack_planes_kernel<uint16_t, FMT, 10><<<grid, 256, 0, s>>>(p, tpr);
+  else if (p.e <= 2) pack_planes_kernel<uint8_t, FMT, 2><<<grid, 256, 0, s>>>(p, tpr);
+  else if (p.e <= 4) pack_planes_kernel<uint8_t, FMT, 4><<<grid, 256, 0, s>>>(p, tpr);
+  else pack_planes_kernel<uint8_t, FMT, 8><<<grid, 256, 0, s>>>(p, tpr);
 }
 
-cudaError_t launch_pack_planes(const PackParams& p, cudaStream_t s, int64_t* launches) {
-  const int64_t gx = ceil_div(ceil_div(p.Kp, NE), 256);
-  const int64_t gy = std::min<int64_t>(p.rows_p, 65535);
+bool plane_offsets(PackParams& p) {
+  if (p.G < 1 || p.G >= 512 || p.P < 0 || p.P > kMaxMasks) return false;
+  const int bits = p.fmt == kFmtBit ? 1 : p.fmt == kFmtByte ? 8 : 4;
+  for (int q = 0; q < p.P; ++q) {
+    const int b = q / (p.nb * p.kb), i = (q / p.kb) % p.nb, j = q % p.kb;
+    const int64_t entries = (int64_t)b * p.bstride + (int64_t)i * (p.emajor ? 1 : p.G) * p.ld + (int64_t)j * p.Kp;
+    p.qoff[q] = entries * bits / 8;
+  }
+  p.gmul = ((1ull << 40) + (uint64_t)p.G - 1) / (uint64_t)p.G;
+  return true;
+}
+
+cudaError_t launch_pack_planes(const PackParams& p0, cudaStream_t s, int64_t* launches) {
+  PackParams p = p0;
+  if (!plane_offsets(p)) return cudaErrorInvalidValue;
+  int64_t tpr, rpb, gx;
+  job_shape(p.Kp, NE, tpr, rpb, gx);
+  const int64_t gy = std::min<int64_t>(ceil_div(p.rows_p, rpb), 65535);
   if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   if (gx <= 0 || gy <= 0) return cudaSuccess;
   const dim3 grid((unsigned)gx, (unsigned)gy);
-  if (p.fmt == kFmtBit) launch_planes_fmt<kFmtBit>(p, grid, s);
-  else if (p.fmt == kFmtByte) launch_planes_fmt<kFmtByte>(p, grid, s);
-  else launch_planes_fmt<kFmtNib>(p, grid, s);
+  if (p.fmt == kFmtBit) launch_planes_fmt<kFmtBit>(p, grid, (int)tpr, s);
+  else if (p.fmt == kFmtByte) launch_planes_fmt<kFmtByte>(p, grid, (int)tpr, s);
+  else launch_planes_fmt<kFmtNib>(p, grid, (int)tpr, s);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+template <int FMT>
+void launch_cols_fmt(const PackParams& p, dim3 grid, cudaStream_t s) {
+  if (p.elem_bytes == 2) pack_planes_cols<uint16_t, FMT, 10><<<grid, 256, 0, s>>>(p);
+  else if (p.e <= 2) pack_planes_cols<uint8_t, FMT, 2><<<grid, 256, 0, s>>>(p);
+  else if (p.e <= 4) pack_planes_cols<uint8_t, FMT, 4><<<grid, 256, 0, s>>>(p);
+  else pack_planes_cols<uint8_t, FMT, 8><<<grid, 256, 0, s>>>(p);
+}
+
+cudaError_t launch_pack_cols(const PackParams& p0, cudaStream_t s, int64_t* launches) {
+  PackParams p = p0;
+  if (!plane_offsets(p)) return cudaErrorInvalidValue;
+  const int64_t gx = ceil_div(p.rows_p, 64), gy = std::min<int64_t>(ceil_div(p.Kp, 128), 65535);
+  if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (gx <= 0 || gy <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)gx, (unsigned)gy);
+  if (p.fmt == kFmtBit) launch_cols_fmt<kFmtBit>(p, grid, s);
+  else if (p.fmt == kFmtByte) launch_cols_fmt<kFmtByte>(p, grid, s);
+  else launch_cols_fmt<kFmtNib>(p, grid, s);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
