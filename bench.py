@@ -54,13 +54,15 @@ CONFIG = config_of(WORKLOAD)
 # summaries (dram__bytes_read.sum + dram__bytes_write.sum).  It is reported only
 # while the kernel source is the one that was profiled (sha256 below).
 TRAFFIC = {
-    "tc_f4/karatsuba": {"bytes": 1.540147e+08 + 1.418368e+07, "source": "profiles/tc_f4_karatsuba_gf16_4096.md"},
-    "tc_f8/karatsuba": {"bytes": 3.021770e+08 + 1.822080e+07, "source": "profiles/tc_f8_karatsuba_gf16_4096.md"},
+    "tc_f4/karatsuba": {"bytes": 1.54019072e+08 + 1.4899968e+07, "source": "profiles/tc_f4_karatsuba_gf16_4096.md"},
+    "tc_f8/karatsuba": {"bytes": 3.0206464e+08 + 1.8095616e+07, "source": "profiles/tc_f8_karatsuba_gf16_4096.md"},
     "popc/alpha_b": {"bytes": 41.965824e6 + 0.164864e6, "source": "profiles/popc_alpha_b_gf16_4096.md"},
 }
-PROFILED_SOURCES = {"tc_f4/karatsuba": ("gemm_tc.cu", "7b2fd2fc93bf9e2259876e4832b4b6807df96f0a6d9152e82c431b60434de01a"),
-                    "tc_f8/karatsuba": ("gemm_tc.cu", "7b2fd2fc93bf9e2259876e4832b4b6807df96f0a6d9152e82c431b60434de01a"),
+PROFILED_SOURCES = {"tc_f4/karatsuba": ("gemm_tc.cu", "d2a2daf03f63e1f706725c52d988f952bab7695dc74f41a10c7970915fd9b194"),
+                    "tc_f8/karatsuba": ("gemm_tc.cu", "d2a2daf03f63e1f706725c52d988f952bab7695dc74f41a10c7970915fd9b194"),
                     "popc/alpha_b": ("gemm_popc.cu", "6fc3d0a61765ce47396627acb19770a9ddecc498caad76ea310bae7c899f3a1b")}
+# tcgen05.mma issue rate measured on this GPU by microbench/mma_rates.cu, MAC per SM clock
+MMA_MAC_PER_CLK = {"tc_f8": 8192, "tc_f4": 16384}
 
 
 def kernel_traffic(key):
@@ -435,6 +437,11 @@ def main():
         roof = {"bound": "tensor", "achieved": flops / gemm_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops / gemm_s / 1e12 / peak, "traffic": kernel_traffic(f"{form}/{sched}"),
                 "peak_source": src}
+        if form in MMA_MAC_PER_CLK:
+            # the instruction's own ceiling at the maximum SM clock
+            ceil = 2.0 * MMA_MAC_PER_CLK[form] * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof["instruction_ceiling"] = {"value": ceil, "frac": flops / gemm_s / 1e12 / ceil,
+                                           "source": "tcgen05.mma issue-rate microbenchmark, M = 128"}
 
     out = {"metric": metric, "value": best["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": best["ms_per_step"], "higher_is_better": True,
