@@ -1,12 +1,14 @@
-"""CPU oracle for GF(2^e) matrix multiplication (test infrastructure only).
+"""CPU oracle for GF(2^e) matrix multiplication and triangular solving (test
+infrastructure only).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never does, and
 this package imports nothing from the product.
 
 The arithmetic lives in ``oracle.c`` (plain C, OpenMP over rows): the field
-product of Section 2 (carry-less multiply, then reduction modulo f), the cubic
-matrix product of Algorithm 1 and the slicing / clinging conversions of
+product of Section 2 (carry-less multiply, then reduction modulo f) and its
+inverse, the cubic matrix product of Algorithm 1, the triangular solve of
+Algorithm 5 (Section 4.3) and the slicing / clinging conversions of
 Section 3.2 and Figure 1.  This module only compiles that file with gcc and
 marshals numpy arrays to it.
 """
@@ -75,6 +77,12 @@ class OracleLib:
         L.oracle_slice.argtypes = [i32, i64, i64, vp, vp, i64]
         L.oracle_cling.restype = None
         L.oracle_cling.argtypes = [i32, i64, i64, vp, i64, vp]
+        L.oracle_gf_inv.restype = u32
+        L.oracle_gf_inv.argtypes = [i32, u32, u32]
+        L.oracle_trsm_upper_left.restype = i32
+        L.oracle_trsm_upper_left.argtypes = [i32, u32, i64, i64, vp, vp]
+        L.oracle_trsm_lower_left.restype = i32
+        L.oracle_trsm_lower_left.argtypes = [i32, u32, i64, i64, vp, vp]
         self.L = L
         self.path = path
 
@@ -139,6 +147,23 @@ class OracleLib:
         self.L.oracle_cling(e, rows, cols, S.ctypes.data, ld_words, out.ctypes.data)
         return out.astype(elem_dtype(e))
 
+    def gf_inv(self, e: int, f: int, a: int) -> int:
+        """a^(2^e - 2), the inverse of a != 0 (0 for a = 0)."""
+        return int(self.L.oracle_gf_inv(e, f, a))
+
+    def trsm(self, e: int, f: int, T, B, upper: bool = True) -> np.ndarray:
+        """Algorithm 5: T^{-1} * B for T square triangular (upper or lower);
+        returns a new array.  Raises ZeroDivisionError on a zero diagonal."""
+        T16 = _as_u16(T, e, "T")
+        B16 = _as_u16(B, e, "B").copy()
+        if T16.ndim != 2 or T16.shape[0] != T16.shape[1] or B16.ndim != 2 or B16.shape[0] != T16.shape[0]:
+            raise ValueError(f"shape mismatch: T {T16.shape}, B {B16.shape}")
+        m, n = B16.shape
+        fn = self.L.oracle_trsm_upper_left if upper else self.L.oracle_trsm_lower_left
+        if m and fn(e, f, m, n, T16.ctypes.data, B16.ctypes.data) != 0:
+            raise ZeroDivisionError("zero on the diagonal")
+        return B16.astype(elem_dtype(e))
+
     def freivalds(self, e: int, f: int, A, B, C, trials: int = 64, seed: int = 0) -> bool:
         """Randomised check that C == A * B: with X an n x trials matrix of
         uniform field elements, compare A(BX) with CX.  A wrong C passes one
@@ -193,3 +218,11 @@ def cling(e, slices, cols):
 
 def freivalds(e, f, A, B, C, trials=64, seed=0):
     return default().freivalds(e, f, A, B, C, trials, seed)
+
+
+def gf_inv(e, f, a):
+    return default().gf_inv(e, f, a)
+
+
+def trsm(e, f, T, B, upper=True):
+    return default().trsm(e, f, T, B, upper)

@@ -1,5 +1,6 @@
 /*
- * CPU oracle for dense matrix multiplication over GF(2^e), 2 <= e <= 10.
+ * CPU oracle for dense matrix multiplication and triangular solving over
+ * GF(2^e), 2 <= e <= 10.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
  * calls this file; only the tests, the smoke check and the CPU-baseline leg of
@@ -20,6 +21,12 @@
  *     of Algorithm 1 are garbled; the standard reading C[r][c] =
  *     sum_t A[r][t] * B[t][c] (A is m x l, B is l x n) is used.
  *   - Addition in characteristic 2 is XOR (Section 1 and Section 3.1).
+ *   - Field inverse: a^(2^e - 2), since the multiplicative group has order
+ *     2^e - 1.
+ *   - Triangular solving with matrices (Section 4.3, Algorithm 5): for U
+ *     upper triangular, rows of B from the last to the first are scaled by
+ *     the inverse diagonal entry and eliminated from the rows above; the
+ *     lower-triangular case runs the same steps from the first row down.
  *   - Slicing (Section 3.2 and Figure 1): slice i of a matrix holds
  *     coefficient i (bit i of the integer encoding) of every entry.  Slices
  *     are stored as rows of 64-bit words, column c at bit (c mod 64) of word
@@ -27,7 +34,8 @@
  *
  * Parity of every function here is pinned by the tests in tests/ against
  * values fixed independently of this file (Figure 1, the GF(4) example of
- * Section 5, brute-force field axioms, logarithm tables, invariants).
+ * Section 5, brute-force field axioms, logarithm tables, invariants, and for
+ * the solver U * X = B checked with the separately pinned product).
  */
 #include <stdint.h>
 #include <string.h>
@@ -132,4 +140,78 @@ void oracle_cling(int e, int64_t rows, int64_t cols, const uint64_t *slices,
             }
             elems[r * cols + c] = (uint16_t)v;
         }
+}
+
+/* Field inverse: a^(2^e - 2) by square-and-multiply with oracle_gf_mul (the
+ * group of non-zero elements has order 2^e - 1).  Returns 0 for a = 0. */
+uint32_t oracle_gf_inv(int e, uint32_t f, uint32_t a)
+{
+    uint32_t r = 1, base = a, x = (1u << e) - 2;
+    if (a == 0)
+        return 0;
+    while (x) {
+        if (x & 1u)
+            r = oracle_gf_mul(e, f, r, base);
+        base = oracle_gf_mul(e, f, base, base);
+        x >>= 1;
+    }
+    return r;
+}
+
+/* Section 4.3, Algorithm 5 (TRSM upper left): B <- U^{-1} * B, U m x m upper
+ * triangular (row-major, leading dimension m), B m x n (leading dimension n).
+ * For i from m-1 down to 0: row i of B is multiplied by U[i][i]^{-1}, then
+ * U[j][i] times row i is added to row j for every j < i.  The algorithm's
+ * table T of the multiples of row i is a speed device only; the products
+ * U[j][i] * B[i][c] are formed directly.  The row updates for one i are
+ * independent and run on several threads.  Returns 0, or -1 if a diagonal
+ * entry is zero (no solution is defined; B is left partly updated). */
+int oracle_trsm_upper_left(int e, uint32_t f, int64_t m, int64_t n, const uint16_t *U, uint16_t *B)
+{
+    int nt = oracle_get_threads();
+    (void)nt;
+    for (int64_t i = m - 1; i >= 0; i--) {
+        uint32_t d = U[i * m + i];
+        if (d == 0)
+            return -1;
+        uint32_t dinv = oracle_gf_inv(e, f, d);
+        uint16_t *bi = B + i * n;
+        for (int64_t c = 0; c < n; c++)
+            bi[c] = (uint16_t)oracle_gf_mul(e, f, dinv, bi[c]);
+#pragma omp parallel for schedule(static) num_threads(nt) if (i * n > 65536)
+        for (int64_t j = 0; j < i; j++) {
+            uint32_t x = U[j * m + i];
+            uint16_t *bj = B + j * n;
+            for (int64_t c = 0; c < n; c++)
+                bj[c] ^= (uint16_t)oracle_gf_mul(e, f, x, bi[c]);
+        }
+    }
+    return 0;
+}
+
+/* The lower-left counterpart: B <- L^{-1} * B, L m x m lower triangular.  For
+ * i from 0 up to m-1: row i is multiplied by L[i][i]^{-1}, then L[j][i] times
+ * row i is added to row j for every j > i.  Returns 0, or -1 on a zero
+ * diagonal entry. */
+int oracle_trsm_lower_left(int e, uint32_t f, int64_t m, int64_t n, const uint16_t *L, uint16_t *B)
+{
+    int nt = oracle_get_threads();
+    (void)nt;
+    for (int64_t i = 0; i < m; i++) {
+        uint32_t d = L[i * m + i];
+        if (d == 0)
+            return -1;
+        uint32_t dinv = oracle_gf_inv(e, f, d);
+        uint16_t *bi = B + i * n;
+        for (int64_t c = 0; c < n; c++)
+            bi[c] = (uint16_t)oracle_gf_mul(e, f, dinv, bi[c]);
+#pragma omp parallel for schedule(static) num_threads(nt) if ((m - i) * n > 65536)
+        for (int64_t j = i + 1; j < m; j++) {
+            uint32_t x = L[j * m + i];
+            uint16_t *bj = B + j * n;
+            for (int64_t c = 0; c < n; c++)
+                bj[c] ^= (uint16_t)oracle_gf_mul(e, f, x, bi[c]);
+        }
+    }
+    return 0;
 }

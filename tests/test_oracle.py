@@ -246,6 +246,89 @@ def test_threads_setting():
     assert oracle.get_threads() == n
 
 
+# ---------------------------------------------------------------- TRSM (Section 4.3, Algorithm 5)
+
+
+def _triangular(e, m, upper, rng, junk=False):
+    """Random triangular matrix with non-zero diagonal; `junk` fills the other
+    triangle with random entries (which a solver must not read)."""
+    T = rng.integers(0, 1 << e, size=(m, m)).astype(np.uint16)
+    keep = np.triu(np.ones((m, m), bool)) if upper else np.tril(np.ones((m, m), bool))
+    if not junk:
+        T[~keep] = 0
+    T[np.arange(m), np.arange(m)] = rng.integers(1, 1 << e, size=m)
+    return T
+
+
+@pytest.mark.parametrize("e", [2, 3, 4, 5, 8, 9, 10])
+def test_field_inverse_against_log_tables(e):
+    f = workloads.FIELD_POLY[e]
+    table = fr.log_table_product(e, f)
+    for a in range(1, 1 << e):
+        assert table[a, oracle.gf_inv(e, f, a)] == 1
+    assert oracle.gf_inv(e, f, 0) == 0
+
+
+@pytest.mark.parametrize("e", [2, 3, 4, 7, 8, 10])
+@pytest.mark.parametrize("upper", [True, False])
+def test_trsm_solves_the_system(e, upper):
+    """T * X == B, the product formed by the slice decomposition of Section 5
+    (fieldref), not by the oracle; X is unique because T is invertible."""
+    rng = np.random.default_rng(100 + e)
+    f = workloads.FIELD_POLY[e]
+    m, n = 29, 17
+    T = _triangular(e, m, upper, rng)
+    B = rng.integers(0, 1 << e, size=(m, n)).astype(np.uint16)
+    X = oracle.trsm(e, f, T, B, upper)
+    assert np.array_equal(fr.slice_product(e, f, T, X), B.astype(np.int64))
+
+
+@pytest.mark.parametrize("upper", [True, False])
+def test_trsm_ignores_the_other_triangle(upper):
+    rng = np.random.default_rng(7)
+    e, f = 4, workloads.FIELD_POLY[4]
+    T = _triangular(e, 20, upper, rng)
+    J = T.copy()
+    keep = np.triu(np.ones(T.shape, bool)) if upper else np.tril(np.ones(T.shape, bool))
+    J[~keep] = rng.integers(0, 1 << e, size=int((~keep).sum()))
+    B = rng.integers(0, 1 << e, size=(20, 9)).astype(np.uint16)
+    assert np.array_equal(oracle.trsm(e, f, T, B, upper), oracle.trsm(e, f, J, B, upper))
+
+
+def test_trsm_identity_and_diagonal():
+    rng = np.random.default_rng(8)
+    e, f = 8, workloads.FIELD_POLY[8]
+    table = fr.log_table_product(e, f)
+    B = rng.integers(0, 256, size=(12, 7)).astype(np.uint16)
+    assert np.array_equal(oracle.trsm(e, f, np.eye(12, dtype=np.uint16), B), B)
+    d = rng.integers(1, 256, size=12)
+    D = np.diag(d).astype(np.uint16)
+    X = oracle.trsm(e, f, D, B, upper=False)
+    # D X = B row by row: d_i * X[i][c] == B[i][c] in the log-table field
+    for i in range(12):
+        assert all(table[d[i], X[i, c]] == B[i, c] for c in range(7))
+
+
+def test_trsm_brute_force_2x2_over_gf4():
+    """Every invertible upper-triangular 2x2 system over GF(4) with every
+    right-hand side: the oracle's X is the unique x with T x = b."""
+    e, f = 2, workloads.FIELD_POLY[2]
+    table = fr.log_table_product(e, f)
+    for t00, t01, t11, b0, b1 in itertools.product(range(1, 4), range(4), range(1, 4), range(4), range(4)):
+        sols = [(x0, x1) for x0 in range(4) for x1 in range(4)
+                if table[t00, x0] ^ table[t01, x1] == b0 and table[t11, x1] == b1]
+        assert len(sols) == 1
+        T = np.array([[t00, t01], [0, t11]], dtype=np.uint16)
+        X = oracle.trsm(e, f, T, np.array([[b0], [b1]], dtype=np.uint16))
+        assert (int(X[0, 0]), int(X[1, 0])) == sols[0]
+
+
+def test_trsm_zero_diagonal_raises():
+    T = np.array([[1, 2], [0, 0]], dtype=np.uint16)
+    with pytest.raises(ZeroDivisionError):
+        oracle.trsm(2, 7, T, np.ones((2, 3), dtype=np.uint16))
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 _MUTANTS = {
@@ -263,6 +346,15 @@ _MUTANTS = {
     "slice_msb": ("row[c / 64] |= (uint64_t)1 << (c % 64);", "row[c / 64] |= (uint64_t)1 << (63 - c % 64);"),
     # addition as OR instead of XOR
     "add_or": ("crow[c] ^= (uint16_t)oracle_gf_mul(e, f, a, brow[c]);", "crow[c] |= (uint16_t)oracle_gf_mul(e, f, a, brow[c]);"),
+    # field inverse with the wrong exponent
+    "inv_exponent": ("x = (1u << e) - 2;", "x = (1u << e) - 3;"),
+    # upper solve reads the multiplier from the transposed position
+    "trsm_transposed": ("uint32_t x = U[j * m + i];", "uint32_t x = U[i * m + j];"),
+    # lower solve skips the row just below the pivot row
+    "trsm_skip_row": ("for (int64_t j = i + 1; j < m; j++) {", "for (int64_t j = i + 2; j < m; j++) {"),
+    # upper solve does not scale by the inverse diagonal entry
+    "trsm_no_scale": ("for (int64_t i = m - 1; i >= 0; i--) {\n        uint32_t d = U[i * m + i];\n        if (d == 0)\n            return -1;\n        uint32_t dinv = oracle_gf_inv(e, f, d);",
+                      "for (int64_t i = m - 1; i >= 0; i--) {\n        uint32_t d = U[i * m + i];\n        if (d == 0)\n            return -1;\n        uint32_t dinv = 1;"),
 }
 
 
@@ -284,6 +376,17 @@ def _pins_pass(O: oracle.OracleLib) -> bool:
             A, B, _ = workloads.random_problem(e, 13, 11, 17, seed=9)
             if not np.array_equal(O.matmul(e, f, A, B).astype(np.int64), fr.slice_product(e, f, A, B)):
                 return False
+        for e in (3, 8):
+            f = workloads.FIELD_POLY[e]
+            table = fr.log_table_product(e, f)
+            if any(table[a, O.gf_inv(e, f, a)] != 1 for a in range(1, 1 << e)):
+                return False
+            rng = np.random.default_rng(e)
+            for upper in (True, False):
+                T = _triangular(e, 9, upper, rng)
+                B = rng.integers(0, 1 << e, size=(9, 5)).astype(np.uint16)
+                if not np.array_equal(fr.slice_product(e, f, T, O.trsm(e, f, T, B, upper)), B.astype(np.int64)):
+                    return False
         return True
     except Exception:
         return False
