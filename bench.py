@@ -182,10 +182,182 @@ def cpu_baseline(rows: int = 256):
              "sample": f"rows 0..{rows - 1} of A times B ({rows}x{w.k}x{w.n}), one run, {dt:.2f} s"}, ref)
 
 
+def trsm_macs(m: int, n: int, nb: int = 128) -> int:
+    """Field multiply-adds of the library's blocked solve: leaf products of the
+    inverted diagonal blocks (nb_i x n x nb_i) and the off-diagonal updates
+    (m1 x n x m2), with the split m1 = roundup(ceil(m/2), nb)."""
+    if m <= nb:
+        return m * m * n
+    m1 = -(-((m + 1) // 2) // nb) * nb
+    return trsm_macs(m1, n, nb) + trsm_macs(m - m1, n, nb) + m1 * (m - m1) * n
+
+
+def trsm_config(name):
+    e, m, n, seed = workloads.TRSM_WORKLOADS[name]
+    ty = "uint8" if e <= 8 else "uint16"
+    return e, m, n, seed, {
+        "workload": f"B <- T^-1 B over GF(2^{e}), f = {hex(workloads.FIELD_POLY[e])}, T {m}x{m} upper triangular, "
+                    f"B {m}x{n} {ty}", "m": m, "n": n, "e": e, "op": "trsm_upper_left",
+        "l2": "flushed between timed steps (512 MB write, not timed)"}
+
+
+def trsm_cpu_sample(e, f, T, B, cols):
+    """The oracle's solve on the first `cols` columns (columns are independent)."""
+    import oracle
+    t0 = time.perf_counter()
+    X = oracle.trsm(e, f, T, np.ascontiguousarray(B[:, :cols]), True)
+    return X, time.perf_counter() - t0
+
+
+def run_reference_trsm(args):
+    e, m, n, seed, config = trsm_config(args.workload)
+    f = workloads.FIELD_POLY[e]
+    T, B = workloads.triangular_system(e, m, n, seed)
+    cols = max(1, args.ref_rows)
+    for _ in range(args.warmup):
+        trsm_cpu_sample(e, f, T, B, cols)
+    times = [trsm_cpu_sample(e, f, T, B, cols)[1] for _ in range(args.steps)]
+    per = sum(times) / len(times)
+    value = float(m) * m * cols / per
+    import oracle
+    out = {"impl": "reference", "metric": f"GF(2^e) triangular solve field-ops/s (m^2 n), {args.workload}",
+           "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u8" if e <= 8 else "u16", "data": "synthetic", "config": config,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                            "sample": f"each step: columns 0..{cols - 1} of B ({m}x{cols})"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_trsm_workload(args, m4, torch, world, rank, local):
+    """B <- T^{-1} B (Section 4.3, Algorithm 5, blocked and recursive over the
+    slice GEMM).  value = m^2 n field operations (m^2 n / 2 multiply-adds) per
+    second of one solve; repeated solves replay the recorded CUDA graph."""
+    e, m, n, seed, config = trsm_config(args.workload)
+    f = workloads.FIELD_POLY[e]
+    T, B = workloads.triangular_system(e, m, n, seed)
+    dT = torch.from_numpy(T).cuda()
+    dB0 = torch.from_numpy(B).cuda()
+    dX = dB0.clone()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = m4.Context(stream)
+    ops = float(m) * m * n
+    results, X_auto = {}, None
+    for form in ("auto", "popc", "tc_f4"):
+        ctx.set_form(form)
+        ctx.set_schedule("auto")
+        dX.copy_(dB0)
+        ctx.trsm(e, f, dT, dX, True)
+        torch.cuda.synchronize()
+        verified = bool(torch.equal(ctx.mul(e, f, dT, dX), dB0))     # T X == B through the product
+        if form == "auto":
+            X_auto = dX.clone()
+        for _ in range(args.warmup):
+            ctx.trsm(e, f, dT, dX, True)
+        torch.cuda.synchronize()
+        launches0 = ctx.kernel_launches()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        with ClockSampler(local) as clk:
+            time.sleep(0.3)
+            torch.cuda.synchronize()
+            clk.mark_start()
+            for i in range(args.steps):
+                flush.fill_(i & 0xFF)
+                starts[i].record(stream)
+                ctx.trsm(e, f, dT, dX, True)
+                stops[i].record(stream)
+            torch.cuda.synchronize()
+            clk.mark_end()
+            time.sleep(0.1)
+        ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops)) / args.steps
+        _, sec = replica_throughput(ops, ms * 1e-3, "cuda")
+        results[form] = {"ms_per_step": sec * 1e3, "value": world * ops / sec, "verified": verified,
+                         "launches": (ctx.kernel_launches() - launches0) // max(args.steps, 1),
+                         "clocks": clk.summary(), "device_status": ctx.device_status()}
+    good = {k: v for k, v in results.items() if v["verified"] and v["device_status"] == m4.OK}
+    best_key = max(good, key=lambda k: good[k]["value"])
+    best = good[best_key]
+
+    # GEMM phase of one eager solve with every product on the FP4 form and the
+    # Karatsuba schedule: its tensor work over its CUDA-event time
+    ctx.set_form("tc_f4")
+    ctx.set_schedule("karatsuba")
+    ctx.enable_timing(True)
+    ctx.phase_times(reset=True)
+    dX.copy_(dB0)
+    ctx.trsm(e, f, dT, dX, True)
+    pack_ms, gemm_ms, rec_ms, nprod = ctx.phase_times(reset=True)
+    ctx.enable_timing(False)
+    r = m4.schedule_products(e, f, "karatsuba")
+    flops = 2.0 * r * trsm_macs(m, n)
+    pk = peaks() or {}
+    peak = pk.get("bf16_tflops", 1900.0) * 6.0
+    ceil = 2.0 * MMA_MAC_PER_CLK["tc_f4"] * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (gemm_ms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": "measured bf16 burst x 6.0 (nominal f4/bf16 dense ratio)",
+            "instruction_ceiling": {"value": ceil, "frac": achieved / ceil,
+                                    "source": "tcgen05.mma issue-rate microbenchmark, M = 128"},
+            "scope": f"slice GEMMs of one eager solve on tc_f4/karatsuba ({nprod} products, "
+                     f"{gemm_ms:.3f} ms of GEMM phase, {pack_ms:.3f} ms packing, {rec_ms:.3f} ms recombination)"}
+
+    # end to end through the public API: pinned host T and B in, X out
+    ctx.set_form(best_key)
+    ctx.set_schedule("auto")
+    hT = torch.from_numpy(T).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hX = torch.empty_like(hB).pin_memory()
+    e2e_steps = max(3, args.steps // 4)
+    times = []
+    for i in range(e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dT.copy_(hT, non_blocking=True)
+        dX.copy_(hB, non_blocking=True)
+        ctx.trsm(e, f, dT, dX, True)
+        hX.copy_(dX, non_blocking=True)
+        torch.cuda.synchronize()
+        if i:
+            times.append(time.perf_counter() - t0)
+    e2e_s = sum(times) / len(times)
+    _, e2e_s = replica_throughput(ops, e2e_s, "cuda")
+
+    out = {"metric": f"GF(2^e) triangular solve field-ops/s (m^2 n), {args.workload}; bit-exact",
+           "value": best["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": best["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u8" if e <= 8 else "u16", "data": "synthetic",
+           "config": dict(config, form=best_key, parallelism=f"replicas{world}"),
+           "clocks": best["clocks"], "gpu_launches": best["launches"],
+           "e2e": {"value": world * ops / e2e_s, "unit": UNIT, "h2d_bytes_per_step": T.nbytes + B.nbytes,
+                   "d2h_bytes_per_step": B.nbytes},
+           "roofline": roof,
+           "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "verified": v["verified"]}
+                     for k, v in results.items()}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cols = 32
+        X_ref, dt = trsm_cpu_sample(e, f, T, B, cols)
+        import oracle
+        out["cpu_baseline"] = {"value": float(m) * m * cols / dt, "unit": UNIT, "cores": oracle.get_threads(),
+                               "kind": "oracle",
+                               "sample": f"columns 0..{cols - 1} of B ({m}x{cols}), one run, {dt:.2f} s"}
+        out["bit_exact_vs_oracle"] = {"columns_checked": cols,
+                                      "equal": bool(np.array_equal(X_auto[:, :cols].cpu().numpy(), X_ref))}
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
+    if args.workload in workloads.TRSM_WORKLOADS:
+        return run_reference_trsm(args)
     import oracle
     w = WORKLOAD
     A, B, _ = w.inputs()
@@ -269,8 +441,10 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     names = {w.name: i for i, w in workloads.WORKLOADS.items()}
-    ap.add_argument("--workload", default="gf16_4096_mul", choices=sorted(names) + ["batched"],
-                    help="gf16_4096_mul (default, the headline), another single-product workload, or batched")
+    ap.add_argument("--workload", default="gf16_4096_mul",
+                    choices=sorted(names) + ["batched"] + sorted(workloads.TRSM_WORKLOADS),
+                    help="gf16_4096_mul (default, the headline), another single-product workload, batched, "
+                         "or a triangular solve (trsm_*)")
     ap.add_argument("--batched-count", type=int, default=workloads.BATCHED_COUNT,
                     help="instances of the batched workload (a prefix of it; the default is the whole batch)")
     ap.add_argument("--single", default=None,
@@ -278,6 +452,10 @@ def main():
                          "(a fixed launch sequence for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    global WORKLOAD, CONFIG
+    if args.workload in names:
+        WORKLOAD = workloads.WORKLOADS[names[args.workload]]
+        CONFIG = config_of(WORKLOAD)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -293,10 +471,9 @@ def main():
 
     if args.workload == "batched":
         return run_batched_workload(args, m4, torch, world, rank, local)
+    if args.workload in workloads.TRSM_WORKLOADS:
+        return run_trsm_workload(args, m4, torch, world, rank, local)
 
-    global WORKLOAD, CONFIG
-    WORKLOAD = workloads.WORKLOADS[names[args.workload]]
-    CONFIG = config_of(WORKLOAD)
     metric = METRIC if WORKLOAD.name == "gf16_4096_mul" else f"GF(2^e) matmul field-ops/s, {WORKLOAD.name}; bit-exact"
     w = WORKLOAD
     A, B, C0 = w.inputs()

@@ -52,7 +52,8 @@ typedef enum m4rie_status {
     M4RIE_ERR_CUDA = 6,       /* a CUDA runtime or driver call failed (see m4rie_last_error) */
     M4RIE_ERR_TIMEOUT = 7,    /* device: a bounded wait inside a kernel ran out; that kernel's output is incomplete */
     M4RIE_ERR_UNSUPPORTED = 8, /* the requested form is not available for this problem or device */
-    M4RIE_ERR_SCRATCH = 9      /* m4rie_mul_noalloc: the operand planes exceed its fixed scratch array */
+    M4RIE_ERR_SCRATCH = 9,     /* m4rie_mul_noalloc: the operand planes exceed its fixed scratch array */
+    M4RIE_ERR_SINGULAR = 10    /* device: a triangular solve met a zero on the diagonal; its output is undefined */
 } m4rie_status;
 
 /* How the GF(2) slice products are computed. */
@@ -112,6 +113,35 @@ m4rie_status m4rie_mul(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, 
  * updated in place; otherwise as m4rie_mul. */
 m4rie_status m4rie_addmul(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
                           const void *A, const void *B, void *C);
+
+/* C = A * B (accumulate == 0) or C = C + A * B (accumulate != 0) over
+ * GF(2^e) on strided windows (the matrix windows Section 3 takes over from
+ * M4RI): row r of A starts at A + r * lda elements, of B at B + r * ldb, of C
+ * at C + r * ldc.  Requires lda >= k, ldb >= n, ldc >= n (M4RIE_ERR_ARG);
+ * the bytes C spans must not overlap those A or B span (M4RIE_ERR_ALIAS).
+ * Otherwise as m4rie_mul; m4rie_mul is m4rie_gemm with lda = k, ldb = ldc = n. */
+m4rie_status m4rie_gemm(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
+                        const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc,
+                        int accumulate);
+
+/* Triangular solving with matrices (Section 4.3, Algorithm 5): B <- T^{-1} * B
+ * over GF(2^e), in place.  T is m x m (row stride ldt >= m), upper triangular
+ * for m4rie_trsm_upper_left, lower triangular for m4rie_trsm_lower_left; the
+ * other triangle is never read, so T may share storage with other data (an
+ * in-place PLE, for instance).  B is m x n (row stride ldb >= n) and must not
+ * overlap T (M4RIE_ERR_ALIAS).  Blocked and recursive: diagonal blocks of 128
+ * rows are inverted in shared memory, every other step is a slice GEMM
+ * (m4rie_gemm).  A zero diagonal entry sets the sticky device status
+ * M4RIE_ERR_SINGULAR (B is then undefined); an entry >= 2^e sets
+ * M4RIE_ERR_RANGE.  Asynchronous on the context's stream; uses a context-owned
+ * scratch of ceil(m / 128) x 128 x 128 elements.  The first solve on given
+ * operands and settings is also recorded as a CUDA graph, which later solves
+ * with the same pointers, sizes, field and settings replay (reading the
+ * buffers' current contents). */
+m4rie_status m4rie_trsm_upper_left(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, const void *T,
+                                   int64_t ldt, void *B, int64_t ldb);
+m4rie_status m4rie_trsm_lower_left(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, const void *T,
+                                   int64_t ldt, void *B, int64_t ldb);
 
 /* m4rie_mul / m4rie_addmul (accumulate != 0) on HOST buffers: copies A, B
  * (and C when accumulating) to context-owned device memory, computes, copies

@@ -14,7 +14,8 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libm4rie_gpu.so")
 
-OK, ERR_ARG, ERR_POLY, ERR_ALIAS, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH = range(10)
+(OK, ERR_ARG, ERR_POLY, ERR_ALIAS, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH,
+ ERR_SINGULAR) = range(11)
 FORM_AUTO, FORM_POPC, FORM_TC_F8, FORM_MMA_S8, FORM_TC_F4 = range(5)
 SCHED_AUTO, SCHED_ALPHA_B, SCHED_KARATSUBA = range(3)
 FORMS = {"auto": FORM_AUTO, "popc": FORM_POPC, "tc_f8": FORM_TC_F8, "mma_s8": FORM_MMA_S8, "tc_f4": FORM_TC_F4}
@@ -49,6 +50,9 @@ def _load() -> ctypes.CDLL:
         "m4rie_set_schedule": (i32, [vp, i32]),
         "m4rie_mul": (i32, [vp, i32, u32, i64, i64, i64, vp, vp, vp]),
         "m4rie_addmul": (i32, [vp, i32, u32, i64, i64, i64, vp, vp, vp]),
+        "m4rie_gemm": (i32, [vp, i32, u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, i32]),
+        "m4rie_trsm_upper_left": (i32, [vp, i32, u32, i64, i64, vp, i64, vp, i64]),
+        "m4rie_trsm_lower_left": (i32, [vp, i32, u32, i64, i64, vp, i64, vp, i64]),
         "m4rie_mul_host": (i32, [vp, i32, u32, i64, i64, i64, vp, vp, vp, i32]),
         "m4rie_pack": (i32, [vp, i32, i64, i64, vp, vp, i64]),
         "m4rie_unpack": (i32, [vp, i32, i64, i64, vp, i64, vp]),
@@ -96,14 +100,22 @@ def _ptr(t):
     return None if t is None or t.numel() == 0 else ctypes.c_void_p(t.data_ptr())
 
 
-def _check_dev(t, e, name):
+def _check_dev(t, e, name, strided=False):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != elem_dtype_torch(e):
         raise TypeError(f"{name} must be {elem_dtype_torch(e)} for e = {e}")
-    if not t.is_contiguous():
+    if strided:
+        if t.dim() != 2 or (t.numel() and t.shape[1] > 1 and t.stride(1) != 1):
+            raise ValueError(f"{name} must be a 2-D window with unit column stride")
+    elif not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous (row-major)")
+
+
+def _ld(t):
+    """Row stride of a 2-D window (elements); any value >= its width is valid for one row."""
+    return max(int(t.stride(0)), int(t.shape[1])) if t.shape[0] > 1 else int(t.shape[1])
 
 
 class Context:
@@ -170,6 +182,34 @@ class Context:
         n = B.shape[1]
         self._raise(lib.m4rie_addmul(self.handle, e, f, m, n, k, _ptr(A), _ptr(B), _ptr(C)), "m4rie_addmul")
         return C
+
+    def gemm(self, e: int, f: int, A, B, C, accumulate: bool = False):
+        """C = A B (or C += A B) on 2-D windows of larger tensors (row strides
+        from the tensors, unit column stride).  Asynchronous."""
+        for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+            _check_dev(t, e, nm, strided=True)
+        m, k = A.shape
+        k2, n = B.shape
+        if k2 != k or tuple(C.shape) != (m, n):
+            raise ValueError("shapes do not match")
+        self._raise(lib.m4rie_gemm(self.handle, e, f, m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(C), _ld(C),
+                                   1 if accumulate else 0), "m4rie_gemm")
+        return C
+
+    def trsm(self, e: int, f: int, T, B, upper: bool = True):
+        """B <- T^{-1} B in place (Algorithm 5), T square triangular (the
+        other triangle is not read); windows with unit column stride.
+        Asynchronous; a zero diagonal shows as ERR_SINGULAR in device_status()."""
+        _check_dev(T, e, "T", strided=True)
+        _check_dev(B, e, "B", strided=True)
+        m = T.shape[0]
+        if T.shape[1] != m or B.shape[0] != m:
+            raise ValueError("T must be m x m and B m x n")
+        n = B.shape[1]
+        fn = lib.m4rie_trsm_upper_left if upper else lib.m4rie_trsm_lower_left
+        self._raise(fn(self.handle, e, f, m, n, _ptr(T), _ld(T), _ptr(B), _ld(B)),
+                    "m4rie_trsm_upper_left" if upper else "m4rie_trsm_lower_left")
+        return B
 
     def mul_host(self, e: int, f: int, A, B, C, accumulate: bool = False):
         """Host-buffer product (torch CPU tensors or numpy arrays); synchronous."""

@@ -67,18 +67,32 @@ m4rie_status check_field(int e, uint32_t f) {
   return M4RIE_OK;
 }
 
-m4rie_status validate(int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
-                      const void* C) {
+// Bytes spanned by a rows x cols window with row stride ld (elements of w bytes).
+size_t span_bytes(int64_t rows, int64_t cols, int64_t ld, size_t w) {
+  return rows && cols ? (size_t)((rows - 1) * ld + cols) * w : 0;
+}
+
+// c_over_b: C may coincide with B (internal callers only; see run_gemm).
+m4rie_status validate_mats(int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x, bool c_over_b = false) {
   m4rie_status st = check_field(e, f);
   if (st != M4RIE_OK) return st;
   if (m < 0 || n < 0 || k < 0) return M4RIE_ERR_ARG;
   // sizes the kernels index with 32-bit block counts and 64-bit offsets
   if (m > (1ll << 31) || n > (1ll << 31) || k > (1ll << 31)) return M4RIE_ERR_ARG;
-  if ((m * k && !A) || (k * n && !B) || (m * n && !C)) return M4RIE_ERR_ARG;
+  if (x.lda < k || x.ldb < n || x.ldc < n || x.lda > (1ll << 40) || x.ldb > (1ll << 40) || x.ldc > (1ll << 40))
+    return M4RIE_ERR_ARG;
+  if ((m * k && !x.A) || (k * n && !x.B) || (m * n && !x.C)) return M4RIE_ERR_ARG;
   const size_t w = elem_bytes(e);
-  if (overlaps(C, (size_t)(m * n) * w, A, (size_t)(m * k) * w) || overlaps(C, (size_t)(m * n) * w, B, (size_t)(k * n) * w))
+  const size_t sc = span_bytes(m, n, x.ldc, w);
+  if (overlaps(x.C, sc, x.A, span_bytes(m, k, x.lda, w)) ||
+      (!c_over_b && overlaps(x.C, sc, x.B, span_bytes(k, n, x.ldb, w))))
     return M4RIE_ERR_ALIAS;
   return M4RIE_OK;
+}
+
+m4rie_status validate(int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                      const void* C) {
+  return validate_mats(e, f, m, n, k, Mats{A, k, B, n, const_cast<void*>(C), n});
 }
 
 m4rie_status ensure_ws(m4rie_ctx* ctx, size_t bytes) {
@@ -104,20 +118,21 @@ m4rie_status ensure_ws(m4rie_ctx* ctx, size_t bytes) {
 }
 
 // AUTO choices: the autotuned entry of the shape class if there is one, else a
-// fixed rule from the measurements on GB300 (tcgen05 FP4 above ~2^21 field
-// multiply-adds, Karatsuba above ~2^27; the bit-packed form for small shapes).
+// fixed rule from the measurements on GB300: tcgen05 FP4 from 2^28 field
+// multiply-adds (below that the bit-packed form wins: 512^3 products and the
+// 128-row products inside triangular solves), Karatsuba from 2^30.
 int resolve_form(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k) {
   if (ctx->form != M4RIE_FORM_AUTO) return ctx->form;
   const TuneEntry& t = ctx->tuned[e][shape_class(m, n, k)];
   if (t.form) return t.form;
-  return shape_class(m, n, k) >= 21 ? M4RIE_FORM_TC_F4 : M4RIE_FORM_POPC;
+  return shape_class(m, n, k) >= 28 ? M4RIE_FORM_TC_F4 : M4RIE_FORM_POPC;
 }
 
 int resolve_schedule(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k) {
   if (ctx->schedule != M4RIE_SCHED_AUTO) return ctx->schedule;
   const TuneEntry& t = ctx->tuned[e][shape_class(m, n, k)];
   if (t.form) return t.sched;
-  return shape_class(m, n, k) >= 27 ? M4RIE_SCHED_KARATSUBA : M4RIE_SCHED_ALPHA_B;
+  return shape_class(m, n, k) >= 30 ? M4RIE_SCHED_KARATSUBA : M4RIE_SCHED_ALPHA_B;
 }
 
 int resolve_group_m(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k, int tiles_m) {
@@ -127,6 +142,12 @@ int resolve_group_m(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k, int 
     if (t.form) g = t.group_m;
   }
   return g > 0 ? std::min(g, tiles_m) : tiles_m;
+}
+
+// tcgen05 GEMMs run 2-CTA clusters on m-tile pairs (rows padded to 256) when
+// the pairing adds no padded tile or m is large enough for it not to matter.
+bool pair_m(const m4rie_ctx* ctx, int64_t m) {
+  return ctx->cluster == 2 && m > 256 && (round_up(m, 256) == round_up(m, 128) || m >= 2048);
 }
 
 struct FormInfo {
@@ -147,8 +168,11 @@ FormInfo form_info(int form) {
 size_t entries_bytes(int64_t entries, int bits) { return (size_t)((entries * bits + 7) / 8); }
 
 // ---------------------------------------------------------------- alpha^j-B
-m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A,
-                         const void* B, void* C, int add) {
+m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x,
+                         int add) {
+  const void* A = x.A;
+  const void* B = x.B;
+  void* C = x.C;
   const FormInfo fi = form_info(form);
   int G;
   if (form == M4RIE_FORM_POPC) G = popc_group(e);
@@ -158,7 +182,8 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   const bool tc = form == M4RIE_FORM_TC_F8 || form == M4RIE_FORM_TC_F4;
   const int64_t Kp = round_up(k, 128);
   const int64_t ld = (int64_t)e * Kp;
-  const int64_t Mp = round_up(m, tc && ctx->cluster == 2 ? 256 : 128);  // CTA pairs take m-tile pairs
+  const bool pair = tc && pair_m(ctx, m);
+  const int64_t Mp = round_up(m, pair ? 256 : 128);  // CTA pairs take m-tile pairs
   const int64_t groups = ceil_div(n, G);
   const int64_t brows = groups * e * G;
   const size_t a_bytes = round_up((int64_t)entries_bytes(Mp * ld, fi.bits), 1024);
@@ -172,7 +197,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   alpha_b_masks(e, f, amask, bmask);
   PackParams pa{};
   pa.X = A;
-  pa.ldx = k;
+  pa.ldx = x.lda;
   pa.elem_bytes = elem_bytes(e);
   pa.rows = m;
   pa.K = k;
@@ -188,7 +213,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   pa.bstride = 0;
   pa.emask = (1u << e) - 1;
   pa.e = e;
-  pa.vec = aligned16(A) && (k * elem_bytes(e)) % 16 == 0;
+  pa.vec = aligned16(A) && (x.lda * elem_bytes(e)) % 16 == 0;
   pa.out = Ap;
   pa.status = ctx->d_status;
   for (int j = 0; j < e; ++j) pa.mask[j] = amask[j];
@@ -199,7 +224,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
 
   PackParams pb = pa;  // columns of B (k x n) are the planes' rows
   pb.X = B;
-  pb.ldx = n;
+  pb.ldx = x.ldb;
   pb.rows = n;
   pb.rows_p = groups * G;
   pb.P = e * e;
@@ -223,7 +248,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     pp.n = n;
     pp.e = e;
     pp.C = C;
-    pp.ldc = n;
+    pp.ldc = x.ldc;
     pp.elem_bytes = elem_bytes(e);
     pp.add = add;
     pp.emask = (1u << e) - 1;
@@ -244,7 +269,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.kc = std::max(1, ctx->tc_chunk / 128);
     tp.group_m = resolve_group_m(ctx, e, m, n, k, tp.tiles_m);
     tp.C = C;
-    tp.ldc = n;
+    tp.ldc = x.ldc;
     tp.elem_bytes = elem_bytes(e);
     tp.add = add;
     tp.emask = (1u << e) - 1;
@@ -253,7 +278,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.wait_limit_ns = ctx->wait_limit_ns;
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
-    tp.cluster = ctx->cluster;
+    tp.cluster = pair ? 2 : 1;
     if (form == M4RIE_FORM_MMA_S8) err = launch_mma_s8(Ap, Bp, ld_bytes, tp, ctx->stream, &ctx->launches);
     else err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld_bytes, tp, ctx->num_sms, ctx->stream, &ctx->launches);
   }
@@ -263,7 +288,10 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
 
 // ---------------------------------------------------------------- Karatsuba
 m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
-                           const void* A, const void* B, void* C, int add) {
+                           const Mats& x, int add) {
+  const void* A = x.A;
+  const void* B = x.B;
+  void* C = x.C;
   if (form != M4RIE_FORM_POPC && form != M4RIE_FORM_TC_F8 && form != M4RIE_FORM_TC_F4) return M4RIE_ERR_UNSUPPORTED;
   Schedule sc;
   if (!karatsuba_schedule(e, f, &sc)) {
@@ -273,7 +301,8 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   const FormInfo fi = form_info(form);
   const int r = sc.r;
   const int64_t Kp = round_up(k, 128);
-  const int64_t Mp = round_up(m, form != M4RIE_FORM_POPC && ctx->cluster == 2 ? 256 : 128);
+  const bool pair = form != M4RIE_FORM_POPC && pair_m(ctx, m);
+  const int64_t Mp = round_up(m, pair ? 256 : 128);
   // popc parity tiles are 128 columns; tcgen05 tiles 256 (FP8) or 224 (FP4, which
   // keeps its scale factors in TMEM next to each accumulator)
   const int ntile = form == M4RIE_FORM_POPC ? 128 : (form == M4RIE_FORM_TC_F8 ? 256 : 224);
@@ -290,7 +319,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
 
   PackParams pa{};
   pa.X = A;
-  pa.ldx = k;
+  pa.ldx = x.lda;
   pa.elem_bytes = elem_bytes(e);
   pa.rows = m;
   pa.K = k;
@@ -306,7 +335,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   pa.bstride = Mp * Kp;
   pa.emask = (1u << e) - 1;
   pa.e = e;
-  pa.vec = aligned16(A) && (k * elem_bytes(e)) % 16 == 0;
+  pa.vec = aligned16(A) && (x.lda * elem_bytes(e)) % 16 == 0;
   pa.out = Ap;
   pa.status = ctx->d_status;
   for (int p = 0; p < r; ++p) pa.mask[p] = sc.amask[p];
@@ -316,7 +345,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   if (err != cudaSuccess) return cuda_fail(ctx, err);
   PackParams pb = pa;  // columns of B (k x n) are the planes' rows
   pb.X = B;
-  pb.ldx = n;
+  pb.ldx = x.ldb;
   pb.rows = n;
   pb.rows_p = Np;
   pb.bstride = Np * Kp;
@@ -366,7 +395,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     tp.wait_limit_ns = ctx->wait_limit_ns;
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
-    tp.cluster = ctx->cluster;
+    tp.cluster = pair ? 2 : 1;
     err = launch_tc(fi.fmt, Ap, (int64_t)r * Mp, Bp, (int64_t)r * Np, ld_bytes, tp, ctx->num_sms, ctx->stream,
                     &ctx->launches);
   }
@@ -381,7 +410,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   rc.m = m;
   rc.n = n;
   rc.C = C;
-  rc.ldc = n;
+  rc.ldc = x.ldc;
   rc.elem_bytes = elem_bytes(e);
   rc.add = add;
   rc.emask = (1u << e) - 1;
@@ -392,22 +421,36 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   return M4RIE_OK;
 }
 
-m4rie_status run_mul(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A,
-                     const void* B, void* C, int add) {
+}  // namespace
+
+namespace m4rie {
+
+m4rie_status run_gemm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x, int add,
+                      bool c_over_b) {
   if (!ctx) return M4RIE_ERR_ARG;
-  m4rie_status st = validate(e, f, m, n, k, A, B, C);
+  m4rie_status st = validate_mats(e, f, m, n, k, x, c_over_b && !add);
   if (st != M4RIE_OK) return st;
   if (m == 0 || n == 0) return M4RIE_OK;
   if (k == 0) {
     if (add) return M4RIE_OK;
-    cudaError_t err = cudaMemsetAsync(C, 0, (size_t)(m * n) * elem_bytes(e), ctx->stream);
+    const size_t w = elem_bytes(e);
+    cudaError_t err = cudaMemset2DAsync(x.C, (size_t)x.ldc * w, 0, (size_t)n * w, (size_t)m, ctx->stream);
     return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
   }
   const int form = resolve_form(ctx, e, m, n, k);
   const int sched = resolve_schedule(ctx, e, m, n, k);
   if (ctx->timing) ++ctx->timed_products;
-  if (sched == M4RIE_SCHED_KARATSUBA) return run_karatsuba(ctx, form, e, f, m, n, k, A, B, C, add);
-  return run_alpha_b(ctx, form, e, f, m, n, k, A, B, C, add);
+  if (sched == M4RIE_SCHED_KARATSUBA) return run_karatsuba(ctx, form, e, f, m, n, k, x, add);
+  return run_alpha_b(ctx, form, e, f, m, n, k, x, add);
+}
+
+}  // namespace m4rie
+
+namespace {
+
+m4rie_status run_mul(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A,
+                     const void* B, void* C, int add) {
+  return run_gemm(ctx, e, f, m, n, k, Mats{A, k, B, n, C, n}, add);
 }
 
 }  // namespace
@@ -446,6 +489,9 @@ void m4rie_destroy(m4rie_ctx* ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->io) cudaFree(ctx->io);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  destroy_trsm_graph(ctx->trsm_graph);
+  if (ctx->tws) cudaFree(ctx->tws);
+  if (ctx->d_gf) cudaFree(ctx->d_gf);
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
   destroy_plan(ctx->plan);
   delete ctx;
@@ -471,6 +517,11 @@ m4rie_status m4rie_mul(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, 
 m4rie_status m4rie_addmul(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A,
                           const void* B, void* C) {
   return run_mul(ctx, e, f, m, n, k, A, B, C, 1);
+}
+
+m4rie_status m4rie_gemm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* A,
+                        int64_t lda, const void* B, int64_t ldb, void* C, int64_t ldc, int accumulate) {
+  return run_gemm(ctx, e, f, m, n, k, Mats{A, lda, B, ldb, C, ldc}, accumulate ? 1 : 0);
 }
 
 m4rie_status m4rie_mul_host(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* hA,
@@ -564,6 +615,7 @@ m4rie_status m4rie_get_device_status(m4rie_ctx* ctx) {
   if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
   if (h & kStatusTimeout) return M4RIE_ERR_TIMEOUT;
+  if (h & kStatusSingular) return M4RIE_ERR_SINGULAR;
   if (h & kStatusRange) return M4RIE_ERR_RANGE;
   return M4RIE_OK;
 }
@@ -635,6 +687,7 @@ const char* m4rie_status_string(m4rie_status s) {
     case M4RIE_ERR_TIMEOUT: return "a bounded wait inside a kernel ran out";
     case M4RIE_ERR_UNSUPPORTED: return "form not available for this problem or device";
     case M4RIE_ERR_SCRATCH: return "problem too large for the fixed scratch of m4rie_mul_noalloc";
+    case M4RIE_ERR_SINGULAR: return "a triangular matrix had a zero on its diagonal";
   }
   return "unknown status";
 }

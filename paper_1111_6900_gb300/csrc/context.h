@@ -10,11 +10,22 @@
 namespace m4rie {
 struct BatchedPlan;
 void destroy_plan(BatchedPlan* plan);
+struct TrsmGraph;
+void destroy_trsm_graph(TrsmGraph* g);
 struct TuneEntry {
   int form = 0, sched = 0, group_m = 0;
   double ms = 0;
 };
 int shape_class(int64_t m, int64_t n, int64_t k);  // floor(log2(m*n*k)), tune.cu
+// Operands of one product: A m x k, B k x n, C m x n, row strides in elements.
+struct Mats {
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  void* C;
+  int64_t ldc;
+};
 }  // namespace m4rie
 
 struct m4rie_ctx {
@@ -46,10 +57,24 @@ struct m4rie_ctx {
   int64_t timed_products = 0;
   // cached plan + CUDA graph of the last batched call (batched.cu)
   m4rie::BatchedPlan* plan = nullptr;
+  // triangular solves (trsm.cu): diagonal-block inverses, a row panel, the
+  // log / antilog tables of the field last used
+  void* tws = nullptr;
+  size_t tws_bytes = 0;
+  uint16_t* d_gf = nullptr;
+  int gf_e = 0;
+  uint32_t gf_f = 0;
+  m4rie::TrsmGraph* trsm_graph = nullptr;  // the last solve, recorded for replay
 };
 
 namespace m4rie {
 // batched.cu: many products in one persistent launch, replayed from a CUDA graph.
 m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* problems, int fmt);
+// api.cu: one product with strided operands (validated, then dispatched by form and schedule).
+// c_over_b (with add == 0): C may be B itself.  Every form reads B only while
+// packing its operand planes, and the kernels that write C run after the
+// packing kernels on the same stream, so C = A * B in place is safe.
+m4rie_status run_gemm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x, int add,
+                      bool c_over_b = false);
 }  // namespace m4rie
 

@@ -7,7 +7,7 @@
 namespace m4rie {
 
 // Device status bits (sticky word owned by the context).
-enum : int { kStatusRange = 1, kStatusTimeout = 2 };
+enum : int { kStatusRange = 1, kStatusTimeout = 2, kStatusSingular = 4 };
 
 // Operand plane formats.  Every plane entry is parity(x & mask) for one
 // element x and one GF(2)-linear mask, stored as:

@@ -1,0 +1,403 @@
+// Triangular solving with matrices over GF(2^e) (Section 4.3, Algorithm 5):
+// B <- T^{-1} * B in place, T upper or lower triangular.
+//
+// Algorithm 5 eliminates one row at a time: scale row i of B by the inverse
+// of the diagonal entry, then add multiples of it to the rows that still
+// depend on it.  Here the same elimination runs by blocks, recursively, so
+// that almost all of its field products are slice GEMMs.  Upper case, with
+// T = [[T00, T01], [0, T11]] and B = [B0; B1]:
+//
+//   X1 = T11^{-1} B1;   B0 <- B0 + T01 X1  (one m4rie_gemm);   X0 = T00^{-1} B0.
+//
+// The lower case mirrors it (first block first).  The recursion splits at
+// multiples of 128 rows and stops at diagonal blocks of at most 128 rows.
+// One kernel launch inverts all of those blocks up front (back substitution
+// on the identity in shared memory, one thread per column, field products
+// from log / antilog tables of the field), and each block's solve is then the
+// slice GEMM X_b = T_bb^{-1} B_b, written over B_b (the product reads B_b only
+// while packing its operand planes, before anything is written).
+//
+// A solve is some 2m/128 library calls of short kernels, so it is bound by
+// launch latency when run call by call.  The first solve for a given set of
+// operands and settings runs eagerly and is also recorded as a CUDA graph on
+// a private stream; a later solve with the same key (pointers, sizes, field,
+// form and schedule settings, workspace) replays the graph in one launch.
+#include <algorithm>
+#include <vector>
+
+#include "context.h"
+
+namespace m4rie {
+namespace {
+
+constexpr int NB = 128;          // diagonal block rows
+constexpr int LOG_WORDS = 1024;  // log table: 2^e entries, e <= 10
+constexpr int EXP_WORDS = 2048;  // antilog table, doubled so that log a + log b needs no reduction
+constexpr size_t INV_SMEM = (size_t)(LOG_WORDS + EXP_WORDS + 2 * NB * NB) * sizeof(uint16_t);
+
+// a * x mod f (shift, then subtract f when the degree reaches e)
+uint32_t times_x(int e, uint32_t f, uint32_t a) {
+  a <<= 1;
+  return ((a >> e) & 1u) ? a ^ f : a;
+}
+
+// a * g mod f as the sum of a * x^i over the bits i of g
+uint32_t times(int e, uint32_t f, uint32_t a, uint32_t g) {
+  uint32_t r = 0;
+  for (; g; g >>= 1, a = times_x(e, f, a))
+    if (g & 1u) r ^= a;
+  return r;
+}
+
+// Log / antilog tables of GF(2^e)* = <g> for the first generator g >= 2:
+// tab[0 .. 1024) = log, tab[1024 .. 1024 + 2(2^e - 1)) = g^i for i < 2(2^e - 1).
+bool build_tables(int e, uint32_t f, std::vector<uint16_t>& tab) {
+  const uint32_t q = (1u << e) - 1;
+  tab.assign(LOG_WORDS + EXP_WORDS, 0);
+  for (uint32_t g = 2; g <= q; ++g) {
+    uint32_t a = 1, i = 0;
+    for (; i < q; ++i) {
+      if (i > 0 && a == 1) break;  // order of g below q
+      tab[LOG_WORDS + i] = (uint16_t)a;
+      tab[LOG_WORDS + i + q] = (uint16_t)a;
+      tab[a] = (uint16_t)i;
+      a = times(e, f, a, g);
+    }
+    if (i == q && a == 1) return true;
+  }
+  return false;
+}
+
+// Inverse of the diagonal block b (rows and columns [128 b, 128 b + nb)) of
+// T: X with T_bb X = I, written to inv + b * 128 * 128 (row stride 128, zero
+// past nb).  Thread c computes column c by back substitution (upper: rows
+// from the last up; lower: from the first down); only the block's own
+// triangle is read.
+template <typename T, bool UPPER>
+__global__ void __launch_bounds__(NB) tri_inverse(int e, const T* __restrict__ Tm, int64_t ldt, int64_t m,
+                                                  const uint16_t* __restrict__ gf, T* __restrict__ inv,
+                                                  int* status) {
+  extern __shared__ uint16_t sh[];
+  uint16_t* lg = sh;
+  uint16_t* ex = sh + LOG_WORDS;
+  uint16_t* tb = ex + EXP_WORDS;  // [NB][NB], the block's triangle
+  uint16_t* xb = tb + NB * NB;    // [NB][NB], the inverse
+  const uint32_t q = (1u << e) - 1;
+  for (int i = threadIdx.x; i < LOG_WORDS + EXP_WORDS; i += NB) sh[i] = gf[i];
+  const int64_t r0 = (int64_t)blockIdx.x * NB;
+  const int nb = m - r0 < NB ? (int)(m - r0) : NB;
+  bool bad = false;
+  for (int idx = threadIdx.x; idx < NB * NB; idx += NB) {
+    const int i = idx / NB, j = idx % NB;
+    uint32_t v = 0;
+    if (i < nb && j < nb && (UPPER ? j >= i : j <= i)) {
+      v = Tm[(r0 + i) * ldt + r0 + j];
+      bad |= v > q;
+      v &= q;
+    }
+    tb[idx] = (uint16_t)v;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusRange);
+  __syncthreads();
+
+  const int c = threadIdx.x;
+  bool singular = false;
+  if (c < nb) {
+    for (int step = 0; step < nb; ++step) {
+      const int i = UPPER ? nb - 1 - step : step;
+      uint32_t s = 0;
+      if (UPPER ? i <= c : i >= c) {
+        // row i of T X = I:  T[i][i] X[i][c] = [i == c] + sum over the other
+        // columns j of row i's triangle with X[j][c] already known
+        s = i == c ? 1u : 0u;
+        const int j0 = UPPER ? i + 1 : c, j1 = UPPER ? c : i - 1;
+        for (int j = j0; j <= j1; ++j) {
+          const uint32_t a = tb[i * NB + j], x = xb[j * NB + c];
+          if (a && x) s ^= ex[lg[a] + lg[x]];
+        }
+        const uint32_t d = tb[i * NB + i];
+        singular |= d == 0;
+        s = (d && s) ? ex[lg[s] + q - lg[d]] : 0u;  // s / d
+      }
+      xb[i * NB + c] = (uint16_t)s;
+    }
+  }
+  if (singular) atomicOr(status, kStatusSingular);
+  T* out = inv + (int64_t)blockIdx.x * NB * NB;
+  for (int i = 0; i < nb; ++i) out[(int64_t)i * NB + c] = c < nb ? (T)xb[i * NB + c] : (T)0;
+}
+
+size_t elem_w(int e) { return e <= 8 ? 1 : 2; }
+
+m4rie_status ensure_tws(m4rie_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->tws_bytes) return M4RIE_OK;
+  cudaError_t err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) {
+    ctx->last_error = cudaGetErrorString(err);
+    return M4RIE_ERR_CUDA;
+  }
+  if (ctx->tws) cudaFree(ctx->tws);
+  ctx->tws = nullptr;
+  ctx->tws_bytes = 0;
+  if (cudaMalloc(&ctx->tws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = "triangular-solve scratch allocation failed";
+    return M4RIE_ERR_NOMEM;
+  }
+  ctx->tws_bytes = bytes;
+  return M4RIE_OK;
+}
+
+m4rie_status field_tables(m4rie_ctx* ctx, int e, uint32_t f) {
+  if (ctx->d_gf && ctx->gf_e == e && ctx->gf_f == f) return M4RIE_OK;
+  std::vector<uint16_t> tab;
+  if (!build_tables(e, f, tab)) return M4RIE_ERR_POLY;
+  cudaError_t err = cudaSuccess;
+  if (!ctx->d_gf) err = cudaMalloc(&ctx->d_gf, tab.size() * sizeof(uint16_t));
+  // the host vector dies here: copy, then wait for the copy
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(ctx->d_gf, tab.data(), tab.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, ctx->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    ctx->gf_e = 0;
+    ctx->last_error = cudaGetErrorString(err);
+    return M4RIE_ERR_CUDA;
+  }
+  ctx->gf_e = e;
+  ctx->gf_f = f;
+  return M4RIE_OK;
+}
+
+struct Solve {
+  m4rie_ctx* ctx;
+  int e;
+  uint32_t f;
+  bool upper;
+  const uint8_t* T;
+  int64_t ldt;
+  uint8_t* B;
+  int64_t ldb;
+  int64_t n;
+  size_t w;
+  const uint8_t* inv;  // inverted diagonal blocks, [nblk][NB][NB]
+};
+
+// Rows [r0, r0 + mb) of the system; r0 is a multiple of NB.
+m4rie_status solve(const Solve& s, int64_t r0, int64_t mb) {
+  const size_t w = s.w;
+  if (mb <= NB) {
+    const uint8_t* Ti = s.inv + (size_t)(r0 / NB) * NB * NB * w;
+    uint8_t* Bb = s.B + (size_t)r0 * s.ldb * w;
+    return run_gemm(s.ctx, s.e, s.f, mb, s.n, mb, Mats{Ti, NB, Bb, s.ldb, Bb, s.ldb}, 0, true);
+  }
+  const int64_t m1 = round_up((mb + 1) / 2, NB), m2 = mb - m1;
+  uint8_t* B0 = s.B + (size_t)r0 * s.ldb * w;
+  uint8_t* B1 = s.B + (size_t)(r0 + m1) * s.ldb * w;
+  m4rie_status st;
+  if (s.upper) {
+    if ((st = solve(s, r0 + m1, m2)) != M4RIE_OK) return st;
+    const uint8_t* T01 = s.T + ((size_t)r0 * s.ldt + r0 + m1) * w;
+    if ((st = run_gemm(s.ctx, s.e, s.f, m1, s.n, m2, Mats{T01, s.ldt, B1, s.ldb, B0, s.ldb}, 1)) != M4RIE_OK)
+      return st;
+    return solve(s, r0, m1);
+  }
+  if ((st = solve(s, r0, m1)) != M4RIE_OK) return st;
+  const uint8_t* T10 = s.T + ((size_t)(r0 + m1) * s.ldt + r0) * w;
+  if ((st = run_gemm(s.ctx, s.e, s.f, m2, s.n, m1, Mats{T10, s.ldt, B0, s.ldb, B1, s.ldb}, 1)) != M4RIE_OK)
+    return st;
+  return solve(s, r0 + m1, m2);
+}
+
+// All kernels of one solve, on ctx->stream: the diagonal-block inverses, then
+// the recursion.
+m4rie_status solve_all(m4rie_ctx* ctx, const Solve& s, int64_t m, int64_t nblk) {
+  cudaError_t err;
+  const size_t w = s.w;
+  if (w == 1) {
+    auto k = s.upper ? tri_inverse<uint8_t, true> : tri_inverse<uint8_t, false>;
+    err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INV_SMEM);
+    if (err == cudaSuccess) {
+      k<<<(unsigned)nblk, NB, INV_SMEM, ctx->stream>>>(s.e, s.T, s.ldt, m, ctx->d_gf, const_cast<uint8_t*>(s.inv),
+                                                       ctx->d_status);
+      err = cudaGetLastError();
+    }
+  } else {
+    auto k = s.upper ? tri_inverse<uint16_t, true> : tri_inverse<uint16_t, false>;
+    err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INV_SMEM);
+    if (err == cudaSuccess) {
+      k<<<(unsigned)nblk, NB, INV_SMEM, ctx->stream>>>(s.e, reinterpret_cast<const uint16_t*>(s.T), s.ldt, m,
+                                                       ctx->d_gf, reinterpret_cast<uint16_t*>(const_cast<uint8_t*>(s.inv)),
+                                                       ctx->d_status);
+      err = cudaGetLastError();
+    }
+  }
+  if (err != cudaSuccess) {
+    ctx->last_error = cudaGetErrorString(err);
+    return M4RIE_ERR_CUDA;
+  }
+  ++ctx->launches;
+  return solve(s, 0, m);
+}
+
+bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
+  if (!an || !bn) return false;
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bn && y < x + an;
+}
+
+}  // namespace
+
+// The key of a recorded solve and its graph.
+struct TrsmGraph {
+  int e = 0;
+  uint32_t f = 0;
+  bool upper = false;
+  int64_t m = 0, n = 0, ldt = 0, ldb = 0;
+  const void* T = nullptr;
+  const void* B = nullptr;
+  int form = 0, schedule = 0, group_m = 0, tc_chunk = 0, cluster = 0, f4nv = 0, stall_test = 0;
+  uint64_t wait_limit_ns = 0;
+  const void* ws = nullptr;
+  size_t ws_bytes = 0;
+  const void* tws = nullptr;
+  // not part of the key
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+
+  bool same(const TrsmGraph& o) const {
+    return e == o.e && f == o.f && upper == o.upper && m == o.m && n == o.n && ldt == o.ldt && ldb == o.ldb &&
+           T == o.T && B == o.B && form == o.form && schedule == o.schedule && group_m == o.group_m &&
+           tc_chunk == o.tc_chunk && cluster == o.cluster && f4nv == o.f4nv && stall_test == o.stall_test &&
+           wait_limit_ns == o.wait_limit_ns && ws == o.ws && ws_bytes == o.ws_bytes && tws == o.tws;
+  }
+};
+
+void destroy_trsm_graph(TrsmGraph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  delete g;
+}
+
+namespace {
+
+TrsmGraph key_of(m4rie_ctx* ctx, const Solve& s, int64_t m) {
+  TrsmGraph k;
+  k.e = s.e;
+  k.f = s.f;
+  k.upper = s.upper;
+  k.m = m;
+  k.n = s.n;
+  k.ldt = s.ldt;
+  k.ldb = s.ldb;
+  k.T = s.T;
+  k.B = s.B;
+  k.form = ctx->form;
+  k.schedule = ctx->schedule;
+  k.group_m = ctx->group_m;
+  k.tc_chunk = ctx->tc_chunk;
+  k.cluster = ctx->cluster;
+  k.f4nv = ctx->f4nv;
+  k.stall_test = ctx->stall_test;
+  k.wait_limit_ns = ctx->wait_limit_ns;
+  k.ws = ctx->ws;
+  k.ws_bytes = ctx->ws_bytes;
+  k.tws = ctx->tws;
+  return k;
+}
+
+// Record the solve just run eagerly (so the workspace already has its final
+// size and nothing in the recursion synchronizes or allocates) as a graph for
+// later replays.  Best effort: on any failure no graph is kept.
+void record(m4rie_ctx* ctx, const Solve& s, int64_t m, int64_t nblk) {
+  destroy_trsm_graph(ctx->trsm_graph);
+  ctx->trsm_graph = nullptr;
+  TrsmGraph* g = new TrsmGraph(key_of(ctx, s, m));
+  if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    destroy_trsm_graph(g);
+    return;
+  }
+  const cudaStream_t saved = ctx->stream;
+  const int64_t launches0 = ctx->launches;
+  const std::string err0 = ctx->last_error;
+  ctx->stream = g->cap;
+  cudaGraph_t graph = nullptr;
+  m4rie_status st = M4RIE_ERR_CUDA;
+  if (cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    st = solve_all(ctx, s, m, nblk);
+    if (cudaStreamEndCapture(g->cap, &graph) != cudaSuccess) st = M4RIE_ERR_CUDA;
+  }
+  ctx->stream = saved;
+  g->launches = ctx->launches - launches0;
+  ctx->launches = launches0;
+  ctx->last_error = err0;
+  // the recursion must not have resized the workspace while recording
+  if (st == M4RIE_OK && graph && ctx->ws == g->ws && ctx->ws_bytes == g->ws_bytes &&
+      cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess)
+    g->exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  if (st != M4RIE_OK || !g->exec) {
+    destroy_trsm_graph(g);
+    return;
+  }
+  ctx->trsm_graph = g;
+}
+
+m4rie_status run_trsm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, const void* T, int64_t ldt, void* B,
+                      int64_t ldb, bool upper) {
+  if (!ctx) return M4RIE_ERR_ARG;
+  m4rie_status st = m4rie_validate(e, f, 0, 0, 0, nullptr, nullptr, nullptr);  // field checks
+  if (st != M4RIE_OK) return st;
+  if (m < 0 || n < 0 || m > (1ll << 31) || n > (1ll << 31) || ldt < m || ldb < n) return M4RIE_ERR_ARG;
+  if ((m && !T) || (m * n && !B)) return M4RIE_ERR_ARG;
+  const size_t w = elem_w(e);
+  const size_t st_bytes = m ? (size_t)((m - 1) * ldt + m) * w : 0;
+  const size_t sb_bytes = m * n ? (size_t)((m - 1) * ldb + n) * w : 0;
+  if (overlaps(B, sb_bytes, T, st_bytes)) return M4RIE_ERR_ALIAS;
+  if (m == 0 || n == 0) return M4RIE_OK;
+  if ((st = field_tables(ctx, e, f)) != M4RIE_OK) return st;
+  const int64_t nblk = ceil_div(m, NB);
+  const size_t inv_bytes = round_up((int64_t)((size_t)nblk * NB * NB * w), 256);
+  if ((st = ensure_tws(ctx, inv_bytes)) != M4RIE_OK) return st;
+  uint8_t* inv = static_cast<uint8_t*>(ctx->tws);
+
+  if (nblk > 0x7fffffffLL) return M4RIE_ERR_ARG;
+  const Solve s{ctx, e, f, upper, static_cast<const uint8_t*>(T), ldt, static_cast<uint8_t*>(B), ldb, n, w, inv};
+  TrsmGraph key = key_of(ctx, s, m);
+  TrsmGraph* g = ctx->trsm_graph;
+  if (!ctx->timing && g && g->exec && g->same(key)) {
+    const cudaError_t err = cudaGraphLaunch(g->exec, ctx->stream);
+    if (err != cudaSuccess) {
+      ctx->last_error = cudaGetErrorString(err);
+      return M4RIE_ERR_CUDA;
+    }
+    ctx->launches += g->launches;
+    return M4RIE_OK;
+  }
+  if ((st = solve_all(ctx, s, m, nblk)) != M4RIE_OK) return st;
+  if (!ctx->timing) record(ctx, s, m, nblk);
+  return M4RIE_OK;
+}
+
+}  // namespace
+}  // namespace m4rie
+
+using namespace m4rie;
+
+extern "C" {
+
+m4rie_status m4rie_trsm_upper_left(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, const void* T,
+                                   int64_t ldt, void* B, int64_t ldb) {
+  return run_trsm(ctx, e, f, m, n, T, ldt, B, ldb, true);
+}
+
+m4rie_status m4rie_trsm_lower_left(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, const void* T,
+                                   int64_t ldt, void* B, int64_t ldb) {
+  return run_trsm(ctx, e, f, m, n, T, ldt, B, ldb, false);
+}
+
+}  // extern "C"

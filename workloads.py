@@ -8,7 +8,9 @@ Input recipe (the paper measures on random dense matrices, Section 4.1 and
 Table 3; no dataset is involved): numpy ``default_rng(seed)``, entries drawn
 i.i.d. uniform in [0, 2^e); for workload i the seed is 1000 + i and the
 matrices are drawn in the order A, B, C; for batched instance j the seed is
-40000 + j and the draw order is e, (m, n, k), A, B.
+40000 + j and the draw order is e, (m, n, k), A, B.  Triangular systems
+(Section 4.3): the triangle of T (upper or lower) uniform, its diagonal
+uniform in [1, 2^e) so that T is invertible, the other triangle zero, then B.
 """
 from __future__ import annotations
 
@@ -95,3 +97,20 @@ def random_problem(e: int, m: int, n: int, k: int, seed: int, with_c: bool = Fal
     B = elements(rng, e, (k, n))
     C = elements(rng, e, (m, n)) if with_c else None
     return A, B, C
+
+
+# Triangular solves B <- T^{-1} B, T m x m upper triangular, B m x n: (e, m, n, seed).
+TRSM_WORKLOADS = {
+    "trsm_gf16_4096": (4, 4096, 4096, 1100),
+    "trsm_gf256_8192": (8, 8192, 8192, 1101),
+}
+
+
+def triangular_system(e: int, m: int, n: int, seed: int, upper: bool = True):
+    """Seeded (T, B): T m x m triangular with a non-zero diagonal, B m x n."""
+    rng = np.random.default_rng(seed)
+    T = elements(rng, e, (m, m))
+    T = np.triu(T) if upper else np.tril(T)
+    T[np.arange(m), np.arange(m)] = rng.integers(1, 1 << e, size=m).astype(T.dtype)
+    B = elements(rng, e, (m, n))
+    return T, B
