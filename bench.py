@@ -245,6 +245,16 @@ def run_trsm_workload(args, m4, torch, world, rank, local):
     stream = torch.cuda.current_stream()
     ctx = m4.Context(stream)
     ops = float(m) * m * n
+    if args.single:
+        form, sched = args.single.split("/")
+        ctx.set_form(form)
+        ctx.set_schedule(sched)
+        for _ in range(args.warmup + 1):
+            ctx.trsm(e, f, dT, dX, True)
+        torch.cuda.synchronize()
+        status = ctx.device_status()
+        ctx.close()
+        return 0 if status == m4.OK else 1
     results, X_auto = {}, None
     for form in ("auto", "popc", "tc_f4"):
         ctx.set_form(form)

@@ -12,8 +12,8 @@
 // The lower case mirrors it (first block first).  The recursion splits at
 // multiples of 128 rows and stops at diagonal blocks of at most 128 rows.
 // One kernel launch inverts all of those blocks up front (back substitution
-// on the identity in shared memory, one thread per column, field products
-// from log / antilog tables of the field), and each block's solve is then the
+// on the identity in shared memory, 8 lanes per column, field products from
+// log / antilog tables of the field), and each block's solve is then the
 // slice GEMM X_b = T_bb^{-1} B_b, written over B_b (the product reads B_b only
 // while packing its operand planes, before anything is written).
 //
@@ -33,7 +33,7 @@ namespace {
 constexpr int NB = 128;          // diagonal block rows
 constexpr int LOG_WORDS = 1024;  // log table: 2^e entries, e <= 10
 constexpr int EXP_WORDS = 2048;  // antilog table, doubled so that log a + log b needs no reduction
-constexpr size_t INV_SMEM = (size_t)(LOG_WORDS + EXP_WORDS + 2 * NB * NB) * sizeof(uint16_t);
+constexpr size_t INV_SMEM = (size_t)(LOG_WORDS + EXP_WORDS + NB * NB + NB * (NB + 2)) * sizeof(uint16_t);
 
 // a * x mod f (shift, then subtract f when the degree reaches e)
 uint32_t times_x(int e, uint32_t f, uint32_t a) {
@@ -70,24 +70,31 @@ bool build_tables(int e, uint32_t f, std::vector<uint16_t>& tab) {
 
 // Inverse of the diagonal block b (rows and columns [128 b, 128 b + nb)) of
 // T: X with T_bb X = I, written to inv + b * 128 * 128 (row stride 128, zero
-// past nb).  Thread c computes column c by back substitution (upper: rows
-// from the last up; lower: from the first down); only the block's own
-// triangle is read.
+// past nb).  Column c of X comes from back substitution on column c of I
+// (upper: rows from the last up; lower: from the first down).  A column
+// belongs to 8 lanes of one warp (a warp holds 4 columns): each lane forms
+// the products of every 8th term of row i's sum, the lanes XOR their partial
+// sums with shuffles, and one lane divides by the diagonal entry and stores
+// X[i][c].  X is kept column-major in shared memory so that the lanes of a
+// column read different banks.  Only the block's own triangle is read.
+constexpr int INV_THREADS = 1024;
+constexpr int XPITCH = NB + 2;  // u16 entries per stored column of X
+
 template <typename T, bool UPPER>
-__global__ void __launch_bounds__(NB) tri_inverse(int e, const T* __restrict__ Tm, int64_t ldt, int64_t m,
-                                                  const uint16_t* __restrict__ gf, T* __restrict__ inv,
-                                                  int* status) {
+__global__ void __launch_bounds__(INV_THREADS) tri_inverse(int e, const T* __restrict__ Tm, int64_t ldt, int64_t m,
+                                                           const uint16_t* __restrict__ gf, T* __restrict__ inv,
+                                                           int* status) {
   extern __shared__ uint16_t sh[];
   uint16_t* lg = sh;
   uint16_t* ex = sh + LOG_WORDS;
-  uint16_t* tb = ex + EXP_WORDS;  // [NB][NB], the block's triangle
-  uint16_t* xb = tb + NB * NB;    // [NB][NB], the inverse
+  uint16_t* tb = ex + EXP_WORDS;  // [NB][NB], the block's triangle, row-major
+  uint16_t* xb = tb + NB * NB;    // [NB][XPITCH], X column-major
   const uint32_t q = (1u << e) - 1;
-  for (int i = threadIdx.x; i < LOG_WORDS + EXP_WORDS; i += NB) sh[i] = gf[i];
+  for (int i = threadIdx.x; i < LOG_WORDS + EXP_WORDS; i += INV_THREADS) sh[i] = gf[i];
   const int64_t r0 = (int64_t)blockIdx.x * NB;
   const int nb = m - r0 < NB ? (int)(m - r0) : NB;
   bool bad = false;
-  for (int idx = threadIdx.x; idx < NB * NB; idx += NB) {
+  for (int idx = threadIdx.x; idx < NB * NB; idx += INV_THREADS) {
     const int i = idx / NB, j = idx % NB;
     uint32_t v = 0;
     if (i < nb && j < nb && (UPPER ? j >= i : j <= i)) {
@@ -100,31 +107,45 @@ __global__ void __launch_bounds__(NB) tri_inverse(int e, const T* __restrict__ T
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusRange);
   __syncthreads();
 
-  const int c = threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int c = (threadIdx.x >> 5) * 4 + (lane >> 3), sl = lane & 7;
+  uint16_t* xc = xb + c * XPITCH;
   bool singular = false;
-  if (c < nb) {
-    for (int step = 0; step < nb; ++step) {
-      const int i = UPPER ? nb - 1 - step : step;
-      uint32_t s = 0;
-      if (UPPER ? i <= c : i >= c) {
-        // row i of T X = I:  T[i][i] X[i][c] = [i == c] + sum over the other
-        // columns j of row i's triangle with X[j][c] already known
-        s = i == c ? 1u : 0u;
-        const int j0 = UPPER ? i + 1 : c, j1 = UPPER ? c : i - 1;
-        for (int j = j0; j <= j1; ++j) {
-          const uint32_t a = tb[i * NB + j], x = xb[j * NB + c];
-          if (a && x) s ^= ex[lg[a] + lg[x]];
-        }
-        const uint32_t d = tb[i * NB + i];
-        singular |= d == 0;
-        s = (d && s) ? ex[lg[s] + q - lg[d]] : 0u;  // s / d
+  for (int step = 0; step < nb; ++step) {
+    const int i = UPPER ? nb - 1 - step : step;
+    const bool active = c < nb && (UPPER ? i <= c : i >= c);
+    // row i of T X = I:  T[i][i] X[i][c] = [i == c] + sum over the other
+    // columns j of row i's triangle, with X[j][c] already known
+    uint32_t s = 0;
+    if (active) {
+      const int j0 = UPPER ? i + 1 : c, j1 = UPPER ? c : i - 1;
+#pragma unroll 2
+      for (int j = j0 + sl; j <= j1; j += 8) {
+        const uint32_t a = tb[i * NB + j], x = xc[j];
+        if (a && x) s ^= ex[lg[a] + lg[x]];
       }
-      xb[i * NB + c] = (uint16_t)s;
     }
+    s ^= __shfl_xor_sync(0xffffffffu, s, 1);
+    s ^= __shfl_xor_sync(0xffffffffu, s, 2);
+    s ^= __shfl_xor_sync(0xffffffffu, s, 4);
+    if (active) {
+      if (i == c) s ^= 1u;
+      const uint32_t d = tb[i * NB + i];
+      singular |= d == 0;
+      s = (d && s) ? ex[lg[s] + q - lg[d]] : 0u;  // s / d
+    } else {
+      s = 0;
+    }
+    if (sl == 0) xc[i] = (uint16_t)s;
+    __syncwarp();
   }
-  if (singular) atomicOr(status, kStatusSingular);
+  if (singular && sl == 0) atomicOr(status, kStatusSingular);
+  __syncthreads();
   T* out = inv + (int64_t)blockIdx.x * NB * NB;
-  for (int i = 0; i < nb; ++i) out[(int64_t)i * NB + c] = c < nb ? (T)xb[i * NB + c] : (T)0;
+  for (int idx = threadIdx.x; idx < nb * NB; idx += INV_THREADS) {
+    const int i = idx / NB, cc = idx % NB;
+    out[idx] = cc < nb ? (T)xb[cc * XPITCH + i] : (T)0;
+  }
 }
 
 size_t elem_w(int e) { return e <= 8 ? 1 : 2; }
@@ -218,7 +239,7 @@ m4rie_status solve_all(m4rie_ctx* ctx, const Solve& s, int64_t m, int64_t nblk) 
     auto k = s.upper ? tri_inverse<uint8_t, true> : tri_inverse<uint8_t, false>;
     err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INV_SMEM);
     if (err == cudaSuccess) {
-      k<<<(unsigned)nblk, NB, INV_SMEM, ctx->stream>>>(s.e, s.T, s.ldt, m, ctx->d_gf, const_cast<uint8_t*>(s.inv),
+      k<<<(unsigned)nblk, INV_THREADS, INV_SMEM, ctx->stream>>>(s.e, s.T, s.ldt, m, ctx->d_gf, const_cast<uint8_t*>(s.inv),
                                                        ctx->d_status);
       err = cudaGetLastError();
     }
@@ -226,7 +247,7 @@ m4rie_status solve_all(m4rie_ctx* ctx, const Solve& s, int64_t m, int64_t nblk) 
     auto k = s.upper ? tri_inverse<uint16_t, true> : tri_inverse<uint16_t, false>;
     err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INV_SMEM);
     if (err == cudaSuccess) {
-      k<<<(unsigned)nblk, NB, INV_SMEM, ctx->stream>>>(s.e, reinterpret_cast<const uint16_t*>(s.T), s.ldt, m,
+      k<<<(unsigned)nblk, INV_THREADS, INV_SMEM, ctx->stream>>>(s.e, reinterpret_cast<const uint16_t*>(s.T), s.ldt, m,
                                                        ctx->d_gf, reinterpret_cast<uint16_t*>(const_cast<uint8_t*>(s.inv)),
                                                        ctx->d_status);
       err = cudaGetLastError();
