@@ -404,7 +404,7 @@ def run_batched_workload(args, m4, torch, world, rank, local):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     ctx = m4.Context(stream)
-    ctx.set_form(args.forms.split(",")[0] if args.forms not in ("popc,tc_f8,tc_f4,mma_s8",) else "auto")
+    ctx.set_form(args.forms.split(",")[0] if args.forms not in ("popc,tc_f8,tc_f4,mma_s8,mma_b1",) else "auto")
     for _ in range(args.warmup):
         ctx.mul_batched(probs)
     torch.cuda.synchronize()
@@ -446,7 +446,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="popc,tc_f8,tc_f4,mma_s8")
+    ap.add_argument("--forms", default="popc,tc_f8,tc_f4,mma_s8,mma_b1")
     ap.add_argument("--schedules", default="alpha_b,karatsuba")
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -526,7 +526,7 @@ def main():
     results = {}
     for form in args.forms.split(","):
         for sched in args.schedules.split(","):
-            if form == "mma_s8" and sched != "alpha_b":
+            if form.startswith("mma_") and sched != "alpha_b":
                 continue
             ctx.set_form(form)
             ctx.set_schedule(sched)
@@ -603,7 +603,12 @@ def main():
     pk = peaks() or {}
     r = m4.schedule_products(w.e, w.f, sched)
     gemm_s = best["gemm_ms"] * 1e-3
-    if form == "popc":
+    if form == "mma_b1":
+        bitmacs = r * w.m * w.n * w.k
+        roof = {"bound": "tensor", "achieved": bitmacs / gemm_s / 1e12, "peak": 73.2, "unit": "T bit-MAC/s",
+                "frac": bitmacs / gemm_s / 1e12 / 73.2, "traffic": None,
+                "peak_source": "measured mma.sync b1 and.popc instruction rate on this GPU"}
+    elif form == "popc":
         # one LOP3 (AND + XOR) per 32 bit-MACs; ALU pipe 16 lanes / SMSP / clock
         bitmacs = r * w.m * w.n * w.k
         sm_mhz = pk.get("sm_max_mhz", 2070.0)

@@ -62,7 +62,9 @@ typedef enum m4rie_form {
     M4RIE_FORM_POPC = 1,   /* bit-packed slices, AND/XOR on the CUDA cores, parity by popcount */
     M4RIE_FORM_TC_F8 = 2,  /* tcgen05 tensor cores; 0/1 operands encoded exactly as FP8 E4M3, FP32 counts */
     M4RIE_FORM_MMA_S8 = 3, /* legacy warp-level INT8 tensor instructions (mma.sync s8), int32 counts */
-    M4RIE_FORM_TC_F4 = 4   /* tcgen05 block-scaled FP4 (E2M1 0/1 operands, unit scales), FP32 counts */
+    M4RIE_FORM_TC_F4 = 4,  /* tcgen05 block-scaled FP4 (E2M1 0/1 operands, unit scales), FP32 counts */
+    M4RIE_FORM_MMA_B1 = 5  /* legacy warp-level binary tensor instructions (mma.sync b1, AND + popcount)
+                              on the bit-packed slices, int32 counts */
 } m4rie_form;
 
 /* Which bilinear schedule reduces the GF(2^e) product to GF(2) products. */
@@ -171,7 +173,7 @@ m4rie_status m4rie_unpack(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, con
  * That work is recorded once into a CUDA graph, cached in the context with
  * its own device memory, and replayed while the same descriptor array contents
  * are passed (a different array rebuilds it; the first call synchronises the
- * stream).  With the POPC or MMA_S8 form the products run one by one. */
+ * stream).  With the POPC, MMA_S8 or MMA_B1 form the products run one by one. */
 m4rie_status m4rie_mul_batched(m4rie_ctx *ctx, int count, const m4rie_problem *problems);
 
 /* Wait for the stream, return the sticky device status (M4RIE_OK,

@@ -16,9 +16,10 @@ LIB_PATH = os.path.join(_HERE, "libm4rie_gpu.so")
 
 (OK, ERR_ARG, ERR_POLY, ERR_ALIAS, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH,
  ERR_SINGULAR) = range(11)
-FORM_AUTO, FORM_POPC, FORM_TC_F8, FORM_MMA_S8, FORM_TC_F4 = range(5)
+FORM_AUTO, FORM_POPC, FORM_TC_F8, FORM_MMA_S8, FORM_TC_F4, FORM_MMA_B1 = range(6)
 SCHED_AUTO, SCHED_ALPHA_B, SCHED_KARATSUBA = range(3)
-FORMS = {"auto": FORM_AUTO, "popc": FORM_POPC, "tc_f8": FORM_TC_F8, "mma_s8": FORM_MMA_S8, "tc_f4": FORM_TC_F4}
+FORMS = {"auto": FORM_AUTO, "popc": FORM_POPC, "tc_f8": FORM_TC_F8, "mma_s8": FORM_MMA_S8, "tc_f4": FORM_TC_F4,
+         "mma_b1": FORM_MMA_B1}
 SCHEDULES = {"auto": SCHED_AUTO, "alpha_b": SCHED_ALPHA_B, "karatsuba": SCHED_KARATSUBA}
 
 

@@ -161,6 +161,7 @@ FormInfo form_info(int form) {
     case M4RIE_FORM_POPC: return {kFmtBit, 1, 1};
     case M4RIE_FORM_TC_F8: return {kFmtByte, 0x38, 8};
     case M4RIE_FORM_MMA_S8: return {kFmtByte, 0x01, 8};
+    case M4RIE_FORM_MMA_B1: return {kFmtBit, 1, 1};
     default: return {kFmtNib, 0x2, 4};
   }
 }
@@ -177,7 +178,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   int G;
   if (form == M4RIE_FORM_POPC) G = popc_group(e);
   else if (form == M4RIE_FORM_TC_F8 || form == M4RIE_FORM_TC_F4) G = tc_group(e, fi.fmt);
-  else if (form == M4RIE_FORM_MMA_S8) G = mma_group(e);
+  else if (form == M4RIE_FORM_MMA_S8 || form == M4RIE_FORM_MMA_B1) G = mma_group(e);
   else return M4RIE_ERR_UNSUPPORTED;
   const bool tc = form == M4RIE_FORM_TC_F8 || form == M4RIE_FORM_TC_F4;
   const int64_t Kp = round_up(k, 128);
@@ -279,7 +280,8 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
     tp.cluster = pair ? 2 : 1;
-    if (form == M4RIE_FORM_MMA_S8) err = launch_mma_s8(Ap, Bp, ld_bytes, tp, ctx->stream, &ctx->launches);
+    if (form == M4RIE_FORM_MMA_S8 || form == M4RIE_FORM_MMA_B1)
+      err = launch_mma(form == M4RIE_FORM_MMA_B1, Ap, Bp, ld_bytes, tp, ctx->stream, &ctx->launches);
     else err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld_bytes, tp, ctx->num_sms, ctx->stream, &ctx->launches);
   }
   if (err != cudaSuccess) return cuda_fail(ctx, err);
@@ -498,7 +500,7 @@ void m4rie_destroy(m4rie_ctx* ctx) {
 }
 
 m4rie_status m4rie_set_form(m4rie_ctx* ctx, int form) {
-  if (!ctx || form < M4RIE_FORM_AUTO || form > M4RIE_FORM_TC_F4) return M4RIE_ERR_ARG;
+  if (!ctx || form < M4RIE_FORM_AUTO || form > M4RIE_FORM_MMA_B1) return M4RIE_ERR_ARG;
   ctx->form = form;
   return M4RIE_OK;
 }
@@ -595,7 +597,7 @@ m4rie_status m4rie_mul_batched(m4rie_ctx* ctx, int count, const m4rie_problem* p
   if (count == 0) return M4RIE_OK;
   // The persistent batched launch uses the tcgen05 forms (FP4 unless FP8 is
   // requested); the CUDA-core and INT8 forms run the products one by one.
-  if (ctx->form == M4RIE_FORM_POPC || ctx->form == M4RIE_FORM_MMA_S8) {
+  if (ctx->form == M4RIE_FORM_POPC || ctx->form == M4RIE_FORM_MMA_S8 || ctx->form == M4RIE_FORM_MMA_B1) {
     for (int i = 0; i < count; ++i) {
       const m4rie_problem& p = problems[i];
       m4rie_status st = run_mul(ctx, p.e, p.f, p.m, p.n, p.k, p.A, p.B, p.C, p.accumulate ? 1 : 0);

@@ -1,9 +1,16 @@
-// GF(2) slice GEMM on the legacy warp-level INT8 tensor instructions
-// (mma.sync.m16n8k32 s8 x s8 -> s32).  Operands are 0/1 bytes; each int32
-// accumulator holds the exact count sum_t a_t b_t (parity is unaffected even
-// by wrap-around, since (x mod 2^32) mod 2 = x mod 2).  This is the INT8
-// tensor form: sm_103a has no tcgen05 kind::i8, and these instructions run far
-// below the tcgen05 rates, so this form exists to measure that route.
+// GF(2) slice GEMM on the legacy warp-level tensor instructions, in two
+// encodings of the same 0/1 operands:
+//   - INT8: mma.sync.m16n8k32 s8 x s8 -> s32 on byte planes (0 / 1);
+//   - b1:   mma.sync.m16n8k256 b1 x b1 -> s32 with AND + popcount, on the
+//           bit planes of the popc form (256 entries of K in 32 bytes).
+// Each int32 accumulator holds the exact count sum_t a_t b_t (parity is
+// unaffected even by wrap-around, since (x mod 2^32) mod 2 = x mod 2).  Per
+// register the two fragment layouts cover the same bytes (a thread's a0 is
+// bytes 4 t .. 4 t + 3 of row g of the 32-byte K step, a2 the same 16 bytes
+// on), so one kernel body serves both; A's and B's fragments hold the same K
+// positions bit for bit, which is all the AND + popcount needs.  sm_103a has
+// no tcgen05 kind::i8, and both instructions run far below the tcgen05
+// rates; these forms exist to measure those routes.
 //
 // Layout as for the tcgen05 form (alpha^j-B schedule): A planes [Mp][e*Kp],
 // B planes in groups of e*G rows (slice i of element c at row i*G + c).
@@ -23,7 +30,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
 
-template <int NT>  // n8 tiles per warp (BN = 16 * NT)
+template <int NT, bool B1>  // n8 tiles per warp (BN = 16 * NT); B1: the b1 AND-popc instruction
 __global__ void __launch_bounds__(256) mma_s8_kernel(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
                                                      int64_t ld, const __grid_constant__ TcParams p) {
   constexpr int BN = 16 * NT;
@@ -84,12 +91,20 @@ __global__ void __launch_bounds__(256) mma_s8_kernel(const uint8_t* __restrict__
         const uint32_t b0 = *reinterpret_cast<const uint32_t*>(rb);
         const uint32_t b1 = *reinterpret_cast<const uint32_t*>(rb + 16);
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
-          asm volatile(
-              "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};"
-              : "+r"(acc[i][j][0]), "+r"(acc[i][j][1]), "+r"(acc[i][j][2]), "+r"(acc[i][j][3])
-              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b0), "r"(b1));
+        for (int i = 0; i < 2; ++i) {
+          if (B1)
+            asm volatile(
+                "mma.sync.aligned.m16n8k256.row.col.s32.b1.b1.s32.and.popc {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+r"(acc[i][j][0]), "+r"(acc[i][j][1]), "+r"(acc[i][j][2]), "+r"(acc[i][j][3])
+                : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b0), "r"(b1));
+          else
+            asm volatile(
+                "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+r"(acc[i][j][0]), "+r"(acc[i][j][1]), "+r"(acc[i][j][2]), "+r"(acc[i][j][3])
+                : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b0), "r"(b1));
+        }
       }
     }
     __syncthreads();
@@ -146,13 +161,31 @@ __global__ void __launch_bounds__(256) mma_s8_kernel(const uint8_t* __restrict__
   if (bad) atomicOr(p.status, kStatusRange);
 }
 
-template <int NT>
+template <int NT, bool B1>
 cudaError_t run(const uint8_t* A, const uint8_t* B, int64_t ld, const TcParams& p, cudaStream_t s) {
   const size_t smem = (size_t)2 * (128 + 16 * NT) * PITCH;
-  cudaError_t err = cudaFuncSetAttribute(mma_s8_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err =
+      cudaFuncSetAttribute(mma_s8_kernel<NT, B1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  mma_s8_kernel<NT><<<dim3((unsigned)p.tiles_m, (unsigned)p.tiles_n), 256, smem, s>>>(A, B, ld, p);
+  mma_s8_kernel<NT, B1><<<dim3((unsigned)p.tiles_m, (unsigned)p.tiles_n), 256, smem, s>>>(A, B, ld, p);
   return cudaGetLastError();
+}
+
+template <bool B1>
+cudaError_t dispatch(const uint8_t* a, const uint8_t* b, int64_t ld, const TcParams& p, cudaStream_t s) {
+  switch (p.BN / 16) {
+    case 1: return run<1, B1>(a, b, ld, p, s);
+    case 2: return run<2, B1>(a, b, ld, p, s);
+    case 3: return run<3, B1>(a, b, ld, p, s);
+    case 4: return run<4, B1>(a, b, ld, p, s);
+    case 5: return run<5, B1>(a, b, ld, p, s);
+    case 6: return run<6, B1>(a, b, ld, p, s);
+    case 7: return run<7, B1>(a, b, ld, p, s);
+    case 8: return run<8, B1>(a, b, ld, p, s);
+    case 9: return run<9, B1>(a, b, ld, p, s);
+    case 10: return run<10, B1>(a, b, ld, p, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -164,26 +197,14 @@ int mma_group(int e) {
   return best;
 }
 
-cudaError_t launch_mma_s8(const void* A, const void* B, int64_t ld, const TcParams& p, cudaStream_t s,
-                          int64_t* launches) {
+cudaError_t launch_mma(bool b1, const void* A, const void* B, int64_t ld, const TcParams& p, cudaStream_t s,
+                       int64_t* launches) {
   if (p.tiles_m <= 0 || p.tiles_n <= 0) return cudaSuccess;
   if (p.tiles_n > 65535 || ld % 16 != 0) return cudaErrorInvalidValue;
   if (launches) ++*launches;
   const uint8_t* a = static_cast<const uint8_t*>(A);
   const uint8_t* b = static_cast<const uint8_t*>(B);
-  switch (p.BN / 16) {
-    case 1: return run<1>(a, b, ld, p, s);
-    case 2: return run<2>(a, b, ld, p, s);
-    case 3: return run<3>(a, b, ld, p, s);
-    case 4: return run<4>(a, b, ld, p, s);
-    case 5: return run<5>(a, b, ld, p, s);
-    case 6: return run<6>(a, b, ld, p, s);
-    case 7: return run<7>(a, b, ld, p, s);
-    case 8: return run<8>(a, b, ld, p, s);
-    case 9: return run<9>(a, b, ld, p, s);
-    case 10: return run<10>(a, b, ld, p, s);
-  }
-  return cudaErrorInvalidValue;
+  return b1 ? dispatch<true>(a, b, ld, p, s) : dispatch<false>(a, b, ld, p, s);
 }
 
 }  // namespace m4rie

@@ -174,10 +174,11 @@ bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld_by
 cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, const int* d_tile_job, int njobs, int64_t total_tiles,
                               int* status, uint64_t wait_limit_ns, int num_sms, cudaStream_t s, int64_t* launches);
 
-// ---------------------------------------------------------------- INT8 mma.sync form
+// ---------------------------------------------------------------- legacy mma.sync forms
 int mma_group(int e);  // elements per block column: block N = e * G <= 160
-cudaError_t launch_mma_s8(const void* Aplanes, const void* Bplanes, int64_t ld_bytes, const TcParams& p,
-                          cudaStream_t s, int64_t* launches);
+// b1 = false: INT8 (byte planes); b1 = true: b1 AND + popcount (bit planes).
+cudaError_t launch_mma(bool b1, const void* Aplanes, const void* Bplanes, int64_t ld_bytes, const TcParams& p,
+                       cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------- helpers
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }

@@ -182,7 +182,7 @@ m4rie_status m4rie_tune_load(m4rie_ctx* ctx, const char* path) {
     int e, c, form, sched, gm;
     double ms;
     if (sscanf(line, "%d %d %d %d %d %lf", &e, &c, &form, &sched, &gm, &ms) != 6) continue;
-    if (e < 2 || e > 10 || c < 0 || c > 63 || form < M4RIE_FORM_POPC || form > M4RIE_FORM_TC_F4 ||
+    if (e < 2 || e > 10 || c < 0 || c > 63 || form < M4RIE_FORM_POPC || form > M4RIE_FORM_MMA_B1 ||
         sched < M4RIE_SCHED_ALPHA_B || sched > M4RIE_SCHED_KARATSUBA || gm < 0)
       continue;
     ctx->tuned[e][c] = TuneEntry{form, sched, gm, ms};

@@ -21,10 +21,10 @@ if not torch.cuda.is_available():
 
 import paper_1111_6900_gb300 as m4  # noqa: E402
 
-FORMS = ["popc", "tc_f8", "tc_f4", "mma_s8"]
+FORMS = ["popc", "tc_f8", "tc_f4", "mma_s8", "mma_b1"]
 # (form, schedule) pairs the library implements; the INT8 mma.sync form runs
 # the alpha^j-B schedule only
-FORM_SCHEDS = [(f, s) for f in FORMS for s in ("alpha_b", "karatsuba") if not (f == "mma_s8" and s == "karatsuba")]
+FORM_SCHEDS = [(f, s) for f in FORMS for s in ("alpha_b", "karatsuba") if not (f.startswith("mma_") and s == "karatsuba")]
 
 
 @pytest.fixture(scope="module")
@@ -139,9 +139,10 @@ def test_out_of_range_entries_flagged_and_masked(ctx, form):
     np.testing.assert_array_equal(host(C), oracle.matmul(e, f, A, B))
 
 
-def test_int8_form_has_no_karatsuba_schedule(ctx):
+@pytest.mark.parametrize("form", ["mma_s8", "mma_b1"])
+def test_legacy_mma_forms_have_no_karatsuba_schedule(ctx, form):
     e, f = 4, workloads.FIELD_POLY[4]
-    ctx.set_form("mma_s8")
+    ctx.set_form(form)
     ctx.set_schedule("karatsuba")
     A = dev(np.ones((8, 8), np.uint8))
     with pytest.raises(m4.M4rieError) as ei:

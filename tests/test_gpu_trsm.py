@@ -55,7 +55,7 @@ def test_trsm_matches_oracle(e, m, n, upper):
 
 @pytest.mark.parametrize("form,sched", [("popc", "alpha_b"), ("popc", "karatsuba"), ("tc_f8", "alpha_b"),
                                         ("tc_f8", "karatsuba"), ("tc_f4", "alpha_b"), ("tc_f4", "karatsuba"),
-                                        ("mma_s8", "alpha_b")])
+                                        ("mma_s8", "alpha_b"), ("mma_b1", "alpha_b")])
 def test_trsm_every_form(form, sched):
     e, f = 4, workloads.FIELD_POLY[4]
     rng = np.random.default_rng(31)
@@ -202,7 +202,8 @@ def test_trsm_gf1024_1100():
 
 
 @pytest.mark.parametrize("form,sched", [("popc", "alpha_b"), ("popc", "karatsuba"), ("tc_f8", "karatsuba"),
-                                        ("tc_f4", "alpha_b"), ("tc_f4", "karatsuba"), ("mma_s8", "alpha_b")])
+                                        ("tc_f4", "alpha_b"), ("tc_f4", "karatsuba"), ("mma_s8", "alpha_b"),
+                                        ("mma_b1", "alpha_b")])
 @pytest.mark.parametrize("e", [3, 8, 10])
 def test_gemm_on_windows(form, sched, e):
     f = workloads.FIELD_POLY[e]
