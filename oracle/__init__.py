@@ -8,8 +8,9 @@ this package imports nothing from the product.
 The arithmetic lives in ``oracle.c`` (plain C, OpenMP over rows): the field
 product of Section 2 (carry-less multiply, then reduction modulo f) and its
 inverse, the cubic matrix product of Algorithm 1, the triangular solve of
-Algorithm 5 (Section 4.3) and the slicing / clinging conversions of
-Section 3.2 and Figure 1.  This module only compiles that file with gcc and
+Algorithm 5 (Section 4.3), the reduced row echelon form of Algorithm 4
+(Section 4.1) and the slicing / clinging conversions of Section 3.2 and
+Figure 1.  This module only compiles that file with gcc and
 marshals numpy arrays to it.
 """
 from __future__ import annotations
@@ -83,6 +84,8 @@ class OracleLib:
         L.oracle_trsm_upper_left.argtypes = [i32, u32, i64, i64, vp, vp]
         L.oracle_trsm_lower_left.restype = i32
         L.oracle_trsm_lower_left.argtypes = [i32, u32, i64, i64, vp, vp]
+        L.oracle_echelon.restype = i64
+        L.oracle_echelon.argtypes = [i32, u32, i64, i64, vp, vp]
         self.L = L
         self.path = path
 
@@ -164,6 +167,17 @@ class OracleLib:
             raise ZeroDivisionError("zero on the diagonal")
         return B16.astype(elem_dtype(e))
 
+    def echelon(self, e: int, f: int, A):
+        """Algorithm 4: (reduced row echelon form of A as a new array, rank,
+        pivot columns of the first rank rows)."""
+        A16 = _as_u16(A, e, "A").copy()
+        if A16.ndim != 2:
+            raise ValueError("A must be 2-D")
+        m, n = A16.shape
+        piv = np.zeros(max(1, min(m, n)), dtype=np.int64)
+        r = int(self.L.oracle_echelon(e, f, m, n, A16.ctypes.data, piv.ctypes.data)) if m and n else 0
+        return A16.astype(elem_dtype(e)), r, piv[:r].copy()
+
     def freivalds(self, e: int, f: int, A, B, C, trials: int = 64, seed: int = 0) -> bool:
         """Randomised check that C == A * B: with X an n x trials matrix of
         uniform field elements, compare A(BX) with CX.  A wrong C passes one
@@ -226,3 +240,7 @@ def gf_inv(e, f, a):
 
 def trsm(e, f, T, B, upper=True):
     return default().trsm(e, f, T, B, upper)
+
+
+def echelon(e, f, A):
+    return default().echelon(e, f, A)

@@ -27,6 +27,10 @@
  *     upper triangular, rows of B from the last to the first are scaled by
  *     the inverse diagonal entry and eliminated from the rows above; the
  *     lower-triangular case runs the same steps from the first row down.
+ *   - Reduced row echelon form (Section 4.1, Algorithm 4): column by column,
+ *     the first row at or below the current rank with a non-zero entry is
+ *     scaled to a leading 1, swapped up, and its multiples are added to every
+ *     other row to clear the column.
  *   - Slicing (Section 3.2 and Figure 1): slice i of a matrix holds
  *     coefficient i (bit i of the integer encoding) of every entry.  Slices
  *     are stored as rows of 64-bit words, column c at bit (c mod 64) of word
@@ -214,4 +218,54 @@ int oracle_trsm_lower_left(int e, uint32_t f, int64_t m, int64_t n, const uint16
         }
     }
     return 0;
+}
+
+/* Section 4.1, Algorithm 4: A (m x n, row-major, leading dimension n) is
+ * brought to reduced row echelon form in place; returns the rank r.  If
+ * pivots is not NULL, pivots[i] receives the pivot column of row i < r.  For
+ * every column j: the first row i >= r with A[i][j] != 0 is multiplied by
+ * A[i][j]^{-1}, swapped with row r, and A[k][j] times it is added to every
+ * other row k; then r grows by one.  (The algorithm's table of the multiples
+ * of row r is a speed device; the products are formed directly.  The clearing
+ * of the other rows is independent per row and runs on several threads.) */
+int64_t oracle_echelon(int e, uint32_t f, int64_t m, int64_t n, uint16_t *A, int64_t *pivots)
+{
+    int nt = oracle_get_threads();
+    (void)nt;
+    int64_t r = 0;
+    for (int64_t j = 0; j < n && r < m; j++) {
+        int64_t i = r;
+        while (i < m && A[i * n + j] == 0)
+            i++;
+        if (i == m)
+            continue;
+        uint32_t inv = oracle_gf_inv(e, f, A[i * n + j]);
+        uint16_t *ai = A + i * n;
+        for (int64_t c = 0; c < n; c++)
+            ai[c] = (uint16_t)oracle_gf_mul(e, f, inv, ai[c]);
+        if (i != r) {
+            uint16_t *ar = A + r * n;
+            for (int64_t c = 0; c < n; c++) {
+                uint16_t t = ar[c];
+                ar[c] = ai[c];
+                ai[c] = t;
+            }
+        }
+        const uint16_t *pr = A + r * n;
+#pragma omp parallel for schedule(static) num_threads(nt) if (m * (n - j) > 65536)
+        for (int64_t k = 0; k < m; k++) {
+            if (k == r)
+                continue;
+            uint32_t x = A[k * n + j];
+            if (x == 0)
+                continue;
+            uint16_t *ak = A + k * n;
+            for (int64_t c = j; c < n; c++)
+                ak[c] ^= (uint16_t)oracle_gf_mul(e, f, x, pr[c]);
+        }
+        if (pivots)
+            pivots[r] = j;
+        r++;
+    }
+    return r;
 }

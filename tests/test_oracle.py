@@ -329,6 +329,102 @@ def test_trsm_zero_diagonal_raises():
         oracle.trsm(2, 7, T, np.ones((2, 3), dtype=np.uint16))
 
 
+# ---------------------------------------------------------------- echelon form (Section 4.1, Algorithm 4)
+
+
+def random_rref(e, m, n, rank, rng):
+    """A random matrix in reduced row echelon form with the given rank: pivot
+    columns drawn at random, leading 1s, zeros in the other rows of pivot
+    columns and left of each pivot, random entries elsewhere."""
+    piv = np.sort(rng.choice(n, size=rank, replace=False))
+    R = np.zeros((m, n), dtype=np.int64)
+    for i, p in enumerate(piv):
+        R[i, p + 1:] = rng.integers(0, 1 << e, size=n - p - 1)
+        R[i, p] = 1
+    for i, p in enumerate(piv):
+        R[:rank, p] = 0
+        R[i, p] = 1
+    return R, piv
+
+
+def random_invertible(e, f, m, rng):
+    """S = L U with L unit lower and U upper triangular with non-zero diagonal."""
+    L = np.tril(rng.integers(0, 1 << e, size=(m, m)), -1) + np.eye(m, dtype=np.int64)
+    U = np.triu(rng.integers(0, 1 << e, size=(m, m)), 1)
+    U[np.arange(m), np.arange(m)] = rng.integers(1, 1 << e, size=m)
+    return fr.slice_product(e, f, L, U)
+
+
+def is_rref(R, rank):
+    lead = -1
+    for i in range(R.shape[0]):
+        nz = np.nonzero(R[i])[0]
+        if i >= rank:
+            if nz.size:
+                return False
+            continue
+        if not nz.size or nz[0] <= lead or R[i, nz[0]] != 1:
+            return False
+        lead = nz[0]
+        col = R[:, lead].copy()
+        col[i] = 0
+        if col.any():
+            return False
+    return True
+
+
+@pytest.mark.parametrize("e,m,n,rank", [(2, 12, 15, 12), (3, 20, 11, 7), (4, 16, 16, 16), (8, 30, 40, 22),
+                                        (10, 9, 25, 5), (5, 14, 14, 0)])
+def test_echelon_recovers_a_constructed_rref(e, m, n, rank):
+    """A = S R with R in reduced row echelon form and S invertible has the
+    row space of R, so its reduced echelon form is exactly R (uniqueness)."""
+    f = workloads.FIELD_POLY[e]
+    rng = np.random.default_rng(e * 100 + m + n + rank)
+    R, piv = random_rref(e, m, n, rank, rng)
+    A = fr.slice_product(e, f, random_invertible(e, f, m, rng), R)
+    E, r, p = oracle.echelon(e, f, A)
+    assert r == rank
+    assert np.array_equal(E.astype(np.int64), R)
+    assert np.array_equal(p, piv)
+
+
+def _row_space(e, table, M):
+    """All linear combinations of the rows of M over GF(2^e) (small M only)."""
+    rows = [tuple(int(v) for v in r) for r in M]
+    space = {tuple([0] * M.shape[1])}
+    for r in rows:
+        space = {tuple(a ^ int(table[c, b]) for a, b in zip(v, r)) for v in space for c in range(1 << e)}
+    return space
+
+
+def test_echelon_brute_force_small_gf4():
+    """Every 2 x 2 and a sample of 3 x 3 matrices over GF(4): the output is in
+    reduced row echelon form, has the input's row space (enumerated), and its
+    rank is the number of non-zero rows."""
+    e, f = 2, workloads.FIELD_POLY[2]
+    table = fr.log_table_product(e, f)
+    cases = [np.array(v, dtype=np.uint8).reshape(2, 2) for v in itertools.product(range(4), repeat=4)]
+    rng = np.random.default_rng(3)
+    cases += [rng.integers(0, 4, size=(3, 3)).astype(np.uint8) for _ in range(300)]
+    cases += [rng.integers(0, 4, size=(2, 4)).astype(np.uint8) for _ in range(100)]
+    for A in cases:
+        E, r, _ = oracle.echelon(e, f, A)
+        assert is_rref(E.astype(np.int64), r), A
+        assert _row_space(e, table, A) == _row_space(e, table, E), A
+        assert r == int((E != 0).any(axis=1).sum())
+
+
+def test_echelon_is_idempotent_and_zero_matrix():
+    e, f = 7, workloads.FIELD_POLY[7]
+    rng = np.random.default_rng(4)
+    A = rng.integers(0, 128, size=(25, 31)).astype(np.uint8)
+    E, r, p = oracle.echelon(e, f, A)
+    E2, r2, p2 = oracle.echelon(e, f, E)
+    assert np.array_equal(E, E2) and r == r2 and np.array_equal(p, p2)
+    Z, rz, pz = oracle.echelon(e, f, np.zeros((5, 6), np.uint8))
+    assert rz == 0 and not Z.any() and pz.size == 0
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 _MUTANTS = {
@@ -352,6 +448,10 @@ _MUTANTS = {
     "trsm_transposed": ("uint32_t x = U[j * m + i];", "uint32_t x = U[i * m + j];"),
     # lower solve skips the row just below the pivot row
     "trsm_skip_row": ("for (int64_t j = i + 1; j < m; j++) {", "for (int64_t j = i + 2; j < m; j++) {"),
+    # echelon form without scaling the pivot row to a leading 1
+    "echelon_no_scale": ("ai[c] = (uint16_t)oracle_gf_mul(e, f, inv, ai[c]);", "ai[c] = ai[c];"),
+    # echelon form that clears only the rows below the pivot (not reduced)
+    "echelon_below_only": ("for (int64_t k = 0; k < m; k++) {\n            if (k == r)", "for (int64_t k = r + 1; k < m; k++) {\n            if (k == r)"),
     # upper solve does not scale by the inverse diagonal entry
     "trsm_no_scale": ("for (int64_t i = m - 1; i >= 0; i--) {\n        uint32_t d = U[i * m + i];\n        if (d == 0)\n            return -1;\n        uint32_t dinv = oracle_gf_inv(e, f, d);",
                       "for (int64_t i = m - 1; i >= 0; i--) {\n        uint32_t d = U[i * m + i];\n        if (d == 0)\n            return -1;\n        uint32_t dinv = 1;"),
@@ -387,6 +487,11 @@ def _pins_pass(O: oracle.OracleLib) -> bool:
                 B = rng.integers(0, 1 << e, size=(9, 5)).astype(np.uint16)
                 if not np.array_equal(fr.slice_product(e, f, T, O.trsm(e, f, T, B, upper)), B.astype(np.int64)):
                     return False
+            R, piv = random_rref(e, 10, 14, 6, rng)
+            A = fr.slice_product(e, f, random_invertible(e, f, 10, rng), R)
+            E, r, p = O.echelon(e, f, A)
+            if r != 6 or not np.array_equal(E.astype(np.int64), R) or not np.array_equal(p, piv):
+                return False
         return True
     except Exception:
         return False
