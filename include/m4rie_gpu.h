@@ -145,6 +145,19 @@ m4rie_status m4rie_trsm_upper_left(m4rie_ctx *ctx, int e, uint32_t f, int64_t m,
 m4rie_status m4rie_trsm_lower_left(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, const void *T,
                                    int64_t ldt, void *B, int64_t ldb);
 
+/* Reduced row echelon form over GF(2^e) in place (Section 4.1, Algorithm 4;
+ * Section 6): A is m x n with row stride lda >= n.  On return A holds the
+ * unique reduced row echelon form of the input, *rank (if rank != NULL) its
+ * rank r, and pivots[0 .. r) (if pivots != NULL; room for min(m, n) entries)
+ * the pivot column of each of the first r rows.  Runs by panels of 64
+ * columns: a candidate block is reduced in shared memory to find the pivots,
+ * and the rest of the matrix is updated with slice GEMMs.  Synchronous (it
+ * reads the pivot list back for every panel).  Entries >= 2^e set the sticky
+ * M4RIE_ERR_RANGE status.  Uses a context-owned scratch of about
+ * 64 m + 256 n elements. */
+m4rie_status m4rie_echelonize(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, void *A, int64_t lda,
+                              int64_t *rank, int64_t *pivots);
+
 /* m4rie_mul / m4rie_addmul (accumulate != 0) on HOST buffers: copies A, B
  * (and C when accumulating) to context-owned device memory, computes, copies
  * C back and waits for the stream.  Host buffers may be pageable or pinned. */

@@ -54,6 +54,7 @@ def _load() -> ctypes.CDLL:
         "m4rie_gemm": (i32, [vp, i32, u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, i32]),
         "m4rie_trsm_upper_left": (i32, [vp, i32, u32, i64, i64, vp, i64, vp, i64]),
         "m4rie_trsm_lower_left": (i32, [vp, i32, u32, i64, i64, vp, i64, vp, i64]),
+        "m4rie_echelonize": (i32, [vp, i32, u32, i64, i64, vp, i64, ctypes.POINTER(i64), vp]),
         "m4rie_mul_host": (i32, [vp, i32, u32, i64, i64, i64, vp, vp, vp, i32]),
         "m4rie_pack": (i32, [vp, i32, i64, i64, vp, vp, i64]),
         "m4rie_unpack": (i32, [vp, i32, i64, i64, vp, i64, vp]),
@@ -211,6 +212,18 @@ class Context:
         self._raise(fn(self.handle, e, f, m, n, _ptr(T), _ld(T), _ptr(B), _ld(B)),
                     "m4rie_trsm_upper_left" if upper else "m4rie_trsm_lower_left")
         return B
+
+    def echelonize(self, e: int, f: int, A):
+        """Reduced row echelon form of A in place (Algorithm 4); returns
+        (rank, list of pivot columns).  Synchronous."""
+        import numpy as np
+        _check_dev(A, e, "A", strided=True)
+        m, n = A.shape
+        rank = ctypes.c_int64()
+        piv = np.zeros(max(1, min(m, n)), dtype=np.int64)
+        self._raise(lib.m4rie_echelonize(self.handle, e, f, m, n, _ptr(A), _ld(A) if m else n, ctypes.byref(rank),
+                                         ctypes.c_void_p(piv.ctypes.data)), "m4rie_echelonize")
+        return int(rank.value), [int(v) for v in piv[:rank.value]]
 
     def mul_host(self, e: int, f: int, A, B, C, accumulate: bool = False):
         """Host-buffer product (torch CPU tensors or numpy arrays); synchronous."""

@@ -493,6 +493,8 @@ void m4rie_destroy(m4rie_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   destroy_trsm_graph(ctx->trsm_graph);
   if (ctx->tws) cudaFree(ctx->tws);
+  if (ctx->ews) cudaFree(ctx->ews);
+  if (ctx->ews_host) cudaFreeHost(ctx->ews_host);
   if (ctx->d_gf) cudaFree(ctx->d_gf);
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
   destroy_plan(ctx->plan);

@@ -65,6 +65,10 @@ struct m4rie_ctx {
   int gf_e = 0;
   uint32_t gf_f = 0;
   m4rie::TrsmGraph* trsm_graph = nullptr;  // the last solve, recorded for replay
+  // echelon forms (echelon.cu): candidate lists, multipliers, panel products
+  void* ews = nullptr;
+  size_t ews_bytes = 0;
+  int* ews_host = nullptr;  // pinned: two slots of row-move lists
 };
 
 namespace m4rie {

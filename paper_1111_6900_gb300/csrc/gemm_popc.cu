@@ -113,23 +113,34 @@ __global__ void __launch_bounds__(256, 2) popc_fused(const __grid_constant__ Pop
 
   OutT* C = static_cast<OutT*>(p.C);
   bool bad = false;
+  // with accumulation, the old values of 4 row groups are loaded before any
+  // of them is written, so the loads' latencies overlap
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int64_t r = m0 + ty + 16 * q;
+  for (int q0 = 0; q0 < 8; q0 += 4) {
+    uint32_t old[4][TNC];
 #pragma unroll
-    for (int v = 0; v < TNC; ++v) {
-      const int64_t c = g * G + tx + 16 * v;
-      if (r < p.m && c < p.n) {
-        uint32_t val = 0;
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int i = 0; i < E; ++i) val |= (uint32_t)(__popc(acc[q][v][i]) & 1) << i;
-        OutT* dst = C + r * p.ldc + c;
-        if (p.add) {
-          const uint32_t old = *dst;
-          bad |= old > p.emask;
-          val ^= old & p.emask;
+      for (int v = 0; v < TNC; ++v) {
+        const int64_t r = m0 + ty + 16 * (q0 + q), c = g * G + tx + 16 * v;
+        old[q][v] = p.add && r < p.m && c < p.n ? (uint32_t)C[r * p.ldc + c] : 0u;
+      }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t r = m0 + ty + 16 * (q0 + q);
+#pragma unroll
+      for (int v = 0; v < TNC; ++v) {
+        const int64_t c = g * G + tx + 16 * v;
+        if (r < p.m && c < p.n) {
+          uint32_t val = 0;
+#pragma unroll
+          for (int i = 0; i < E; ++i) val |= (uint32_t)(__popc(acc[q0 + q][v][i]) & 1) << i;
+          if (p.add) {
+            bad |= old[q][v] > p.emask;
+            val ^= old[q][v] & p.emask;
+          }
+          C[r * p.ldc + c] = (OutT)val;
         }
-        *dst = (OutT)val;
       }
     }
   }

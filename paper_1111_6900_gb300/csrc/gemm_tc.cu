@@ -521,35 +521,46 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int w = 0; w < 8; ++w) wbits[lane * 9 + w] = bits[w];
       wbits[lane * 9 + 8] = 0;  // sentinel word for the funnel shift
       __syncwarp();
-      const int G = t.G, E = t.e;
+      const int G = t.G, E = t.e;  // G <= 128 (tile N = e * G <= 256, e >= 2)
       const int64_t c0 = (int64_t)tn * G;
       bool bad = false;
-      for (int rl = 0; rl < 32; ++rl) {
-        const int64_t r = r0 + 32 * q + rl;
-        if (r >= t.m) break;
-        const uint32_t* rb = wbits + rl * 9;
-        for (int cl = lane; cl < G; cl += 32) {
-          const int64_t c = c0 + cl;
-          if (c >= t.n) break;
-          const int pos = cl * E;
-          const uint64_t pair = rb[pos >> 5] | ((uint64_t)rb[(pos >> 5) + 1] << 32);
-          uint32_t val = (uint32_t)(pair >> (pos & 31)) & t.emask;
-          if (t.elem_bytes == 1) {
-            uint8_t* dst = static_cast<uint8_t*>(t.C) + r * t.ldc + c;
-            if (t.add) {
-              const uint32_t old = *dst;
-              bad |= old > t.emask;
-              val ^= old & t.emask;
+      // A lane takes elements lane, lane + 32, lane + 64, lane + 96 of each row.
+      // With accumulation, the old values of 8 rows are loaded before any of
+      // them is written, so the loads' latencies overlap.
+      for (int rl0 = 0; rl0 < 32; rl0 += 8) {
+        uint32_t old[8][4];
+        if (t.add) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int64_t r = r0 + 32 * q + rl0 + i, c = c0 + lane + 32 * u;
+              old[i][u] = 0;
+              if (r < t.m && lane + 32 * u < G && c < t.n)
+                old[i][u] = t.elem_bytes == 1 ? (uint32_t)static_cast<const uint8_t*>(t.C)[r * t.ldc + c]
+                                              : (uint32_t)static_cast<const uint16_t*>(t.C)[r * t.ldc + c];
             }
-            *dst = (uint8_t)val;
-          } else {
-            uint16_t* dst = static_cast<uint16_t*>(t.C) + r * t.ldc + c;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int rl = rl0 + i;
+          const int64_t r = r0 + 32 * q + rl;
+          if (r >= t.m) break;
+          const uint32_t* rb = wbits + rl * 9;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int cl = lane + 32 * u;
+            const int64_t c = c0 + cl;
+            if (cl >= G || c >= t.n) break;
+            const int pos = cl * E;
+            const uint64_t pair = rb[pos >> 5] | ((uint64_t)rb[(pos >> 5) + 1] << 32);
+            uint32_t val = (uint32_t)(pair >> (pos & 31)) & t.emask;
             if (t.add) {
-              const uint32_t old = *dst;
-              bad |= old > t.emask;
-              val ^= old & t.emask;
+              bad |= old[i][u] > t.emask;
+              val ^= old[i][u] & t.emask;
             }
-            *dst = (uint16_t)val;
+            if (t.elem_bytes == 1) static_cast<uint8_t*>(t.C)[r * t.ldc + c] = (uint8_t)val;
+            else static_cast<uint16_t*>(t.C)[r * t.ldc + c] = (uint16_t)val;
           }
         }
       }

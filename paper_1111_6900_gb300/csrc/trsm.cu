@@ -32,7 +32,7 @@ namespace {
 
 constexpr int NB = 128;          // diagonal block rows
 constexpr int LOG_WORDS = 1024;  // log table: 2^e entries, e <= 10
-constexpr int EXP_WORDS = 2048;  // antilog table, doubled so that log a + log b needs no reduction
+constexpr int EXP_WORDS = 4096;  // antilog table g^i for i < 2(2^e - 1), then zeros (see build_tables)
 constexpr size_t INV_SMEM = (size_t)(LOG_WORDS + EXP_WORDS + NB * NB + NB * (NB + 2)) * sizeof(uint16_t);
 
 // a * x mod f (shift, then subtract f when the degree reaches e)
@@ -50,7 +50,9 @@ uint32_t times(int e, uint32_t f, uint32_t a, uint32_t g) {
 }
 
 // Log / antilog tables of GF(2^e)* = <g> for the first generator g >= 2:
-// tab[0 .. 1024) = log, tab[1024 .. 1024 + 2(2^e - 1)) = g^i for i < 2(2^e - 1).
+// tab[0 .. 1024) = log, tab[1024 + i] = g^i for i < 2(2^e - 1) and 0 for
+// 2(2^e - 1) <= i <= 4(2^e - 1).  log 0 is set to 2(2^e - 1), so that
+// a * b = antilog[log a + log b] holds for zero operands too.
 bool build_tables(int e, uint32_t f, std::vector<uint16_t>& tab) {
   const uint32_t q = (1u << e) - 1;
   tab.assign(LOG_WORDS + EXP_WORDS, 0);
@@ -63,7 +65,10 @@ bool build_tables(int e, uint32_t f, std::vector<uint16_t>& tab) {
       tab[a] = (uint16_t)i;
       a = times(e, f, a, g);
     }
-    if (i == q && a == 1) return true;
+    if (i == q && a == 1) {
+      tab[0] = (uint16_t)(2 * q);
+      return true;
+    }
   }
   return false;
 }
@@ -120,10 +125,7 @@ __global__ void __launch_bounds__(INV_THREADS) tri_inverse(int e, const T* __res
     if (active) {
       const int j0 = UPPER ? i + 1 : c, j1 = UPPER ? c : i - 1;
 #pragma unroll 2
-      for (int j = j0 + sl; j <= j1; j += 8) {
-        const uint32_t a = tb[i * NB + j], x = xc[j];
-        if (a && x) s ^= ex[lg[a] + lg[x]];
-      }
+      for (int j = j0 + sl; j <= j1; j += 8) s ^= ex[lg[tb[i * NB + j]] + lg[xc[j]]];
     }
     s ^= __shfl_xor_sync(0xffffffffu, s, 1);
     s ^= __shfl_xor_sync(0xffffffffu, s, 2);
@@ -268,6 +270,8 @@ bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
 }
 
 }  // namespace
+
+m4rie_status ensure_field_tables(m4rie_ctx* ctx, int e, uint32_t f) { return field_tables(ctx, e, f); }
 
 // The key of a recorded solve and its graph.
 struct TrsmGraph {
