@@ -362,12 +362,171 @@ def run_trsm_workload(args, m4, torch, world, rank, local):
     return 0
 
 
+# The paper's CPU times for the same echelon workloads (milliseconds): the
+# introduction's 4000 x 4000 over GF(4) and Table 2's Newton-John column for
+# 1000 x 1000 over GF(2^8).
+PAPER_ECHELON_MS = {"rref_gf4_4000": 400.0, "rref_gf256_1000": 81.0}
+
+
+def echelon_config(name):
+    e, m, n, seed = workloads.ECHELON_WORKLOADS[name]
+    ty = "uint8" if e <= 8 else "uint16"
+    return e, m, n, seed, {
+        "workload": f"reduced row echelon form over GF(2^{e}), f = {hex(workloads.FIELD_POLY[e])}, random {m}x{n} {ty}",
+        "m": m, "n": n, "e": e, "op": "echelonize", "l2": "flushed between timed steps (512 MB write, not timed)"}
+
+
+def echelon_cpu_sample(e, f, A):
+    """The oracle on the leading block of at most 1000 x 1000, scaled to the
+    whole matrix by (rows x columns x rank), i.e. by (m n min(m, n)) / (s^2 min)."""
+    import oracle
+    m, n = A.shape
+    s = min(1000, m, n)
+    t0 = time.perf_counter()
+    oracle.echelon(e, f, np.ascontiguousarray(A[:s, :s]))
+    dt = time.perf_counter() - t0
+    scale = (m * n * min(m, n)) / float(s * s * s)
+    return dt * scale, f"leading {s}x{s} block ({dt:.2f} s), scaled by m n min(m,n) / {s}^3 = {scale:.1f} (extrapolated)"
+
+
+def run_reference_echelon(args):
+    e, m, n, seed, config = echelon_config(args.workload)
+    f = workloads.FIELD_POLY[e]
+    A = workloads.echelon_matrix(e, m, n, seed)
+    for _ in range(min(args.warmup, 1)):
+        echelon_cpu_sample(e, f, A)
+    times = []
+    for _ in range(args.steps):
+        t, sample = echelon_cpu_sample(e, f, A)
+        times.append(t)
+    ms = sum(times) / len(times) * 1e3
+    import oracle
+    base = PAPER_ECHELON_MS.get(args.workload)
+    out = {"impl": "reference", "metric": f"GF(2^e) reduced echelon form time, {args.workload}", "value": ms,
+           "unit": "ms", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": ms / base if base else None,
+           "dtype": "u8" if e <= 8 else "u16", "data": "synthetic", "config": config,
+           "cpu_baseline": {"value": ms, "unit": "ms", "cores": oracle.get_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_echelon_workload(args, m4, torch, world, rank, local):
+    """Reduced row echelon form of a random dense matrix (Section 4.1,
+    Algorithm 4, by panels over the slice GEMM); value = ms per echelon form."""
+    e, m, n, seed, config = echelon_config(args.workload)
+    f = workloads.FIELD_POLY[e]
+    A = workloads.echelon_matrix(e, m, n, seed)
+    dA0 = torch.from_numpy(A).cuda()
+    dA = dA0.clone()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = m4.Context(stream)
+    if args.single:
+        for _ in range(args.warmup + 1):
+            dA.copy_(dA0)
+            ctx.echelonize(e, f, dA)
+        torch.cuda.synchronize()
+        status = ctx.device_status()
+        ctx.close()
+        return 0 if status == m4.OK else 1
+    rank0, piv0 = ctx.echelonize(e, f, dA)
+    E0 = dA.clone()
+    for _ in range(args.warmup):
+        dA.copy_(dA0)
+        ctx.echelonize(e, f, dA)
+    torch.cuda.synchronize()
+    launches0 = ctx.kernel_launches()
+    ms_list = []
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        clk.mark_start()
+        for i in range(args.steps):
+            dA.copy_(dA0)
+            flush.fill_(i & 0xFF)
+            s, t = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            rk, _ = ctx.echelonize(e, f, dA)
+            t.record(stream)
+            torch.cuda.synchronize()
+            ms_list.append(s.elapsed_time(t))
+        clk.mark_end()
+        time.sleep(0.1)
+    ms = sum(ms_list) / len(ms_list)
+    _, sec = replica_throughput(1.0, ms * 1e-3, "cuda")
+    ms = sec * 1e3
+    launches = (ctx.kernel_launches() - launches0) // max(args.steps, 1)
+    same = bool(torch.equal(dA, E0))
+
+    # slice-GEMM phase of one solve: the update products are HBM-bound (K = 64)
+    ctx.enable_timing(True)
+    ctx.phase_times(reset=True)
+    dA.copy_(dA0)
+    ctx.echelonize(e, f, dA)
+    pack_ms, gemm_ms, rec_ms, nprod = ctx.phase_times(reset=True)
+    ctx.enable_timing(False)
+    w = 1 if e <= 8 else 2
+    # every panel reads and writes columns c0.. of all m rows (the update) and the pivot rows (X)
+    W = 64
+    upd = sum(2.0 * m * (n - c0) * w + 2.0 * W * (n - c0) * w for c0 in range(0, min(n, rank0 + W), W))
+    pk = peaks() or {}
+    hbm = pk.get("hbm_gbs", 6800.0)
+    achieved = upd / ((gemm_ms + pack_ms + rec_ms) * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+            "scope": f"the {nprod} slice products of one echelon form (packing + GEMM + recombination: "
+                     f"{pack_ms + gemm_ms + rec_ms:.2f} of {ms:.2f} ms); algorithmic bytes = read + write of the "
+                     f"updated columns of every row per panel"}
+
+    # end to end: pinned host matrix in, echelon form out
+    hA = torch.from_numpy(A).pin_memory()
+    hE = torch.empty_like(hA).pin_memory()
+    e2e = []
+    for i in range(max(3, args.steps // 2) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dA.copy_(hA, non_blocking=True)
+        ctx.echelonize(e, f, dA)
+        hE.copy_(dA, non_blocking=True)
+        torch.cuda.synchronize()
+        if i:
+            e2e.append(time.perf_counter() - t0)
+    e2e_ms = sum(e2e) / len(e2e) * 1e3
+    base = PAPER_ECHELON_MS.get(args.workload)
+    out = {"metric": f"GF(2^e) reduced echelon form time, {args.workload}; bit-exact", "value": ms, "unit": "ms",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": ms / base if base else None,
+           "dtype": "u8" if e <= 8 else "u16", "data": "synthetic",
+           "config": dict(config, rank=rank0, parallelism=f"replicas{world}"),
+           "clocks": clk.summary(), "gpu_launches": launches,
+           "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": A.nbytes, "d2h_bytes_per_step": A.nbytes},
+           "roofline": roof, "repeatable": same}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t, sample = echelon_cpu_sample(e, f, A)
+        out["cpu_baseline"] = {"value": t * 1e3, "unit": "ms", "cores": oracle.get_threads(), "kind": "oracle",
+                               "sample": sample}
+        s = min(1000, m, n)
+        if s == min(m, n) and m == n:
+            E_ref, r_ref, p_ref = oracle.echelon(e, f, A)
+            out["bit_exact_vs_oracle"] = {"equal": bool(np.array_equal(E0.cpu().numpy(), E_ref)), "rank": r_ref}
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
     if args.workload in workloads.TRSM_WORKLOADS:
         return run_reference_trsm(args)
+    if args.workload in workloads.ECHELON_WORKLOADS:
+        return run_reference_echelon(args)
     import oracle
     w = WORKLOAD
     A, B, _ = w.inputs()
@@ -452,7 +611,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     names = {w.name: i for i, w in workloads.WORKLOADS.items()}
     ap.add_argument("--workload", default="gf16_4096_mul",
-                    choices=sorted(names) + ["batched"] + sorted(workloads.TRSM_WORKLOADS),
+                    choices=sorted(names) + ["batched"] + sorted(workloads.TRSM_WORKLOADS)
+                    + sorted(workloads.ECHELON_WORKLOADS),
                     help="gf16_4096_mul (default, the headline), another single-product workload, batched, "
                          "or a triangular solve (trsm_*)")
     ap.add_argument("--batched-count", type=int, default=workloads.BATCHED_COUNT,
@@ -483,6 +643,8 @@ def main():
         return run_batched_workload(args, m4, torch, world, rank, local)
     if args.workload in workloads.TRSM_WORKLOADS:
         return run_trsm_workload(args, m4, torch, world, rank, local)
+    if args.workload in workloads.ECHELON_WORKLOADS:
+        return run_echelon_workload(args, m4, torch, world, rank, local)
 
     metric = METRIC if WORKLOAD.name == "gf16_4096_mul" else f"GF(2^e) matmul field-ops/s, {WORKLOAD.name}; bit-exact"
     w = WORKLOAD

@@ -142,21 +142,25 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_factor(int e, const T* __
     if ((done0 >> j) & 1ull) continue;
     if (tid == 0) sel = R;
     __syncthreads();
-    if (part == 0 && row < cnt && !is_piv[row] && br[j] != 0) atomicMin(&sel, row);
+    {
+      // lowest candidate row (not yet a pivot) with a non-zero entry: a
+      // ballot per warp (8 rows), then one atomic per warp
+      const bool hit = part == 0 && row < cnt && !is_piv[row] && br[j] != 0;
+      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+      if ((tid & 31) == 0 && bal) atomicMin(&sel, (tid + __ffs(bal) - 1) >> 2);
+    }
     __syncthreads();
     const int p = sel;
     if (p == R) continue;  // no pivot in this column among the candidates
-    // scale the pivot row to a leading 1 (its entries left of j are zero)
-    const uint32_t d = blk[p * BP + j];
-    const uint32_t ld = q - lg[d];  // log of d^{-1}
-    __syncwarp();                   // the 4 threads of row p have read d before any of them scales
-    if (row == p) {
-#pragma unroll
-      for (int i = 0; i < W / 4; ++i) {
-        const int c = part + 4 * i;
-        const uint32_t v = ex[lg[br[c]] + ld];
-        br[c] = (uint16_t)v;
-        plg[c] = lg[v];
+    // scale the pivot row to a leading 1 (its entries left of j are zero),
+    // one thread per column, and keep the logs of its entries
+    {
+      const uint32_t ld = q - lg[blk[p * BP + j]];  // log of the inverse pivot
+      __syncthreads();                               // every thread has read the pivot
+      if (tid < W) {
+        const uint32_t v = ex[lg[blk[p * BP + tid]] + ld];
+        blk[p * BP + tid] = (uint16_t)v;
+        plg[tid] = lg[v];
       }
     }
     __syncthreads();
@@ -199,7 +203,11 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_factor(int e, const T* __
   for (int t = 0; t < k; ++t) {
     if (tid == 0) sel = W;
     __syncthreads();
-    if (part == 0 && row >= t && row < k && gr[t] != 0) atomicMin(&sel, row);
+    {
+      const bool hit = part == 0 && row >= t && row < k && gr[t] != 0;
+      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+      if ((tid & 31) == 0 && bal) atomicMin(&sel, (tid + __ffs(bal) - 1) >> 2);
+    }
     __syncthreads();
     const int p = sel;  // exists: M is invertible
     // swap rows p and t (the 4 threads of row t each swap their columns)
@@ -212,15 +220,13 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_factor(int e, const T* __
       }
     }
     __syncthreads();
-    const uint32_t ld = q - lg[g[t * GP + t]];
-    __syncwarp();  // the 4 threads of row t have read the pivot before any of them scales
-    if (row == t) {
-#pragma unroll
-      for (int i = 0; i < 2 * W / 4; ++i) {
-        const int c = part + 4 * i;
-        const uint32_t v = ex[lg[gr[c]] + ld];
-        gr[c] = (uint16_t)v;
-        plg[c] = lg[v];
+    {
+      const uint32_t ld = q - lg[g[t * GP + t]];
+      __syncthreads();  // every thread has read the pivot
+      if (tid < 2 * W) {
+        const uint32_t v = ex[lg[g[t * GP + tid]] + ld];
+        g[t * GP + tid] = (uint16_t)v;
+        plg[tid] = lg[v];
       }
     }
     __syncthreads();

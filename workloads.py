@@ -114,3 +114,18 @@ def triangular_system(e: int, m: int, n: int, seed: int, upper: bool = True):
     T[np.arange(m), np.arange(m)] = rng.integers(1, 1 << e, size=m).astype(T.dtype)
     B = elements(rng, e, (m, n))
     return T, B
+
+
+# Reduced row echelon forms of random dense matrices (Section 4.1; the
+# introduction's 4000 x 4000 over GF(4) and Table 2's 1000 x 1000 sizes):
+# (e, m, n, seed).
+ECHELON_WORKLOADS = {
+    "rref_gf4_4000": (2, 4000, 4000, 1200),
+    "rref_gf256_1000": (8, 1000, 1000, 1201),
+    "rref_gf16_8192": (4, 8192, 8192, 1202),
+}
+
+
+def echelon_matrix(e: int, m: int, n: int, seed: int):
+    """Seeded m x n matrix, entries uniform in [0, 2^e)."""
+    return elements(np.random.default_rng(seed), e, (m, n))
