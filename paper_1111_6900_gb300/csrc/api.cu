@@ -477,7 +477,9 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
     delete ctx;
     return M4RIE_ERR_CUDA;
   }
-  if (const char* s = getenv("M4RIE_TC_CHUNK")) ctx->tc_chunk = std::max(128, atoi(s));
+  // counts per chunk stay below 2^23 (FP32-exact, and the epilogue's parity trick needs x < 2^23):
+  // a chunk holds at most 2 * tc_chunk FP4 entries
+  if (const char* s = getenv("M4RIE_TC_CHUNK")) ctx->tc_chunk = std::min(std::max(128, atoi(s)), 1 << 21);
   if (const char* s = getenv("M4RIE_F4_KIND")) ctx->f4nv = strcmp(s, "nvf4") == 0 ? 1 : 0;
   if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) == 2 ? 2 : 1;
   if (const char* s = getenv("M4RIE_TUNE_CACHE")) m4rie_tune_load(ctx, s);  // a missing file is not an error

@@ -494,7 +494,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             } else {
               uint32_t w = 0;
 #pragma unroll
-              for (int j = 0; j < 16; ++j) w |= ((uint32_t)__float2int_rz(__uint_as_float(v[j])) & 1u) << j;
+              // parity of an integer count x < 2^23 held exactly in FP32: x + 2^23 is exact and
+              // leaves x in the low mantissa bits, so bit 0 of its encoding is x mod 2
+              for (int j = 0; j < 16; ++j) w |= (__float_as_uint(__uint_as_float(v[j]) + 8388608.0f) & 1u) << j;
               bits[c16 >> 1] ^= w << (16 * (c16 & 1));
             }
           }
