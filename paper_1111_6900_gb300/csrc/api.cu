@@ -218,11 +218,6 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   pa.out = Ap;
   pa.status = ctx->d_status;
   for (int j = 0; j < e; ++j) pa.mask[j] = amask[j];
-  PhaseTimer timer(ctx);
-  timer.begin(kPhasePack);
-  cudaError_t err = launch_pack_planes(pa, ctx->stream, &ctx->launches);
-  if (err != cudaSuccess) return cuda_fail(ctx, err);
-
   PackParams pb = pa;  // columns of B (k x n) are the planes' rows
   pb.X = B;
   pb.ldx = x.ldb;
@@ -236,7 +231,9 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   pb.emajor = (form == M4RIE_FORM_TC_F8 || form == M4RIE_FORM_TC_F4) ? 1 : 0;
   pb.out = Bp;
   for (int q = 0; q < e * e; ++q) pb.mask[q] = bmask[q];
-  err = launch_pack_cols(pb, ctx->stream, &ctx->launches);
+  PhaseTimer timer(ctx);
+  timer.begin(kPhasePack);
+  cudaError_t err = launch_pack_pair(pa, pb, ctx->stream, &ctx->launches);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
   timer.begin(kPhaseGemm);
 
@@ -341,10 +338,6 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   pa.out = Ap;
   pa.status = ctx->d_status;
   for (int p = 0; p < r; ++p) pa.mask[p] = sc.amask[p];
-  PhaseTimer timer(ctx);
-  timer.begin(kPhasePack);
-  cudaError_t err = launch_pack_planes(pa, ctx->stream, &ctx->launches);
-  if (err != cudaSuccess) return cuda_fail(ctx, err);
   PackParams pb = pa;  // columns of B (k x n) are the planes' rows
   pb.X = B;
   pb.ldx = x.ldb;
@@ -353,7 +346,9 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   pb.bstride = Np * Kp;
   pb.out = Bp;
   for (int p = 0; p < r; ++p) pb.mask[p] = sc.bmask[p];
-  err = launch_pack_cols(pb, ctx->stream, &ctx->launches);
+  PhaseTimer timer(ctx);
+  timer.begin(kPhasePack);
+  cudaError_t err = launch_pack_pair(pa, pb, ctx->stream, &ctx->launches);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
   timer.begin(kPhaseGemm);
 

@@ -61,6 +61,8 @@ bool plane_offsets(PackParams& p);
 // memory.  launch_transpose serves the batched path, which transposes first.
 cudaError_t launch_pack_planes(const PackParams& p, cudaStream_t s, int64_t* launches);
 cudaError_t launch_pack_cols(const PackParams& p, cudaStream_t s, int64_t* launches);
+// Both at once (A by rows, B by columns) in one launch.
+cudaError_t launch_pack_pair(const PackParams& a, const PackParams& b, cudaStream_t s, int64_t* launches);
 cudaError_t launch_transpose(const void* X, int64_t ldx, int64_t K, int64_t rows, int elem_bytes, void* Xt,
                              cudaStream_t s, int64_t* launches);
 

@@ -223,13 +223,19 @@ struct PlaneSmem {
 // covers longer rows in chunks of 256 threads x NE elements, grid.y strides
 // over row groups.
 template <typename T, int FMT, int E>
-__global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant__ PackParams p, int tpr) {
-  __shared__ PlaneSmem sm;
-  plane_tables<E>(p, sm.mexp);
+__device__ __forceinline__ void rows_body(const PackParams& p, int tpr, uint32_t bx, uint32_t by, uint32_t gy,
+                                          uint32_t* mexp) {
+  plane_tables<E>(p, mexp);
   __syncthreads();
   const int rpb = 256 / tpr;
-  pack_planes_rows<T, FMT, E>(p, sm.mexp, (int64_t)blockIdx.x * 256 + threadIdx.x % tpr,
-                              (int64_t)blockIdx.y * rpb + threadIdx.x / tpr, (int64_t)gridDim.y * rpb);
+  pack_planes_rows<T, FMT, E>(p, mexp, (int64_t)bx * 256 + threadIdx.x % tpr, (int64_t)by * rpb + threadIdx.x / tpr,
+                              (int64_t)gy * rpb);
+}
+
+template <typename T, int FMT, int E>
+__global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant__ PackParams p, int tpr) {
+  __shared__ PlaneSmem sm;
+  rows_body<T, FMT, E>(p, tpr, blockIdx.x, blockIdx.y, gridDim.y, sm.mexp);
 }
 
 // ---- Operand planes of the columns of X (X is K x rows, row-major; plane
@@ -256,8 +262,15 @@ __device__ __forceinline__ void transpose_words(const uint32_t (&r)[4 / sizeof(T
   }
 }
 
+// Shared words of the column kernel's tile.
+template <typename T>
+__host__ __device__ constexpr int col_tile_words() { return 64 * (128 / (4 / (int)sizeof(T)) + 1); }
+
+// Block (bx, by) of a grid with gy rows of blocks: column tile bx, t tiles
+// by, by + gy, ...
 template <typename T, int FMT, int E>
-__global__ void __launch_bounds__(256) pack_planes_cols(const __grid_constant__ PackParams p) {
+__device__ __forceinline__ void cols_body(const PackParams& p, uint32_t bx, uint32_t by, uint32_t gy, uint32_t* mexp,
+                                          uint32_t* tile) {
   constexpr int PER = 4 / sizeof(T);       // elements per word
   constexpr int TT = 128, TC = 64;         // tile: t x columns
   constexpr int WPC = TT / PER;            // words per tile column
@@ -266,14 +279,13 @@ __global__ void __launch_bounds__(256) pack_planes_cols(const __grid_constant__ 
   constexpr int CG = TC / CPT;             // column groups: 8 (u8), 16 (u16)
   constexpr int PASSES = WPC * CG / 256;   // 1 (u8), 4 (u16)
   constexpr int W = NE * (int)sizeof(T) / 4;
-  __shared__ PlaneSmem sm;
-  __shared__ uint32_t tile[TC * PITCH];
-  plane_tables<E>(p, sm.mexp);
+  static_assert(TC * PITCH == col_tile_words<T>(), "tile size");
+  plane_tables<E>(p, mexp);
   const T* X = static_cast<const T*>(p.X);
-  const int64_t c0 = (int64_t)blockIdx.x * TC;
+  const int64_t c0 = (int64_t)bx * TC;
   const bool aligned8 = ((reinterpret_cast<uintptr_t>(X) | (uintptr_t)(p.ldx * sizeof(T))) & 7u) == 0;
   const uint32_t erep = Swar<T>::rep(p.emask);
-  for (int64_t tt0 = (int64_t)blockIdx.y * TT; tt0 < p.Kp; tt0 += (int64_t)gridDim.y * TT) {
+  for (int64_t tt0 = (int64_t)by * TT; tt0 < p.Kp; tt0 += (int64_t)gy * TT) {
     const bool fast = aligned8 && c0 + TC <= p.rows && tt0 + TT <= p.K;
 #pragma unroll
     for (int pass = 0; pass < PASSES; ++pass) {
@@ -323,7 +335,32 @@ __global__ void __launch_bounds__(256) pack_planes_cols(const __grid_constant__ 
     }
     flag_range(p.status, bad);
     const int64_t r = c0 + cl, t0 = tt0 + (int64_t)ch * NE;
-    if (r < p.rows_p && t0 < p.Kp) plane_out<T, FMT, E>(p, sm.mexp, r, t0, v);
+    if (r < p.rows_p && t0 < p.Kp) plane_out<T, FMT, E>(p, mexp, r, t0, v);
+  }
+}
+
+template <typename T, int FMT, int E>
+__global__ void __launch_bounds__(256) pack_planes_cols(const __grid_constant__ PackParams p) {
+  __shared__ PlaneSmem sm;
+  __shared__ uint32_t tile[col_tile_words<T>()];
+  cols_body<T, FMT, E>(p, blockIdx.x, blockIdx.y, gridDim.y, sm.mexp, tile);
+}
+
+// Both operands of a product in one launch: blocks [0, gxa * gya) run the row
+// kernel on pa (A), the others the column kernel on pb (B), so the two sides
+// stream concurrently.
+template <typename T, int FMT, int E>
+__global__ void __launch_bounds__(256) pack_planes_pair(const __grid_constant__ PackParams pa, int tpr, uint32_t gxa,
+                                                        uint32_t gya, const __grid_constant__ PackParams pb,
+                                                        uint32_t gxb, uint32_t gyb) {
+  __shared__ PlaneSmem sm;
+  __shared__ uint32_t tile[col_tile_words<T>()];
+  const uint32_t b = blockIdx.x, na = gxa * gya;
+  if (b < na) {
+    rows_body<T, FMT, E>(pa, tpr, b % gxa, b / gxa, gya, sm.mexp);
+  } else {
+    const uint32_t bb = b - na;
+    cols_body<T, FMT, E>(pb, bb % gxb, bb / gxb, gyb, sm.mexp, tile);
   }
 }
 
@@ -647,6 +684,41 @@ cudaError_t launch_pack_cols(const PackParams& p0, cudaStream_t s, int64_t* laun
   if (p.fmt == kFmtBit) launch_cols_fmt<kFmtBit>(p, grid, s);
   else if (p.fmt == kFmtByte) launch_cols_fmt<kFmtByte>(p, grid, s);
   else launch_cols_fmt<kFmtNib>(p, grid, s);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+template <int FMT>
+void launch_pair_fmt(const PackParams& a, int tpr, uint32_t gxa, uint32_t gya, const PackParams& b, uint32_t gxb,
+                     uint32_t gyb, unsigned grid, cudaStream_t s) {
+  if (a.elem_bytes == 2) pack_planes_pair<uint16_t, FMT, 10><<<grid, 256, 0, s>>>(a, tpr, gxa, gya, b, gxb, gyb);
+  else if (a.e <= 2) pack_planes_pair<uint8_t, FMT, 2><<<grid, 256, 0, s>>>(a, tpr, gxa, gya, b, gxb, gyb);
+  else if (a.e <= 4) pack_planes_pair<uint8_t, FMT, 4><<<grid, 256, 0, s>>>(a, tpr, gxa, gya, b, gxb, gyb);
+  else pack_planes_pair<uint8_t, FMT, 8><<<grid, 256, 0, s>>>(a, tpr, gxa, gya, b, gxb, gyb);
+}
+
+cudaError_t launch_pack_pair(const PackParams& a0, const PackParams& b0, cudaStream_t s, int64_t* launches) {
+  if (a0.fmt != b0.fmt || a0.e != b0.e || a0.elem_bytes != b0.elem_bytes) {
+    cudaError_t err = launch_pack_planes(a0, s, launches);
+    return err != cudaSuccess ? err : launch_pack_cols(b0, s, launches);
+  }
+  PackParams a = a0, b = b0;
+  if (!plane_offsets(a) || !plane_offsets(b)) return cudaErrorInvalidValue;
+  int64_t tpr, rpb, gxa;
+  job_shape(a.Kp, NE, tpr, rpb, gxa);
+  const int64_t gya = std::min<int64_t>(ceil_div(a.rows_p, rpb), 65535);
+  const int64_t gxb = ceil_div(b.rows_p, 64), gyb = std::min<int64_t>(ceil_div(b.Kp, 128), 65535);
+  const int64_t na = gxa * gya, nb = gxb * gyb;
+  if (na <= 0 || nb <= 0) {  // one side empty: the single launchers handle it
+    cudaError_t err = launch_pack_planes(a0, s, launches);
+    return err != cudaSuccess ? err : launch_pack_cols(b0, s, launches);
+  }
+  if (na + nb > 0x7fffffffLL || gxa > 0xffffffffLL) return cudaErrorInvalidConfiguration;
+  const unsigned grid = (unsigned)(na + nb);
+  if (a.fmt == kFmtBit) launch_pair_fmt<kFmtBit>(a, (int)tpr, (uint32_t)gxa, (uint32_t)gya, b, (uint32_t)gxb, (uint32_t)gyb, grid, s);
+  else if (a.fmt == kFmtByte)
+    launch_pair_fmt<kFmtByte>(a, (int)tpr, (uint32_t)gxa, (uint32_t)gya, b, (uint32_t)gxb, (uint32_t)gyb, grid, s);
+  else launch_pair_fmt<kFmtNib>(a, (int)tpr, (uint32_t)gxa, (uint32_t)gya, b, (uint32_t)gxb, (uint32_t)gyb, grid, s);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
