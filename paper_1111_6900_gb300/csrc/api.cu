@@ -147,7 +147,7 @@ int resolve_group_m(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k, int 
 // tcgen05 GEMMs run 2-CTA clusters on m-tile pairs (rows padded to 256) when
 // the pairing adds no padded tile or m is large enough for it not to matter.
 bool pair_m(const m4rie_ctx* ctx, int64_t m) {
-  return ctx->cluster == 2 && m > 256 && (round_up(m, 256) == round_up(m, 128) || m >= 2048);
+  return ctx->cluster >= 2 && m > 256 && (round_up(m, 256) == round_up(m, 128) || m >= 2048);
 }
 
 struct FormInfo {
@@ -276,7 +276,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.wait_limit_ns = ctx->wait_limit_ns;
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
-    tp.cluster = pair ? 2 : 1;
+    tp.cluster = pair ? ctx->cluster : 1;
     if (form == M4RIE_FORM_MMA_S8 || form == M4RIE_FORM_MMA_B1)
       err = launch_mma(form == M4RIE_FORM_MMA_B1, Ap, Bp, ld_bytes, tp, ctx->stream, &ctx->launches);
     else err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld_bytes, tp, ctx->num_sms, ctx->stream, &ctx->launches);
@@ -392,7 +392,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     tp.wait_limit_ns = ctx->wait_limit_ns;
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
-    tp.cluster = pair ? 2 : 1;
+    tp.cluster = pair ? ctx->cluster : 1;
     err = launch_tc(fi.fmt, Ap, (int64_t)r * Mp, Bp, (int64_t)r * Np, ld_bytes, tp, ctx->num_sms, ctx->stream,
                     &ctx->launches);
   }
@@ -476,7 +476,7 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
   // a chunk holds at most 2 * tc_chunk FP4 entries
   if (const char* s = getenv("M4RIE_TC_CHUNK")) ctx->tc_chunk = std::min(std::max(128, atoi(s)), 1 << 21);
   if (const char* s = getenv("M4RIE_F4_KIND")) ctx->f4nv = strcmp(s, "nvf4") == 0 ? 1 : 0;
-  if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) == 2 ? 2 : 1;
+  if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) >= 2 && atoi(s) <= 3 ? atoi(s) : 1;
   if (const char* s = getenv("M4RIE_TUNE_CACHE")) m4rie_tune_load(ctx, s);  // a missing file is not an error
   *out = ctx;
   return M4RIE_OK;

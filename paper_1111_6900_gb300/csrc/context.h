@@ -45,7 +45,10 @@ struct m4rie_ctx {
   int tc_chunk = 4096;  // elements of K' per FP32 accumulation chunk
   int f4nv = 0;         // FP4 form: kind::mxf4nvf4 instead of kind::mxf4
   int stall_test = 0;   // m4rie_set_test_hook flag 1
-  int cluster = 2;      // tcgen05 GEMMs: 2-CTA clusters sharing B tiles (M4RIE_TC_CLUSTER=1: single CTAs)
+  // tcgen05 GEMMs on CTA pairs: 3 = 2-SM MMAs (cta_group::2, default); 2 =
+  // single-CTA MMAs with B tiles multicast to both CTAs; 1 = single CTAs
+  // (M4RIE_TC_CLUSTER)
+  int cluster = 3;
   int group_m = 0;      // tcgen05 tile raster: m-tiles per column group (0: all m-tiles)
   m4rie::TuneEntry tuned[11][64];  // [e][floor(log2(m*n*k))] -> autotuned choice (form 0: none)
   // phase timing (m4rie_enable_timing)

@@ -30,6 +30,9 @@ constexpr int B_SLOT = 256 * 128;  // bytes (tile N <= 256)
 // Ring depth and B slot size: 4 stages of 256-row B slots, or 5 stages of
 // 224-row slots (tile N <= 224), which still fit in 227 KB of shared memory.
 __host__ __device__ constexpr int b_slot(int stages) { return stages > 4 ? 224 * 128 : B_SLOT; }
+// 2-SM pairs hold half of B per CTA: at most 120 rows (FP4 tiles N <= 240) or
+// 128 rows (FP8, N <= 256).
+__host__ __device__ constexpr int cg2_b_slot(int fmt) { return (fmt == kFmtNib ? 120 : 128) * 128; }
 constexpr int ACC_COLS = 256;
 constexpr int THREADS = 192;
 // Bound on the waits that drain copies and MMAs already in flight when a CTA
@@ -167,6 +170,65 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap
       : "memory");
 }
 
+// ---- 2-SM (cta_group::2) forms: one MMA of M = 256 rows reads 128 rows of A
+// and half of B from the shared memory of each CTA of a 2-CTA cluster and
+// writes 128 accumulator rows into each CTA's tensor memory.
+__device__ __forceinline__ void mma_f8_cg2(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+template <bool NV>
+__device__ __forceinline__ void mma_f4_cg2(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t sf,
+                                           uint32_t acc) {
+  if (NV)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %5, 0;\n"
+        "tcgen05.mma.cta_group::2.kind::mxf4nvf4.block_scale.scale_vec::4X [%0], %1, %2, %3, [%4], [%4], p;\n}\n" ::
+            "r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(sf), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %5, 0;\n"
+        "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%4], p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(sf), "r"(acc)
+        : "memory");
+}
+
+// Arrive (once the pair's MMAs issued so far complete) on the barrier at the
+// same shared-memory offset in both CTAs.
+__device__ __forceinline__ void mma_commit_cg2(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"((uint16_t)3)
+      : "memory");
+}
+
+// TMA load into this CTA's shared memory whose byte count completes on an
+// mbarrier of the CTA pair (bar: a shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_cg2(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// The shared::cluster address of `addr` (a shared::cta address) in CTA `rank`.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -225,7 +287,7 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
                                          const CUtensorMap* tmB, int tile, int& jc, TileV& t, int rank = 0) {
   if (!BATCHED) {
     tile_coords(p, tile, t.b, t.tm, t.tn);
-    if (CL == 2) t.tm = 2 * t.tm + rank;
+    if (CL >= 2) t.tm = 2 * t.tm + rank;
     t.ma = tmA;
     t.mb = tmB;
     t.arow = (int)(t.b * p.a_brows) + t.tm * 128;
@@ -275,19 +337,30 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
 // same n-tile; each CTA loads half of the B tile and multicasts it to both,
 // and each CTA's MMA commits release a stage in both CTAs (p.tiles_m counts
 // m-tile pairs, the B tensor map's box is half a tile).
+// CL = 3: 2-SM MMAs (cta_group::2).  The even CTA issues MMAs of M = 256 that
+// read A's 128 rows and B's half tile from each CTA's shared memory and write
+// 128 accumulator rows into each CTA's tensor memory; each CTA holds only its
+// half of B, so a stage is 128 rows of A and half of B and more stages fit.
+// Both CTAs' copies complete on the even CTA's full barriers, its commits
+// release stages and accumulators in both CTAs, and both epilogues release the
+// even CTA's accumulator barriers.
 template <int FMT, bool BATCHED, bool NV = false, int CL = 1, int STAGES = 4>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ TcParams p, const TcJob* __restrict__ jobs) {
-  constexpr int B_SLOT = b_slot(STAGES);
-  static_assert(2 * STAGES + 6 <= 16, "barrier block holds 16 words");
+  constexpr bool CG2 = CL == 3;
+  constexpr int CLN = CL == 1 ? 1 : 2;  // CTAs per cluster
+  constexpr int B_SLOT = CG2 ? cg2_b_slot(FMT) : b_slot(STAGES);
+  constexpr int NBAR = (2 * STAGES + 6 + 1) & ~1;  // barrier words, even
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * A_TILE;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_SLOT);
+  // CG2 keeps the B slots first, so that every B-operand read of a stage,
+  // even one past its half tile, stays inside this CTA's allocation
+  uint8_t* sA = CG2 ? smem + STAGES * B_SLOT : smem;
+  uint8_t* sB = CG2 ? smem : smem + STAGES * A_TILE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * (A_TILE + B_SLOT));
   // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain, never
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint32_t* sbits = tmem_slot + 4;  // [4 warps][32 rows][9 words] (8 bit words + a zero sentinel)
 
@@ -300,11 +373,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, CL);  // released by the MMA commits of every CTA of the cluster
+      // released by the MMA commits of every CTA of the cluster (CG2: the even CTA's, multicast)
+      mbar_init(empty0 + 8 * s, CG2 ? 1 : CL);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, 128);
+      mbar_init(tempty0 + 8 * b, CG2 ? 256 : 128);  // CG2: both CTAs' epilogues
     }
     mbar_init(drain, 1);
     mbar_init(never, 1);
@@ -316,16 +390,24 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * ACC_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (CG2) {
+      // one warp of each CTA of the pair allocates collectively
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(2 * ACC_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(2 * ACC_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t crank = CL == 2 ? cluster_rank() : 0;
-  if (CL == 2) cluster_sync();  // the peer's barriers are initialised before anything lands in them
+  const uint32_t crank = CLN == 2 ? cluster_rank() : 0;
+  if (CLN == 2) cluster_sync();  // the peer's barriers are initialised before anything lands in them
   const uint32_t tmem = *tmem_slot;
   if (FMT == kFmtNib) {
     // Unit block-scale factors (UE8M0 0x7F = 2^0) for every lane, written by
@@ -342,12 +424,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     fence_before();
     __syncthreads();
     fence_after();
+    // CG2: the even CTA's MMAs read the peer's scale factors too
+    if (CG2) cluster_sync();
   }
   const int total = BATCHED ? p.tiles_m : p.batch * p.tiles_m * p.tiles_n;
   const uint64_t lim = p.wait_limit_ns;
   // tile loop: every CTA (CL = 1) or every cluster (CL = 2) takes every
   // (gridDim.x / CL)-th tile
-  const int tfirst = blockIdx.x / CL, tstep = gridDim.x / CL;
+  const int tfirst = blockIdx.x / CLN, tstep = gridDim.x / CLN;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -365,16 +449,25 @@ __global__ void __launch_bounds__(THREADS, 1)
           asm volatile("prefetch.tensormap [%0];" ::"l"(&nj.ma) : "memory");
           asm volatile("prefetch.tensormap [%0];" ::"l"(&nj.mb) : "memory");
         }
-        const uint32_t bytes = A_TILE + (uint32_t)t.BN * 128;
+        // CG2: the even CTA's full barrier counts both CTAs' bytes
+        const uint32_t bytes = (CG2 ? 2 * A_TILE : A_TILE) + (uint32_t)t.BN * 128;
         for (int kb = 0; kb < t.kblocks; ++kb) {
           if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status, lim)) {
             ok = false;
             break;
           }
           const uint32_t fb = full0 + 8 * stage;
-          mbar_expect_tx(fb, bytes);
-          tma_load_2d(smem_u32(sA + stage * A_TILE), t.ma, fb, kb * 128, t.arow);
-          if (CL == 2) {
+          if (CG2) {
+            const uint32_t fb_even = mapa_rank(fb, 0);
+            if (crank == 0) mbar_expect_tx(fb, bytes);
+            tma_load_2d_cg2(smem_u32(sA + stage * A_TILE), t.ma, fb_even, kb * 128, t.arow);
+            tma_load_2d_cg2(smem_u32(sB + stage * B_SLOT), t.mb, fb_even, kb * 128, t.brow + (int)crank * (t.BN / 2));
+          } else {
+            mbar_expect_tx(fb, bytes);
+            tma_load_2d(smem_u32(sA + stage * A_TILE), t.ma, fb, kb * 128, t.arow);
+          }
+          if (CG2) {
+          } else if (CL == 2) {
             // this CTA's half of the B tile, into both CTAs (the peer sends the other half)
             const int half = t.BN / 2;
             tma_load_2d_pair(smem_u32(sB + stage * B_SLOT + crank * half * 128), t.mb, fb, kb * 128,
@@ -391,13 +484,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (!ok) {
-        // Aborting: wait (bounded) for the copies this thread issued.
-        for (int s = 0; s < STAGES; ++s)
-          if (issued_mask >> s & 1u) {
-            const uint64_t t0 = gtimer();
-            while (!mbar_try(full0 + 8 * s, (issued_parity >> s) & 1u) && gtimer() - t0 < DRAIN_NS) {
-            }
+        // Aborting: wait (bounded) for the copies this thread issued.  The odd
+        // CTA of a CG2 pair cannot observe its copies (they complete on the
+        // even CTA's barriers, which the even CTA drains); it waits 50 us.
+        if (CG2 && crank != 0) {
+          const uint64_t t0 = gtimer();
+          while (gtimer() - t0 < 50000ull) {
           }
+        } else {
+          for (int s = 0; s < STAGES; ++s)
+            if (issued_mask >> s & 1u) {
+              const uint64_t t0 = gtimer();
+              while (!mbar_try(full0 + 8 * s, (issued_parity >> s) & 1u) && gtimer() - t0 < DRAIN_NS) {
+              }
+            }
+        }
       }
     }
   } else if (warp == 1) {
@@ -408,10 +509,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t phase = 0;
       int chunk = 0;
       bool ok = true;
-      for (int tile = tfirst; tile < total && ok; tile += tstep) {
+      // CG2: only the even CTA issues MMAs (for both CTAs)
+      const int my_total = CG2 && crank != 0 ? 0 : total;
+      for (int tile = tfirst; tile < my_total && ok; tile += tstep) {
         TileV t;
         get_tile<BATCHED, CL>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
-        const uint32_t idesc = FMT == kFmtNib ? idesc_f4(128, t.BN, NV) : idesc_f8(128, t.BN);
+        constexpr int MM = CG2 ? 256 : 128;
+        const uint32_t idesc = FMT == kFmtNib ? idesc_f4(MM, t.BN, NV) : idesc_f8(MM, t.BN);
         for (int kb0 = 0; kb0 < t.kblocks && ok; kb0 += t.kc) {
           const int kb1 = min(kb0 + t.kc, t.kblocks);
           const int buf = chunk & 1;
@@ -432,10 +536,16 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA: 32 FP8 or 64 FP4 entries
               const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
-              if (FMT == kFmtNib) mma_f4<NV>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, sf, acc);
-              else mma_f8(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, acc);
+              if (CG2) {
+                if (FMT == kFmtNib) mma_f4_cg2<NV>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, sf, acc);
+                else mma_f8_cg2(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, acc);
+              } else {
+                if (FMT == kFmtNib) mma_f4<NV>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, sf, acc);
+                else mma_f8(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, acc);
+              }
             }
-            if (CL == 2) mma_commit_pair(empty0 + 8 * stage);
+            if (CG2) mma_commit_cg2(empty0 + 8 * stage);
+            else if (CL == 2) mma_commit_pair(empty0 + 8 * stage);
             else mma_commit(empty0 + 8 * stage);
             if (++stage == STAGES) {
               stage = 0;
@@ -443,13 +553,16 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
           }
           if (!ok) break;
-          mma_commit(tfull0 + 8 * buf);
+          if (CG2) mma_commit_cg2(tfull0 + 8 * buf);
+          else mma_commit(tfull0 + 8 * buf);
           ++chunk;
         }
       }
       // Every MMA this thread issued has completed once `drain` flips; only
-      // then may TMEM be freed (bounded wait, also on the abort path).
-      mma_commit(drain);
+      // then may TMEM be freed (bounded wait, also on the abort path).  CG2:
+      // the even CTA's commit flips `drain` in both CTAs.
+      if (!CG2) mma_commit(drain);
+      else if (crank == 0) mma_commit_cg2(drain);
       const uint64_t t0 = gtimer();
       while (!mbar_try(drain, 0) && gtimer() - t0 < DRAIN_NS) {
       }
@@ -502,7 +615,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
         fence_before();
-        mbar_arrive(tempty0 + 8 * buf);
+        if (CG2) mbar_arrive_cluster(mapa_rank(tempty0 + 8 * buf, 0));  // the even CTA's barrier
+        else mbar_arrive(tempty0 + 8 * buf);
         ++chunk;
       }
       if (!ok || p.mode == 1) continue;
@@ -573,11 +687,15 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_before();
   __syncthreads();
   fence_after();
-  // no CTA of a cluster leaves while the peer may still write into its shared memory
-  if (CL == 2) cluster_sync();
+  // no CTA of a cluster leaves while the peer may still write into its shared
+  // (CG2: or tensor) memory
+  if (CLN == 2) cluster_sync();
   if (warp == 1) {
     __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS) : "memory");
+    if (CG2)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS) : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS) : "memory");
   }
 }
 
@@ -627,6 +745,13 @@ size_t tc_smem_bytes(int stages = STAGES) {
   return 1024 + (size_t)stages * (A_TILE + b_slot(stages)) + 16 * 8 + 16 + 128 * 9 * 4;
 }
 
+// 2-SM pairs: 7 stages of A + half of B for FP4, 6 for FP8.
+constexpr int cg2_stages(int fmt) { return fmt == kFmtNib ? 7 : 6; }
+size_t tc_smem_bytes_cg2(int fmt) {
+  const int st = cg2_stages(fmt);
+  return 1024 + (size_t)st * (A_TILE + cg2_b_slot(fmt)) + (size_t)((2 * st + 6 + 1) & ~1) * 8 + 16 + 128 * 9 * 4;
+}
+
 cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
                       int64_t ld_bytes, const TcParams& p, int num_sms, cudaStream_t s, int64_t* launches) {
   if (fmt != kFmtByte && fmt != kFmtNib) return cudaErrorNotSupported;
@@ -635,13 +760,44 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
   CUtensorMap ma, mb;
   // 2-CTA clusters share B tiles when the m-tiles pair up (the caller pads the
   // planes' rows to a multiple of 256 for that)
-  const bool pair = p.cluster == 2 && p.tiles_m % 2 == 0 && num_sms >= 2;
+  const bool pair = p.cluster >= 2 && p.tiles_m % 2 == 0 && num_sms >= 2;
   if (!tc_make_map(&ma, Aplanes, a_rows, ld_bytes, 128) ||
       !tc_make_map(&mb, Bplanes, b_rows, ld_bytes, pair ? p.BN / 2 : p.BN))
     return cudaErrorInvalidValue;
   // FP4 tiles of N <= 224 take the 5-stage ring
   const bool deep = fmt == kFmtNib && p.BN <= 224;
   const size_t smem = tc_smem_bytes(deep ? 5 : 4);
+  if (pair && p.cluster == 3) {
+    // 2-SM MMAs: the pair computes M = 256 rows per tile
+    auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, cg2_stages(kFmtNib)>
+                                           : tc_kernel<kFmtNib, false, false, 3, cg2_stages(kFmtNib)>)
+                                 : tc_kernel<kFmtByte, false, false, 3, cg2_stages(kFmtByte)>;
+    const size_t smem2 = tc_smem_bytes_cg2(fmt);
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (err != cudaSuccess) return err;
+    TcParams q = p;
+    q.tiles_m = p.tiles_m / 2;
+    q.group_m = std::max(1, std::min(q.tiles_m, p.group_m / 2));
+    const int64_t pairs = (int64_t)q.batch * q.tiles_m * q.tiles_n;
+    if (pairs > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const int clusters = (int)std::min<int64_t>(pairs, num_sms / 2);
+    if (clusters <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = smem2;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    err = cudaLaunchKernelEx(&cfg, kernel, ma, mb, q, (const TcJob*)nullptr);
+    if (launches) ++*launches;
+    return err != cudaSuccess ? err : cudaGetLastError();
+  }
   if (pair) {
     auto kernel = fmt == kFmtNib ? (deep ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 2, 5>
                                                    : tc_kernel<kFmtNib, false, false, 2, 5>)
