@@ -239,6 +239,17 @@ __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// 16 consecutive accumulator columns of this thread's lane, without waiting
+// (tmem_wait_ld waits for every load issued before it).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -592,25 +603,34 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         fence_after();
         const uint32_t ta = tmem + lane_base + buf * ACC_COLS;
+        // 64 columns per round: four loads in flight, then one wait
 #pragma unroll
-        for (int c16 = 0; c16 < 16; ++c16) {
-          if (c16 < nc16) {
-            uint32_t v[16];
-            tmem_ld16(ta + 16 * c16, v);
-            if (p.mode == 1) {
-              if (kb0 == 0) {
-                uint32_t* out = static_cast<uint32_t*>(t.C) + ((int64_t)tm * 128 + row) * t.ldc +
-                                (int64_t)tn * t.BN + 16 * c16;
+        for (int g = 0; g < 4; ++g) {
+          uint32_t v[4][16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) out[j] = (uint32_t)__float2int_rz(__uint_as_float(v[j]));
+          for (int h = 0; h < 4; ++h)
+            if (4 * g + h < nc16) tmem_ld16_async(ta + 16 * (4 * g + h), v[h]);
+          if (4 * g < nc16) tmem_wait_ld();
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const int c16 = 4 * g + h;
+            if (c16 < nc16) {
+              if (p.mode == 1) {
+                if (kb0 == 0) {
+                  uint32_t* out = static_cast<uint32_t*>(t.C) + ((int64_t)tm * 128 + row) * t.ldc +
+                                  (int64_t)tn * t.BN + 16 * c16;
+#pragma unroll
+                  for (int j = 0; j < 16; ++j) out[j] = (uint32_t)__float2int_rz(__uint_as_float(v[h][j]));
+                }
+              } else {
+                uint32_t w = 0;
+                // parity of an integer count x < 2^23 held exactly in FP32: x + 2^23 is exact and
+                // leaves x in the low mantissa bits, so bit 0 of its encoding is x mod 2
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  w |= (__float_as_uint(__uint_as_float(v[h][j]) + 8388608.0f) & 1u) << j;
+                bits[c16 >> 1] ^= w << (16 * (c16 & 1));
               }
-            } else {
-              uint32_t w = 0;
-#pragma unroll
-              // parity of an integer count x < 2^23 held exactly in FP32: x + 2^23 is exact and
-              // leaves x in the low mantissa bits, so bit 0 of its encoding is x mod 2
-              for (int j = 0; j < 16; ++j) w |= (__float_as_uint(__uint_as_float(v[j]) + 8388608.0f) & 1u) << j;
-              bits[c16 >> 1] ^= w << (16 * (c16 & 1));
             }
           }
         }
