@@ -306,7 +306,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   // keeps its scale factors in TMEM next to each accumulator)
   const int ntile = form == M4RIE_FORM_POPC ? 128 : (form == M4RIE_FORM_TC_F8 ? 256 : 224);
   const int64_t Np = round_up(n, ntile);
-  const int64_t ldp = Np / 32;  // words per parity row
+  const int64_t ldp = round_up(Np / 32, 4);  // words per parity row (whole 16-byte groups)
   const size_t a_bytes = round_up((int64_t)entries_bytes((int64_t)r * Mp * Kp, fi.bits), 1024);
   const size_t b_bytes = round_up((int64_t)entries_bytes((int64_t)r * Np * Kp, fi.bits), 1024);
   const size_t p_bytes = round_up((int64_t)r * Mp * ldp * 4, 1024);

@@ -533,37 +533,12 @@ __global__ void __launch_bounds__(256) cling_kernel(int e, int64_t rows, int64_t
 
 // ---- Karatsuba recombination: bit s of C[r][c] is the parity of the
 // products selected by out_mask[s] (reduction mod f folded in).  One thread
-// per (row, 32 columns): XOR the r parity words into E output slice words
-// (which products feed which slices comes from a per-block table), then
-// transpose the bits into 32 elements.
+// per (row, 128 columns): it loads the r parity planes' 4 words with 16-byte
+// loads (rows of the planes are padded to whole 16-byte groups), XORs them
+// into E output slice words each (which products feed which slices comes from
+// a per-block table), then transposes the bits into elements.
 template <typename T, int E>
-__global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecombineParams p) {
-  __shared__ uint32_t qmask[64];  // bit s: product q feeds output slice s
-  for (int q = threadIdx.x; q < p.r; q += blockDim.x) {
-    uint32_t m = 0;
-#pragma unroll
-    for (int s = 0; s < E; ++s) m |= (uint32_t)((p.out_mask[s] >> q) & 1ull) << s;
-    qmask[q] = m;
-  }
-  __syncthreads();
-  const int64_t nw = (p.n + 31) / 32;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = idx < p.m * nw;
-  const int64_t r = live ? idx / nw : 0, w = live ? idx % nw : 0;
-  uint32_t out[E];
-#pragma unroll
-  for (int s = 0; s < E; ++s) out[s] = 0;
-  if (live) {
-    const uint32_t* src = p.P + r * p.ldw + w;
-    const int64_t pstride = p.rows_p * p.ldw;
-#pragma unroll 4
-    for (int q = 0; q < p.r; ++q) {
-      const uint32_t pw = __ldg(src + q * pstride);
-      const uint32_t m = qmask[q];
-#pragma unroll
-      for (int s = 0; s < E; ++s) out[s] ^= (m >> s & 1u) ? pw : 0u;
-    }
-  }
+__device__ __forceinline__ bool store_elements(const RecombineParams& p, int64_t r, int64_t w, const uint32_t* out) {
   // elements c = 32 w + b, packed 4 (u8) or 2 (u16) per 32-bit word
   constexpr int PER = 4 / sizeof(T);
   constexpr int NW = 32 / PER;
@@ -584,34 +559,81 @@ __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ 
   const bool full = 32 * w + 32 <= p.n;
   const bool vec = full && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
   bool bad = false;
-  if (live) {
-    if (vec) {
-      uint4* d4 = reinterpret_cast<uint4*>(dst);
+  if (vec) {
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    uint4 old[NW / 4];
+    if (p.add) {
 #pragma unroll
-      for (int h = 0; h < NW / 4; ++h) {
-        uint4 o = make_uint4(vals[4 * h], vals[4 * h + 1], vals[4 * h + 2], vals[4 * h + 3]);
-        if (p.add) {
-          const uint4 old = d4[h];
-          const uint32_t rep = sizeof(T) == 1 ? p.emask * 0x01010101u : p.emask * 0x00010001u;
-          bad |= ((old.x | old.y | old.z | old.w) & ~rep) != 0;
-          o.x ^= old.x & rep, o.y ^= old.y & rep, o.z ^= old.z & rep, o.w ^= old.w & rep;
-        }
-        d4[h] = o;
+      for (int h = 0; h < NW / 4; ++h) old[h] = d4[h];
+    }
+#pragma unroll
+    for (int h = 0; h < NW / 4; ++h) {
+      uint4 o = make_uint4(vals[4 * h], vals[4 * h + 1], vals[4 * h + 2], vals[4 * h + 3]);
+      if (p.add) {
+        const uint32_t rep = sizeof(T) == 1 ? p.emask * 0x01010101u : p.emask * 0x00010001u;
+        bad |= ((old[h].x | old[h].y | old[h].z | old[h].w) & ~rep) != 0;
+        o.x ^= old[h].x & rep, o.y ^= old[h].y & rep, o.z ^= old[h].z & rep, o.w ^= old[h].w & rep;
       }
-    } else {
+      d4[h] = o;
+    }
+  } else {
 #pragma unroll
-      for (int b = 0; b < 32; ++b) {
-        if (32 * w + b < p.n) {
-          uint32_t v = (vals[b / PER] >> (8 * sizeof(T) * (b % PER))) & (sizeof(T) == 1 ? 0xFFu : 0xFFFFu);
-          if (p.add) {
-            const uint32_t old = dst[b];
-            bad |= old > p.emask;
-            v ^= old & p.emask;
-          }
-          dst[b] = (T)v;
+    for (int b = 0; b < 32; ++b) {
+      if (32 * w + b < p.n) {
+        uint32_t v = (vals[b / PER] >> (8 * sizeof(T) * (b % PER))) & (sizeof(T) == 1 ? 0xFFu : 0xFFFFu);
+        if (p.add) {
+          const uint32_t old = dst[b];
+          bad |= old > p.emask;
+          v ^= old & p.emask;
         }
+        dst[b] = (T)v;
       }
     }
+  }
+  return bad;
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecombineParams p) {
+  __shared__ uint32_t qmask[64];  // bit s: product q feeds output slice s
+  for (int q = threadIdx.x; q < p.r; q += blockDim.x) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int s = 0; s < E; ++s) m |= (uint32_t)((p.out_mask[s] >> q) & 1ull) << s;
+    qmask[q] = m;
+  }
+  __syncthreads();
+  const int64_t nw = (p.n + 31) / 32, ng = (nw + 3) / 4;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = idx < p.m * ng;
+  const int64_t r = live ? idx / ng : 0, w0 = live ? (idx % ng) * 4 : 0;
+  uint32_t out[4][E];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int s = 0; s < E; ++s) out[u][s] = 0;
+  if (live) {
+    const uint4* src = reinterpret_cast<const uint4*>(p.P + r * p.ldw + w0);
+    const int64_t pstride = p.rows_p * p.ldw / 4;  // in 16-byte groups
+#pragma unroll 4
+    for (int q = 0; q < p.r; ++q) {
+      const uint4 pw = __ldg(src + q * pstride);
+      const uint32_t m = qmask[q];
+#pragma unroll
+      for (int s = 0; s < E; ++s)
+        if ((m >> s) & 1u) {
+          out[0][s] ^= pw.x;
+          out[1][s] ^= pw.y;
+          out[2][s] ^= pw.z;
+          out[3][s] ^= pw.w;
+        }
+    }
+  }
+  bool bad = false;
+  if (live) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (w0 + u < nw) bad |= store_elements<T, E>(p, r, w0 + u, out[u]);
   }
   flag_range(p.status, bad);
 }
@@ -800,9 +822,9 @@ cudaError_t launch_cling(int e, int64_t rows, int64_t cols, const uint64_t* slic
 }
 
 cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches) {
-  const int64_t n = p.m * ((p.n + 31) / 32);
+  const int64_t n = p.m * ceil_div(ceil_div(p.n, 32), 4);
   const int64_t g = ceil_div(n, 256);
-  if (p.r > 64) return cudaErrorInvalidValue;
+  if (p.r > 64 || p.ldw % 4 != 0 || (reinterpret_cast<uintptr_t>(p.P) & 15u) != 0) return cudaErrorInvalidValue;
   switch (p.e) {
     case 2: return launch(recombine_kernel<uint8_t, 2>, g, 256, s, launches, p);
     case 3: return launch(recombine_kernel<uint8_t, 3>, g, 256, s, launches, p);
