@@ -63,8 +63,11 @@ typedef enum m4rie_form {
     M4RIE_FORM_TC_F8 = 2,  /* tcgen05 tensor cores; 0/1 operands encoded exactly as FP8 E4M3, FP32 counts */
     M4RIE_FORM_MMA_S8 = 3, /* legacy warp-level INT8 tensor instructions (mma.sync s8), int32 counts */
     M4RIE_FORM_TC_F4 = 4,  /* tcgen05 block-scaled FP4 (E2M1 0/1 operands, unit scales), FP32 counts */
-    M4RIE_FORM_MMA_B1 = 5  /* legacy warp-level binary tensor instructions (mma.sync b1, AND + popcount)
+    M4RIE_FORM_MMA_B1 = 5, /* legacy warp-level binary tensor instructions (mma.sync b1, AND + popcount)
                               on the bit-packed slices, int32 counts */
+    M4RIE_FORM_NEWTON_JOHN = 6 /* no slicing: Newton-John tables (Section 4, Algorithms 2 and 3) of the
+                              packed rows of B (Section 3.1) in shared memory, one table row added per
+                              entry of A; for small products (see m4rie_mul_packed) */
 } m4rie_form;
 
 /* Which bilinear schedule reduces the GF(2^e) product to GF(2) products. */
@@ -176,6 +179,43 @@ m4rie_status m4rie_pack(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, const
 m4rie_status m4rie_unpack(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, const uint64_t *slices,
                           int64_t ld_words, void *elems);
 
+/* Packed representation (Section 3.1, Figure 1): every element padded to
+ * m4rie_packed_width(e) bits (2 for e = 2, 4 for e = 3, 4, 8 for e = 5 .. 8,
+ * 16 for e = 9, 10: the next length dividing 64), rows of 64-bit words with
+ * column c in field (c mod (64 / w)) of word floor(c / (64 / w)), lowest
+ * field first.  Returns 0 for e outside [2, 10]. */
+int m4rie_packed_width(int e);
+
+/* Elements (rows x cols, row stride lde >= cols elements) to packed rows
+ * (row r at words + r * ld_words, ld_words >= ceil(cols / (64 / w))).
+ * Padding fields, the bits above e of each field and padding words are written
+ * as zero; entries >= 2^e set the sticky M4RIE_ERR_RANGE status.  The two
+ * arrays must not overlap (M4RIE_ERR_ALIAS).  Device pointers, asynchronous. */
+m4rie_status m4rie_to_packed(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, const void *elems, int64_t lde,
+                             uint64_t *words, int64_t ld_words);
+
+/* The inverse of m4rie_to_packed: reads the low e bits of the first cols
+ * fields of every row (padding is ignored) and writes rows x cols elements
+ * with row stride lde.  Device pointers, asynchronous. */
+m4rie_status m4rie_from_packed(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, const uint64_t *words,
+                               int64_t ld_words, void *elems, int64_t lde);
+
+/* C = A * B (accumulate == 0) or C = C + A * B on packed matrices by
+ * Newton-John multiplication (Section 4, Algorithms 2 and 3): for every row t
+ * of B a table of its 2^e multiples (for e >= 8 two tables, of the multiples
+ * of B_t and of alpha^b B_t by scalars of e - b and b bits) is built in shared
+ * memory from the rows alpha^i B_t, and every row r of C adds the table row
+ * indexed by A[r][t].  A is m x k, B k x n, C m x n, each a packed matrix
+ * with row stride lda / ldb / ldc 64-bit words (>= the words of one row).
+ * Input padding is ignored; C's padding fields are written as zero.  A field
+ * whose bits above e are set sets the sticky M4RIE_ERR_RANGE status (its low
+ * e bits are used).  C must not overlap A or B (M4RIE_ERR_ALIAS).  One launch;
+ * small products split k over a cluster of up to 8 CTAs and reduce their
+ * partial tiles in distributed shared memory.  Asynchronous. */
+m4rie_status m4rie_mul_packed(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
+                              const uint64_t *A, int64_t lda, const uint64_t *B, int64_t ldb, uint64_t *C,
+                              int64_t ldc, int accumulate);
+
 /* Many independent products (each with its own e, f, m, n, k and
  * accumulate flag) in one persistent launch.  `problems` is a HOST array of
  * `count` descriptors (reserved fields zero), validated like m4rie_mul; no
@@ -186,7 +226,8 @@ m4rie_status m4rie_unpack(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols, con
  * That work is recorded once into a CUDA graph, cached in the context with
  * its own device memory, and replayed while the same descriptor array contents
  * are passed (a different array rebuilds it; the first call synchronises the
- * stream).  With the POPC, MMA_S8 or MMA_B1 form the products run one by one. */
+ * stream).  With the POPC, MMA_S8, MMA_B1 or NEWTON_JOHN form the products run
+ * one by one. */
 m4rie_status m4rie_mul_batched(m4rie_ctx *ctx, int count, const m4rie_problem *problems);
 
 /* Wait for the stream, return the sticky device status (M4RIE_OK,

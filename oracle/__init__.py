@@ -9,8 +9,8 @@ The arithmetic lives in ``oracle.c`` (plain C, OpenMP over rows): the field
 product of Section 2 (carry-less multiply, then reduction modulo f) and its
 inverse, the cubic matrix product of Algorithm 1, the triangular solve of
 Algorithm 5 (Section 4.3), the reduced row echelon form of Algorithm 4
-(Section 4.1) and the slicing / clinging conversions of Section 3.2 and
-Figure 1.  This module only compiles that file with gcc and
+(Section 4.1), the packed representation of Section 3.1 and the slicing /
+clinging conversions of Section 3.2 and Figure 1.  This module only compiles that file with gcc and
 marshals numpy arrays to it.
 """
 from __future__ import annotations
@@ -78,6 +78,12 @@ class OracleLib:
         L.oracle_slice.argtypes = [i32, i64, i64, vp, vp, i64]
         L.oracle_cling.restype = None
         L.oracle_cling.argtypes = [i32, i64, i64, vp, i64, vp]
+        L.oracle_packed_width.restype = i32
+        L.oracle_packed_width.argtypes = [i32]
+        L.oracle_pack.restype = None
+        L.oracle_pack.argtypes = [i32, i64, i64, vp, vp, i64]
+        L.oracle_unpack.restype = None
+        L.oracle_unpack.argtypes = [i32, i64, i64, vp, i64, vp]
         L.oracle_gf_inv.restype = u32
         L.oracle_gf_inv.argtypes = [i32, u32, u32]
         L.oracle_trsm_upper_left.restype = i32
@@ -148,6 +154,29 @@ class OracleLib:
         _, rows, ld_words = S.shape
         out = np.empty((rows, cols), dtype=np.uint16)
         self.L.oracle_cling(e, rows, cols, S.ctypes.data, ld_words, out.ctypes.data)
+        return out.astype(elem_dtype(e))
+
+    def packed_width(self, e: int) -> int:
+        """Section 3.1: bits per element in the packed representation."""
+        return int(self.L.oracle_packed_width(e))
+
+    def to_packed(self, e: int, elems, ld_words: int | None = None) -> np.ndarray:
+        """Section 3.1: packed representation, uint64 array (rows, ld_words)."""
+        X = _as_u16(elems, e, "elems")
+        rows, cols = X.shape
+        per = 64 // self.packed_width(e)
+        if ld_words is None:
+            ld_words = (cols + per - 1) // per
+        out = np.empty((rows, ld_words), dtype=np.uint64)
+        self.L.oracle_pack(e, rows, cols, X.ctypes.data, out.ctypes.data, ld_words)
+        return out
+
+    def from_packed(self, e: int, words, cols: int) -> np.ndarray:
+        """Section 3.1: elements of a packed matrix (padding ignored)."""
+        Wd = np.ascontiguousarray(words, dtype=np.uint64)
+        rows, ld_words = Wd.shape
+        out = np.empty((rows, cols), dtype=np.uint16)
+        self.L.oracle_unpack(e, rows, cols, Wd.ctypes.data, ld_words, out.ctypes.data)
         return out.astype(elem_dtype(e))
 
     def gf_inv(self, e: int, f: int, a: int) -> int:
@@ -244,3 +273,15 @@ def trsm(e, f, T, B, upper=True):
 
 def echelon(e, f, A):
     return default().echelon(e, f, A)
+
+
+def packed_width(e):
+    return default().packed_width(e)
+
+
+def to_packed(e, elems, ld_words=None):
+    return default().to_packed(e, elems, ld_words)
+
+
+def from_packed(e, words, cols):
+    return default().from_packed(e, words, cols)

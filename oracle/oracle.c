@@ -31,6 +31,11 @@
  *     the first row at or below the current rank with a non-zero entry is
  *     scaled to a leading 1, swapped up, and its multiples are added to every
  *     other row to clear the column.
+ *   - Packed representation (Section 3.1 and Figure 1): each element is
+ *     padded to the next field width that divides 64 (2, 4, 8 or 16 bits;
+ *     F_32 elements take 8 bits, Figure 1's F_8 elements 4) and a row is a
+ *     sequence of 64-bit words, column c in field (c mod (64 / w)) of word
+ *     floor(c / (64 / w)), the lowest field first; padding is zero.
  *   - Slicing (Section 3.2 and Figure 1): slice i of a matrix holds
  *     coefficient i (bit i of the integer encoding) of every entry.  Slices
  *     are stored as rows of 64-bit words, column c at bit (c mod 64) of word
@@ -129,6 +134,48 @@ void oracle_slice(int e, int64_t rows, int64_t cols, const uint16_t *elems,
                     row[c / 64] |= (uint64_t)1 << (c % 64);
         }
     }
+}
+
+/* Section 3.1: bits per element in the packed representation, the smallest
+ * of 2, 4, 8, 16 (lengths dividing 64) that holds e bits. */
+int oracle_packed_width(int e)
+{
+    int w = 2;
+    while (w < e)
+        w *= 2;
+    return w;
+}
+
+/* Section 3.1 / Figure 1: packed representation.  elems is rows x cols
+ * (uint16, row-major); row r of the output starts at words + r * ld_words;
+ * element c sits in bits [w * (c mod (64/w)), w * (c mod (64/w)) + w) of word
+ * floor(c / (64/w)), w = oracle_packed_width(e).  Everything else is zero. */
+void oracle_pack(int e, int64_t rows, int64_t cols, const uint16_t *elems, uint64_t *words,
+                 int64_t ld_words)
+{
+    const int w = oracle_packed_width(e);
+    const int per = 64 / w;
+    for (int64_t r = 0; r < rows; r++) {
+        uint64_t *row = words + r * ld_words;
+        for (int64_t j = 0; j < ld_words; j++)
+            row[j] = 0;
+        for (int64_t c = 0; c < cols; c++)
+            row[c / per] |= (uint64_t)elems[r * cols + c] << (w * (c % per));
+    }
+}
+
+/* Section 3.1: the inverse of oracle_pack.  Padding is ignored: only the low
+ * e bits of each field and the first cols fields of a row are read. */
+void oracle_unpack(int e, int64_t rows, int64_t cols, const uint64_t *words, int64_t ld_words,
+                   uint16_t *elems)
+{
+    const int w = oracle_packed_width(e);
+    const int per = 64 / w;
+    for (int64_t r = 0; r < rows; r++)
+        for (int64_t c = 0; c < cols; c++) {
+            const uint64_t word = words[r * ld_words + c / per];
+            elems[r * cols + c] = (uint16_t)((word >> (w * (c % per))) & ((1u << e) - 1u));
+        }
 }
 
 /* Section 3.2: clinging, the inverse of slicing.  Padding bits are ignored. */

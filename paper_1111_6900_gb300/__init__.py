@@ -16,10 +16,10 @@ LIB_PATH = os.path.join(_HERE, "libm4rie_gpu.so")
 
 (OK, ERR_ARG, ERR_POLY, ERR_ALIAS, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH,
  ERR_SINGULAR) = range(11)
-FORM_AUTO, FORM_POPC, FORM_TC_F8, FORM_MMA_S8, FORM_TC_F4, FORM_MMA_B1 = range(6)
+FORM_AUTO, FORM_POPC, FORM_TC_F8, FORM_MMA_S8, FORM_TC_F4, FORM_MMA_B1, FORM_NEWTON_JOHN = range(7)
 SCHED_AUTO, SCHED_ALPHA_B, SCHED_KARATSUBA = range(3)
 FORMS = {"auto": FORM_AUTO, "popc": FORM_POPC, "tc_f8": FORM_TC_F8, "mma_s8": FORM_MMA_S8, "tc_f4": FORM_TC_F4,
-         "mma_b1": FORM_MMA_B1}
+         "mma_b1": FORM_MMA_B1, "newton_john": FORM_NEWTON_JOHN}
 SCHEDULES = {"auto": SCHED_AUTO, "alpha_b": SCHED_ALPHA_B, "karatsuba": SCHED_KARATSUBA}
 
 
@@ -59,6 +59,10 @@ def _load() -> ctypes.CDLL:
         "m4rie_pack": (i32, [vp, i32, i64, i64, vp, vp, i64]),
         "m4rie_unpack": (i32, [vp, i32, i64, i64, vp, i64, vp]),
         "m4rie_mul_batched": (i32, [vp, i32, vp]),
+        "m4rie_packed_width": (i32, [i32]),
+        "m4rie_to_packed": (i32, [vp, i32, i64, i64, vp, i64, vp, i64]),
+        "m4rie_from_packed": (i32, [vp, i32, i64, i64, vp, i64, vp, i64]),
+        "m4rie_mul_packed": (i32, [vp, i32, u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, i32]),
         "m4rie_get_device_status": (i32, [vp]),
         "m4rie_schedule_products": (i32, [i32, u32, i32]),
         "m4rie_schedule_masks": (i32, [i32, u32, i32, i32, vp, vp, vp]),
@@ -259,6 +263,43 @@ class Context:
         self._raise(lib.m4rie_unpack(self.handle, e, rows, cols, _ptr(slices), ld_words, _ptr(X)), "m4rie_unpack")
         return X
 
+    def to_packed(self, e: int, elems, ld_words: int | None = None):
+        """Packed representation (Section 3.1) of a 2-D window of elements:
+        int64 tensor (rows, ld_words) holding the 64-bit words."""
+        import torch
+        _check_dev(elems, e, "elems", strided=True)
+        rows, cols = elems.shape
+        per = 64 // packed_width(e)
+        if ld_words is None:
+            ld_words = (cols + per - 1) // per
+        W = torch.empty((rows, ld_words), dtype=torch.int64, device=elems.device)
+        self._raise(lib.m4rie_to_packed(self.handle, e, rows, cols, _ptr(elems), _ld(elems) if rows else cols,
+                                        _ptr(W), ld_words), "m4rie_to_packed")
+        return W
+
+    def from_packed(self, e: int, words, cols: int, out=None):
+        """Elements of a packed matrix (int64 words, rows x ld_words)."""
+        import torch
+        rows, ld_words = words.shape
+        X = out if out is not None else torch.empty((rows, cols), dtype=elem_dtype_torch(e), device=words.device)
+        _check_dev(X, e, "out", strided=True)
+        self._raise(lib.m4rie_from_packed(self.handle, e, rows, cols, _ptr(words), ld_words, _ptr(X),
+                                          _ld(X) if rows else cols), "m4rie_from_packed")
+        return X
+
+    def mul_packed(self, e: int, f: int, A, B, C, n: int, k: int, accumulate: bool = False):
+        """Newton-John product of packed matrices (int64 word tensors, row
+        strides from the tensors): C = A B or C += A B, A m x k, B k x n."""
+        for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+            if not t.is_cuda or t.dtype.itemsize != 8 or t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1):
+                raise TypeError(f"{nm} must be a 2-D CUDA tensor of 64-bit words with unit column stride")
+        m = A.shape[0]
+        if B.shape[0] != k or C.shape[0] != m:
+            raise ValueError("shapes do not match")
+        self._raise(lib.m4rie_mul_packed(self.handle, e, f, m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(C),
+                                         _ld(C), 1 if accumulate else 0), "m4rie_mul_packed")
+        return C
+
     def mul_batched(self, problems):
         """problems: list of (e, f, A, B, C, accumulate) with CUDA tensors."""
         arr = (_Problem * len(problems))()
@@ -319,6 +360,11 @@ def mul_noalloc(e: int, f: int, A, B, C, accumulate: bool = False, device_status
     n = B.shape[1]
     return int(lib.m4rie_mul_noalloc(e, f, m, n, k, _ptr(A), _ptr(B), _ptr(C), 1 if accumulate else 0,
                                      _ptr(device_status), ctypes.c_void_p(stream.cuda_stream)))
+
+
+def packed_width(e: int) -> int:
+    """Bits per element in the packed representation (Section 3.1)."""
+    return int(lib.m4rie_packed_width(e))
 
 
 def schedule_products(e: int, f: int, schedule) -> int:

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "context.h"
+#include "newton_john.h"
 #include "schedule.h"
 
 using namespace m4rie;
@@ -118,14 +119,29 @@ m4rie_status ensure_ws(m4rie_ctx* ctx, size_t bytes) {
 }
 
 // AUTO choices: the autotuned entry of the shape class if there is one, else a
-// fixed rule from the measurements on GB300: tcgen05 FP4 from 2^28 field
-// multiply-adds (below that the bit-packed form wins: 512^3 products and the
-// 128-row products inside triangular solves), Karatsuba from 2^30.
+// fixed rule from the measurements on GB300:
+//  - Newton-John tables for thin inner dimensions and small products: k <= 64;
+//    k <= 128 for e >= 3 when m n >= 2^22 (rank-64 and rank-128 updates, 2-5x
+//    faster than the sliced forms there, whose fixed cost per output tile
+//    dominates); every product of at most 2^24 multiply-adds (2^25 for e <= 4);
+//  - else tcgen05 FP4 from 2^28 field multiply-adds, below that the bit-packed
+//    form; Karatsuba from 2^30.
+bool newton_john_wins(int e, int64_t m, int64_t n, int64_t k) {
+  const double mnk = (double)m * n * k;
+  if (k <= 64) return true;
+  if (e >= 3 && k <= 128 && (double)m * n >= (double)(1 << 22)) return true;
+  return mnk <= (double)(1 << (e <= 4 ? 25 : 24));
+}
+
+int sliced_form(int64_t m, int64_t n, int64_t k) {
+  return shape_class(m, n, k) >= 28 ? M4RIE_FORM_TC_F4 : M4RIE_FORM_POPC;
+}
+
 int resolve_form(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k) {
   if (ctx->form != M4RIE_FORM_AUTO) return ctx->form;
   const TuneEntry& t = ctx->tuned[e][shape_class(m, n, k)];
   if (t.form) return t.form;
-  return shape_class(m, n, k) >= 28 ? M4RIE_FORM_TC_F4 : M4RIE_FORM_POPC;
+  return newton_john_wins(e, m, n, k) ? M4RIE_FORM_NEWTON_JOHN : sliced_form(m, n, k);
 }
 
 int resolve_schedule(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k) {
@@ -418,6 +434,38 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   return M4RIE_OK;
 }
 
+// Newton-John multiplication (newton_john.cu) on element arrays or packed rows.
+m4rie_status run_newton_john(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x,
+                             int add, bool packed) {
+  PhaseTimer timer(ctx);
+  timer.begin(kPhaseGemm);
+  NjParams p{};
+  p.A = x.A;
+  p.B = x.B;
+  p.C = x.C;
+  // packed leading dimensions arrive in 64-bit words; the kernel indexes 32-bit words
+  p.lda = packed ? 2 * x.lda : x.lda;
+  p.ldb = packed ? 2 * x.ldb : x.ldb;
+  p.ldc = packed ? 2 * x.ldc : x.ldc;
+  p.m = m;
+  p.n = n;
+  p.k = k;
+  p.packed = packed ? 1 : 0;
+  p.add = add;
+  p.flow = f & ((1u << e) - 1u);
+  p.status = ctx->d_status;
+  if (!packed) {
+    const int w = elem_bytes(e);
+    auto rows4 = [w](const void* ptr, int64_t ld) { return (reinterpret_cast<uintptr_t>(ptr) & 3u) == 0 && (ld * w) % 4 == 0; };
+    p.vec_a = rows4(x.A, x.lda);
+    p.vec_b = rows4(x.B, x.ldb);
+    p.vec_c = rows4(x.C, x.ldc);
+  }
+  const NjPlan pl = plan_newton_john(e, m, n, k, packed, ctx->num_sms);
+  cudaError_t err = launch_newton_john(e, p, pl, ctx->stream, &ctx->launches);
+  return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+}
+
 }  // namespace
 
 namespace m4rie {
@@ -434,9 +482,13 @@ m4rie_status run_gemm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, i
     cudaError_t err = cudaMemset2DAsync(x.C, (size_t)x.ldc * w, 0, (size_t)n * w, (size_t)m, ctx->stream);
     return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
   }
-  const int form = resolve_form(ctx, e, m, n, k);
+  int form = resolve_form(ctx, e, m, n, k);
+  // Newton-John reads B while it writes C: an in-place product (C over B)
+  // takes a sliced form, which reads B only while slicing it.
+  if (form == M4RIE_FORM_NEWTON_JOHN && c_over_b) form = sliced_form(m, n, k);
   const int sched = resolve_schedule(ctx, e, m, n, k);
   if (ctx->timing) ++ctx->timed_products;
+  if (form == M4RIE_FORM_NEWTON_JOHN) return run_newton_john(ctx, e, f, m, n, k, x, add, false);
   if (sched == M4RIE_SCHED_KARATSUBA) return run_karatsuba(ctx, form, e, f, m, n, k, x, add);
   return run_alpha_b(ctx, form, e, f, m, n, k, x, add);
 }
@@ -499,7 +551,7 @@ void m4rie_destroy(m4rie_ctx* ctx) {
 }
 
 m4rie_status m4rie_set_form(m4rie_ctx* ctx, int form) {
-  if (!ctx || form < M4RIE_FORM_AUTO || form > M4RIE_FORM_MMA_B1) return M4RIE_ERR_ARG;
+  if (!ctx || form < M4RIE_FORM_AUTO || form > M4RIE_FORM_NEWTON_JOHN) return M4RIE_ERR_ARG;
   ctx->form = form;
   return M4RIE_OK;
 }
@@ -595,8 +647,10 @@ m4rie_status m4rie_mul_batched(m4rie_ctx* ctx, int count, const m4rie_problem* p
   }
   if (count == 0) return M4RIE_OK;
   // The persistent batched launch uses the tcgen05 forms (FP4 unless FP8 is
-  // requested); the CUDA-core and INT8 forms run the products one by one.
-  if (ctx->form == M4RIE_FORM_POPC || ctx->form == M4RIE_FORM_MMA_S8 || ctx->form == M4RIE_FORM_MMA_B1) {
+  // requested); the CUDA-core, INT8, b1 and Newton-John forms run the products
+  // one by one.
+  if (ctx->form == M4RIE_FORM_POPC || ctx->form == M4RIE_FORM_MMA_S8 || ctx->form == M4RIE_FORM_MMA_B1 ||
+      ctx->form == M4RIE_FORM_NEWTON_JOHN) {
     for (int i = 0; i < count; ++i) {
       const m4rie_problem& p = problems[i];
       m4rie_status st = run_mul(ctx, p.e, p.f, p.m, p.n, p.k, p.A, p.B, p.C, p.accumulate ? 1 : 0);
@@ -605,6 +659,63 @@ m4rie_status m4rie_mul_batched(m4rie_ctx* ctx, int count, const m4rie_problem* p
     return M4RIE_OK;
   }
   return run_batched(ctx, count, problems, ctx->form == M4RIE_FORM_TC_F8 ? kFmtByte : kFmtNib);
+}
+
+int m4rie_packed_width(int e) { return e < 2 || e > 10 ? 0 : packed_width(e); }
+
+m4rie_status m4rie_to_packed(m4rie_ctx* ctx, int e, int64_t rows, int64_t cols, const void* elems, int64_t lde,
+                             uint64_t* words, int64_t ld_words) {
+  if (!ctx || e < 2 || e > 10 || rows < 0 || cols < 0 || lde < cols || rows > (1ll << 31) || cols > (1ll << 31))
+    return M4RIE_ERR_ARG;
+  const int per = 64 / packed_width(e);
+  if (ld_words < ceil_div(cols, per) || ld_words > (1ll << 40)) return M4RIE_ERR_ARG;
+  if (rows == 0 || ld_words == 0) return M4RIE_OK;
+  if ((cols && !elems) || !words) return M4RIE_ERR_ARG;
+  if (overlaps(words, span_bytes(rows, ld_words, ld_words, 8), elems, span_bytes(rows, cols, lde, elem_bytes(e))))
+    return M4RIE_ERR_ALIAS;
+  cudaError_t err = launch_to_packed(e, rows, cols, elems, lde, reinterpret_cast<uint32_t*>(words), 2 * ld_words,
+                                     ctx->d_status, ctx->stream, &ctx->launches);
+  return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+}
+
+m4rie_status m4rie_from_packed(m4rie_ctx* ctx, int e, int64_t rows, int64_t cols, const uint64_t* words,
+                               int64_t ld_words, void* elems, int64_t lde) {
+  if (!ctx || e < 2 || e > 10 || rows < 0 || cols < 0 || lde < cols || rows > (1ll << 31) || cols > (1ll << 31))
+    return M4RIE_ERR_ARG;
+  const int per = 64 / packed_width(e);
+  if (ld_words < ceil_div(cols, per) || ld_words > (1ll << 40)) return M4RIE_ERR_ARG;
+  if (rows == 0 || cols == 0) return M4RIE_OK;
+  if (!elems || !words) return M4RIE_ERR_ARG;
+  if (overlaps(words, span_bytes(rows, ld_words, ld_words, 8), elems, span_bytes(rows, cols, lde, elem_bytes(e))))
+    return M4RIE_ERR_ALIAS;
+  cudaError_t err = launch_from_packed(e, rows, cols, reinterpret_cast<const uint32_t*>(words), 2 * ld_words, elems,
+                                       lde, ctx->stream, &ctx->launches);
+  return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+}
+
+m4rie_status m4rie_mul_packed(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
+                              const uint64_t* A, int64_t lda, const uint64_t* B, int64_t ldb, uint64_t* C,
+                              int64_t ldc, int accumulate) {
+  if (!ctx) return M4RIE_ERR_ARG;
+  m4rie_status st = check_field(e, f);
+  if (st != M4RIE_OK) return st;
+  if (m < 0 || n < 0 || k < 0 || m > (1ll << 31) || n > (1ll << 31) || k > (1ll << 31)) return M4RIE_ERR_ARG;
+  const int per = 64 / packed_width(e);
+  const int64_t kw = ceil_div(k, per), nw = ceil_div(n, per);
+  if (lda < kw || ldb < nw || ldc < nw || lda > (1ll << 40) || ldb > (1ll << 40) || ldc > (1ll << 40))
+    return M4RIE_ERR_ARG;
+  if ((m * k && !A) || (k * n && !B) || (m * n && !C)) return M4RIE_ERR_ARG;
+  const size_t sc = span_bytes(m, nw, ldc, 8);
+  if (overlaps(C, sc, A, span_bytes(m, kw, lda, 8)) || overlaps(C, sc, B, span_bytes(k, nw, ldb, 8)))
+    return M4RIE_ERR_ALIAS;
+  if (m == 0 || n == 0) return M4RIE_OK;
+  if (k == 0) {
+    if (accumulate) return M4RIE_OK;
+    cudaError_t err = cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)nw * 8, (size_t)m, ctx->stream);
+    return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+  }
+  if (ctx->timing) ++ctx->timed_products;
+  return run_newton_john(ctx, e, f, m, n, k, Mats{A, lda, B, ldb, C, ldc}, accumulate ? 1 : 0, true);
 }
 
 m4rie_status m4rie_get_device_status(m4rie_ctx* ctx) {

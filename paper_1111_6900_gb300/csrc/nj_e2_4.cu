@@ -1,0 +1,8 @@
+// Newton-John kernels for GF(2^e), e = 2, 3, 4 (template in nj_kernel.cuh).
+#include "nj_kernel.cuh"
+
+namespace m4rie {
+template cudaError_t nj_launch<2>(const NjParams&, int, int64_t, int64_t, cudaStream_t);
+template cudaError_t nj_launch<3>(const NjParams&, int, int64_t, int64_t, cudaStream_t);
+template cudaError_t nj_launch<4>(const NjParams&, int, int64_t, int64_t, cudaStream_t);
+}  // namespace m4rie

@@ -91,6 +91,7 @@ m4rie_status m4rie_tune(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n,
       else
         for (int gm : {0, 8}) cands.push_back({form, sched, gm});
     }
+  cands.push_back({M4RIE_FORM_NEWTON_JOHN, M4RIE_SCHED_ALPHA_B, 0});  // no slicing: the schedule is unused
   const int saved_form = ctx->form, saved_sched = ctx->schedule, saved_gm = ctx->group_m;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -182,7 +183,7 @@ m4rie_status m4rie_tune_load(m4rie_ctx* ctx, const char* path) {
     int e, c, form, sched, gm;
     double ms;
     if (sscanf(line, "%d %d %d %d %d %lf", &e, &c, &form, &sched, &gm, &ms) != 6) continue;
-    if (e < 2 || e > 10 || c < 0 || c > 63 || form < M4RIE_FORM_POPC || form > M4RIE_FORM_MMA_B1 ||
+    if (e < 2 || e > 10 || c < 0 || c > 63 || form < M4RIE_FORM_POPC || form > M4RIE_FORM_NEWTON_JOHN ||
         sched < M4RIE_SCHED_ALPHA_B || sched > M4RIE_SCHED_KARATSUBA || gm < 0)
       continue;
     ctx->tuned[e][c] = TuneEntry{form, sched, gm, ms};

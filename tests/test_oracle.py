@@ -19,19 +19,29 @@ from tests import fieldref as fr
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _read_fig1():
+def _fig1_sections():
     lines = [l.split("#")[0].strip() for l in open(os.path.join(GOLDEN, "fig1_gf8.txt"))]
     lines = [l for l in lines if l]
     e = int(lines[0].split()[1])
-    assert lines[1] == "elements"
-    elems = np.array([[int(v) for v in lines[2].split()], [int(v) for v in lines[3].split()]])
-    slices = []
-    i = 4
+    sections = {}
+    i = 1
     while i < len(lines):
-        assert lines[i].startswith("slice")
-        slices.append(np.array([[int(v) for v in lines[i + 1].split()], [int(v) for v in lines[i + 2].split()]]))
+        sections[lines[i]] = [lines[i + 1].split(), lines[i + 2].split()]
         i += 3
+    return e, sections
+
+
+def _read_fig1():
+    e, sec = _fig1_sections()
+    elems = np.array([[int(v) for v in row] for row in sec["elements"]])
+    slices = [np.array([[int(v) for v in row] for row in sec[f"slice {i}"]]) for i in range(e)]
     return e, elems, slices
+
+
+def _read_fig1_packed():
+    """Figure 1's packed row as a list of rows of bit-strings (highest bit first)."""
+    _, sec = _fig1_sections()
+    return sec["packed"]
 
 
 # ---------------------------------------------------------------- Figure 1
@@ -51,6 +61,52 @@ def test_fig1_slicing_matches_figure():
 def test_fig1_clinging_inverts_slicing():
     e, elems, _ = _read_fig1()
     np.testing.assert_array_equal(oracle.cling(e, oracle.slice_(e, elems), 2), elems)
+
+
+# ------------------------------------------------ packed representation
+
+
+def test_fig1_packed_matches_figure():
+    """Figure 1, second row: F_8 entries in 4-bit fields, the top (padding)
+    bit zero.  The figure does not fix the order of the fields inside a word;
+    the lowest field first (the slices' column order) is the reading used."""
+    e, elems, _ = _read_fig1()
+    fields = _read_fig1_packed()
+    assert oracle.packed_width(e) == len(fields[0][0]) == 4
+    W = oracle.to_packed(e, elems)
+    assert W.shape == (2, 1)
+    for r in range(2):
+        want = sum(int(fields[r][c], 2) << (4 * c) for c in range(2))
+        assert int(W[r, 0]) == want
+    np.testing.assert_array_equal(oracle.from_packed(e, W, 2), elems)
+
+
+def test_packed_widths():
+    """Section 3.1: the next length dividing 64; F_32 entries take 8 bits
+    (three zero coefficients on top)."""
+    assert oracle.packed_width(5) == 8
+    for e in range(2, 11):
+        w = oracle.packed_width(e)
+        assert 64 % w == 0 and w >= e and (w == 2 or w // 2 < e)
+
+
+@pytest.mark.parametrize("e", list(range(2, 11)))
+def test_packed_bits_and_roundtrip(e):
+    """Every field of a packed word, read back bit by bit, is the element;
+    padding fields and bits are zero; unpacking ignores padding."""
+    rng = np.random.default_rng(70 + e)
+    cols = 37
+    X = workloads.elements(rng, e, (5, cols))
+    w = oracle.packed_width(e)
+    per = 64 // w
+    W = oracle.to_packed(e, X, ld_words=(cols + per - 1) // per + 1)
+    for r in range(5):
+        for c in range(W.shape[1] * per):
+            field = (int(W[r, c // per]) >> (w * (c % per))) & ((1 << w) - 1)
+            assert field == (int(X[r, c]) if c < cols else 0)
+    dirty = W.copy()
+    dirty[:, -1] = np.uint64(0xFFFFFFFFFFFFFFFF)  # padding word
+    np.testing.assert_array_equal(oracle.from_packed(e, dirty, cols), X)
 
 
 def test_slice_cling_roundtrip_random_and_padding():
@@ -442,6 +498,11 @@ _MUTANTS = {
     "slice_msb": ("row[c / 64] |= (uint64_t)1 << (c % 64);", "row[c / 64] |= (uint64_t)1 << (63 - c % 64);"),
     # addition as OR instead of XOR
     "add_or": ("crow[c] ^= (uint16_t)oracle_gf_mul(e, f, a, brow[c]);", "crow[c] |= (uint16_t)oracle_gf_mul(e, f, a, brow[c]);"),
+    # packed fields placed highest first in the word
+    "packed_msb": ("row[c / per] |= (uint64_t)elems[r * cols + c] << (w * (c % per));",
+                   "row[c / per] |= (uint64_t)elems[r * cols + c] << (w * (per - 1 - c % per));"),
+    # packing as many elements as fit instead of padding to a length dividing 64
+    "packed_no_pad": ("    while (w < e)\n        w *= 2;\n    return w;", "    return e;"),
     # field inverse with the wrong exponent
     "inv_exponent": ("x = (1u << e) - 2;", "x = (1u << e) - 3;"),
     # upper solve reads the multiplier from the transposed position
@@ -467,6 +528,12 @@ def _pins_pass(O: oracle.OracleLib) -> bool:
             got = np.array([[(int(planes[i, r, 0]) >> c) & 1 for c in range(2)] for r in range(2)])
             if not np.array_equal(got, slices[i]):
                 return False
+        fields = _read_fig1_packed()
+        if O.packed_width(e) != 4 or O.packed_width(5) != 8:
+            return False
+        Wd = O.to_packed(e, elems)
+        if any(int(Wd[r, 0]) != sum(int(fields[r][c], 2) << (4 * c) for c in range(2)) for r in range(2)):
+            return False
         for e in (2, 4, 8, 10):
             f = workloads.FIELD_POLY[e]
             if not np.array_equal(O.mul_table(e, f).astype(np.int64), fr.log_table_product(e, f)):
