@@ -54,22 +54,25 @@ CONFIG = config_of(WORKLOAD)
 # summaries (dram__bytes_read.sum + dram__bytes_write.sum).  It is reported only
 # while the kernel source is the one that was profiled (sha256 below).
 TRAFFIC = {
-    "tc_f4/karatsuba": {"bytes": 1.54019072e+08 + 1.4899968e+07, "source": "profiles/tc_f4_karatsuba_gf16_4096.md"},
-    "tc_f8/karatsuba": {"bytes": 3.0206464e+08 + 1.8095616e+07, "source": "profiles/tc_f8_karatsuba_gf16_4096.md"},
+    "tc_f4/karatsuba": {"bytes": 154.708224e6 + 15.304448e6, "source": "profiles/tc_f4_karatsuba_gf16_4096.md"},
     "popc/alpha_b": {"bytes": 41.965824e6 + 0.164864e6, "source": "profiles/popc_alpha_b_gf16_4096.md"},
+    "newton_john/alpha_b": {"bytes": 68.3008e6 + 11.918848e6, "source": "profiles/nj_rank64_gf256_8192.md",
+                            "workload": "gf256_8192x64x8192_addmul"},
 }
-PROFILED_SOURCES = {"tc_f4/karatsuba": ("gemm_tc.cu", "d2a2daf03f63e1f706725c52d988f952bab7695dc74f41a10c7970915fd9b194"),
-                    "tc_f8/karatsuba": ("gemm_tc.cu", "d2a2daf03f63e1f706725c52d988f952bab7695dc74f41a10c7970915fd9b194"),
-                    "popc/alpha_b": ("gemm_popc.cu", "6fc3d0a61765ce47396627acb19770a9ddecc498caad76ea310bae7c899f3a1b")}
+PROFILED_SOURCES = {"tc_f4/karatsuba": ("gemm_tc.cu", "02a070fd3f12ca394e8447ab1db05952aafa668d33d463939800b9b7a500d3bf"),
+                    "popc/alpha_b": ("gemm_popc.cu", "6fc3d0a61765ce47396627acb19770a9ddecc498caad76ea310bae7c899f3a1b"),
+                    "newton_john/alpha_b": ("nj_kernel.cuh",
+                                            "ab5019c0f2f75eb955730f6c2c9c2210cfe2bba7a25bc6a210f536b813b88f17")}
 # tcgen05.mma issue rate measured on this GPU by microbench/mma_rates.cu, MAC per SM clock
 MMA_MAC_PER_CLK = {"tc_f8": 8192, "tc_f4": 16384}
 
 
 def kernel_traffic(key):
-    """Traffic of the profiled kernel, or None if its source changed since."""
+    """Traffic of the profiled kernel, or None if its source changed since or
+    the profile was taken on another workload."""
     import hashlib
     t = TRAFFIC.get(key)
-    if not t:
+    if not t or t.get("workload", "gf16_4096_mul") != WORKLOAD.name:
         return None
     fname, sha = PROFILED_SOURCES[key]
     path = os.path.join(ROOT, "paper_1111_6900_gb300", "csrc", fname)
@@ -563,7 +566,8 @@ def run_batched_workload(args, m4, torch, world, rank, local):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     ctx = m4.Context(stream)
-    ctx.set_form(args.forms.split(",")[0] if args.forms not in ("popc,tc_f8,tc_f4,mma_s8,mma_b1",) else "auto")
+    ctx.set_form(args.forms.split(",")[0] if args.forms not in ("popc,tc_f8,tc_f4,mma_s8,mma_b1,newton_john",)
+                 else "auto")
     for _ in range(args.warmup):
         ctx.mul_batched(probs)
     torch.cuda.synchronize()
@@ -605,7 +609,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="popc,tc_f8,tc_f4,mma_s8,mma_b1")
+    ap.add_argument("--forms", default="popc,tc_f8,tc_f4,mma_s8,mma_b1,newton_john")
     ap.add_argument("--schedules", default="alpha_b,karatsuba")
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -688,8 +692,8 @@ def main():
     results = {}
     for form in args.forms.split(","):
         for sched in args.schedules.split(","):
-            if form.startswith("mma_") and sched != "alpha_b":
-                continue
+            if (form.startswith("mma_") or form == "newton_john") and sched != "alpha_b":
+                continue  # alpha^j-B only (mma_*), or no slicing schedule at all (newton_john)
             ctx.set_form(form)
             ctx.set_schedule(sched)
             try:
@@ -733,7 +737,8 @@ def main():
                 "ms_per_step": ms, "value": world * w.field_ops / (ms * 1e-3),
                 "gemm_ms": gemm_ms / max(nprod, 1), "pack_ms": pack_ms / max(nprod, 1),
                 "recombine_ms": rec_ms / max(nprod, 1), "launches": ctx.kernel_launches() - launches0,
-                "products": m4.schedule_products(w.e, w.f, sched), "clocks": clk.summary(),
+                "products": None if form == "newton_john" else m4.schedule_products(w.e, w.f, sched),
+                "clocks": clk.summary(),
                 "device_status": status}
 
     good = {k: v for k, v in results.items() if "value" in v and v["device_status"] == m4.OK and v["verified"]}
@@ -765,7 +770,18 @@ def main():
     pk = peaks() or {}
     r = m4.schedule_products(w.e, w.f, sched)
     gemm_s = best["gemm_ms"] * 1e-3
-    if form == "mma_b1":
+    if form == "newton_john":
+        # shared-memory bound: 4 bytes per packed 32-bit word of a C row read
+        # from a table for every entry of A (twice with the split tables of e >= 6)
+        P = 32 // m4.packed_width(w.e)
+        lookups = 2 if w.e >= 6 else 1
+        nbytes = float(w.m) * w.k * (-(-w.n // P)) * 4 * lookups
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e9
+        roof = {"bound": "smem", "achieved": nbytes / gemm_s / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": nbytes / gemm_s / 1e9 / peak, "traffic": kernel_traffic(f"{form}/{sched}"),
+                "peak_source": "derived: 152 SMs x 128 bytes of shared-memory reads per clock x max SM clock"}
+    elif form == "mma_b1":
         bitmacs = r * w.m * w.n * w.k
         roof = {"bound": "tensor", "achieved": bitmacs / gemm_s / 1e12, "peak": 73.2, "unit": "T bit-MAC/s",
                 "frac": bitmacs / gemm_s / 1e12 / 73.2, "traffic": None,

@@ -71,6 +71,9 @@ WORKLOADS = {
     2: Workload("gf16_4096_mul", "mul", 4, 4096, 4096, 4096, 1002),
     3: Workload("gf256_8192_addmul", "addmul", 8, 8192, 8192, 8192, 1003),
     5: Workload("gf1024_16384x4096x16384_mul", "mul", 10, 16384, 4096, 16384, 1005),
+    # the rank-64 update of a reduced echelon form's panel step (Section 6),
+    # C += A B with A 8192 x 64 and B 64 x 8192 over GF(2^8)
+    "rank64": Workload("gf256_8192x64x8192_addmul", "addmul", 8, 8192, 64, 8192, 1006),
 }
 
 BATCHED_COUNT = 4096
