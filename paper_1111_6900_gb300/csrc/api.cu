@@ -233,6 +233,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   pa.vec = aligned16(A) && (x.lda * elem_bytes(e)) % 16 == 0;
   pa.out = Ap;
   pa.status = ctx->d_status;
+  pa.pdl = ctx->pdl;
   for (int j = 0; j < e; ++j) pa.mask[j] = amask[j];
   PackParams pb = pa;  // columns of B (k x n) are the planes' rows
   pb.X = B;
@@ -267,6 +268,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     pp.add = add;
     pp.emask = (1u << e) - 1;
     pp.status = ctx->d_status;
+    pp.pdl = ctx->pdl;
     err = launch_popc_fused(pp, ctx->stream, &ctx->launches);
   } else {
     TcParams tp{};
@@ -293,6 +295,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
     tp.cluster = pair ? ctx->cluster : 1;
+    tp.pdl = ctx->pdl;
     if (form == M4RIE_FORM_MMA_S8 || form == M4RIE_FORM_MMA_B1)
       err = launch_mma(form == M4RIE_FORM_MMA_B1, Ap, Bp, ld_bytes, tp, ctx->stream, &ctx->launches);
     else err = launch_tc(fi.fmt, Ap, Mp, Bp, brows, ld_bytes, tp, ctx->num_sms, ctx->stream, &ctx->launches);
@@ -323,9 +326,12 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   const int ntile = form == M4RIE_FORM_POPC ? 128 : (form == M4RIE_FORM_TC_F8 ? 256 : 224);
   const int64_t Np = round_up(n, ntile);
   const int64_t ldp = round_up(Np / 32, 4);  // words per parity row (whole 16-byte groups)
+  // tcgen05 on 2-SM pairs, e <= 8: the GEMM's epilogue recombines the products
+  // of each output tile itself (no parity planes, no recombination kernel)
+  const bool fused = form != M4RIE_FORM_POPC && pair && ctx->cluster == 3 && e <= 8 && ctx->fuse_recombine && r <= 64;
   const size_t a_bytes = round_up((int64_t)entries_bytes((int64_t)r * Mp * Kp, fi.bits), 1024);
   const size_t b_bytes = round_up((int64_t)entries_bytes((int64_t)r * Np * Kp, fi.bits), 1024);
-  const size_t p_bytes = round_up((int64_t)r * Mp * ldp * 4, 1024);
+  const size_t p_bytes = fused ? 0 : round_up((int64_t)r * Mp * ldp * 4, 1024);
   m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes + p_bytes);
   if (st != M4RIE_OK) return st;
   uint8_t* Ap = static_cast<uint8_t*>(ctx->ws);
@@ -353,6 +359,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   pa.vec = aligned16(A) && (x.lda * elem_bytes(e)) % 16 == 0;
   pa.out = Ap;
   pa.status = ctx->d_status;
+  pa.pdl = ctx->pdl;
   for (int p = 0; p < r; ++p) pa.mask[p] = sc.amask[p];
   PackParams pb = pa;  // columns of B (k x n) are the planes' rows
   pb.X = B;
@@ -379,6 +386,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     pp.C = Pp;
     pp.ldc = ldp;
     pp.status = ctx->d_status;
+    pp.pdl = ctx->pdl;
     pp.batch = r;
     pp.a_bstride = Mp * Kp / 32;
     pp.b_bstride = Np * Kp / 32;
@@ -409,10 +417,26 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
     tp.cluster = pair ? ctx->cluster : 1;
+    tp.pdl = ctx->pdl;
+    if (fused) {
+      tp.mode = 3;
+      tp.C = C;
+      tp.ldc = x.ldc;
+      tp.elem_bytes = elem_bytes(e);
+      tp.add = add;
+      tp.emask = (1u << e) - 1;
+      tp.vec_c = aligned16(C) && x.ldc % 16 == 0;
+      for (int q = 0; q < r; ++q) {
+        uint32_t qm = 0;
+        for (int s = 0; s < e; ++s) qm |= (uint32_t)((sc.out_mask[s] >> q) & 1ull) << s;
+        tp.qmask[q] = (uint8_t)qm;
+      }
+    }
     err = launch_tc(fi.fmt, Ap, (int64_t)r * Mp, Bp, (int64_t)r * Np, ld_bytes, tp, ctx->num_sms, ctx->stream,
                     &ctx->launches);
   }
   if (err != cudaSuccess) return cuda_fail(ctx, err);
+  if (fused) return M4RIE_OK;
   timer.begin(kPhaseRecombine);
   RecombineParams rc{};
   rc.P = Pp;
@@ -428,6 +452,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   rc.add = add;
   rc.emask = (1u << e) - 1;
   rc.status = ctx->d_status;
+  rc.pdl = ctx->pdl;
   for (int s = 0; s < 10; ++s) rc.out_mask[s] = sc.out_mask[s];
   err = launch_recombine(rc, ctx->stream, &ctx->launches);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
@@ -454,6 +479,7 @@ m4rie_status run_newton_john(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64
   p.add = add;
   p.flow = f & ((1u << e) - 1u);
   p.status = ctx->d_status;
+  p.pdl = ctx->pdl;
   if (!packed) {
     const int w = elem_bytes(e);
     auto rows4 = [w](const void* ptr, int64_t ld) { return (reinterpret_cast<uintptr_t>(ptr) & 3u) == 0 && (ld * w) % 4 == 0; };
@@ -529,6 +555,8 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
   if (const char* s = getenv("M4RIE_TC_CHUNK")) ctx->tc_chunk = std::min(std::max(128, atoi(s)), 1 << 21);
   if (const char* s = getenv("M4RIE_F4_KIND")) ctx->f4nv = strcmp(s, "nvf4") == 0 ? 1 : 0;
   if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) >= 2 && atoi(s) <= 3 ? atoi(s) : 1;
+  if (const char* s = getenv("M4RIE_PDL")) ctx->pdl = atoi(s) != 0;
+  if (const char* s = getenv("M4RIE_FUSE_RECOMBINE")) ctx->fuse_recombine = atoi(s) != 0;
   if (const char* s = getenv("M4RIE_TUNE_CACHE")) m4rie_tune_load(ctx, s);  // a missing file is not an error
   *out = ctx;
   return M4RIE_OK;

@@ -49,6 +49,14 @@ struct m4rie_ctx {
   // single-CTA MMAs with B tiles multicast to both CTAs; 1 = single CTAs
   // (M4RIE_TC_CLUSTER)
   int cluster = 3;
+  // kernels of a product launch with programmatic dependent launch, so each
+  // one's launch and prologue overlap the previous one's tail (M4RIE_PDL=0: off)
+  int pdl = 1;
+  // Karatsuba on tcgen05 2-SM pairs (e <= 8) can recombine in the GEMM's
+  // epilogue (M4RIE_FUSE_RECOMBINE=1).  Off by default: it runs every product
+  // of an output tile back to back, and that tile order costs the GEMM more
+  // L2 misses than the recombination kernel costs.
+  int fuse_recombine = 0;
   int group_m = 0;      // tcgen05 tile raster: m-tiles per column group (0: all m-tiles)
   m4rie::TuneEntry tuned[11][64];  // [e][floor(log2(m*n*k))] -> autotuned choice (form 0: none)
   // phase timing (m4rie_enable_timing)

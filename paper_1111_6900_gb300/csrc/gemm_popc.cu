@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(256, 2) popc_fused(const __grid_constant__ Pop
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * kPopcBM;
   const int64_t g = blockIdx.y;
+  pdl_enter();
   const uint32_t* Ag = p.A + m0 * p.ldw;
   const uint32_t* Bg = p.B + g * RB * p.ldw;
   const int ktiles = (int)((p.ldw + BKW - 1) / BKW);
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(256, 2) popc_parity(const __grid_constant__ Po
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * kPopcBM;
   const int64_t n0 = (int64_t)blockIdx.y * RB;
+  pdl_enter();
   const int b = blockIdx.z;
   const uint32_t* Ag = p.A + b * p.a_bstride + m0 * p.ldw;
   const uint32_t* Bg = p.B + b * p.b_bstride + n0 * p.ldw;
@@ -251,11 +253,13 @@ cudaError_t run_fused(const PopcParams& p, cudaStream_t s) {
   if (p.elem_bytes == 2) {
     err = cudaFuncSetAttribute(popc_fused<E, TNC, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    popc_fused<E, TNC, uint16_t><<<dim3((unsigned)gx, (unsigned)gy), 256, smem, s>>>(p);
+    err = launch_ex(popc_fused<E, TNC, uint16_t>, dim3((unsigned)gx, (unsigned)gy), dim3(256), smem, s, p.pdl != 0, p);
+    if (err != cudaSuccess) return err;
   } else {
     err = cudaFuncSetAttribute(popc_fused<E, TNC, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    popc_fused<E, TNC, uint8_t><<<dim3((unsigned)gx, (unsigned)gy), 256, smem, s>>>(p);
+    err = launch_ex(popc_fused<E, TNC, uint8_t>, dim3((unsigned)gx, (unsigned)gy), dim3(256), smem, s, p.pdl != 0, p);
+    if (err != cudaSuccess) return err;
   }
   return cudaGetLastError();
 }
@@ -288,9 +292,9 @@ cudaError_t launch_popc_parity(const PopcParams& p, cudaStream_t s, int64_t* lau
   const size_t smem = (size_t)STAGES * (kPopcBM + 128) * PITCH * 4;
   cudaError_t err = cudaFuncSetAttribute(popc_parity, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  popc_parity<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)p.batch), 256, smem, s>>>(p);
+  err = launch_ex(popc_parity, dim3((unsigned)gx, (unsigned)gy, (unsigned)p.batch), dim3(256), smem, s, p.pdl != 0, p);
   if (launches) ++*launches;
-  return cudaGetLastError();
+  return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 }  // namespace m4rie

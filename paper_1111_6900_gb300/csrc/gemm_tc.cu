@@ -272,6 +272,19 @@ __device__ __forceinline__ void tile_coords(const TcParams& p, int tile, int& b,
   tn = local / gm;
 }
 
+// Tile order of one CTA (pair).  Without FE: every tstep-th tile.  With FE
+// (mode 3): tile u * batch + b is product b of output tile u; a pair runs the
+// batch products of an output tile back to back, then moves tstep units on.
+template <int FE>
+__device__ __forceinline__ int first_tile(const TcParams& p, int tfirst) {
+  return FE ? tfirst * p.batch : tfirst;
+}
+template <int FE>
+__device__ __forceinline__ int next_tile(const TcParams& p, int tile, int tstep) {
+  if (!FE) return tile + tstep;
+  return (tile + 1) % p.batch ? tile + 1 : tile + 1 + (tstep - 1) * p.batch;
+}
+
 // FP4 only: TMEM columns [SF_COL, SF_COL + 16) hold the unit scale factors.
 constexpr int SF_COL = 240;
 
@@ -293,11 +306,17 @@ struct TileV {
 // Batched: the tile's job comes from the tile -> job table.
 // CL = 2: tile indices count pairs of m-tiles (2 tm, 2 tm + 1) handled by the
 // two CTAs of a cluster, which share the B tile; `rank` picks this CTA's m-tile.
-template <bool BATCHED, int CL = 1>
+template <bool BATCHED, int CL = 1, int FE = 0>
 __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restrict__ jobs, const CUtensorMap* tmA,
                                          const CUtensorMap* tmB, int tile, int& jc, TileV& t, int rank = 0) {
   if (!BATCHED) {
-    tile_coords(p, tile, t.b, t.tm, t.tn);
+    if (FE) {
+      int u0;
+      tile_coords(p, tile / p.batch, u0, t.tm, t.tn);  // u0 = 0: units index the m x n tiles
+      t.b = tile % p.batch;
+    } else {
+      tile_coords(p, tile, t.b, t.tm, t.tn);
+    }
     if (CL >= 2) t.tm = 2 * t.tm + rank;
     t.ma = tmA;
     t.mb = tmB;
@@ -355,7 +374,79 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
 // Both CTAs' copies complete on the even CTA's full barriers, its commits
 // release stages and accumulators in both CTAs, and both epilogues release the
 // even CTA's accumulator barriers.
-template <int FMT, bool BATCHED, bool NV = false, int CL = 1, int STAGES = 4>
+// Mode 3 epilogue of one unit: row r of the output tile's columns
+// tn * BN .. + BN as field elements (bytes, e <= FE <= 8) from the FE output
+// slices (bit c of outs[s][c / 32] = coefficient s of column c); with
+// accumulation the old values are XOR-ed in.  Returns true if an old entry
+// was out of range.
+template <int FE>
+__device__ __forceinline__ bool store_slices(const TcParams& p, const TileV& t, int64_t r, int tn,
+                                             const uint32_t (&outs)[FE][8]) {
+  if (r >= t.m) return false;
+  const int64_t c0 = (int64_t)tn * t.BN;
+  const int ncols = t.n - c0 < t.BN ? (int)(t.n - c0) : t.BN;
+  uint8_t* dst = static_cast<uint8_t*>(t.C) + r * t.ldc + c0;
+  const uint32_t rep = 0x01010101u * t.emask;
+  bool bad = false;
+  // Four elements (columns 32 w + 4 q .. + 3) as one word of bytes: spread four
+  // bits of each slice to the low bits of four bytes.  Every index is a
+  // compile-time constant, so outs stays in registers.
+  auto quad = [&](int w, int q) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int s = 0; s < FE; ++s) v |= ((((outs[s][w] >> (4 * q)) & 0xFu) * 0x00204081u) & 0x01010101u) << s;
+    return v;
+  };
+  if (ncols == t.BN && p.vec_c) {
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int w0 = 0; w0 < 8; w0 += 2) {  // 64 columns per round: four 16-byte stores, old values loaded first
+      uint4 old[4];
+      if (t.add) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (16 * (2 * w0 + u) < t.BN) old[u] = d4[2 * w0 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int w = w0 + (u >> 1), q0 = 4 * (u & 1);
+        if (16 * (2 * w0 + u) >= t.BN) break;
+        uint4 v = make_uint4(quad(w, q0), quad(w, q0 + 1), quad(w, q0 + 2), quad(w, q0 + 3));
+        if (t.add) {
+          bad |= ((old[u].x | old[u].y | old[u].z | old[u].w) & ~rep) != 0;
+          v.x ^= old[u].x & rep;
+          v.y ^= old[u].y & rep;
+          v.z ^= old[u].z & rep;
+          v.w ^= old[u].w & rep;
+        }
+        d4[2 * w0 + u] = v;
+      }
+    }
+    return bad;
+  }
+#pragma unroll
+  for (int w = 0; w < 8; ++w)  // ragged or unaligned: byte by byte
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (32 * w + 4 * q >= ncols) continue;
+      const uint32_t v = quad(w, q);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int c = 32 * w + 4 * q + i;
+        if (c >= ncols) break;
+        uint32_t x = (v >> (8 * i)) & 0xFFu;
+        if (t.add) {
+          const uint32_t o = dst[c];
+          bad |= o > t.emask;
+          x ^= o & t.emask;
+        }
+        dst[c] = (uint8_t)x;
+      }
+    }
+  return bad;
+}
+
+template <int FMT, bool BATCHED, bool NV = false, int CL = 1, int STAGES = 4, int FE = 0>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ TcParams p, const TcJob* __restrict__ jobs) {
@@ -443,6 +534,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   // tile loop: every CTA (CL = 1) or every cluster (CL = 2) takes every
   // (gridDim.x / CL)-th tile
   const int tfirst = blockIdx.x / CLN, tstep = gridDim.x / CLN;
+  // everything above overlaps the previous kernel's tail; no role touches
+  // global memory before that kernel (the operand planes' producer) is done
+  pdl_enter();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -451,9 +545,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t phase = 0;
       uint32_t issued_mask = 0, issued_parity = 0;
       bool ok = true;
-      for (int tile = tfirst; tile < total && ok; tile += tstep) {
+      for (int tile = first_tile<FE>(p, tfirst); tile < total && ok; tile = next_tile<FE>(p, tile, tstep)) {
         TileV t;
-        get_tile<BATCHED, CL>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
+        get_tile<BATCHED, CL, FE>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
         if (BATCHED && tile + (int)gridDim.x < total) {
           // fetch the next tile's tensor maps into the TMA descriptor cache early
           const TcJob& nj = jobs[__ldg(p.tile_job + tile + gridDim.x)];
@@ -522,9 +616,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       // CG2: only the even CTA issues MMAs (for both CTAs)
       const int my_total = CG2 && crank != 0 ? 0 : total;
-      for (int tile = tfirst; tile < my_total && ok; tile += tstep) {
+      for (int tile = first_tile<FE>(p, tfirst); tile < my_total && ok; tile = next_tile<FE>(p, tile, tstep)) {
         TileV t;
-        get_tile<BATCHED, CL>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
+        get_tile<BATCHED, CL, FE>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
         constexpr int MM = CG2 ? 256 : 128;
         const uint32_t idesc = FMT == kFmtNib ? idesc_f4(MM, t.BN, NV) : idesc_f8(MM, t.BN);
         for (int kb0 = 0; kb0 < t.kblocks && ok; kb0 += t.kc) {
@@ -587,9 +681,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     int chunk = 0, jc = 0;
     // failure-detection test: a wait that can only run out
     bool ok = !p.stall_test || __all_sync(0xffffffffu, mbar_wait(never, 0, abort_flag, p.status, lim));
-    for (int tile = tfirst; tile < total && ok; tile += tstep) {
+    // mode 3: the output slices of this thread's row, XOR-summed over the products of a unit
+    uint32_t outs[FE ? FE : 1][8];
+#pragma unroll
+    for (int s = 0; s < (FE ? FE : 1); ++s)
+#pragma unroll
+      for (int w = 0; w < 8; ++w) outs[s][w] = 0;
+    for (int tile = first_tile<FE>(p, tfirst); tile < total && ok; tile = next_tile<FE>(p, tile, tstep)) {
       TileV t;
-      get_tile<BATCHED, CL>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
+      get_tile<BATCHED, CL, FE>(p, jobs, &tmA, &tmB, tile, jc, t, crank);
       const int b = t.b, tm = t.tm, tn = t.tn;
       const int nc16 = t.BN / 16;
       uint32_t bits[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -641,6 +741,24 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (!ok || p.mode == 1) continue;
       const int64_t r0 = (int64_t)tm * 128;
+      if constexpr (FE > 0) {
+        // Karatsuba recombination (Section 5): output slice s is the XOR of
+        // the parities of the products that feed it
+        const uint32_t qm = p.qmask[b];
+#pragma unroll
+        for (int s = 0; s < FE; ++s)
+          if ((qm >> s) & 1u)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) outs[s][w] ^= bits[w];
+        if (b == p.batch - 1) {
+          if (store_slices<FE>(p, t, r0 + row, tn, outs)) atomicOr(p.status, kStatusRange);
+#pragma unroll
+          for (int s = 0; s < FE; ++s)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) outs[s][w] = 0;
+        }
+        continue;
+      }
       if (p.mode == 2) {
         // parity planes: row r0+row, columns tn*BN .. +BN
         uint32_t* P = static_cast<uint32_t*>(t.C) + b * p.p_bstride + (r0 + row) * p.ldp + (int64_t)tn * t.BN / 32;
@@ -787,11 +905,20 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
   // FP4 tiles of N <= 224 take the 5-stage ring
   const bool deep = fmt == kFmtNib && p.BN <= 224;
   const size_t smem = tc_smem_bytes(deep ? 5 : 4);
+  if (p.mode == 3 && !(pair && p.cluster == 3 && p.e <= 8)) return cudaErrorInvalidValue;
   if (pair && p.cluster == 3) {
     // 2-SM MMAs: the pair computes M = 256 rows per tile
-    auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, cg2_stages(kFmtNib)>
-                                           : tc_kernel<kFmtNib, false, false, 3, cg2_stages(kFmtNib)>)
-                                 : tc_kernel<kFmtByte, false, false, 3, cg2_stages(kFmtByte)>;
+    constexpr int S4 = cg2_stages(kFmtNib), S8 = cg2_stages(kFmtByte);
+    auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S4> : tc_kernel<kFmtNib, false, false, 3, S4>)
+                                 : tc_kernel<kFmtByte, false, false, 3, S8>;
+    if (p.mode == 3) {
+      // Karatsuba with the recombination in the epilogue: output slices for e <= 4 or e <= 8
+      if (fmt == kFmtNib)
+        kernel = p.e <= 4 ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S4, 4> : tc_kernel<kFmtNib, false, false, 3, S4, 4>)
+                          : (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S4, 8> : tc_kernel<kFmtNib, false, false, 3, S4, 8>);
+      else
+        kernel = p.e <= 4 ? tc_kernel<kFmtByte, false, false, 3, S8, 4> : tc_kernel<kFmtByte, false, false, 3, S8, 8>;
+    }
     const size_t smem2 = tc_smem_bytes_cg2(fmt);
     cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (err != cudaSuccess) return err;
@@ -807,13 +934,15 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = smem2;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = p.pdl ? 2 : 1;
     err = cudaLaunchKernelEx(&cfg, kernel, ma, mb, q, (const TcJob*)nullptr);
     if (launches) ++*launches;
     return err != cudaSuccess ? err : cudaGetLastError();
@@ -837,13 +966,15 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = p.pdl ? 2 : 1;
     err = cudaLaunchKernelEx(&cfg, kernel, ma, mb, q, (const TcJob*)nullptr);
     if (launches) ++*launches;
     return err != cudaSuccess ? err : cudaGetLastError();
@@ -859,9 +990,9 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
     return cudaErrorInvalidValue;
   const int grid = total < num_sms ? (int)total : num_sms;
   if (grid <= 0) return cudaSuccess;
-  kernel<<<grid, THREADS, smem, s>>>(ma, mb, p, nullptr);
+  err = launch_ex(kernel, dim3(grid), dim3(THREADS), smem, s, p.pdl != 0, ma, mb, p, (const TcJob*)nullptr);
   if (launches) ++*launches;
-  return cudaGetLastError();
+  return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, const int* d_tile_job, int njobs, int64_t total_tiles,

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the library.
 #pragma once
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 #include <cuda.h>
 
@@ -8,6 +9,34 @@ namespace m4rie {
 
 // Device status bits (sticky word owned by the context).
 enum : int { kStatusRange = 1, kStatusTimeout = 2, kStatusSingular = 4 };
+
+// Programmatic dependent launch.  A kernel launched with the attribute may
+// start while the previous kernel of the stream is finishing; pdl_enter()
+// waits until that kernel has completed and its writes are visible, then lets
+// the next kernel launch early in turn.  Kernels call it before their first
+// access to global memory.  Without the attribute both instructions return at
+// once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// cudaLaunchKernelEx with the programmatic-serialization attribute when pdl.
+template <typename... Params, typename... Args>
+cudaError_t launch_ex(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                      Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Operand plane formats.  Every plane entry is parity(x & mask) for one
 // element x and one GF(2)-linear mask, stored as:
@@ -50,6 +79,7 @@ struct PackParams {
   // r / G = (r * gmul) >> 40 for r < 2^31, G < 512.
   int64_t qoff[kMaxMasks];
   uint64_t gmul;
+  int pdl;            // launch with programmatic dependent launch
 };
 
 // Fill qoff and gmul of p from its layout fields; false if G is out of range.
@@ -102,6 +132,7 @@ struct RecombineParams {
   uint32_t emask;
   int* status;
   uint64_t out_mask[10];  // bit p of out_mask[s]: product p contributes to output slice s
+  int pdl;                // launch with programmatic dependent launch
 };
 cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches);
 
@@ -125,6 +156,7 @@ struct PopcParams {
   // parity (batched) mode
   int batch;
   int64_t a_bstride, b_bstride, c_bstride;  // words between batch planes
+  int pdl;            // launch with programmatic dependent launch
 };
 cudaError_t launch_popc_fused(const PopcParams& p, cudaStream_t s, int64_t* launches);
 cudaError_t launch_popc_parity(const PopcParams& p, cudaStream_t s, int64_t* launches);
@@ -156,6 +188,11 @@ struct TcParams {
   int f4nv;             // FP4: 1 = kind::mxf4nvf4 (UE4M3 scales per 16), 0 = kind::mxf4 (UE8M0 per 32)
   int stall_test;       // test hook: the epilogue first waits on a barrier that is never signalled
   int cluster;          // 2: pairs of CTAs share B tiles (tiles_m must be even), 1: single CTAs
+  int pdl;              // launch with programmatic dependent launch
+  // mode 3 (Karatsuba with the recombination in the epilogue; 2-SM pairs, e <= 8):
+  // every product of an output tile runs on one pair, back to back
+  uint8_t qmask[64];    // bit s: product b feeds output slice s
+  int vec_c;            // C and its rows are 16-byte aligned: 16-byte element stores
 };
 // fmt: kFmtByte (E4M3) or kFmtNib (E2M1, block scaled).
 cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,

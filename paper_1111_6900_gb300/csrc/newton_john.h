@@ -22,6 +22,7 @@ struct NjParams {
   uint32_t flow;  // f without its x^e term
   int* status;    // sticky device status word
   int vec_a, vec_b, vec_c;  // element rows of A / B / C start on 4-byte boundaries: 32-bit accesses allowed
+  int pdl;        // launch with programmatic dependent launch
   // filled by launch_newton_john from the plan
   int64_t nw;     // 32-bit words per packed row of B and C
   int lg;         // log2 of the tile width in words

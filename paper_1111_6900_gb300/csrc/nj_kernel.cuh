@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(kThreads, 2) nj_kernel(const __grid_constant__
   const int64_t kbeg = (int64_t)blockIdx.z * p.kper;
   const int64_t kend = p.k < kbeg + p.kper ? p.k : kbeg + p.kper;
   bool bad = false;
+  pdl_enter();
   uint4 acc[R];
 #pragma unroll
   for (int i = 0; i < R; ++i) acc[i] = make_uint4(0, 0, 0, 0);
@@ -457,13 +458,22 @@ cudaError_t launch_er(const NjParams& p, int64_t tiles_m, int64_t tiles_n, cudaS
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 1;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = (unsigned)p.ks;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (p.ks > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = 1;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = (unsigned)p.ks;
+    ++na;
+  }
+  if (p.pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = p.ks > 1 ? 1 : 0;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kern, p);
 }
 

@@ -235,6 +235,7 @@ __device__ __forceinline__ void rows_body(const PackParams& p, int tpr, uint32_t
 template <typename T, int FMT, int E>
 __global__ void __launch_bounds__(256) pack_planes_kernel(const __grid_constant__ PackParams p, int tpr) {
   __shared__ PlaneSmem sm;
+  pdl_enter();
   rows_body<T, FMT, E>(p, tpr, blockIdx.x, blockIdx.y, gridDim.y, sm.mexp);
 }
 
@@ -343,6 +344,7 @@ template <typename T, int FMT, int E>
 __global__ void __launch_bounds__(256) pack_planes_cols(const __grid_constant__ PackParams p) {
   __shared__ PlaneSmem sm;
   __shared__ uint32_t tile[col_tile_words<T>()];
+  pdl_enter();
   cols_body<T, FMT, E>(p, blockIdx.x, blockIdx.y, gridDim.y, sm.mexp, tile);
 }
 
@@ -355,6 +357,7 @@ __global__ void __launch_bounds__(256) pack_planes_pair(const __grid_constant__ 
                                                         uint32_t gxb, uint32_t gyb) {
   __shared__ PlaneSmem sm;
   __shared__ uint32_t tile[col_tile_words<T>()];
+  pdl_enter();
   const uint32_t b = blockIdx.x, na = gxa * gya;
   if (b < na) {
     rows_body<T, FMT, E>(pa, tpr, b % gxa, b / gxa, gya, sm.mexp);
@@ -596,6 +599,7 @@ __device__ __forceinline__ bool store_elements(const RecombineParams& p, int64_t
 template <typename T, int E>
 __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecombineParams p) {
   __shared__ uint32_t qmask[64];  // bit s: product q feeds output slice s
+  pdl_enter();
   for (int q = threadIdx.x; q < p.r; q += blockDim.x) {
     uint32_t m = 0;
 #pragma unroll
@@ -647,6 +651,16 @@ cudaError_t launch(K kernel, int64_t blocks, int threads, cudaStream_t s, int64_
   return cudaGetLastError();
 }
 
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Params...), int64_t blocks, int threads, cudaStream_t s, int64_t* launches,
+                       bool pdl, Args... args) {
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  cudaError_t err = launch_ex(kernel, dim3((unsigned)blocks), dim3(threads), 0, s, pdl, args...);
+  if (launches) ++*launches;
+  return err != cudaSuccess ? err : cudaGetLastError();
+}
+
 }  // namespace
 
 // Slice counts the plane kernels are built for: e = 2, 3..4, 5..8 (bytes),
@@ -654,10 +668,11 @@ cudaError_t launch(K kernel, int64_t blocks, int threads, cudaStream_t s, int64_
 // slices that no mask selects.
 template <int FMT>
 void launch_planes_fmt(const PackParams& p, dim3 grid, int tpr, cudaStream_t s) {
-  if (p.elem_bytes == 2) pack_planes_kernel<uint16_t, FMT, 10><<<grid, 256, 0, s>>>(p, tpr);
-  else if (p.e <= 2) pack_planes_kernel<uint8_t, FMT, 2><<<grid, 256, 0, s>>>(p, tpr);
-  else if (p.e <= 4) pack_planes_kernel<uint8_t, FMT, 4><<<grid, 256, 0, s>>>(p, tpr);
-  else pack_planes_kernel<uint8_t, FMT, 8><<<grid, 256, 0, s>>>(p, tpr);
+  const bool pdl = p.pdl != 0;
+  if (p.elem_bytes == 2) launch_ex(pack_planes_kernel<uint16_t, FMT, 10>, grid, 256, 0, s, pdl, p, tpr);
+  else if (p.e <= 2) launch_ex(pack_planes_kernel<uint8_t, FMT, 2>, grid, 256, 0, s, pdl, p, tpr);
+  else if (p.e <= 4) launch_ex(pack_planes_kernel<uint8_t, FMT, 4>, grid, 256, 0, s, pdl, p, tpr);
+  else launch_ex(pack_planes_kernel<uint8_t, FMT, 8>, grid, 256, 0, s, pdl, p, tpr);
 }
 
 bool plane_offsets(PackParams& p) {
@@ -690,10 +705,11 @@ cudaError_t launch_pack_planes(const PackParams& p0, cudaStream_t s, int64_t* la
 
 template <int FMT>
 void launch_cols_fmt(const PackParams& p, dim3 grid, cudaStream_t s) {
-  if (p.elem_bytes == 2) pack_planes_cols<uint16_t, FMT, 10><<<grid, 256, 0, s>>>(p);
-  else if (p.e <= 2) pack_planes_cols<uint8_t, FMT, 2><<<grid, 256, 0, s>>>(p);
-  else if (p.e <= 4) pack_planes_cols<uint8_t, FMT, 4><<<grid, 256, 0, s>>>(p);
-  else pack_planes_cols<uint8_t, FMT, 8><<<grid, 256, 0, s>>>(p);
+  const bool pdl = p.pdl != 0;
+  if (p.elem_bytes == 2) launch_ex(pack_planes_cols<uint16_t, FMT, 10>, grid, 256, 0, s, pdl, p);
+  else if (p.e <= 2) launch_ex(pack_planes_cols<uint8_t, FMT, 2>, grid, 256, 0, s, pdl, p);
+  else if (p.e <= 4) launch_ex(pack_planes_cols<uint8_t, FMT, 4>, grid, 256, 0, s, pdl, p);
+  else launch_ex(pack_planes_cols<uint8_t, FMT, 8>, grid, 256, 0, s, pdl, p);
 }
 
 cudaError_t launch_pack_cols(const PackParams& p0, cudaStream_t s, int64_t* launches) {
@@ -713,10 +729,12 @@ cudaError_t launch_pack_cols(const PackParams& p0, cudaStream_t s, int64_t* laun
 template <int FMT>
 void launch_pair_fmt(const PackParams& a, int tpr, uint32_t gxa, uint32_t gya, const PackParams& b, uint32_t gxb,
                      uint32_t gyb, unsigned grid, cudaStream_t s) {
-  if (a.elem_bytes == 2) pack_planes_pair<uint16_t, FMT, 10><<<grid, 256, 0, s>>>(a, tpr, gxa, gya, b, gxb, gyb);
-  else if (a.e <= 2) pack_planes_pair<uint8_t, FMT, 2><<<grid, 256, 0, s>>>(a, tpr, gxa, gya, b, gxb, gyb);
-  else if (a.e <= 4) pack_planes_pair<uint8_t, FMT, 4><<<grid, 256, 0, s>>>(a, tpr, gxa, gya, b, gxb, gyb);
-  else pack_planes_pair<uint8_t, FMT, 8><<<grid, 256, 0, s>>>(a, tpr, gxa, gya, b, gxb, gyb);
+  const bool pdl = a.pdl != 0;
+  const dim3 g(grid);
+  if (a.elem_bytes == 2) launch_ex(pack_planes_pair<uint16_t, FMT, 10>, g, 256, 0, s, pdl, a, tpr, gxa, gya, b, gxb, gyb);
+  else if (a.e <= 2) launch_ex(pack_planes_pair<uint8_t, FMT, 2>, g, 256, 0, s, pdl, a, tpr, gxa, gya, b, gxb, gyb);
+  else if (a.e <= 4) launch_ex(pack_planes_pair<uint8_t, FMT, 4>, g, 256, 0, s, pdl, a, tpr, gxa, gya, b, gxb, gyb);
+  else launch_ex(pack_planes_pair<uint8_t, FMT, 8>, g, 256, 0, s, pdl, a, tpr, gxa, gya, b, gxb, gyb);
 }
 
 cudaError_t launch_pack_pair(const PackParams& a0, const PackParams& b0, cudaStream_t s, int64_t* launches) {
@@ -826,15 +844,15 @@ cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* 
   const int64_t g = ceil_div(n, 256);
   if (p.r > 64 || p.ldw % 4 != 0 || (reinterpret_cast<uintptr_t>(p.P) & 15u) != 0) return cudaErrorInvalidValue;
   switch (p.e) {
-    case 2: return launch(recombine_kernel<uint8_t, 2>, g, 256, s, launches, p);
-    case 3: return launch(recombine_kernel<uint8_t, 3>, g, 256, s, launches, p);
-    case 4: return launch(recombine_kernel<uint8_t, 4>, g, 256, s, launches, p);
-    case 5: return launch(recombine_kernel<uint8_t, 5>, g, 256, s, launches, p);
-    case 6: return launch(recombine_kernel<uint8_t, 6>, g, 256, s, launches, p);
-    case 7: return launch(recombine_kernel<uint8_t, 7>, g, 256, s, launches, p);
-    case 8: return launch(recombine_kernel<uint8_t, 8>, g, 256, s, launches, p);
-    case 9: return launch(recombine_kernel<uint16_t, 9>, g, 256, s, launches, p);
-    case 10: return launch(recombine_kernel<uint16_t, 10>, g, 256, s, launches, p);
+    case 2: return launch_pdl(recombine_kernel<uint8_t, 2>, g, 256, s, launches, p.pdl != 0, p);
+    case 3: return launch_pdl(recombine_kernel<uint8_t, 3>, g, 256, s, launches, p.pdl != 0, p);
+    case 4: return launch_pdl(recombine_kernel<uint8_t, 4>, g, 256, s, launches, p.pdl != 0, p);
+    case 5: return launch_pdl(recombine_kernel<uint8_t, 5>, g, 256, s, launches, p.pdl != 0, p);
+    case 6: return launch_pdl(recombine_kernel<uint8_t, 6>, g, 256, s, launches, p.pdl != 0, p);
+    case 7: return launch_pdl(recombine_kernel<uint8_t, 7>, g, 256, s, launches, p.pdl != 0, p);
+    case 8: return launch_pdl(recombine_kernel<uint8_t, 8>, g, 256, s, launches, p.pdl != 0, p);
+    case 9: return launch_pdl(recombine_kernel<uint16_t, 9>, g, 256, s, launches, p.pdl != 0, p);
+    case 10: return launch_pdl(recombine_kernel<uint16_t, 10>, g, 256, s, launches, p.pdl != 0, p);
   }
   return cudaErrorInvalidValue;
 }

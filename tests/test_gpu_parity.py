@@ -232,3 +232,37 @@ def test_full_size_workloads(ctx, idx, form, sched):
                                           else oracle.matmul(w.e, w.f, A[:4], B)))   # first rows (first tile)
     lhs = C if C0 is None else (C ^ C0)
     assert oracle.freivalds(w.e, w.f, A, B, lhs, trials=4, seed=idx)   # whole product, error <= 2^(-4e)
+
+
+# ---------------------------------------------------------------- recombination in the epilogue
+
+
+@pytest.mark.parametrize("form", ["tc_f8", "tc_f4"])
+@pytest.mark.parametrize("e,m,n,k,add", [(2, 512, 700, 300, False), (4, 1024, 513, 257, True),
+                                         (8, 768, 1100, 96, True), (5, 2048, 448, 640, False),
+                                         (3, 2100, 333, 129, True)])
+def test_karatsuba_recombined_in_the_epilogue(form, e, m, n, k, add, monkeypatch):
+    """M4RIE_FUSE_RECOMBINE=1: the 2-SM tcgen05 GEMM runs every product of an
+    output tile back to back and recombines them in its epilogue (no parity
+    planes; m is a multiple of 256 or at least 2048, so the products run on
+    2-SM pairs); the result must be the oracle's, ragged edges and
+    accumulation included."""
+    monkeypatch.setenv("M4RIE_FUSE_RECOMBINE", "1")
+    c = m4.Context()
+    try:
+        c.set_form(form)
+        c.set_schedule("karatsuba")
+        f = workloads.FIELD_POLY[e]
+        A, B, C0 = workloads.random_problem(e, m, n, k, seed=e * 100 + m, with_c=True)
+        if add:
+            C = dev(C0)
+            c.addmul(e, f, dev(A), dev(B), C)
+            want = oracle.addmul(e, f, A, B, C0)
+        else:
+            C = c.mul(e, f, dev(A), dev(B))
+            want = oracle.matmul(e, f, A, B)
+        torch.cuda.synchronize()
+        assert c.device_status() == m4.OK
+        np.testing.assert_array_equal(host(C), want)
+    finally:
+        c.close()
