@@ -403,9 +403,15 @@ m4rie_status run_trsm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, c
     ctx->launches += g->launches;
     return M4RIE_OK;
   }
-  if ((st = solve_all(ctx, s, m, nblk)) != M4RIE_OK) return st;
-  if (!ctx->timing) record(ctx, s, m, nblk);
-  return M4RIE_OK;
+  // The solve's kernels launch without programmatic dependent launch: inside
+  // the recorded graph it made the solve about 10% slower (4096^2 over
+  // GF(2^4): 1.15 against 1.03 ms).
+  const int pdl = ctx->pdl;
+  ctx->pdl = 0;
+  st = solve_all(ctx, s, m, nblk);
+  if (st == M4RIE_OK && !ctx->timing) record(ctx, s, m, nblk);
+  ctx->pdl = pdl;
+  return st;
 }
 
 }  // namespace
