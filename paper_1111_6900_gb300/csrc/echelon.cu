@@ -10,9 +10,10 @@
 //   1. Candidates: R = 96 rows at or below r, at first simply the next R
 //      rows; in later rounds of a panel the rows with a non-zero entry in one
 //      of the panel's columns that have no pivot yet, moved to rows r, r+1, ...
-//   2. One CTA reduces the candidate block in shared memory, column by
-//      column (first non-zero candidate row), to find the pivot rows and
-//      columns, and inverts M = the pivot rows' entries at the pivot columns.
+//   2. One CTA reduces the candidate block, column by column (first non-zero
+//      candidate row), on its bit slices held in registers, to find the pivot
+//      rows and columns and M^{-1} (M = the pivot rows' entries at the pivot
+//      columns), which it tracks during the elimination.
 //   3. The pivot rows move to rows r .. r + k - 1.  With X = M^{-1} times the
 //      pivot rows (columns c0 .. n-1, one product), every row i gets
 //      A[i][c0..] += A[i][pivot columns] X (one product over all m rows, the
@@ -46,11 +47,6 @@ constexpr int W = 64;         // panel columns
 constexpr int R = 96;         // candidate rows per round
 constexpr int LOGW = 1024;    // log table entries
 constexpr int EXPW = 4096;    // antilog entries (doubled, then zeros: log 0 points there)
-constexpr int PANEL_THREADS = 4 * R;  // 4 threads per candidate row, every 4th column each
-// Shared row strides (u16 entries): an odd number of 32-bit words, so that the
-// 8 rows a warp works on fall in different banks.
-constexpr int BP = W + 2;          // candidate block [R][BP]
-constexpr int GP = 2 * W + 2;      // [M | I] system [W][GP]
 
 struct PanelOut {
   int k;            // pivots found this round
@@ -98,159 +94,149 @@ __global__ void scatter_rows(T* __restrict__ A, int64_t lda, int64_t c0, int64_t
     d[c] = s[c];
 }
 
-// Step 2 on the candidate block A[r .. r+cnt)[c0 .. c0+wc) (cnt <= R): find
-// the pivots (columns in order, skipping done ones; the first candidate row
-// not yet a pivot with a non-zero entry after the previous eliminations) and
-// write M^{-1} (k x k, row stride W) to minv.  Entries >= 2^e set the range
-// flag and are used by their low e bits.
-template <typename T>
-__global__ void __launch_bounds__(PANEL_THREADS) panel_factor(int e, const T* __restrict__ A, int64_t lda, int64_t r,
-                                                              int64_t c0, int cnt, int wc, uint64_t done0,
-                                                              uint64_t done1, const uint16_t* __restrict__ gf,
+// Step 2 on the candidate block A[r .. r+cnt)[c0 .. c0+wc) (cnt <= R): the
+// pivot rows and columns and M^{-1}, from the slices of the block (Section 3.2).  Thread (row, word) of the
+// 384 holds, for its candidate row, the E slices of one 32-bit word: words 0
+// and 1 are the panel's 64 columns, words 2 and 3 a transform of 64 entries
+// indexed by pivot order.  Column j (not done): the lowest non-pivot row with
+// a non-zero entry becomes pivot number a; its transform gets coefficient 1
+// at a (its own original row); every other row i with entry x_i adds
+// (x_i / pv) times the pivot row, a GF(2)-linear map of the E slices (the
+// columns of the matrix of multiplication by x_i / pv are (x_i / pv) x^t mod f).
+// Only pivot rows are ever added into other rows, so a transform holds the
+// row's combination of original pivot rows.  Pivot rows are not scaled in the
+// loop (later steps never change a pivot's own entry), so at the end pivot
+// row a has pv_a at its pivot column and zeros at the others, and
+// M^{-1}[a][b] = pv_a^{-1} * transform[a][b].  Two barriers per column.
+constexpr int BS_THREADS = 4 * R;
+
+template <typename T, int E>
+__global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restrict__ A, int64_t lda, int64_t r,
+                                                              int64_t c0, int cnt, int wc, uint64_t done,
+                                                              uint32_t flow, const uint16_t* __restrict__ gf,
                                                               PanelOut* __restrict__ out, T* __restrict__ minv,
                                                               int* status) {
-  extern __shared__ uint16_t sh[];
-  uint16_t* lg = sh;
-  uint16_t* ex = sh + LOGW;
-  uint16_t* blk = ex + EXPW;  // [R][BP], later [W][GP] for the inversion
-  __shared__ int piv_row[W], piv_col[W], is_piv[R];
-  __shared__ uint16_t plg[2 * W];  // logs of the current pivot row
-  __shared__ int sel, kk;
-  const uint32_t q = (1u << e) - 1;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < LOGW + EXPW; i += PANEL_THREADS) sh[i] = gf[i];
+  __shared__ uint16_t lg[LOGW];
+  __shared__ uint16_t ex[EXPW];
+  __shared__ uint32_t pivs[E][4];  // slices of the current pivot row
+  __shared__ int wmin[BS_THREADS / 32];
+  __shared__ uint32_t pv_s;
+  __shared__ int piv_row[W], piv_col[W];
+  __shared__ uint32_t piv_val[W];
+  const uint32_t q = (1u << E) - 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = warp * 8 + (lane >> 2), word = lane & 3;
+  for (int i = tid; i < LOGW + EXPW; i += BS_THREADS) (i < LOGW ? lg[i] : ex[i - LOGW]) = gf[i];
+  // slices of this thread's word (panel words only; transforms start at zero)
+  uint32_t sl[E];
+#pragma unroll
+  for (int t = 0; t < E; ++t) sl[t] = 0;
   bool bad = false;
-  for (int idx = tid; idx < R * W; idx += PANEL_THREADS) {
-    const int i = idx / W, j = idx % W;
-    uint32_t v = 0;
-    if (i < cnt && j < wc) {
-      v = A[(r + i) * lda + c0 + j];
+  if (word < 2 && row < cnt) {
+    const T* src = A + (r + row) * lda + c0 + 32 * word;
+    for (int b = 0; b < 32; ++b) {
+      if (32 * word + b >= wc) break;
+      uint32_t v = src[b];
       bad |= v > q;
       v &= q;
+#pragma unroll
+      for (int t = 0; t < E; ++t) sl[t] |= ((v >> t) & 1u) << b;
     }
-    blk[i * BP + j] = (uint16_t)v;
   }
-  for (int i = tid; i < R; i += PANEL_THREADS) is_piv[i] = 0;
-  (void)done1;
-  if (tid == 0) kk = 0;
-  if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(status, kStatusRange);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStatusRange);
   __syncthreads();
 
-  const int row = tid >> 2, part = tid & 3;  // this thread: row `row`, columns part, part + 4, ...
-  uint16_t* br = blk + row * BP;
+  int k = 0, my_a = -1;  // pivots so far (uniform), this row's pivot number
   for (int j = 0; j < wc; ++j) {
-    if ((done0 >> j) & 1ull) continue;
-    if (tid == 0) sel = R;
-    __syncthreads();
-    {
-      // lowest candidate row (not yet a pivot) with a non-zero entry: a
-      // ballot per warp (8 rows), then one atomic per warp
-      const bool hit = part == 0 && row < cnt && !is_piv[row] && br[j] != 0;
-      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-      if ((tid & 31) == 0 && bal) atomicMin(&sel, (tid + __ffs(bal) - 1) >> 2);
-    }
-    __syncthreads();
-    const int p = sel;
-    if (p == R) continue;  // no pivot in this column among the candidates
-    // scale the pivot row to a leading 1 (its entries left of j are zero),
-    // one thread per column, and keep the logs of its entries
-    {
-      const uint32_t ld = q - lg[blk[p * BP + j]];  // log of the inverse pivot
-      __syncthreads();                               // every thread has read the pivot
-      if (tid < W) {
-        const uint32_t v = ex[lg[blk[p * BP + tid]] + ld];
-        blk[p * BP + tid] = (uint16_t)v;
-        plg[tid] = lg[v];
-      }
-    }
-    __syncthreads();
-    // clear column j from every other candidate row (the pivot row is zero
-    // left of j, and log 0 leads to a zero product)
-    const uint32_t x = row != p && row < cnt ? br[j] : 0u;
-    __syncwarp();
-    if (x) {
-      const uint32_t lx = lg[x];
+    if ((done >> j) & 1ull) continue;
+    const int wj = j >> 5, bj = j & 31;
+    uint32_t x = 0;
+    if (word == wj) {
 #pragma unroll
-      for (int i = 0; i < W / 4; ++i) {
-        const int c = part + 4 * i;
-        br[c] ^= ex[plg[c] + lx];
+      for (int t = 0; t < E; ++t) x |= ((sl[t] >> bj) & 1u) << t;
+    }
+    x = __shfl_sync(0xffffffffu, x, (lane & ~3) | wj);  // the entry at column j, to the row's four lanes
+    const bool hit = word == wj && row < cnt && my_a < 0 && x != 0;
+    const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) wmin[warp] = bal ? warp * 8 + ((__ffs(bal) - 1) >> 2) : R;
+    __syncthreads();
+    int p = R;
+#pragma unroll
+    for (int w = 0; w < BS_THREADS / 32; ++w) p = min(p, wmin[w]);
+    if (p == R) {  // no pivot in this column among the candidates (uniform)
+      __syncthreads();  // every thread has read wmin before the next column writes it
+      continue;
+    }
+    if (row == p) {
+      my_a = k;
+      if (word == 2 + (k >> 5)) sl[0] ^= 1u << (k & 31);  // coefficient 1 on its own original row
+#pragma unroll
+      for (int t = 0; t < E; ++t) pivs[t][word] = sl[t];
+      if (word == 0) {
+        pv_s = x;
+        piv_row[k] = p;
+        piv_col[k] = j;
+        piv_val[k] = x;
       }
     }
-    if (tid == 0) {
-      is_piv[p] = 1;
-      piv_row[kk] = p;
-      piv_col[kk] = j;
-      ++kk;
-    }
+    ++k;
     __syncthreads();
+    if (row != p && x != 0) {
+      // row += (x / pv) * pivot row, slice by slice
+      uint32_t m = ex[lg[x] + q - lg[pv_s]];
+#pragma unroll
+      for (int t = 0; t < E; ++t) {
+        const uint32_t pt = pivs[t][word];
+#pragma unroll
+        for (int s2 = 0; s2 < E; ++s2) sl[s2] ^= pt & (0u - ((m >> s2) & 1u));
+        m = (m << 1) ^ (((m >> (E - 1)) & 1u) ? (flow | (1u << E)) : 0u);  // times x mod f
+      }
+    }
   }
-  const int k = kk;
 
-  // M^{-1} by Gauss-Jordan on [M | I] (M invertible: k pivots were found);
-  // thread (row, part) owns row `row` and columns part, part + 4, ... of the
-  // k x 2k system (M in columns 0 .. W-1, I in W .. 2W-1), row stride GP.
-  uint16_t* g = blk;
-  __syncthreads();
-  for (int idx = tid; idx < W * 2 * W; idx += PANEL_THREADS) {
-    const int a = idx / (2 * W), b = idx % (2 * W);
-    uint32_t v = 0;
-    if (a < k && b < k) v = (uint32_t)A[(r + piv_row[a]) * lda + c0 + piv_col[b]] & q;
-    else if (a < k && b >= W && b - W == a) v = 1;
-    g[a * GP + b] = (uint16_t)v;
-  }
-  __syncthreads();
-  uint16_t* gr = g + row * GP;
-  for (int t = 0; t < k; ++t) {
-    if (tid == 0) sel = W;
-    __syncthreads();
-    {
-      const bool hit = part == 0 && row >= t && row < k && gr[t] != 0;
-      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-      if ((tid & 31) == 0 && bal) atomicMin(&sel, (tid + __ffs(bal) - 1) >> 2);
-    }
-    __syncthreads();
-    const int p = sel;  // exists: M is invertible
-    // swap rows p and t (the 4 threads of row t each swap their columns)
-    if (row == t && p != t) {
-      uint16_t* rp = g + p * GP;
-      for (int c = part; c < 2 * W; c += 4) {
-        const uint16_t s = gr[c];
-        gr[c] = rp[c];
-        rp[c] = s;
-      }
-    }
-    __syncthreads();
-    {
-      const uint32_t ld = q - lg[g[t * GP + t]];
-      __syncthreads();  // every thread has read the pivot
-      if (tid < 2 * W) {
-        const uint32_t v = ex[lg[g[t * GP + tid]] + ld];
-        g[t * GP + tid] = (uint16_t)v;
-        plg[tid] = lg[v];
-      }
-    }
-    __syncthreads();
-    const uint32_t x = row != t && row < k ? gr[t] : 0u;
-    __syncwarp();
-    if (x) {
-      const uint32_t lx = lg[x];
+  // M^{-1}: pivot row a's transform scaled by pv_a^{-1}
+  if (my_a >= 0 && word >= 2) {
+    const uint32_t linv = q - lg[piv_val[my_a]];
+    for (int b0 = 0; b0 < 32; ++b0) {
+      const int b = 32 * (word - 2) + b0;
+      if (b >= k) break;
+      uint32_t v = 0;
 #pragma unroll
-      for (int i = 0; i < 2 * W / 4; ++i) {
-        const int c = part + 4 * i;
-        gr[c] ^= ex[plg[c] + lx];
-      }
+      for (int t = 0; t < E; ++t) v |= ((sl[t] >> b0) & 1u) << t;
+      minv[my_a * W + b] = (T)(v ? ex[lg[v] + linv] : 0u);
     }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < k * W; idx += PANEL_THREADS) {
-    const int a = idx / W, b = idx % W;
-    minv[idx] = b < k ? (T)g[a * GP + W + b] : (T)0;
   }
   if (tid == 0) out->k = k;
-  for (int a = tid; a < k; a += PANEL_THREADS) {
+  __syncthreads();
+  for (int a = tid; a < k; a += BS_THREADS) {
     out->rows[a] = piv_row[a];
     out->cols[a] = piv_col[a];
   }
+}
+
+template <typename T>
+cudaError_t launch_panel_bitsliced(int e, const T* A, int64_t lda, int64_t r, int64_t c0, int cnt, int wc,
+                                   uint64_t done, uint32_t f, const uint16_t* gf, PanelOut* out, T* minv, int* status,
+                                   cudaStream_t s) {
+  const uint32_t flow = f & ((1u << e) - 1u);
+#define M4RIE_PANEL_CASE(EE)                                                                                       \
+  case EE:                                                                                                         \
+    panel_bitsliced<T, EE><<<1, BS_THREADS, 0, s>>>(A, lda, r, c0, cnt, wc, done, flow, gf, out, minv, status); \
+    break;
+  switch (e) {
+    M4RIE_PANEL_CASE(2)
+    M4RIE_PANEL_CASE(3)
+    M4RIE_PANEL_CASE(4)
+    M4RIE_PANEL_CASE(5)
+    M4RIE_PANEL_CASE(6)
+    M4RIE_PANEL_CASE(7)
+    M4RIE_PANEL_CASE(8)
+    M4RIE_PANEL_CASE(9)
+    M4RIE_PANEL_CASE(10)
+    default: return cudaErrorInvalidValue;
+  }
+#undef M4RIE_PANEL_CASE
+  return cudaGetLastError();
 }
 
 // Multipliers of every row: mult[i][a] = A[i][c0 + cols[a]].
@@ -369,10 +355,6 @@ m4rie_status echelon_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t 
   ws.host = ctx->ews_host;
   int* d_count = ws.cand + R;
 
-  const size_t panel_smem = (size_t)(LOGW + EXPW + std::max(R * BP, W * GP)) * sizeof(uint16_t);
-  if ((err = cudaFuncSetAttribute(panel_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem)) !=
-      cudaSuccess)
-    return fail(ctx, err);
 
   std::vector<int64_t> piv_cols;
   int64_t r = 0;
@@ -407,9 +389,9 @@ m4rie_status echelon_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t 
         if ((err = move_rows<T>(ctx, ws, 0, A, lda, c0, nt, src, dst)) != cudaSuccess) return fail(ctx, err);
       }
       // 2. pivots of the candidate block and M^{-1}
-      panel_factor<T><<<1, PANEL_THREADS, panel_smem, ctx->stream>>>(e, A, lda, r, c0, cnt, wc, done, 0, ctx->d_gf,
-                                                                    ws.po, reinterpret_cast<T*>(ws.minv),
-                                                                    ctx->d_status);
+      if ((err = launch_panel_bitsliced<T>(e, A, lda, r, c0, cnt, wc, done, f, ctx->d_gf, ws.po,
+                                           reinterpret_cast<T*>(ws.minv), ctx->d_status, ctx->stream)) != cudaSuccess)
+        return fail(ctx, err);
       ++ctx->launches;
       if ((err = cudaMemcpyAsync(&hpo, ws.po, sizeof(PanelOut), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess ||
           (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
