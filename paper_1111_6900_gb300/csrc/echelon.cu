@@ -119,14 +119,19 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
   __shared__ uint16_t lg[LOGW];
   __shared__ uint16_t ex[EXPW];
   __shared__ uint32_t pivs[E][4];  // slices of the current pivot row
-  __shared__ int wmin[BS_THREADS / 32];
+  __shared__ int cand[2];          // lowest candidate row of a column (two, used alternately)
   __shared__ uint32_t pv_s;
   __shared__ int piv_row[W], piv_col[W];
   __shared__ uint32_t piv_val[W];
   const uint32_t q = (1u << E) - 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = warp * 8 + (lane >> 2), word = lane & 3;
-  for (int i = tid; i < LOGW + EXPW; i += BS_THREADS) (i < LOGW ? lg[i] : ex[i - LOGW]) = gf[i];
+  // the logs of the non-zero elements and the antilogs up to 2(2^e - 1)
+  for (int i = tid; i < (int)(3 * q); i += BS_THREADS) {
+    if (i < (int)q) lg[i + 1] = gf[i + 1];
+    else ex[i - q] = gf[LOGW + i - q];
+  }
+  if (tid < 2) cand[tid] = R;
   // slices of this thread's word (panel words only; transforms start at zero)
   uint32_t sl[E];
 #pragma unroll
@@ -147,6 +152,7 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
   __syncthreads();
 
   int k = 0, my_a = -1;  // pivots so far (uniform), this row's pivot number
+  int it = 0;            // columns processed (uniform): cand[it & 1] serves column it
   for (int j = 0; j < wc; ++j) {
     if ((done >> j) & 1ull) continue;
     const int wj = j >> 5, bj = j & 31;
@@ -158,13 +164,15 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
     x = __shfl_sync(0xffffffffu, x, (lane & ~3) | wj);  // the entry at column j, to the row's four lanes
     const bool hit = word == wj && row < cnt && my_a < 0 && x != 0;
     const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-    if (lane == 0) wmin[warp] = bal ? warp * 8 + ((__ffs(bal) - 1) >> 2) : R;
+    if (lane == 0 && bal) atomicMin(&cand[it & 1], warp * 8 + ((__ffs(bal) - 1) >> 2));
     __syncthreads();
-    int p = R;
-#pragma unroll
-    for (int w = 0; w < BS_THREADS / 32; ++w) p = min(p, wmin[w]);
+    const int p = cand[it & 1];
+    // the other slot serves the next column: its last reads were before this
+    // column's barrier, its next writes come after the barrier below
+    if (tid == 0) cand[(it + 1) & 1] = R;
+    ++it;
     if (p == R) {  // no pivot in this column among the candidates (uniform)
-      __syncthreads();  // every thread has read wmin before the next column writes it
+      __syncthreads();
       continue;
     }
     if (row == p) {
