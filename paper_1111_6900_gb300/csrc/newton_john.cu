@@ -102,10 +102,14 @@ NjPlan plan_newton_john(int e, int64_t m, int64_t n, int64_t k, bool packed, int
   const int64_t want = 2 * (int64_t)num_sms;
   int ks = 1;
   int64_t tiles_m = ceil_div(m, (int64_t)kWarps * R * G);
+  // Shorter tiles only while the CTAs still fit one wave: a second wave of
+  // short-lived CTAs cost more than the longer tiles (GF(4) 4000^2 x 64:
+  // 44 against 54 us).
   while (tiles_m * pl.tiles_n * ks < want) {
     if (ks < 8 && ceil_div(k, (int64_t)KT) >= 2 * ks) {
       ks *= 2;
-    } else if (R > 1 && ceil_div(m, (int64_t)kWarps * (R / 2) * G) > tiles_m) {
+    } else if (R > 1 && ceil_div(m, (int64_t)kWarps * (R / 2) * G) > tiles_m &&
+               ceil_div(m, (int64_t)kWarps * (R / 2) * G) * pl.tiles_n * ks <= want) {
       R /= 2;
       tiles_m = ceil_div(m, (int64_t)kWarps * R * G);
     } else {
