@@ -163,7 +163,10 @@ m4rie_status m4rie_echelonize(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int6
 
 /* m4rie_mul / m4rie_addmul (accumulate != 0) on HOST buffers: copies A, B
  * (and C when accumulating) to context-owned device memory, computes, copies
- * C back and waits for the stream.  Host buffers may be pageable or pinned. */
+ * C back and waits for the stream.  Host buffers may be pageable or pinned.
+ * When all three are pinned and mapped into the device's address space and
+ * the product moves at most 8 MiB, the kernels read and write them in place
+ * instead (no staging copies). */
 m4rie_status m4rie_mul_host(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
                             const void *hostA, const void *hostB, void *hostC, int accumulate);
 

@@ -557,6 +557,7 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
   if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) >= 2 && atoi(s) <= 3 ? atoi(s) : 1;
   if (const char* s = getenv("M4RIE_PDL")) ctx->pdl = atoi(s) != 0;
   if (const char* s = getenv("M4RIE_FUSE_RECOMBINE")) ctx->fuse_recombine = atoi(s) != 0;
+  if (const char* s = getenv("M4RIE_ZERO_COPY")) ctx->zero_copy = atoi(s) != 0;
   if (const char* s = getenv("M4RIE_TUNE_CACHE")) m4rie_tune_load(ctx, s);  // a missing file is not an error
   *out = ctx;
   return M4RIE_OK;
@@ -605,12 +606,44 @@ m4rie_status m4rie_gemm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n,
   return run_gemm(ctx, e, f, m, n, k, Mats{A, lda, B, ldb, C, ldc}, accumulate ? 1 : 0);
 }
 
+namespace {
+
+// Device address of a pinned, device-mapped host buffer (nullptr otherwise:
+// pageable memory, or a host allocation the driver does not map).
+void* mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+}  // namespace
+
 m4rie_status m4rie_mul_host(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* hA,
                             const void* hB, void* hC, int accumulate) {
   if (!ctx) return M4RIE_ERR_ARG;
   m4rie_status st = validate(e, f, m, n, k, hA, hB, hC);
   if (st != M4RIE_OK) return st;
   const size_t w = elem_bytes(e);
+  const double total = (double)(m * k + k * n + (accumulate ? 2 : 1) * m * n) * (double)w;
+  if (ctx->zero_copy && m * k && k * n && m * n && total <= (double)(8 << 20)) {
+    // Small products on pinned buffers the GPU can address: the kernels read
+    // A and B and write C in host memory directly (over the CPU-GPU link), no
+    // staging copies.  (Large ones stage: the copy engines move about 200 GB/s
+    // each way, more than these kernels' host accesses.)
+    void* dA = mapped_host(hA);
+    void* dB = mapped_host(hB);
+    void* dC = mapped_host(hC);
+    if (dA && dB && dC) {
+      st = run_mul(ctx, e, f, m, n, k, dA, dB, dC, accumulate);
+      if (st != M4RIE_OK) return st;
+      const cudaError_t err = cudaStreamSynchronize(ctx->stream);
+      return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+    }
+  }
   const size_t sa = round_up((int64_t)(m * k * w), 256), sb = round_up((int64_t)(k * n * w), 256);
   const size_t sc = round_up((int64_t)(m * n * w), 256);
   if (sa + sb + sc > ctx->io_bytes) {

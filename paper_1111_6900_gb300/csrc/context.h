@@ -57,6 +57,9 @@ struct m4rie_ctx {
   // of an output tile back to back, and that tile order costs the GEMM more
   // L2 misses than the recombination kernel costs.
   int fuse_recombine = 0;
+  // m4rie_mul_host: kernels use pinned, device-mapped host buffers of small
+  // products in place (M4RIE_ZERO_COPY=0: always staging copies)
+  int zero_copy = 1;
   int group_m = 0;      // tcgen05 tile raster: m-tiles per column group (0: all m-tiles)
   m4rie::TuneEntry tuned[11][64];  // [e][floor(log2(m*n*k))] -> autotuned choice (form 0: none)
   // phase timing (m4rie_enable_timing)

@@ -266,3 +266,33 @@ def test_karatsuba_recombined_in_the_epilogue(form, e, m, n, k, add, monkeypatch
         np.testing.assert_array_equal(host(C), want)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("form,sched", [("popc", "alpha_b"), ("tc_f4", "karatsuba"), ("tc_f8", "alpha_b"),
+                                        ("newton_john", "alpha_b"), ("mma_s8", "alpha_b")])
+def test_host_buffers_in_place_when_pinned(form, sched, monkeypatch):
+    """M4RIE_ZERO_COPY=1: with pinned (device-mapped) host buffers the kernels
+    read A, B and write C in host memory directly; pageable buffers still go
+    through staging copies.  Both must give the oracle's result."""
+    monkeypatch.setenv("M4RIE_ZERO_COPY", "1")
+    c = m4.Context()
+    try:
+        c.set_form(form)
+        c.set_schedule(sched)
+        for e, (m, n, k) in [(4, (600, 520, 300)), (9, (130, 70, 257))]:
+            f = workloads.FIELD_POLY[e]
+            A, B, C0 = workloads.random_problem(e, m, n, k, seed=e + m, with_c=True)
+            hA = torch.from_numpy(A).pin_memory()
+            hB = torch.from_numpy(B).pin_memory()
+            hC = torch.zeros((m, n), dtype=hA.dtype).pin_memory()
+            c.mul_host(e, f, hA, hB, hC)
+            np.testing.assert_array_equal(hC.numpy(), oracle.matmul(e, f, A, B))
+            hC.copy_(torch.from_numpy(C0))
+            c.mul_host(e, f, hA, hB, hC, accumulate=True)
+            np.testing.assert_array_equal(hC.numpy(), oracle.addmul(e, f, A, B, C0))
+            Cp = C0.copy()  # pageable: the staging path
+            c.mul_host(e, f, A, B, Cp, accumulate=True)
+            np.testing.assert_array_equal(Cp, oracle.addmul(e, f, A, B, C0))
+        assert c.device_status() == m4.OK
+    finally:
+        c.close()
