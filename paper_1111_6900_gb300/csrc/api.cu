@@ -185,8 +185,11 @@ FormInfo form_info(int form) {
 size_t entries_bytes(int64_t entries, int bits) { return (size_t)((entries * bits + 7) / 8); }
 
 // ---------------------------------------------------------------- alpha^j-B
+// reuse_b: the B planes in the workspace are those of this B from the previous
+// call (same form, n and k): only A is sliced.  The B planes sit at the start
+// of the workspace, so their place does not depend on m.
 m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x,
-                         int add) {
+                         int add, bool reuse_b = false) {
   const void* A = x.A;
   const void* B = x.B;
   void* C = x.C;
@@ -207,8 +210,8 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   const size_t b_bytes = round_up((int64_t)entries_bytes(brows * ld, fi.bits), 1024);
   m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes);
   if (st != M4RIE_OK) return st;
-  uint8_t* Ap = static_cast<uint8_t*>(ctx->ws);
-  uint8_t* Bp = Ap + a_bytes;
+  uint8_t* Bp = static_cast<uint8_t*>(ctx->ws);
+  uint8_t* Ap = Bp + b_bytes;
 
   uint16_t amask[10], bmask[100];
   alpha_b_masks(e, f, amask, bmask);
@@ -250,7 +253,8 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
   for (int q = 0; q < e * e; ++q) pb.mask[q] = bmask[q];
   PhaseTimer timer(ctx);
   timer.begin(kPhasePack);
-  cudaError_t err = launch_pack_pair(pa, pb, ctx->stream, &ctx->launches);
+  cudaError_t err = reuse_b ? launch_pack_planes(pa, ctx->stream, &ctx->launches)
+                            : launch_pack_pair(pa, pb, ctx->stream, &ctx->launches);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
   timer.begin(kPhaseGemm);
 
@@ -306,7 +310,7 @@ m4rie_status run_alpha_b(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m,
 
 // ---------------------------------------------------------------- Karatsuba
 m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
-                           const Mats& x, int add) {
+                           const Mats& x, int add, bool reuse_b = false) {
   const void* A = x.A;
   const void* B = x.B;
   void* C = x.C;
@@ -334,9 +338,9 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   const size_t p_bytes = fused ? 0 : round_up((int64_t)r * Mp * ldp * 4, 1024);
   m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes + p_bytes);
   if (st != M4RIE_OK) return st;
-  uint8_t* Ap = static_cast<uint8_t*>(ctx->ws);
-  uint8_t* Bp = Ap + a_bytes;
-  uint32_t* Pp = reinterpret_cast<uint32_t*>(Bp + b_bytes);
+  uint8_t* Bp = static_cast<uint8_t*>(ctx->ws);
+  uint8_t* Ap = Bp + b_bytes;
+  uint32_t* Pp = reinterpret_cast<uint32_t*>(Ap + a_bytes);
 
   PackParams pa{};
   pa.X = A;
@@ -371,7 +375,8 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   for (int p = 0; p < r; ++p) pb.mask[p] = sc.bmask[p];
   PhaseTimer timer(ctx);
   timer.begin(kPhasePack);
-  cudaError_t err = launch_pack_pair(pa, pb, ctx->stream, &ctx->launches);
+  cudaError_t err = reuse_b ? launch_pack_planes(pa, ctx->stream, &ctx->launches)
+                            : launch_pack_pair(pa, pb, ctx->stream, &ctx->launches);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
   timer.begin(kPhaseGemm);
 
@@ -498,6 +503,11 @@ namespace m4rie {
 
 m4rie_status run_gemm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x, int add,
                       bool c_over_b) {
+  return run_gemm_as(ctx, e, f, m, n, k, x, add, c_over_b, -1, -1, false);
+}
+
+m4rie_status run_gemm_as(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x, int add,
+                         bool c_over_b, int form_as, int sched_as, bool reuse_b) {
   if (!ctx) return M4RIE_ERR_ARG;
   m4rie_status st = validate_mats(e, f, m, n, k, x, c_over_b && !add);
   if (st != M4RIE_OK) return st;
@@ -508,15 +518,15 @@ m4rie_status run_gemm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, i
     cudaError_t err = cudaMemset2DAsync(x.C, (size_t)x.ldc * w, 0, (size_t)n * w, (size_t)m, ctx->stream);
     return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
   }
-  int form = resolve_form(ctx, e, m, n, k);
+  int form = form_as >= 0 ? form_as : resolve_form(ctx, e, m, n, k);
   // Newton-John reads B while it writes C: an in-place product (C over B)
   // takes a sliced form, which reads B only while slicing it.
   if (form == M4RIE_FORM_NEWTON_JOHN && c_over_b) form = sliced_form(m, n, k);
-  const int sched = resolve_schedule(ctx, e, m, n, k);
+  const int sched = sched_as >= 0 ? sched_as : resolve_schedule(ctx, e, m, n, k);
   if (ctx->timing) ++ctx->timed_products;
   if (form == M4RIE_FORM_NEWTON_JOHN) return run_newton_john(ctx, e, f, m, n, k, x, add, false);
-  if (sched == M4RIE_SCHED_KARATSUBA) return run_karatsuba(ctx, form, e, f, m, n, k, x, add);
-  return run_alpha_b(ctx, form, e, f, m, n, k, x, add);
+  if (sched == M4RIE_SCHED_KARATSUBA) return run_karatsuba(ctx, form, e, f, m, n, k, x, add, reuse_b);
+  return run_alpha_b(ctx, form, e, f, m, n, k, x, add, reuse_b);
 }
 
 }  // namespace m4rie
@@ -574,6 +584,10 @@ void m4rie_destroy(m4rie_ctx* ctx) {
   if (ctx->ews) cudaFree(ctx->ews);
   if (ctx->ews_host) cudaFreeHost(ctx->ews_host);
   if (ctx->d_gf) cudaFree(ctx->d_gf);
+  for (cudaEvent_t ev : ctx->io_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
+  if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
   destroy_plan(ctx->plan);
   delete ctx;
@@ -620,6 +634,18 @@ void* mapped_host(const void* p) {
   return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
+// The copy streams and events of the pipelined host-buffer products (created
+// once per context; non-blocking, so they order against the context's stream
+// through events only).
+m4rie_status io_streams(m4rie_ctx* ctx) {
+  if (ctx->s_in) return M4RIE_OK;
+  cudaError_t err = cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 * kIoPanels && err == cudaSuccess; ++i)
+    err = cudaEventCreateWithFlags(&ctx->io_ev[i], cudaEventDisableTiming);
+  return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+}
+
 }  // namespace
 
 m4rie_status m4rie_mul_host(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void* hA,
@@ -662,6 +688,44 @@ m4rie_status m4rie_mul_host(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_
   uint8_t* dB = dA + sa;
   uint8_t* dC = dB + sb;
   cudaError_t err = cudaSuccess;
+  if (m >= 1024 && total >= (double)(32 << 20)) {
+    // Row panels: the copies of the next panels of A (and C) in, and of the
+    // finished panels of C out, overlap the products of the others.  B is
+    // copied and sliced once; every panel takes the form and schedule chosen
+    // for the whole product, so that the later panels reuse its planes.
+    if ((st = io_streams(ctx)) != M4RIE_OK) return st;
+    constexpr int P = kIoPanels;
+    const int64_t mp = round_up(ceil_div(m, P), 256);
+    const int form = resolve_form(ctx, e, m, n, k), sched = resolve_schedule(ctx, e, m, n, k);
+    const uint8_t* hA8 = static_cast<const uint8_t*>(hA);
+    uint8_t* hC8 = static_cast<uint8_t*>(hC);
+    err = cudaMemcpyAsync(dB, hB, k * n * w, cudaMemcpyHostToDevice, ctx->s_in);
+    int np = 0;
+    for (int p = 0; p < P && err == cudaSuccess; ++p) {
+      const int64_t r0 = p * mp, rows = std::min(m, r0 + mp) - r0;
+      if (rows <= 0) break;
+      err = cudaMemcpyAsync(dA + r0 * k * w, hA8 + r0 * k * w, rows * k * w, cudaMemcpyHostToDevice, ctx->s_in);
+      if (err == cudaSuccess && accumulate)
+        err = cudaMemcpyAsync(dC + r0 * n * w, hC8 + r0 * n * w, rows * n * w, cudaMemcpyHostToDevice, ctx->s_in);
+      if (err == cudaSuccess) err = cudaEventRecord(ctx->io_ev[p], ctx->s_in);
+      ++np;
+    }
+    if (err != cudaSuccess) return cuda_fail(ctx, err);
+    for (int p = 0; p < np; ++p) {
+      const int64_t r0 = p * mp, rows = std::min(m, r0 + mp) - r0;
+      if ((err = cudaStreamWaitEvent(ctx->stream, ctx->io_ev[p], 0)) != cudaSuccess) return cuda_fail(ctx, err);
+      st = run_gemm_as(ctx, e, f, rows, n, k, Mats{dA + r0 * k * w, k, dB, n, dC + r0 * n * w, n}, accumulate, false,
+                       form, sched, p > 0);
+      if (st != M4RIE_OK) return st;
+      if ((err = cudaEventRecord(ctx->io_ev[P + p], ctx->stream)) != cudaSuccess ||
+          (err = cudaStreamWaitEvent(ctx->s_out, ctx->io_ev[P + p], 0)) != cudaSuccess ||
+          (err = cudaMemcpyAsync(hC8 + r0 * n * w, dC + r0 * n * w, rows * n * w, cudaMemcpyDeviceToHost,
+                                 ctx->s_out)) != cudaSuccess)
+        return cuda_fail(ctx, err);
+    }
+    err = cudaStreamSynchronize(ctx->s_out);
+    return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
+  }
   if (m * k) err = cudaMemcpyAsync(dA, hA, m * k * w, cudaMemcpyHostToDevice, ctx->stream);
   if (err == cudaSuccess && k * n) err = cudaMemcpyAsync(dB, hB, k * n * w, cudaMemcpyHostToDevice, ctx->stream);
   if (err == cudaSuccess && accumulate && m * n)

@@ -18,6 +18,8 @@ struct TuneEntry {
 };
 int shape_class(int64_t m, int64_t n, int64_t k);  // floor(log2(m*n*k)), tune.cu
 // Operands of one product: A m x k, B k x n, C m x n, row strides in elements.
+constexpr int kIoPanels = 4;  // row panels of a pipelined host-buffer product
+
 struct Mats {
   const void* A;
   int64_t lda;
@@ -60,6 +62,9 @@ struct m4rie_ctx {
   // m4rie_mul_host: kernels use pinned, device-mapped host buffers of small
   // products in place (M4RIE_ZERO_COPY=0: always staging copies)
   int zero_copy = 1;
+  // pipelined host-buffer products: copy streams and their events
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t io_ev[2 * m4rie::kIoPanels] = {};
   int group_m = 0;      // tcgen05 tile raster: m-tiles per column group (0: all m-tiles)
   m4rie::TuneEntry tuned[11][64];  // [e][floor(log2(m*n*k))] -> autotuned choice (form 0: none)
   // phase timing (m4rie_enable_timing)
@@ -94,5 +99,10 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* problem
 // packing kernels on the same stream, so C = A * B in place is safe.
 m4rie_status run_gemm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x, int add,
                       bool c_over_b = false);
+// run_gemm with the form and schedule given (>= 0) instead of resolved, and
+// reuse_b: the B planes from the previous call on this B (same form,
+// schedule, n, k) are reused.  The row panels of one host-buffer product.
+m4rie_status run_gemm_as(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k, const Mats& x, int add,
+                         bool c_over_b, int form_as, int sched_as, bool reuse_b);
 }  // namespace m4rie
 

@@ -296,3 +296,37 @@ def test_host_buffers_in_place_when_pinned(form, sched, monkeypatch):
         assert c.device_status() == m4.OK
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_host_buffers_pipelined_row_panels(pinned, accumulate):
+    """A host-buffer product of more than 32 MiB runs in four row panels whose
+    copies overlap the other panels' products (B sliced once, reused).  The
+    result equals the device-buffer product and, on rows sampled from every
+    panel (including the ragged last one), the oracle."""
+    e, f = 4, workloads.FIELD_POLY[4]
+    m, n, k = 2148, 4096, 4096
+    A, B, C0 = workloads.random_problem(e, m, n, k, seed=77, with_c=True)
+    c = m4.Context()
+    try:
+        dC = dev(C0)
+        if accumulate:
+            c.addmul(e, f, dev(A), dev(B), dC)
+        else:
+            c.mul(e, f, dev(A), dev(B), dC)
+        if pinned:
+            hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+            hC = torch.from_numpy(C0.copy()).pin_memory()
+            c.mul_host(e, f, hA, hB, hC, accumulate=accumulate)
+            got = hC.numpy()
+        else:
+            got = C0.copy()
+            c.mul_host(e, f, A, B, got, accumulate=accumulate)
+        np.testing.assert_array_equal(got, host(dC))
+        rows = np.array([0, 1, 600, 639, 640, 641, 1279, 1280, 1919, 1920, 2100, 2147])
+        want = oracle.addmul(e, f, A[rows], B, C0[rows]) if accumulate else oracle.matmul(e, f, A[rows], B)
+        np.testing.assert_array_equal(got[rows], want)
+        assert c.device_status() == m4.OK
+    finally:
+        c.close()
