@@ -2,11 +2,12 @@
 // recorded once into a CUDA graph and replayed.
 //
 // A plan holds, in one device allocation, the per-product tables (tensor maps
-// and tile ranges of the GEMM jobs, operand-plane jobs, transpose jobs) and the
-// operand planes of every product.  Its graph is: memsets for k = 0 products,
-// one batched transpose of the B operands, one batched plane kernel per side,
-// and one persistent GEMM over all tiles of all products (alpha^j-B schedule,
-// element epilogue).  The plan is cached in the context and reused while the
+// and tile ranges of the GEMM jobs, operand-plane jobs) and the operand planes
+// of every product.  Its graph is: memsets for k = 0 products, one batched
+// plane kernel for the rows of the A operands and one for the columns of the B
+// operands (read through shared-memory tiles, no transpose), and one
+// persistent GEMM over all tiles of all products (alpha^j-B schedule, element
+// epilogue).  The plan is cached in the context and reused while the
 // caller passes the same descriptor array contents (same pointers, sizes and
 // fields); a different array rebuilds it.
 #include <algorithm>
@@ -74,7 +75,7 @@ m4rie_status fail(m4rie_ctx* ctx, cudaError_t err, BatchedPlan* plan) {
 struct Layout {
   int e, eb, G, BN;
   int64_t Kp, ld, ld_bytes, Mp, groups, brows;
-  size_t a_off, b_off, t_off;  // offsets into the workspace
+  size_t a_off, b_off;  // offsets into the workspace
 };
 
 }  // namespace
@@ -133,30 +134,24 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
     ws += round_up(L.Mp * L.ld_bytes, 1024);
     L.b_off = ws;
     ws += round_up(L.brows * L.ld_bytes, 1024);
-    L.t_off = ws;
-    ws += round_up(p.n * p.k * L.eb, 1024);
     live.push_back(i);
   }
   const int nl = (int)live.size();
 
-  // ---- device tables: GEMM jobs, plane jobs (A u8, A u16, B u8, B u16 groups), transpose jobs
+  // ---- device tables: GEMM jobs, plane jobs (A u8, A u16, B u8, B u16 groups)
   std::vector<TcJob> tjobs(nl);
   std::vector<PackParams> pjobs;                    // grouped: A/u8, A/u16, B/u8, B/u16
   std::vector<int64_t> pstart;                      // block starts per group, each followed by the total
-  std::vector<TransposeJob> xjobs;                  // grouped: u8, u16
-  std::vector<int64_t> xstart;
-  int pcount[4] = {0, 0, 0, 0}, xcount[2] = {0, 0};
-  int64_t pblocks[4] = {0, 0, 0, 0}, xblocks[2] = {0, 0};
+  int pcount[4] = {0, 0, 0, 0};
+  int64_t pblocks[4] = {0, 0, 0, 0};
 
   const size_t off_tjobs = 0;
   const size_t off_pjobs = round_up(sizeof(TcJob) * (size_t)std::max(nl, 1), 256);
   const size_t off_pstart = off_pjobs + round_up(sizeof(PackParams) * 2 * (size_t)std::max(nl, 1), 256);
-  const size_t off_xjobs = off_pstart + round_up(sizeof(int64_t) * (2 * (size_t)nl + 4), 256);
-  const size_t off_xstart = off_xjobs + round_up(sizeof(TransposeJob) * (size_t)std::max(nl, 1), 256);
   // tile -> job table (upper bound on the tile count: every job's tiles)
   int64_t tiles_ub = 0;
   for (int i : live) tiles_ub += (lay[i].Mp / 128) * lay[i].groups;
-  const size_t off_tilejob = off_xstart + round_up(sizeof(int64_t) * ((size_t)nl + 2), 256);
+  const size_t off_tilejob = off_pstart + round_up(sizeof(int64_t) * (2 * (size_t)nl + 4), 256);
   const size_t off_ws = off_tilejob + round_up(sizeof(int) * (size_t)std::max<int64_t>(tiles_ub, 1), 1024);
   err = cudaMalloc(&plan->dmem, off_ws + ws);
   if (err != cudaSuccess) {
@@ -207,7 +202,7 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
   for (int t = 0; t < nl; ++t)
     for (int64_t x = 0; x < (int64_t)tjobs[t].tiles_m * tjobs[t].tiles_n; ++x) tile_job[tjobs[t].tile_start + x] = t;
 
-  // plane and transpose jobs, grouped by side and element width
+  // plane jobs, grouped by side and element width
   for (int grp = 0; grp < 4; ++grp) {
     const bool bside = grp >= 2;
     const int want_eb = (grp & 1) ? 2 : 1;
@@ -240,9 +235,8 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
         q.out = wbase + L.a_off;
         for (int jj = 0; jj < p.e; ++jj) q.mask[jj] = amask[jj];
       } else {
-        q.X = wbase + L.t_off;
-        q.ldx = p.k;
-        q.vec = (p.k * L.eb) % 16 == 0;
+        q.X = p.B;  // k x n: the plane rows are its columns
+        q.ldx = p.n;
         q.rows = p.n;
         q.rows_p = L.groups * L.G;
         q.P = p.e * p.e;
@@ -257,31 +251,11 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
         return M4RIE_ERR_UNSUPPORTED;
       }
       pstart.push_back(pblocks[grp]);
-      pblocks[grp] += pack_job_blocks(q);
+      pblocks[grp] += bside ? cols_job_blocks(q) : pack_job_blocks(q);
       pjobs.push_back(q);
       ++pcount[grp];
     }
     pstart.push_back(pblocks[grp]);  // group terminator (not read by the kernel)
-  }
-  for (int grp = 0; grp < 2; ++grp) {
-    const int want_eb = grp ? 2 : 1;
-    for (int i : live) {
-      const m4rie_problem& p = pr[i];
-      const Layout& L = lay[i];
-      if (L.eb != want_eb) continue;
-      TransposeJob x{};
-      x.X = p.B;
-      x.ldx = p.n;
-      x.K = p.k;
-      x.rows = p.n;
-      x.Xt = wbase + L.t_off;
-      x.vec = ((uintptr_t)p.B & 15u) == 0 && (p.n * L.eb) % 16 == 0 && (p.k * L.eb) % 16 == 0;
-      xstart.push_back(xblocks[grp]);
-      xblocks[grp] += transpose_job_blocks(x);
-      xjobs.push_back(x);
-      ++xcount[grp];
-    }
-    xstart.push_back(xblocks[grp]);
   }
   if (nl) {
     err = cudaMemcpy(dbase + off_tjobs, tjobs.data(), sizeof(TcJob) * nl, cudaMemcpyHostToDevice);
@@ -289,10 +263,6 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
       err = cudaMemcpy(dbase + off_pjobs, pjobs.data(), sizeof(PackParams) * pjobs.size(), cudaMemcpyHostToDevice);
     if (err == cudaSuccess)
       err = cudaMemcpy(dbase + off_pstart, pstart.data(), sizeof(int64_t) * pstart.size(), cudaMemcpyHostToDevice);
-    if (err == cudaSuccess)
-      err = cudaMemcpy(dbase + off_xjobs, xjobs.data(), sizeof(TransposeJob) * xjobs.size(), cudaMemcpyHostToDevice);
-    if (err == cudaSuccess)
-      err = cudaMemcpy(dbase + off_xstart, xstart.data(), sizeof(int64_t) * xstart.size(), cudaMemcpyHostToDevice);
     if (err == cudaSuccess)
       err = cudaMemcpy(dbase + off_tilejob, tile_job.data(), sizeof(int) * tile_job.size(), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) return fail(ctx, err, plan);
@@ -309,20 +279,15 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
     if (rec == cudaSuccess)
       rec = cudaMemsetAsync(pr[i].C, 0, (size_t)(pr[i].m * pr[i].n) * (pr[i].e <= 8 ? 1 : 2), plan->cap);
   {
-    const auto* xj = reinterpret_cast<const TransposeJob*>(dbase + off_xjobs);
-    const auto* xs = reinterpret_cast<const int64_t*>(dbase + off_xstart);
-    if (rec == cudaSuccess) rec = launch_transpose_batched(xj, xs, xcount[0], xblocks[0], 1, plan->cap, &launches);
-    if (rec == cudaSuccess)
-      rec = launch_transpose_batched(xj + xcount[0], xs + xcount[0] + 1, xcount[1], xblocks[1], 2, plan->cap, &launches);
-  }
-  {
     const auto* pj = reinterpret_cast<const PackParams*>(dbase + off_pjobs);
     const auto* ps = reinterpret_cast<const int64_t*>(dbase + off_pstart);
     int jo = 0, so = 0;
     for (int grp = 0; grp < 4; ++grp) {
       if (rec == cudaSuccess)
-        rec = launch_pack_batched(pj + jo, ps + so, pcount[grp], pblocks[grp], fmt, (grp & 1) ? 2 : 1, plan->cap,
-                                  &launches);
+        rec = grp >= 2 ? launch_cols_batched(pj + jo, ps + so, pcount[grp], pblocks[grp], fmt, (grp & 1) ? 2 : 1,
+                                             plan->cap, &launches)
+                       : launch_pack_batched(pj + jo, ps + so, pcount[grp], pblocks[grp], fmt, (grp & 1) ? 2 : 1,
+                                             plan->cap, &launches);
       jo += pcount[grp];
       so += pcount[grp] + 1;
     }

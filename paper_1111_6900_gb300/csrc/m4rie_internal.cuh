@@ -88,7 +88,7 @@ bool plane_offsets(PackParams& p);
 // Pack launchers (pack.cu).  launch_pack_planes: rows of X (rows x K, row
 // stride ldx) are the planes' rows.  launch_pack_cols: columns of X (K x rows,
 // row stride ldx) are the planes' rows, transposed on the way through shared
-// memory.  launch_transpose serves the batched path, which transposes first.
+// memory.  launch_transpose serves the entry point without allocation.
 cudaError_t launch_pack_planes(const PackParams& p, cudaStream_t s, int64_t* launches);
 cudaError_t launch_pack_cols(const PackParams& p, cudaStream_t s, int64_t* launches);
 // Both at once (A by rows, B by columns) in one launch.
@@ -98,18 +98,15 @@ cudaError_t launch_transpose(const void* X, int64_t ldx, int64_t K, int64_t rows
 
 // Batched forms: job j owns blocks [start[j], start[j+1]) of one launch (all
 // jobs of a launch share the element width and the plane format).
-struct TransposeJob {
-  const void* X;
-  int64_t ldx, K, rows;
-  void* Xt;
-  int vec;
-};
 int64_t pack_job_blocks(const PackParams& p);
-int64_t transpose_job_blocks(const TransposeJob& j);
 cudaError_t launch_pack_batched(const PackParams* d_jobs, const int64_t* d_start, int njobs, int64_t blocks, int fmt,
                                 int elem_bytes, cudaStream_t s, int64_t* launches);
-cudaError_t launch_transpose_batched(const TransposeJob* d_jobs, const int64_t* d_start, int njobs, int64_t blocks,
-                                     int elem_bytes, cudaStream_t s, int64_t* launches);
+
+// Column planes of many jobs (X read by columns, no transpose): blocks per job
+// and the launch over the job table (same conventions as the row version).
+int64_t cols_job_blocks(const PackParams& p);
+cudaError_t launch_cols_batched(const PackParams* d_jobs, const int64_t* d_start, int njobs, int64_t blocks, int fmt,
+                                int elem_bytes, cudaStream_t s, int64_t* launches);
 
 // Public slice format (Section 3.2): pack.cu.
 cudaError_t launch_slice(int e, int64_t rows, int64_t cols, const void* elems, uint64_t* slices,

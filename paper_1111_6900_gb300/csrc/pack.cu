@@ -416,6 +416,32 @@ __global__ void __launch_bounds__(256) pack_planes_batched(const PackParams* __r
                               r < p.rows_p ? r : 0, p.rows_p);
 }
 
+// Column planes of many jobs in one launch (the B operands of a batch, read
+// by columns through shared memory, no transpose): block b belongs to job j
+// with start[j] <= b < start[j+1] and covers its column tile l % gx, k tiles
+// l / gx, l / gx + gy, ... (l = b - start[j], gx, gy as in launch_pack_cols).
+__host__ __device__ inline void cols_shape(const PackParams& p, int64_t& gx, int64_t& gy) {
+  gx = (p.rows_p + 63) / 64;
+  gy = (p.Kp + 127) / 128;
+  if (gy > 65535) gy = 65535;
+}
+
+template <typename T, int FMT>
+__global__ void __launch_bounds__(256) pack_cols_batched(const PackParams* __restrict__ jobs,
+                                                         const int64_t* __restrict__ start, int njobs) {
+  constexpr int E = sizeof(T) == 1 ? 8 : 10;
+  __shared__ PlaneSmem sm;
+  __shared__ uint32_t tile[col_tile_words<T>()];
+  __shared__ int sj;
+  if (threadIdx.x == 0) sj = find_job(start, njobs, blockIdx.x);
+  __syncthreads();
+  const PackParams& p = jobs[sj];
+  int64_t gx, gy;
+  cols_shape(p, gx, gy);
+  const int64_t l = (int64_t)blockIdx.x - start[sj];
+  cols_body<T, FMT, E>(p, (uint32_t)(l % gx), (uint32_t)(l / gx), (uint32_t)gy, sm.mexp, tile);
+}
+
 // ---- Element transpose X (K x rows, row-major) -> Xt (rows x K), tiles of
 // 64 x 64 elements through shared memory (one 32-bit word per element).
 template <typename T>
@@ -476,20 +502,6 @@ __global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ X,
   transpose_tiles<T>(X, ldx, K, rows, Xt, vec, (int64_t)blockIdx.x * 64, blockIdx.y, gridDim.y, tile);
 }
 
-// Many transposes in one launch (block ranges per job as in pack_planes_batched).
-template <typename T>
-__global__ void __launch_bounds__(256) transpose_batched(const TransposeJob* __restrict__ jobs,
-                                                         const int64_t* __restrict__ start, int njobs) {
-  __shared__ uint32_t tile[64][65];
-  __shared__ int sj;
-  if (threadIdx.x == 0) sj = find_job(start, njobs, blockIdx.x);
-  __syncthreads();
-  const TransposeJob& j = jobs[sj];
-  const int64_t gx = (j.rows + 63) / 64;
-  const int64_t l = (int64_t)blockIdx.x - start[sj];
-  transpose_tiles<T>(static_cast<const T*>(j.X), j.ldx, j.K, j.rows, static_cast<T*>(j.Xt), j.vec, (l % gx) * 64,
-                     l / gx, (j.K + 63) / 64, tile);
-}
 
 // ---- Public slice format: one warp per (row, 64-bit word).
 template <typename T>
@@ -807,17 +819,32 @@ int64_t pack_job_blocks(const PackParams& p) {
   return gx * ceil_div(p.rows_p, rpb);
 }
 
-int64_t transpose_job_blocks(const TransposeJob& j) { return ceil_div(j.rows, 64) * ceil_div(j.K, 64); }
+int64_t cols_job_blocks(const PackParams& p) {
+  int64_t gx, gy;
+  cols_shape(p, gx, gy);
+  return gx * gy;
+}
 
-cudaError_t launch_transpose_batched(const TransposeJob* d_jobs, const int64_t* d_start, int njobs, int64_t blocks,
-                                     int elem_bytes, cudaStream_t s, int64_t* launches) {
+cudaError_t launch_cols_batched(const PackParams* d_jobs, const int64_t* d_start, int njobs, int64_t blocks, int fmt,
+                                int elem_bytes, cudaStream_t s, int64_t* launches) {
   if (njobs <= 0 || blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  if (elem_bytes == 2) transpose_batched<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(d_jobs, d_start, njobs);
-  else transpose_batched<uint8_t><<<(unsigned)blocks, 256, 0, s>>>(d_jobs, d_start, njobs);
+  const unsigned g = (unsigned)blocks;
+  const bool u16 = elem_bytes == 2;
+  if (fmt == kFmtBit) {
+    if (u16) pack_cols_batched<uint16_t, kFmtBit><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+    else pack_cols_batched<uint8_t, kFmtBit><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+  } else if (fmt == kFmtByte) {
+    if (u16) pack_cols_batched<uint16_t, kFmtByte><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+    else pack_cols_batched<uint8_t, kFmtByte><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+  } else {
+    if (u16) pack_cols_batched<uint16_t, kFmtNib><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+    else pack_cols_batched<uint8_t, kFmtNib><<<g, 256, 0, s>>>(d_jobs, d_start, njobs);
+  }
   if (launches) ++*launches;
   return cudaGetLastError();
 }
+
 
 cudaError_t launch_slice(int e, int64_t rows, int64_t cols, const void* elems, uint64_t* slices, int64_t ld_words,
                          int* status, cudaStream_t s, int64_t* launches) {
