@@ -31,6 +31,19 @@
  *  - Zero sizes: m == 0 or n == 0 is a no-op.  k == 0 makes m4rie_mul write
  *    zeros to C and leaves C unchanged for m4rie_addmul.
  *  - Errors never trap or abort on the device.
+ *
+ * Environment variables read by m4rie_create (tuning and measurement):
+ *  - M4RIE_TUNE_CACHE: autotuner cache file to load (see m4rie_tune_load).
+ *  - M4RIE_TC_CHUNK: entries per FP32 accumulation chunk of the tcgen05 forms
+ *    (at most 2^21, so that every count stays below 2^23).
+ *  - M4RIE_TC_CLUSTER: tcgen05 tiles on 2-SM pairs (3, default), on CTA pairs
+ *    sharing B tiles (2) or on single CTAs (1).
+ *  - M4RIE_F4_KIND=nvf4: FP4 products with kind::mxf4nvf4 instead of kind::mxf4.
+ *  - M4RIE_PDL=0: launch kernels without programmatic dependent launch.
+ *  - M4RIE_FUSE_RECOMBINE=1: Karatsuba on 2-SM pairs (e <= 8) recombines in the
+ *    GEMM's epilogue instead of a separate kernel (slower on the measured
+ *    shapes; off by default).
+ *  - M4RIE_ZERO_COPY=0: m4rie_mul_host always stages through device memory.
  */
 #ifndef M4RIE_GPU_H
 #define M4RIE_GPU_H
@@ -224,8 +237,9 @@ m4rie_status m4rie_mul_packed(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int6
  * `count` descriptors (reserved fields zero), validated like m4rie_mul; no
  * output may overlap another output or any input (M4RIE_ERR_ALIAS).
  * With the AUTO, TC_F4 or TC_F8 form the products use the alpha^j-B schedule
- * on the tcgen05 tensor cores: one batched transpose, one batched operand-plane
- * kernel per side and one persistent GEMM over the tiles of all products.
+ * on the tcgen05 tensor cores: one batched operand-plane kernel per side (the
+ * B operands read by columns) and one persistent GEMM over the tiles of all
+ * products.
  * That work is recorded once into a CUDA graph, cached in the context with
  * its own device memory, and replayed while the same descriptor array contents
  * are passed (a different array rebuilds it; the first call synchronises the
