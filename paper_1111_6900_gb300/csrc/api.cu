@@ -588,6 +588,10 @@ void m4rie_destroy(m4rie_ctx* ctx) {
     if (ev) cudaEventDestroy(ev);
   if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
   if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
+  for (cudaEvent_t ev : ctx->ech_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->ech_side) cudaStreamDestroy(ctx->ech_side);
+  if (ctx->ech_po_host) cudaFreeHost(ctx->ech_po_host);
   for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
   destroy_plan(ctx->plan);
   delete ctx;

@@ -64,6 +64,10 @@ struct m4rie_ctx {
   int zero_copy = 1;
   // pipelined host-buffer products: copy streams and their events
   cudaStream_t s_in = nullptr, s_out = nullptr;
+  // echelon form look-ahead: side stream, its two events, pinned pivot list
+  cudaStream_t ech_side = nullptr;
+  cudaEvent_t ech_ev[2] = {};
+  void* ech_po_host = nullptr;
   cudaEvent_t io_ev[2 * m4rie::kIoPanels] = {};
   int group_m = 0;      // tcgen05 tile raster: m-tiles per column group (0: all m-tiles)
   m4rie::TuneEntry tuned[11][64];  // [e][floor(log2(m*n*k))] -> autotuned choice (form 0: none)

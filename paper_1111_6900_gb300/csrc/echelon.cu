@@ -364,6 +364,18 @@ m4rie_status echelon_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t 
   int* d_count = ws.cand + R;
 
 
+  // look-ahead: the next panel's factorisation on a side stream (non-blocking,
+  // ordered against ctx->stream by events), its pivot list into pinned memory
+  if (!ctx->ech_side) {
+    if ((err = cudaStreamCreateWithFlags(&ctx->ech_side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&ctx->ech_ev[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&ctx->ech_ev[1], cudaEventDisableTiming)) != cudaSuccess ||
+        (err = cudaMallocHost(&ctx->ech_po_host, sizeof(PanelOut))) != cudaSuccess)
+      return fail(ctx, err);
+  }
+  PanelOut* hpo_next = static_cast<PanelOut*>(ctx->ech_po_host);
+  bool ahead = false;  // the current panel's round-0 factorisation was launched by the previous panel
+
   std::vector<int64_t> piv_cols;
   int64_t r = 0;
   std::vector<int> src, dst, hc(R + 1);
@@ -397,13 +409,24 @@ m4rie_status echelon_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t 
         if ((err = move_rows<T>(ctx, ws, 0, A, lda, c0, nt, src, dst)) != cudaSuccess) return fail(ctx, err);
       }
       // 2. pivots of the candidate block and M^{-1}
-      if ((err = launch_panel_bitsliced<T>(e, A, lda, r, c0, cnt, wc, done, f, ctx->d_gf, ws.po,
-                                           reinterpret_cast<T*>(ws.minv), ctx->d_status, ctx->stream)) != cudaSuccess)
-        return fail(ctx, err);
-      ++ctx->launches;
-      if ((err = cudaMemcpyAsync(&hpo, ws.po, sizeof(PanelOut), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess ||
-          (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
-        return fail(ctx, err);
+      if (round == 0 && ahead) {
+        // launched on the side stream while the previous panel's update ran
+        if ((err = cudaEventSynchronize(ctx->ech_ev[1])) != cudaSuccess ||
+            (err = cudaStreamWaitEvent(ctx->stream, ctx->ech_ev[1], 0)) != cudaSuccess)
+          return fail(ctx, err);
+        hpo = *hpo_next;
+        ahead = false;
+      } else {
+        if ((err = launch_panel_bitsliced<T>(e, A, lda, r, c0, cnt, wc, done, f, ctx->d_gf, ws.po,
+                                             reinterpret_cast<T*>(ws.minv), ctx->d_status, ctx->stream)) !=
+            cudaSuccess)
+          return fail(ctx, err);
+        ++ctx->launches;
+        if ((err = cudaMemcpyAsync(&hpo, ws.po, sizeof(PanelOut), cudaMemcpyDeviceToHost, ctx->stream)) !=
+                cudaSuccess ||
+            (err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+          return fail(ctx, err);
+      }
       const int k = hpo.k;
       if (k <= 0) {
         if (round == 0) continue;  // no pivot among the next R rows: search all rows
@@ -436,7 +459,34 @@ m4rie_status echelon_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t 
       T* Ar = A + r * lda + c0;
       m4rie_status st = run_gemm(ctx, e, f, k, nt, k, Mats{ws.minv, W, Ar, lda, ws.X, nt}, 0);
       if (st != M4RIE_OK) return st;
-      if ((st = run_gemm(ctx, e, f, m, nt, k, Mats{ws.mult, W, ws.X, nt, A + c0, lda}, 1)) != M4RIE_OK) return st;
+      uint64_t done_after = done;
+      for (int a = 0; a < k; ++a) done_after |= 1ull << hpo.cols[a];
+      const bool last = __builtin_popcountll(done_after) == wc || r + k >= m;
+      // Look-ahead (last round of a panel, with a next panel and candidates for
+      // it): update this panel's and the next panel's columns first, start the
+      // next panel's factorisation on the side stream, then update the rest.
+      const int64_t r_next = r + k, c_next = c0 + W;
+      const bool look = last && c_next < n && r_next < m && nt > 2 * W;
+      const int64_t n1 = look ? 2 * W : nt;
+      if ((st = run_gemm(ctx, e, f, m, n1, k, Mats{ws.mult, W, ws.X, nt, A + c0, lda}, 1)) != M4RIE_OK) return st;
+      if (look) {
+        const int cnt_next = (int)std::min<int64_t>(R, m - r_next);
+        const int wc_next = (int)std::min<int64_t>(W, n - c_next);
+        if ((err = cudaEventRecord(ctx->ech_ev[0], ctx->stream)) != cudaSuccess ||
+            (err = cudaStreamWaitEvent(ctx->ech_side, ctx->ech_ev[0], 0)) != cudaSuccess ||
+            (err = launch_panel_bitsliced<T>(e, A, lda, r_next, c_next, cnt_next, wc_next, 0, f, ctx->d_gf, ws.po,
+                                             reinterpret_cast<T*>(ws.minv), ctx->d_status, ctx->ech_side)) !=
+                cudaSuccess ||
+            (err = cudaMemcpyAsync(hpo_next, ws.po, sizeof(PanelOut), cudaMemcpyDeviceToHost, ctx->ech_side)) !=
+                cudaSuccess ||
+            (err = cudaEventRecord(ctx->ech_ev[1], ctx->ech_side)) != cudaSuccess)
+          return fail(ctx, err);
+        ++ctx->launches;
+        ahead = true;
+        if ((st = run_gemm(ctx, e, f, m, nt - n1, k, Mats{ws.mult, W, ws.X + n1 * w, nt, A + c0 + n1, lda}, 1)) !=
+            M4RIE_OK)
+          return st;
+      }
       if ((err = cudaMemcpy2DAsync(Ar, (size_t)lda * w, ws.X, (size_t)nt * w, (size_t)nt * w, (size_t)k,
                                    cudaMemcpyDeviceToDevice, ctx->stream)) != cudaSuccess)
         return fail(ctx, err);
@@ -469,6 +519,7 @@ m4rie_status echelon_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t 
     }
     piv_cols.insert(piv_cols.end(), panel_cols.begin(), panel_cols.end());
   }
+  if (ahead && (err = cudaEventSynchronize(ctx->ech_ev[1])) != cudaSuccess) return fail(ctx, err);
   if ((err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return fail(ctx, err);
   if (rank) *rank = r;
   if (pivots)
