@@ -61,7 +61,6 @@ __device__ __forceinline__ void flag_range(int* status, bool bad) {
 }
 
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
-__device__ __forceinline__ uint32_t word(const uint4& a, int j) { return j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : a.w; }
 
 // x * (every field of w) in F2[x]/<f>, all fields at once: shift each field up
 // by one and add f's low part where the top coefficient fell out.
@@ -274,6 +273,49 @@ __device__ __forceinline__ void store_word(const NjParams& p, int64_t r, int64_t
     }
 }
 
+// Store the four packed words w0 .. w0 + 3 of row r of C (the 16 bytes of
+// one lane).  Element output with whole, aligned words: every old value of
+// the four words is loaded before any store, so the loads' latencies overlap
+// (a store could alias a later load, so the compiler keeps them in order).
+// Otherwise word by word.
+template <int E>
+__device__ __forceinline__ void store_quad(const NjParams& p, int64_t r, int64_t w0, const uint4& val, bool& bad) {
+  using S = Nj<E>;
+  constexpr int Q = epw<E>();
+  const int64_t c0 = w0 * S::P;
+  if (!p.packed && p.vec_c && c0 + 4 * S::P <= p.n) {
+    uint32_t* dst = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(p.C) + (r * p.ldc + c0) * S::EB);
+    uint32_t x[4][Q];
+    elements_of<E>(val.x, x[0]);
+    elements_of<E>(val.y, x[1]);
+    elements_of<E>(val.z, x[2]);
+    elements_of<E>(val.w, x[3]);
+    if (p.add) {
+      uint32_t old[4][Q];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) old[j][q] = dst[j * Q + q];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          bad |= (old[j][q] & ~S::ELEMS) != 0;
+          x[j][q] ^= old[j][q] & S::ELEMS;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) dst[j * Q + q] = x[j][q];
+    return;
+  }
+  if (w0 < p.nw) store_word<E>(p, r, w0, val.x, bad);
+  if (w0 + 1 < p.nw) store_word<E>(p, r, w0 + 1, val.y, bad);
+  if (w0 + 2 < p.nw) store_word<E>(p, r, w0 + 2, val.z, bad);
+  if (w0 + 3 < p.nw) store_word<E>(p, r, w0 + 3, val.w, bad);
+}
+
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -405,10 +447,7 @@ __global__ void __launch_bounds__(kThreads, 2) nj_kernel(const __grid_constant__
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int64_t r = r0 + (warp * R + i) * G + g;
-      if (r < p.m)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (w0 + j < p.nw) store_word<E>(p, r, w0 + j, word(acc[i], j), bad);
+      if (r < p.m) store_quad<E>(p, r, w0, acc[i], bad);
     }
   } else {
     // XOR the partial tiles of the cluster's CTAs (one k range each): every
@@ -427,10 +466,7 @@ __global__ void __launch_bounds__(kThreads, 2) nj_kernel(const __grid_constant__
       for (int s = 0; s < p.ks; ++s) val = xor4(val, ld_cluster4(sC + q, (uint32_t)s));
       const int64_t r = r0 + (q >> ll);
       const int64_t wq = ((int64_t)blockIdx.y * L + (q & (L - 1))) * 4;
-      if (r < p.m)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (wq + j < p.nw) store_word<E>(p, r, wq + j, word(val, j), bad);
+      if (r < p.m) store_quad<E>(p, r, wq, val, bad);
     }
     cluster_sync_all();  // no CTA leaves while another still reads its tile
   }
