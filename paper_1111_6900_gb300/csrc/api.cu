@@ -491,6 +491,8 @@ m4rie_status run_newton_john(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64
     p.vec_a = rows4(x.A, x.lda);
     p.vec_b = rows4(x.B, x.ldb);
     p.vec_c = rows4(x.C, x.ldc);
+    p.vec16_b = aligned16(x.B) && (x.ldb * w) % 16 == 0;
+    p.vec16_c = aligned16(x.C) && (x.ldc * w) % 16 == 0;
   }
   const NjPlan pl = plan_newton_john(e, m, n, k, packed, ctx->num_sms);
   cudaError_t err = launch_newton_john(e, p, pl, ctx->stream, &ctx->launches);

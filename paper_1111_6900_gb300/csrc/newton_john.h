@@ -22,6 +22,7 @@ struct NjParams {
   uint32_t flow;  // f without its x^e term
   int* status;    // sticky device status word
   int vec_a, vec_b, vec_c;  // element rows of A / B / C start on 4-byte boundaries: 32-bit accesses allowed
+  int vec16_b, vec16_c;    // element rows of B / C start on 16-byte boundaries: 16-byte accesses allowed
   int pdl;        // launch with programmatic dependent launch
   // filled by launch_newton_john from the plan
   int64_t nw;     // 32-bit words per packed row of B and C

@@ -184,6 +184,38 @@ __device__ __forceinline__ uint32_t load_b_word(const NjParams& p, int64_t t, in
   return w;
 }
 
+// The four packed words w0 .. w0 + 3 of row t of B (one lane's 16 bytes of
+// table row).  A lane's words cover 16 * epw bytes of elements, a multiple of
+// 16 that starts on a 16-byte boundary when the rows do: whole words then come
+// from 16-byte loads (a quarter of the 32-bit loads, each warp access touching
+// as many cache lines); otherwise word by word.
+template <int E>
+__device__ __forceinline__ uint4 load_b_quad(const NjParams& p, int64_t t, int64_t w0, bool& bad) {
+  using S = Nj<E>;
+  constexpr int Q = epw<E>();
+  const int64_t c0 = w0 * S::P;
+  if (!p.packed && p.vec16_b && c0 + 4 * S::P <= p.n) {
+    const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(p.B) + (t * p.ldb + c0) * S::EB);
+    uint32_t x[4 * Q];
+#pragma unroll
+    for (int u = 0; u < Q; ++u) {
+      const uint4 v = __ldg(src + u);
+      x[4 * u] = v.x;
+      x[4 * u + 1] = v.y;
+      x[4 * u + 2] = v.z;
+      x[4 * u + 3] = v.w;
+    }
+#pragma unroll
+    for (int q = 0; q < 4 * Q; ++q) {
+      bad |= (x[q] & ~S::ELEMS) != 0;
+      x[q] &= S::ELEMS;
+    }
+    return make_uint4(fields_of<E>(x), fields_of<E>(x + Q), fields_of<E>(x + 2 * Q), fields_of<E>(x + 3 * Q));
+  }
+  return make_uint4(load_b_word<E>(p, t, w0, bad), load_b_word<E>(p, t, w0 + 1, bad),
+                    load_b_word<E>(p, t, w0 + 2, bad), load_b_word<E>(p, t, w0 + 3, bad));
+}
+
 // AW consecutive entries (r, t .. t + AW) of A in one 32-bit word (zero
 // outside A), as staged in shared memory.
 template <int E>
@@ -276,13 +308,39 @@ __device__ __forceinline__ void store_word(const NjParams& p, int64_t r, int64_t
 // Store the four packed words w0 .. w0 + 3 of row r of C (the 16 bytes of
 // one lane).  Element output with whole, aligned words: every old value of
 // the four words is loaded before any store, so the loads' latencies overlap
-// (a store could alias a later load, so the compiler keeps them in order).
-// Otherwise word by word.
+// (a store could alias a later load, so the compiler keeps them in order);
+// 16-byte accesses where the rows start on 16-byte boundaries (the lane's
+// 16 * epw bytes then do too), else 32-bit ones.  Otherwise word by word.
 template <int E>
 __device__ __forceinline__ void store_quad(const NjParams& p, int64_t r, int64_t w0, const uint4& val, bool& bad) {
   using S = Nj<E>;
   constexpr int Q = epw<E>();
   const int64_t c0 = w0 * S::P;
+  if (!p.packed && p.vec16_c && c0 + 4 * S::P <= p.n) {
+    uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(p.C) + (r * p.ldc + c0) * S::EB);
+    uint32_t x[4 * Q];
+    elements_of<E>(val.x, x);
+    elements_of<E>(val.y, x + Q);
+    elements_of<E>(val.z, x + 2 * Q);
+    elements_of<E>(val.w, x + 3 * Q);
+    if (p.add) {
+      uint4 old[Q];
+#pragma unroll
+      for (int u = 0; u < Q; ++u) old[u] = dst[u];
+#pragma unroll
+      for (int u = 0; u < Q; ++u) {
+        const uint32_t o[4] = {old[u].x, old[u].y, old[u].z, old[u].w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          bad |= (o[c] & ~S::ELEMS) != 0;
+          x[4 * u + c] ^= o[c] & S::ELEMS;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < Q; ++u) dst[u] = make_uint4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
+    return;
+  }
   if (!p.packed && p.vec_c && c0 + 4 * S::P <= p.n) {
     uint32_t* dst = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(p.C) + (r * p.ldc + c0) * S::EB);
     uint32_t x[4][Q];
@@ -371,12 +429,7 @@ __global__ void __launch_bounds__(kThreads, 2) nj_kernel(const __grid_constant__
     for (int n = 0; n < NBI; ++n) {
       const int tl = (warp + kWarps * n) / NT;
       bq[n] = make_uint4(0, 0, 0, 0);
-      if (tl < kt) {
-        bq[n].x = load_b_word<E>(p, t0 + tl, w0, bad);
-        bq[n].y = load_b_word<E>(p, t0 + tl, w0 + 1, bad);
-        bq[n].z = load_b_word<E>(p, t0 + tl, w0 + 2, bad);
-        bq[n].w = load_b_word<E>(p, t0 + tl, w0 + 3, bad);
-      }
+      if (tl < kt) bq[n] = load_b_quad<E>(p, t0 + tl, w0, bad);
     }
 #pragma unroll
     for (int n = 0; n < S::PW0; ++n) {

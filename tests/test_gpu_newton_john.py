@@ -168,6 +168,64 @@ def test_newton_john_windows(ctx, e):
     np.testing.assert_array_equal(dC.cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("e", ALL_E)
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_newton_john_16_byte_rows(ctx, e, accumulate):
+    """Rows of B and C on 16-byte boundaries (n = 208 elements): a lane's whole
+    words move as 16-byte vectors; for e <= 4 the last words of a row are a
+    partial group of four and go one by one."""
+    f = workloads.FIELD_POLY[e]
+    A, B, C = workloads.random_problem(e, 150, 208, 70, seed=e + 40, with_c=True)
+    if accumulate:
+        np.testing.assert_array_equal(nj_mul(ctx, e, A, B, C), oracle.addmul(e, f, A, B, C))
+    else:
+        np.testing.assert_array_equal(nj_mul(ctx, e, A, B), oracle.matmul(e, f, A, B))
+
+
+@pytest.mark.parametrize("e", [2, 4, 8, 10])
+def test_newton_john_16_byte_windows(ctx, e):
+    """Windows whose rows start on 16-byte boundaries (16-byte path) inside
+    larger matrices: nothing outside the window of C changes."""
+    f = workloads.FIELD_POLY[e]
+    rng = np.random.default_rng(e + 200)
+    bigA = workloads.elements(rng, e, (90, 120))
+    bigB = workloads.elements(rng, e, (130, 240))
+    bigC = workloads.elements(rng, e, (70, 256))
+    dA, dB, dC = dev(bigA), dev(bigB), dev(bigC)
+    ctx.set_form("newton_john")
+    try:
+        ctx.gemm(e, f, dA[3:63, 10:110], dB[5:105, 16:224], dC[4:64, 32:240], accumulate=True)
+        torch.cuda.synchronize()
+        assert ctx.device_status() == m4.OK
+    finally:
+        ctx.set_form("auto")
+    want = bigC.copy()
+    want[4:64, 32:240] = oracle.addmul(e, f, bigA[3:63, 10:110], bigB[5:105, 16:224], bigC[4:64, 32:240])
+    np.testing.assert_array_equal(dC.cpu().numpy(), want)
+
+
+def test_newton_john_16_byte_range_flag(ctx):
+    """Entries >= 2^e in B and in the old C, inside words that take the 16-byte
+    path: the status says so and the product uses their low e bits."""
+    e = 4
+    f = workloads.FIELD_POLY[e]
+    A, B, C = workloads.random_problem(e, 64, 256, 40, seed=77, with_c=True)
+    B2, C2 = B.copy(), C.copy()
+    B2[11, 5] = 0xF3
+    C2[9, 130] = 0x5A
+    ctx.set_form("newton_john")
+    try:
+        dC = dev(C2)
+        ctx.addmul(e, f, dev(A), dev(B2), dC)
+        torch.cuda.synchronize()
+        assert ctx.device_status() == m4.ERR_RANGE
+    finally:
+        ctx.set_form("auto")
+    B2[11, 5] &= 15
+    C2[9, 130] &= 15
+    np.testing.assert_array_equal(dC.cpu().numpy(), oracle.addmul(e, f, A, B2, C2))
+
+
 def test_newton_john_range_flag(ctx):
     e = 5
     A, B, _ = workloads.random_problem(e, 40, 30, 50, seed=5)
