@@ -82,7 +82,7 @@ m4rie_status validate_mats(int e, uint32_t f, int64_t m, int64_t n, int64_t k, c
   if (m > (1ll << 31) || n > (1ll << 31) || k > (1ll << 31)) return M4RIE_ERR_ARG;
   if (x.lda < k || x.ldb < n || x.ldc < n || x.lda > (1ll << 40) || x.ldb > (1ll << 40) || x.ldc > (1ll << 40))
     return M4RIE_ERR_ARG;
-  if ((m * k && !x.A) || (k * n && !x.B) || (m * n && !x.C)) return M4RIE_ERR_ARG;
+  if ((m > 0 && k > 0 && !x.A) || (k > 0 && n > 0 && !x.B) || (m > 0 && n > 0 && !x.C)) return M4RIE_ERR_ARG;
   const size_t w = elem_bytes(e);
   const size_t sc = span_bytes(m, n, x.ldc, w);
   if (overlaps(x.C, sc, x.A, span_bytes(m, k, x.lda, w)) ||
@@ -661,7 +661,7 @@ m4rie_status m4rie_mul_host(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_
   if (st != M4RIE_OK) return st;
   const size_t w = elem_bytes(e);
   const double total = (double)(m * k + k * n + (accumulate ? 2 : 1) * m * n) * (double)w;
-  if (ctx->zero_copy && m * k && k * n && m * n && total <= (double)(8 << 20)) {
+  if (ctx->zero_copy && m > 0 && n > 0 && k > 0 && total <= (double)(8 << 20)) {
     // Small products on pinned buffers the GPU can address: the kernels read
     // A and B and write C in host memory directly (over the CPU-GPU link), no
     // staging copies.  (Large ones stage: the copy engines move about 200 GB/s
@@ -732,14 +732,16 @@ m4rie_status m4rie_mul_host(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_
     err = cudaStreamSynchronize(ctx->s_out);
     return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
   }
-  if (m * k) err = cudaMemcpyAsync(dA, hA, m * k * w, cudaMemcpyHostToDevice, ctx->stream);
-  if (err == cudaSuccess && k * n) err = cudaMemcpyAsync(dB, hB, k * n * w, cudaMemcpyHostToDevice, ctx->stream);
-  if (err == cudaSuccess && accumulate && m * n)
+  if (m > 0 && k > 0) err = cudaMemcpyAsync(dA, hA, m * k * w, cudaMemcpyHostToDevice, ctx->stream);
+  if (err == cudaSuccess && k > 0 && n > 0)
+    err = cudaMemcpyAsync(dB, hB, k * n * w, cudaMemcpyHostToDevice, ctx->stream);
+  if (err == cudaSuccess && accumulate && m > 0 && n > 0)
     err = cudaMemcpyAsync(dC, hC, m * n * w, cudaMemcpyHostToDevice, ctx->stream);
   if (err != cudaSuccess) return cuda_fail(ctx, err);
-  st = run_mul(ctx, e, f, m, n, k, m * k ? dA : nullptr, k * n ? dB : nullptr, m * n ? dC : nullptr, accumulate);
+  st = run_mul(ctx, e, f, m, n, k, m > 0 && k > 0 ? dA : nullptr, k > 0 && n > 0 ? dB : nullptr,
+               m > 0 && n > 0 ? dC : nullptr, accumulate);
   if (st != M4RIE_OK) return st;
-  if (m * n) err = cudaMemcpyAsync(hC, dC, m * n * w, cudaMemcpyDeviceToHost, ctx->stream);
+  if (m > 0 && n > 0) err = cudaMemcpyAsync(hC, dC, m * n * w, cudaMemcpyDeviceToHost, ctx->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
   return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
 }
@@ -748,8 +750,8 @@ m4rie_status m4rie_pack(m4rie_ctx* ctx, int e, int64_t rows, int64_t cols, const
                         int64_t ld_words) {
   if (!ctx || e < 2 || e > 10 || rows < 0 || cols < 0) return M4RIE_ERR_ARG;
   if (ld_words < (cols + 63) / 64) return M4RIE_ERR_ARG;
-  if (rows * cols && (!elems || !slices)) return M4RIE_ERR_ARG;
-  if (rows * ld_words && !slices) return M4RIE_ERR_ARG;
+  if (rows > 0 && cols > 0 && (!elems || !slices)) return M4RIE_ERR_ARG;
+  if (rows > 0 && ld_words > 0 && !slices) return M4RIE_ERR_ARG;
   if (overlaps(slices, (size_t)(e * rows * ld_words) * 8, elems, (size_t)(rows * cols) * elem_bytes(e)))
     return M4RIE_ERR_ALIAS;
   if (rows == 0 || ld_words == 0) return M4RIE_OK;
@@ -761,7 +763,7 @@ m4rie_status m4rie_unpack(m4rie_ctx* ctx, int e, int64_t rows, int64_t cols, con
                           void* elems) {
   if (!ctx || e < 2 || e > 10 || rows < 0 || cols < 0) return M4RIE_ERR_ARG;
   if (ld_words < (cols + 63) / 64) return M4RIE_ERR_ARG;
-  if (rows * cols && (!elems || !slices)) return M4RIE_ERR_ARG;
+  if (rows > 0 && cols > 0 && (!elems || !slices)) return M4RIE_ERR_ARG;
   if (overlaps(slices, (size_t)(e * rows * ld_words) * 8, elems, (size_t)(rows * cols) * elem_bytes(e)))
     return M4RIE_ERR_ALIAS;
   if (rows == 0 || cols == 0) return M4RIE_OK;
@@ -835,7 +837,7 @@ m4rie_status m4rie_mul_packed(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int6
   const int64_t kw = ceil_div(k, per), nw = ceil_div(n, per);
   if (lda < kw || ldb < nw || ldc < nw || lda > (1ll << 40) || ldb > (1ll << 40) || ldc > (1ll << 40))
     return M4RIE_ERR_ARG;
-  if ((m * k && !A) || (k * n && !B) || (m * n && !C)) return M4RIE_ERR_ARG;
+  if ((m > 0 && k > 0 && !A) || (k > 0 && n > 0 && !B) || (m > 0 && n > 0 && !C)) return M4RIE_ERR_ARG;
   const size_t sc = span_bytes(m, nw, ldc, 8);
   if (overlaps(C, sc, A, span_bytes(m, kw, lda, 8)) || overlaps(C, sc, B, span_bytes(k, nw, ldb, 8)))
     return M4RIE_ERR_ALIAS;

@@ -50,9 +50,9 @@ bool outputs_disjoint(int count, const m4rie_problem* pr) {
   iv.reserve(3 * count);
   for (int i = 0; i < count; ++i) {
     const uintptr_t w = pr[i].e <= 8 ? 1 : 2;
-    if (pr[i].m * pr[i].k) iv.push_back({(uintptr_t)pr[i].A, (uintptr_t)pr[i].A + w * pr[i].m * pr[i].k, false});
-    if (pr[i].k * pr[i].n) iv.push_back({(uintptr_t)pr[i].B, (uintptr_t)pr[i].B + w * pr[i].k * pr[i].n, false});
-    if (pr[i].m * pr[i].n) iv.push_back({(uintptr_t)pr[i].C, (uintptr_t)pr[i].C + w * pr[i].m * pr[i].n, true});
+    if (pr[i].m > 0 && pr[i].k > 0) iv.push_back({(uintptr_t)pr[i].A, (uintptr_t)pr[i].A + w * pr[i].m * pr[i].k, false});
+    if (pr[i].k > 0 && pr[i].n > 0) iv.push_back({(uintptr_t)pr[i].B, (uintptr_t)pr[i].B + w * pr[i].k * pr[i].n, false});
+    if (pr[i].m > 0 && pr[i].n > 0) iv.push_back({(uintptr_t)pr[i].C, (uintptr_t)pr[i].C + w * pr[i].m * pr[i].n, true});
   }
   std::sort(iv.begin(), iv.end(), [](const Interval& a, const Interval& b) { return a.lo < b.lo; });
   // sweep: the furthest-reaching interval seen so far, and the furthest-reaching output

@@ -539,7 +539,7 @@ m4rie_status m4rie_echelonize(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int6
   if (!ctx) return M4RIE_ERR_ARG;
   m4rie_status st = m4rie_validate(e, f, 0, 0, 0, nullptr, nullptr, nullptr);
   if (st != M4RIE_OK) return st;
-  if (m < 0 || n < 0 || m > (1ll << 31) - 1 || n > (1ll << 31) || lda < n || (m * n && !A)) return M4RIE_ERR_ARG;
+  if (m < 0 || n < 0 || m > (1ll << 31) - 1 || n > (1ll << 31) || lda < n || (m > 0 && n > 0 && !A)) return M4RIE_ERR_ARG;
   if (rank) *rank = 0;
   if (m == 0 || n == 0) return M4RIE_OK;
   if ((st = ensure_field_tables(ctx, e, f)) != M4RIE_OK) return st;

@@ -198,7 +198,7 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
 // One product of a batched persistent launch (element epilogue, alpha^j-B
 // layout).  Its tiles are global tiles [tile_start, tile_start + tiles_m *
 // tiles_n), m-fastest.  Tensor maps live in device memory with the job.
-struct alignas(64) TcJob {
+struct alignas(alignof(CUtensorMap)) TcJob {
   CUtensorMap ma, mb;
   void* C;
   int64_t m, n, ldc;

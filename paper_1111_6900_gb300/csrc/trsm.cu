@@ -378,10 +378,10 @@ m4rie_status run_trsm(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, c
   m4rie_status st = m4rie_validate(e, f, 0, 0, 0, nullptr, nullptr, nullptr);  // field checks
   if (st != M4RIE_OK) return st;
   if (m < 0 || n < 0 || m > (1ll << 31) || n > (1ll << 31) || ldt < m || ldb < n) return M4RIE_ERR_ARG;
-  if ((m && !T) || (m * n && !B)) return M4RIE_ERR_ARG;
+  if ((m > 0 && !T) || (m > 0 && n > 0 && !B)) return M4RIE_ERR_ARG;
   const size_t w = elem_w(e);
   const size_t st_bytes = m ? (size_t)((m - 1) * ldt + m) * w : 0;
-  const size_t sb_bytes = m * n ? (size_t)((m - 1) * ldb + n) * w : 0;
+  const size_t sb_bytes = m > 0 && n > 0 ? (size_t)((m - 1) * ldb + n) * w : 0;
   if (overlaps(B, sb_bytes, T, st_bytes)) return M4RIE_ERR_ALIAS;
   if (m == 0 || n == 0) return M4RIE_OK;
   if ((st = field_tables(ctx, e, f)) != M4RIE_OK) return st;
