@@ -76,13 +76,15 @@ def kernel_traffic(key):
         return None
     fname, sha = PROFILED_SOURCES[key]
     path = os.path.join(ROOT, "paper_1111_6900_gb300", "csrc", fname)
-    cur = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    with open(path, "rb") as fh:
+        cur = hashlib.sha256(fh.read()).hexdigest()
     return t["bytes"] if sha is None or sha == cur else None
 
 
 def peaks():
     try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
     except Exception:
         return None
 

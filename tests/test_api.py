@@ -19,7 +19,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared_functions():
     names = set()
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
-        text = open(h).read()
+        with open(h) as fh:
+            text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for mt in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(m4rie_\w+)\s*\(", text, flags=re.M):
             names.add(mt.group(1))
@@ -124,7 +125,8 @@ def test_product_counts():
     Karatsuba-like schedules use fewer, within the table's best-known counts
     plus the gap of the recursive constructions for e = 5, 6, 7."""
     import paper_1111_6900_gb300 as m4
-    rows = [l.split("#")[0].split() for l in open(os.path.join(ROOT, "tests", "golden", "table3_counts.txt"))]
+    with open(os.path.join(ROOT, "tests", "golden", "table3_counts.txt")) as fh:
+        rows = [l.split("#")[0].split() for l in fh]
     table = {int(r[0]): (int(r[1]), int(r[2])) for r in rows if r}
     got = {}
     for e, f in workloads.FIELD_POLY.items():

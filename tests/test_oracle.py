@@ -20,7 +20,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def _fig1_sections():
-    lines = [l.split("#")[0].strip() for l in open(os.path.join(GOLDEN, "fig1_gf8.txt"))]
+    with open(os.path.join(GOLDEN, "fig1_gf8.txt")) as fh:
+        lines = [l.split("#")[0].strip() for l in fh]
     lines = [l for l in lines if l]
     e = int(lines[0].split()[1])
     sections = {}
@@ -145,7 +146,8 @@ def test_irreducibility_check_rejects_reducible():
 
 
 def test_aes_worked_products():
-    rows = [l.split("#")[0].split() for l in open(os.path.join(GOLDEN, "aes_gf256.txt"))]
+    with open(os.path.join(GOLDEN, "aes_gf256.txt")) as fh:
+        rows = [l.split("#")[0].split() for l in fh]
     rows = [r for r in rows if r]
     e = int(rows[0][1])
     f = int(rows[1][1], 16)
@@ -571,7 +573,8 @@ def test_pins_pass_on_the_oracle():
 @pytest.mark.parametrize("name", sorted(_MUTANTS))
 def test_pins_catch_planted_mistake(name, tmp_path):
     old, new = _MUTANTS[name]
-    src = open(oracle.SOURCE).read()
+    with open(oracle.SOURCE) as fh:
+        src = fh.read()
     assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
     mut = tmp_path / f"oracle_{name}.c"
     mut.write_text(src.replace(old, new))

@@ -25,9 +25,9 @@ def test_replica_throughput_two_gloo_ranks():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    mgr = mp.Manager()
+    ctx = mp.get_context("spawn")  # no fork of this (multi-threaded) process
+    mgr = ctx.Manager()
     out = mgr.dict()
-    ctx = mp.get_context("spawn")
     procs = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
     for p in procs:
         p.start()
