@@ -106,6 +106,35 @@ def _ptr(t):
     return None if t is None or t.numel() == 0 else ctypes.c_void_p(t.data_ptr())
 
 
+def _host_matrix(x, e, name, shape, writable=False):
+    """Address of a host matrix for the host-buffer entry point: a torch CPU
+    tensor or a numpy array, 2-D of the given shape, C-contiguous, one integer
+    element of the field's width per entry (1 byte for e <= 8, 2 for e > 8).
+    None for a matrix without entries."""
+    import numpy as np
+    width = 1 if e <= 8 else 2
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.device.type != "cpu":
+            raise TypeError(f"{name} must be a host tensor (device tensors go through mul / addmul)")
+        integer = not (x.dtype.is_floating_point or x.dtype.is_complex or x.dtype == torch.bool)
+        size, contiguous, ok_write, addr = x.element_size(), x.is_contiguous(), True, x.data_ptr()
+    elif isinstance(x, np.ndarray):
+        integer = x.dtype.kind in "ui"
+        size, contiguous, ok_write, addr = x.itemsize, x.flags.c_contiguous, x.flags.writeable, x.ctypes.data
+    else:
+        raise TypeError(f"{name} must be a torch CPU tensor or a numpy array")
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} must be {shape[0]} x {shape[1]}, not {tuple(x.shape)}")
+    if not integer or size != width:
+        raise TypeError(f"{name} must hold {8 * width}-bit integers for e = {e}")
+    if not contiguous:
+        raise ValueError(f"{name} must be C-contiguous (row-major)")
+    if writable and not ok_write:
+        raise ValueError(f"{name} must be writable")
+    return ctypes.c_void_p(addr) if shape[0] * shape[1] else None
+
+
 def _check_dev(t, e, name, strided=False):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
@@ -230,17 +259,17 @@ class Context:
         return int(rank.value), [int(v) for v in piv[:rank.value]]
 
     def mul_host(self, e: int, f: int, A, B, C, accumulate: bool = False):
-        """Host-buffer product (torch CPU tensors or numpy arrays); synchronous."""
-        import numpy as np
-
-        def addr(x):
-            if hasattr(x, "data_ptr"):
-                return ctypes.c_void_p(x.data_ptr()) if x.numel() else None
-            x = np.asarray(x)
-            return ctypes.c_void_p(x.ctypes.data) if x.size else None
+        """Host-buffer product (torch CPU tensors or numpy arrays, row-major,
+        one element of 1 byte for e <= 8 and 2 bytes for e > 8); synchronous.
+        C is written in place."""
+        if len(getattr(A, "shape", ())) != 2 or len(getattr(B, "shape", ())) != 2:
+            raise ValueError("A and B must be 2-D")
         m, k = A.shape
         n = B.shape[1]
-        self._raise(lib.m4rie_mul_host(self.handle, e, f, m, n, k, addr(A), addr(B), addr(C), 1 if accumulate else 0),
+        pa = _host_matrix(A, e, "A", (m, k))
+        pb = _host_matrix(B, e, "B", (k, n))
+        pc = _host_matrix(C, e, "C", (m, n), writable=True)
+        self._raise(lib.m4rie_mul_host(self.handle, e, f, m, n, k, pa, pb, pc, 1 if accumulate else 0),
                     "m4rie_mul_host")
         return C
 

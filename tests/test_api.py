@@ -137,3 +137,58 @@ def test_product_counts():
         assert naive == e * e
         assert best <= got[e] <= best + 2, (e, got[e], best)
     assert got == {2: 3, 3: 6, 4: 9, 5: 15, 6: 18, 7: 24, 8: 27, 9: 36, 10: 45}
+
+
+def test_host_matrix_checks():
+    """The host-buffer entry point's argument check (no GPU needed): row-major
+    integer matrices of the field's element width, of the stated shape."""
+    import numpy as np
+    import torch
+    import paper_1111_6900_gb300 as m4
+    a8 = np.zeros((3, 5), np.uint8)
+    a16 = np.zeros((3, 5), np.uint16)
+    assert m4._host_matrix(a8, 4, "A", (3, 5)).value == a8.ctypes.data
+    assert m4._host_matrix(a16, 10, "A", (3, 5)).value == a16.ctypes.data
+    t = torch.zeros((3, 5), dtype=torch.uint8)
+    assert m4._host_matrix(t, 8, "A", (3, 5)).value == t.data_ptr()
+    assert m4._host_matrix(np.zeros((0, 5), np.uint8), 4, "A", (0, 5)) is None
+    with pytest.raises(TypeError):
+        m4._host_matrix(a8, 10, "A", (3, 5))            # e > 8 stores two bytes per element
+    with pytest.raises(TypeError):
+        m4._host_matrix(a16, 4, "A", (3, 5))
+    with pytest.raises(TypeError):
+        m4._host_matrix(np.zeros((3, 5), np.float32), 4, "A", (3, 5))
+    with pytest.raises(TypeError):
+        m4._host_matrix([[0] * 5] * 3, 4, "A", (3, 5))   # a list would be a temporary copy
+    with pytest.raises(ValueError):
+        m4._host_matrix(np.zeros((3, 10), np.uint8)[:, ::2], 4, "A", (3, 5))
+    with pytest.raises(ValueError):
+        m4._host_matrix(a8, 4, "A", (5, 3))
+    ro = np.zeros((3, 5), np.uint8)
+    ro.flags.writeable = False
+    assert m4._host_matrix(ro, 4, "A", (3, 5)) is not None
+    with pytest.raises(ValueError):
+        m4._host_matrix(ro, 4, "C", (3, 5), writable=True)
+
+
+def test_mul_host_marshalling_reaches_the_library():
+    """mul_host's whole Python path on the CPU: the arguments reach the C entry
+    point, which rejects a null context before any CUDA call; a bad host array
+    is refused before the call."""
+    import numpy as np
+    import paper_1111_6900_gb300 as m4
+
+    class NoContext:
+        handle = None
+        seen = []
+
+        def _raise(self, status, where):
+            self.seen.append((status, where))
+
+    A, B, C = np.zeros((4, 3), np.uint8), np.zeros((3, 5), np.uint8), np.zeros((4, 5), np.uint8)
+    nc = NoContext()
+    assert m4.Context.mul_host(nc, 4, 0x13, A, B, C) is C
+    assert nc.seen == [(m4.ERR_ARG, "m4rie_mul_host")]
+    with pytest.raises(ValueError):
+        m4.Context.mul_host(nc, 4, 0x13, A, B, np.zeros((5, 4), np.uint8))
+    assert len(nc.seen) == 1
