@@ -135,6 +135,29 @@ def _host_matrix(x, e, name, shape, writable=False):
     return ctypes.c_void_p(addr) if shape[0] * shape[1] else None
 
 
+def _fields_per_word(e: int) -> int:
+    """Fields of the packed representation per 64-bit word."""
+    w = packed_width(e)
+    if w <= 0:
+        raise ValueError(f"e = {e} is outside 2..10")
+    return 64 // w
+
+
+def _check_words(t, name, dims):
+    """A contiguous CUDA tensor of 64-bit words with `dims` dimensions."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.element_size() != 8 or t.is_floating_point():
+        raise TypeError(f"{name} must be a CUDA tensor of 64-bit words")
+    if t.dim() != dims or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dims}-D tensor")
+
+
+def _check_word_window(t, name):
+    """A 2-D CUDA tensor of 64-bit words with unit column stride (any row stride)."""
+    if not t.is_cuda or t.dtype.itemsize != 8 or t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1):
+        raise TypeError(f"{name} must be a 2-D CUDA tensor of 64-bit words with unit column stride")
+
+
 def _check_dev(t, e, name, strided=False):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
@@ -206,6 +229,8 @@ class Context:
         if C is None:
             C = torch.empty((m, n), dtype=A.dtype, device=A.device)
         _check_dev(C, e, "C")
+        if tuple(C.shape) != (m, n):
+            raise ValueError(f"C must be {m} x {n}, not {tuple(C.shape)}")
         self._raise(lib.m4rie_mul(self.handle, e, f, m, n, k, _ptr(A), _ptr(B), _ptr(C)), "m4rie_mul")
         return C
 
@@ -214,7 +239,9 @@ class Context:
         for t, nm in ((A, "A"), (B, "B"), (C, "C")):
             _check_dev(t, e, nm)
         m, k = A.shape
-        n = B.shape[1]
+        k2, n = B.shape
+        if k2 != k or tuple(C.shape) != (m, n):
+            raise ValueError("shapes do not match: A m x k, B k x n, C m x n")
         self._raise(lib.m4rie_addmul(self.handle, e, f, m, n, k, _ptr(A), _ptr(B), _ptr(C)), "m4rie_addmul")
         return C
 
@@ -287,6 +314,9 @@ class Context:
     def unpack(self, e: int, slices, cols: int):
         """Clinging: (e, rows, ld_words) words -> rows x cols elements."""
         import torch
+        _check_words(slices, "slices", 3)
+        if slices.shape[0] != e:
+            raise ValueError(f"slices must hold e = {e} slices, not {slices.shape[0]}")
         _, rows, ld_words = slices.shape
         X = torch.empty((rows, cols), dtype=elem_dtype_torch(e), device=slices.device)
         self._raise(lib.m4rie_unpack(self.handle, e, rows, cols, _ptr(slices), ld_words, _ptr(X)), "m4rie_unpack")
@@ -298,7 +328,7 @@ class Context:
         import torch
         _check_dev(elems, e, "elems", strided=True)
         rows, cols = elems.shape
-        per = 64 // packed_width(e)
+        per = _fields_per_word(e)
         if ld_words is None:
             ld_words = (cols + per - 1) // per
         W = torch.empty((rows, ld_words), dtype=torch.int64, device=elems.device)
@@ -309,9 +339,12 @@ class Context:
     def from_packed(self, e: int, words, cols: int, out=None):
         """Elements of a packed matrix (int64 words, rows x ld_words)."""
         import torch
+        _check_words(words, "words", 2)
         rows, ld_words = words.shape
         X = out if out is not None else torch.empty((rows, cols), dtype=elem_dtype_torch(e), device=words.device)
         _check_dev(X, e, "out", strided=True)
+        if tuple(X.shape) != (rows, cols):
+            raise ValueError(f"out must be {rows} x {cols}, not {tuple(X.shape)}")
         self._raise(lib.m4rie_from_packed(self.handle, e, rows, cols, _ptr(words), ld_words, _ptr(X),
                                           _ld(X) if rows else cols), "m4rie_from_packed")
         return X
@@ -320,11 +353,14 @@ class Context:
         """Newton-John product of packed matrices (int64 word tensors, row
         strides from the tensors): C = A B or C += A B, A m x k, B k x n."""
         for t, nm in ((A, "A"), (B, "B"), (C, "C")):
-            if not t.is_cuda or t.dtype.itemsize != 8 or t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1):
-                raise TypeError(f"{nm} must be a 2-D CUDA tensor of 64-bit words with unit column stride")
+            _check_word_window(t, nm)
         m = A.shape[0]
+        per = _fields_per_word(e)
+        kw, nw = -(-k // per), -(-n // per)
         if B.shape[0] != k or C.shape[0] != m:
             raise ValueError("shapes do not match")
+        if A.shape[1] < kw or B.shape[1] < nw or C.shape[1] < nw:
+            raise ValueError(f"rows of A need {kw} words, rows of B and C {nw}")
         self._raise(lib.m4rie_mul_packed(self.handle, e, f, m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(C),
                                          _ld(C), 1 if accumulate else 0), "m4rie_mul_packed")
         return C
@@ -333,8 +369,12 @@ class Context:
         """problems: list of (e, f, A, B, C, accumulate) with CUDA tensors."""
         arr = (_Problem * len(problems))()
         for i, (e, f, A, B, C, acc) in enumerate(problems):
+            for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+                _check_dev(t, e, f"{nm} of problem {i}")
             m, k = A.shape
-            n = B.shape[1]
+            k2, n = B.shape
+            if k2 != k or tuple(C.shape) != (m, n):
+                raise ValueError(f"problem {i}: shapes do not match (A m x k, B k x n, C m x n)")
             arr[i] = _Problem(e, f, m, n, k, A.data_ptr(), B.data_ptr(), C.data_ptr(), 1 if acc else 0, 0)
         self._raise(lib.m4rie_mul_batched(self.handle, len(problems), arr), "m4rie_mul_batched")
 

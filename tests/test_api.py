@@ -192,3 +192,55 @@ def test_mul_host_marshalling_reaches_the_library():
     with pytest.raises(ValueError):
         m4.Context.mul_host(nc, 4, 0x13, A, B, np.zeros((5, 4), np.uint8))
     assert len(nc.seen) == 1
+
+
+def test_binding_shape_checks(monkeypatch):
+    """The binding refuses mismatched shapes before the library could write past
+    a buffer; matching shapes reach the C entry points (which reject the null
+    context used here before any CUDA call).  The device checks are stubbed so
+    that CPU tensors can stand in."""
+    import torch
+    import paper_1111_6900_gb300 as m4
+
+    for name in ("_check_dev", "_check_words", "_check_word_window"):
+        monkeypatch.setattr(m4, name, lambda *a, **k: None)
+
+    class NoContext:
+        handle = None
+
+        def __init__(self):
+            self.seen = []
+
+        def _raise(self, status, where):
+            self.seen.append((status, where))
+
+    u8 = lambda *shape: torch.zeros(shape, dtype=torch.uint8)     # noqa: E731
+    w64 = lambda *shape: torch.zeros(shape, dtype=torch.int64)    # noqa: E731
+    nc = NoContext()
+    Ctx = m4.Context
+    # mul / addmul
+    Ctx.mul(nc, 4, 0x13, u8(4, 3), u8(3, 5), u8(4, 5))
+    Ctx.addmul(nc, 4, 0x13, u8(4, 3), u8(3, 5), u8(4, 5))
+    assert [w for _, w in nc.seen] == ["m4rie_mul", "m4rie_addmul"]
+    assert all(st == m4.ERR_ARG for st, _ in nc.seen)
+    for bad in (lambda: Ctx.mul(nc, 4, 0x13, u8(4, 3), u8(2, 5)),
+                lambda: Ctx.mul(nc, 4, 0x13, u8(4, 3), u8(3, 5), u8(5, 4)),
+                lambda: Ctx.addmul(nc, 4, 0x13, u8(4, 3), u8(2, 5), u8(4, 5)),
+                lambda: Ctx.addmul(nc, 4, 0x13, u8(4, 3), u8(3, 5), u8(4, 6)),
+                lambda: Ctx.mul_batched(nc, [(4, 0x13, u8(4, 3), u8(3, 5), u8(4, 4), False)]),
+                lambda: Ctx.unpack(nc, 4, w64(3, 2, 1), 10),                       # 3 slices for e = 4
+                lambda: Ctx.from_packed(nc, 4, w64(2, 1), 10, out=u8(2, 11)),
+                lambda: Ctx.mul_packed(nc, 4, 0x13, w64(5, 2), w64(40, 3), w64(5, 3), n=40, k=40),  # A: 3 words
+                lambda: Ctx.mul_packed(nc, 4, 0x13, w64(5, 3), w64(40, 2), w64(5, 3), n=40, k=40),  # B: 3 words
+                lambda: Ctx.mul_packed(nc, 11, 0x13, w64(5, 3), w64(40, 3), w64(5, 3), n=40, k=40)):
+        with pytest.raises(ValueError):
+            bad()
+    assert len(nc.seen) == 2
+    # matching shapes reach the library
+    Ctx.mul_batched(nc, [(4, 0x13, u8(4, 3), u8(3, 5), u8(4, 5), False)])
+    Ctx.unpack(nc, 4, w64(4, 2, 1), 10)
+    Ctx.from_packed(nc, 4, w64(2, 1), 10, out=u8(2, 10))
+    Ctx.mul_packed(nc, 4, 0x13, w64(5, 3), w64(40, 3), w64(5, 3), n=40, k=40)
+    assert [w for _, w in nc.seen[2:]] == ["m4rie_mul_batched", "m4rie_unpack", "m4rie_from_packed",
+                                          "m4rie_mul_packed"]
+    assert all(st == m4.ERR_ARG for st, _ in nc.seen)
