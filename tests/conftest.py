@@ -8,6 +8,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+@pytest.hookimpl(tryfirst=True)
 def pytest_configure(config):
+    # temporary files (the planted-mistake oracles, tuner files) stay inside the
+    # repository, in a git-ignored folder that pytest clears at each session
+    if not config.option.basetemp:
+        config.option.basetemp = os.path.join(ROOT, ".pytest_tmp")
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built extension")
     config.addinivalue_line("markers", "slow: longer CPU or GPU test")
