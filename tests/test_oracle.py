@@ -515,6 +515,26 @@ _MUTANTS = {
     "echelon_no_scale": ("ai[c] = (uint16_t)oracle_gf_mul(e, f, inv, ai[c]);", "ai[c] = ai[c];"),
     # echelon form that clears only the rows below the pivot (not reduced)
     "echelon_below_only": ("for (int64_t k = 0; k < m; k++) {\n            if (k == r)", "for (int64_t k = r + 1; k < m; k++) {\n            if (k == r)"),
+    # echelon form that searches for a pivot from the top instead of at or below the rank
+    "echelon_search_from_top": ("        int64_t i = r;\n        while (i < m && A[i * n + j] == 0)",
+                                "        int64_t i = 0;\n        while (i < m && A[i * n + j] == 0)"),
+    # echelon form that leaves the pivot row where it was found
+    "echelon_no_swap": ("        if (i != r) {\n            uint16_t *ar = A + r * n;", "        if (0) {\n            uint16_t *ar = A + r * n;"),
+    # echelon form that records the pivot's row instead of its column
+    "echelon_pivot_row": ("            pivots[r] = j;", "            pivots[r] = i;"),
+    # echelon form that clears the other rows only right of the pivot column
+    "echelon_keeps_pivot_column": ("            for (int64_t c = j; c < n; c++)\n                ak[c] ^=",
+                                   "            for (int64_t c = j + 1; c < n; c++)\n                ak[c] ^="),
+    # lower solve reads the multiplier from the transposed position
+    "trsm_lower_transposed": ("            uint32_t x = L[j * m + i];", "            uint32_t x = L[i * m + j];"),
+    # slices in reverse order (slice 0 = the highest coefficient)
+    "slice_reversed": ("                if ((elems[r * cols + c] >> i) & 1u)", "                if ((elems[r * cols + c] >> (e - 1 - i)) & 1u)"),
+    # clinging puts slice i at the wrong bit
+    "cling_reversed": ("                v |= (uint32_t)((row[c / 64] >> (c % 64)) & 1u) << i;",
+                       "                v |= (uint32_t)((row[c / 64] >> (c % 64)) & 1u) << (e - 1 - i);"),
+    # unpacking keeps the padding bits of a field
+    "unpack_keeps_padding": ("(uint16_t)((word >> (w * (c % per))) & ((1u << e) - 1u));",
+                             "(uint16_t)((word >> (w * (c % per))) & ((1u << w) - 1u));"),
     # upper solve does not scale by the inverse diagonal entry
     "trsm_no_scale": ("for (int64_t i = m - 1; i >= 0; i--) {\n        uint32_t d = U[i * m + i];\n        if (d == 0)\n            return -1;\n        uint32_t dinv = oracle_gf_inv(e, f, d);",
                       "for (int64_t i = m - 1; i >= 0; i--) {\n        uint32_t d = U[i * m + i];\n        if (d == 0)\n            return -1;\n        uint32_t dinv = 1;"),
@@ -530,11 +550,30 @@ def _pins_pass(O: oracle.OracleLib) -> bool:
             got = np.array([[(int(planes[i, r, 0]) >> c) & 1 for c in range(2)] for r in range(2)])
             if not np.array_equal(got, slices[i]):
                 return False
+        # clinging of the printed slices (built from the figure, not by slice_)
+        printed = np.zeros((e, 2, 1), np.uint64)
+        for i in range(e):
+            for r in range(2):
+                printed[i, r, 0] = sum(int(slices[i][r][c]) << c for c in range(2))
+        if not np.array_equal(O.cling(e, printed, 2).astype(np.int64), np.asarray(elems, np.int64)):
+            return False
         fields = _read_fig1_packed()
         if O.packed_width(e) != 4 or O.packed_width(5) != 8:
             return False
         Wd = O.to_packed(e, elems)
         if any(int(Wd[r, 0]) != sum(int(fields[r][c], 2) << (4 * c) for c in range(2)) for r in range(2)):
+            return False
+        # unpacking of the printed packed rows with every padding bit set: bit 3 of
+        # each 4-bit field (above e = 3) and the unused fields 2..15
+        dirty = np.zeros((2, 1), np.uint64)
+        for r in range(2):
+            word = sum(int(fields[r][c], 2) << (4 * c) for c in range(2))
+            dirty[r, 0] = word | 0x88 | (((1 << 64) - 1) ^ 0xFF)
+        if not np.array_equal(O.from_packed(e, dirty, 2).astype(np.int64), np.asarray(elems, np.int64)):
+            return False
+        # a pivot below the current row: the permutation matrix reduces to the identity
+        E, r, p = O.echelon(2, 7, np.array([[0, 1], [1, 0]], np.uint8))
+        if r != 2 or not np.array_equal(E.astype(np.int64), np.eye(2, dtype=np.int64)) or list(p) != [0, 1]:
             return False
         for e in (2, 4, 8, 10):
             f = workloads.FIELD_POLY[e]
