@@ -498,6 +498,9 @@ _MUTANTS = {
     "transposed_a": ("uint32_t a = A[r * k + t];", "uint32_t a = A[(t % m) * k + (r % k)];"),
     # slicing uses most-significant-bit-first columns
     "slice_msb": ("row[c / 64] |= (uint64_t)1 << (c % 64);", "row[c / 64] |= (uint64_t)1 << (63 - c % 64);"),
+    # accumulation that overwrites C instead of adding to it
+    "addmul_overwrites": ("        if (!accumulate)\n            for (int64_t c = 0; c < n; c++)\n                crow[c] = 0;",
+                          "        if (1)\n            for (int64_t c = 0; c < n; c++)\n                crow[c] = 0;"),
     # addition as OR instead of XOR
     "add_or": ("crow[c] ^= (uint16_t)oracle_gf_mul(e, f, a, brow[c]);", "crow[c] |= (uint16_t)oracle_gf_mul(e, f, a, brow[c]);"),
     # packed fields placed highest first in the word
@@ -581,8 +584,11 @@ def _pins_pass(O: oracle.OracleLib) -> bool:
                 return False
         for e in (2, 5):
             f = workloads.FIELD_POLY[e]
-            A, B, _ = workloads.random_problem(e, 13, 11, 17, seed=9)
+            A, B, C = workloads.random_problem(e, 13, 11, 17, seed=9, with_c=True)
             if not np.array_equal(O.matmul(e, f, A, B).astype(np.int64), fr.slice_product(e, f, A, B)):
+                return False
+            if not np.array_equal(O.addmul(e, f, A, B, C).astype(np.int64),
+                                  fr.slice_product(e, f, A, B) ^ C.astype(np.int64)):
                 return False
         for e in (3, 8):
             f = workloads.FIELD_POLY[e]
