@@ -80,7 +80,9 @@ typedef enum m4rie_form {
                               on the bit-packed slices, int32 counts */
     M4RIE_FORM_NEWTON_JOHN = 6 /* no slicing: Newton-John tables (Section 4, Algorithms 2 and 3) of the
                               packed rows of B (Section 3.1) in shared memory, one table row added per
-                              entry of A; for small products (see m4rie_mul_packed) */
+                              entry of A; for small products and thin inner dimensions (see
+                              m4rie_mul_packed).  Element rows of B and C that start on 16-byte
+                              boundaries (base and row stride) move as 16-byte vectors, the fast case */
 } m4rie_form;
 
 /* Which bilinear schedule reduces the GF(2^e) product to GF(2) products. */
@@ -218,10 +220,10 @@ m4rie_status m4rie_from_packed(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols
 
 /* C = A * B (accumulate == 0) or C = C + A * B on packed matrices by
  * Newton-John multiplication (Section 4, Algorithms 2 and 3): for every row t
- * of B a table of its 2^e multiples (for e >= 8 two tables, of the multiples
- * of B_t and of alpha^b B_t by scalars of e - b and b bits) is built in shared
- * memory from the rows alpha^i B_t, and every row r of C adds the table row
- * indexed by A[r][t].  A is m x k, B k x n, C m x n, each a packed matrix
+ * of B a table of its 2^e multiples (for e >= 6 two tables, of the multiples
+ * of B_t by scalars of b = ceil(e / 2) bits and of alpha^b B_t by scalars of
+ * e - b bits, two lookups per entry) is built in shared memory from the rows
+ * alpha^i B_t, and every row r of C adds the table row(s) indexed by A[r][t].  A is m x k, B k x n, C m x n, each a packed matrix
  * with row stride lda / ldb / ldc 64-bit words (>= the words of one row).
  * Input padding is ignored; C's padding fields are written as zero.  A field
  * whose bits above e are set sets the sticky M4RIE_ERR_RANGE status (its low
