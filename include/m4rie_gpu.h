@@ -181,7 +181,10 @@ m4rie_status m4rie_echelonize(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int6
  * C back and waits for the stream.  Host buffers may be pageable or pinned.
  * When all three are pinned and mapped into the device's address space and
  * the product moves at most 8 MiB, the kernels read and write them in place
- * instead (no staging copies). */
+ * instead (no staging copies).  Products of more than 32 MiB with m >= 1024
+ * run in four row panels of A and C on two further streams, so that copies
+ * of some panels overlap the products of others (B is copied and sliced
+ * once). */
 m4rie_status m4rie_mul_host(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k,
                             const void *hostA, const void *hostB, void *hostC, int accumulate);
 
@@ -223,8 +226,9 @@ m4rie_status m4rie_from_packed(m4rie_ctx *ctx, int e, int64_t rows, int64_t cols
  * of B a table of its 2^e multiples (for e >= 6 two tables, of the multiples
  * of B_t by scalars of b = ceil(e / 2) bits and of alpha^b B_t by scalars of
  * e - b bits, two lookups per entry) is built in shared memory from the rows
- * alpha^i B_t, and every row r of C adds the table row(s) indexed by A[r][t].  A is m x k, B k x n, C m x n, each a packed matrix
- * with row stride lda / ldb / ldc 64-bit words (>= the words of one row).
+ * alpha^i B_t, and every row r of C adds the table row(s) indexed by A[r][t].
+ * A is m x k, B k x n, C m x n, each a packed matrix with row stride lda / ldb
+ * / ldc 64-bit words (>= the words of one row).
  * Input padding is ignored; C's padding fields are written as zero.  A field
  * whose bits above e are set sets the sticky M4RIE_ERR_RANGE status (its low
  * e bits are used).  C must not overlap A or B (M4RIE_ERR_ALIAS).  One launch;
@@ -249,8 +253,9 @@ m4rie_status m4rie_mul_packed(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int6
  * one by one. */
 m4rie_status m4rie_mul_batched(m4rie_ctx *ctx, int count, const m4rie_problem *problems);
 
-/* Wait for the stream, return the sticky device status (M4RIE_OK,
- * M4RIE_ERR_RANGE or M4RIE_ERR_TIMEOUT; TIMEOUT wins) and clear it. */
+/* Wait for the stream, return the sticky device status and clear it:
+ * M4RIE_OK, or the most severe condition seen since the last call
+ * (M4RIE_ERR_TIMEOUT before M4RIE_ERR_SINGULAR before M4RIE_ERR_RANGE). */
 m4rie_status m4rie_get_device_status(m4rie_ctx *ctx);
 
 /* Number of GF(2) slice products that `schedule` uses for GF(2^e) with the
