@@ -63,7 +63,8 @@ PROFILED_SOURCES = {"tc_f4/karatsuba": ("gemm_tc.cu", "35bd391bb8bc5fa7c2dc653c6
                     "popc/alpha_b": ("gemm_popc.cu", "6fc3d0a61765ce47396627acb19770a9ddecc498caad76ea310bae7c899f3a1b"),
                     "newton_john/alpha_b": ("nj_kernel.cuh",
                                             "401c1b6ee335e2c2bd6faefe5fa10256758b5175f58f22d194d82c5451a879dd")}
-# tcgen05.mma issue rate measured on this GPU by microbench/mma_rates.cu, MAC per SM clock
+# tcgen05.mma issue rate measured on GB300 (one CTA per SM issuing MMAs on shared-memory
+# operands back to back), MAC per SM clock
 MMA_MAC_PER_CLK = {"tc_f8": 8192, "tc_f4": 16384}
 
 

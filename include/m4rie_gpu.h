@@ -36,8 +36,8 @@
  *  - M4RIE_TUNE_CACHE: autotuner cache file to load (see m4rie_tune_load).
  *  - M4RIE_TC_CHUNK: entries per FP32 accumulation chunk of the tcgen05 forms
  *    (at most 2^21, so that every count stays below 2^23).
- *  - M4RIE_TC_CLUSTER: tcgen05 tiles on 2-SM pairs (3, default), on CTA pairs
- *    sharing B tiles (2) or on single CTAs (1).
+ *  - M4RIE_TC_CLUSTER: tcgen05 tiles on 2-SM pairs (3, default) or on single
+ *    CTAs (1).
  *  - M4RIE_F4_KIND=nvf4: FP4 products with kind::mxf4nvf4 instead of kind::mxf4.
  *  - M4RIE_PDL=0: launch kernels without programmatic dependent launch.
  *  - M4RIE_FUSE_RECOMBINE=1: Karatsuba on 2-SM pairs (e <= 8) recombines in the

@@ -160,10 +160,10 @@ int resolve_group_m(m4rie_ctx* ctx, int e, int64_t m, int64_t n, int64_t k, int 
   return g > 0 ? std::min(g, tiles_m) : tiles_m;
 }
 
-// tcgen05 GEMMs run 2-CTA clusters on m-tile pairs (rows padded to 256) when
+// tcgen05 GEMMs run 2-SM pairs on m-tile pairs (rows padded to 256) when
 // the pairing adds no padded tile or m is large enough for it not to matter.
 bool pair_m(const m4rie_ctx* ctx, int64_t m) {
-  return ctx->cluster >= 2 && m > 256 && (round_up(m, 256) == round_up(m, 128) || m >= 2048);
+  return ctx->cluster == 3 && m > 256 && (round_up(m, 256) == round_up(m, 128) || m >= 2048);
 }
 
 struct FormInfo {
@@ -332,7 +332,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   const int64_t ldp = round_up(Np / 32, 4);  // words per parity row (whole 16-byte groups)
   // tcgen05 on 2-SM pairs, e <= 8: the GEMM's epilogue recombines the products
   // of each output tile itself (no parity planes, no recombination kernel)
-  const bool fused = form != M4RIE_FORM_POPC && pair && ctx->cluster == 3 && e <= 8 && ctx->fuse_recombine && r <= 64;
+  const bool fused = form != M4RIE_FORM_POPC && pair && e <= 8 && ctx->fuse_recombine && r <= 64;
   const size_t a_bytes = round_up((int64_t)entries_bytes((int64_t)r * Mp * Kp, fi.bits), 1024);
   const size_t b_bytes = round_up((int64_t)entries_bytes((int64_t)r * Np * Kp, fi.bits), 1024);
   const size_t p_bytes = fused ? 0 : round_up((int64_t)r * Mp * ldp * 4, 1024);
@@ -566,7 +566,7 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
   // a chunk holds at most 2 * tc_chunk FP4 entries
   if (const char* s = getenv("M4RIE_TC_CHUNK")) ctx->tc_chunk = std::min(std::max(128, atoi(s)), 1 << 21);
   if (const char* s = getenv("M4RIE_F4_KIND")) ctx->f4nv = strcmp(s, "nvf4") == 0 ? 1 : 0;
-  if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) >= 2 && atoi(s) <= 3 ? atoi(s) : 1;
+  if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) == 1 ? 1 : 3;
   if (const char* s = getenv("M4RIE_PDL")) ctx->pdl = atoi(s) != 0;
   if (const char* s = getenv("M4RIE_FUSE_RECOMBINE")) ctx->fuse_recombine = atoi(s) != 0;
   if (const char* s = getenv("M4RIE_ZERO_COPY")) ctx->zero_copy = atoi(s) != 0;

@@ -47,8 +47,7 @@ struct m4rie_ctx {
   int tc_chunk = 4096;  // elements of K' per FP32 accumulation chunk
   int f4nv = 0;         // FP4 form: kind::mxf4nvf4 instead of kind::mxf4
   int stall_test = 0;   // m4rie_set_test_hook flag 1
-  // tcgen05 GEMMs on CTA pairs: 3 = 2-SM MMAs (cta_group::2, default); 2 =
-  // single-CTA MMAs with B tiles multicast to both CTAs; 1 = single CTAs
+  // tcgen05 GEMMs: 3 = 2-SM pairs (cta_group::2, default); 1 = single CTAs
   // (M4RIE_TC_CLUSTER)
   int cluster = 3;
   // kernels of a product launch with programmatic dependent launch, so each

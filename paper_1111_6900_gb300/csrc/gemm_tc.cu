@@ -1,21 +1,30 @@
 // GF(2) slice GEMM on the tcgen05 tensor cores (sm_103a).
 //
-// Operands are the 0/1 slice planes encoded exactly as FP8 E4M3 (1.0 = 0x38);
-// each tcgen05.mma accumulates integer counts sum_t a_t b_t in FP32 in tensor
-// memory.  Counts are bounded per accumulation chunk (kc k-blocks of 128), so
-// every partial sum is a small integer and exact; after each chunk the
-// epilogue warps take the low bit (the GF(2) sum) and XOR it into per-row bit
-// vectors.  With the alpha^j-B schedule the tile's columns are the e slices of
-// G consecutive output elements (column c*e + i holds slice i of element c),
-// so the epilogue assembles finished field elements (Section 5: product of
-// slice polynomials with the reduction mod f folded into B).
+// Operands are 0/1 slice planes encoded exactly as FP8 E4M3 (1.0 = 0x38,
+// kind::f8f6f4) or as FP4 E2M1 (1.0 = 0x2, kind::mxf4 / mxf4nvf4 with unit
+// block scales held in tensor memory).  Each tcgen05.mma accumulates integer
+// counts sum_t a_t b_t in FP32 in tensor memory.  Counts are bounded per
+// accumulation chunk (kc k-blocks of 128 bytes), so every partial sum is an
+// integer below 2^23 and exact; after each chunk the epilogue warps take the
+// low bit (the GF(2) sum) and XOR it into per-row bit vectors.  With the
+// alpha^j-B schedule the tile's columns are the e slices of G consecutive
+// output elements (column c*e + i holds slice i of element c), so the
+// epilogue assembles finished field elements (Section 5: product of slice
+// polynomials with the reduction mod f folded into B); with the Karatsuba
+// schedule it writes one parity plane per GF(2) product, or XORs the
+// products of a tile into its output slices itself (mode 3).
 //
-// Structure: persistent, one CTA per SM, 6 warps.  Warp 0 issues TMA loads
-// (128-byte swizzled tiles) into a 4-stage shared-memory ring, warp 1 issues
-// the MMAs into two 256-column TMEM accumulators, warps 2-5 drain TMEM.  Every
-// wait is bounded by a global-timer limit; on expiry the CTA sets the timeout
-// status, stops issuing, waits (bounded) for its copies in flight, frees TMEM
-// and returns.
+// Structure: persistent, 6 warps per CTA.  Warp 0 issues TMA loads
+// (128-byte swizzled tiles) into a shared-memory ring, warp 1 issues the
+// MMAs into two TMEM accumulators, warps 2-5 drain TMEM.  The default runs
+// 2-SM pairs (cta_group::2, M = 256): each CTA of a 2-CTA cluster loads its
+// 128 rows of A and half of the B tile, the even CTA issues the MMAs for
+// both and its commits release stages and accumulators in both (7 stages of
+// FP4 or 6 of FP8 fit beside half a B tile).  Single-CTA tiles (M = 128,
+// 4 or 5 stages) serve small m and the batched launch.  No TMA load is
+// multicast: every CTA loads its own tiles.  Every wait is bounded by a
+// global-timer limit; on expiry the CTA sets the timeout status, stops
+// issuing, waits (bounded) for its copies in flight, frees TMEM and returns.
 #include <algorithm>
 #include <cstring>
 
@@ -149,25 +158,6 @@ __device__ __forceinline__ void mma_f4(uint32_t d, uint64_t a, uint64_t b, uint3
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Arrive on the barrier at the same shared-memory offset in both CTAs of a
-// 2-CTA cluster once this thread's MMAs have completed.
-__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-      "h"((uint16_t)3)
-      : "memory");
-}
-
-// TMA load whose data and transaction count land at the same shared-memory
-// offsets in both CTAs of a 2-CTA cluster.
-__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%3, "
-      "%4}], [%2], %5;" ::"r"(dst),
-      "l"(map), "r"(bar), "r"(c0), "r"(c1), "h"((uint16_t)3)
-      : "memory");
 }
 
 // ---- 2-SM (cta_group::2) forms: one MMA of M = 256 rows reads 128 rows of A
@@ -304,8 +294,8 @@ struct TileV {
 
 // Non-batched: one problem (or a batch of equally shaped parity products) in p.
 // Batched: the tile's job comes from the tile -> job table.
-// CL = 2: tile indices count pairs of m-tiles (2 tm, 2 tm + 1) handled by the
-// two CTAs of a cluster, which share the B tile; `rank` picks this CTA's m-tile.
+// CL = 3: tile indices count pairs of m-tiles (2 tm, 2 tm + 1) handled by the
+// two CTAs of a 2-SM pair, which share the B tile; `rank` picks this CTA's m-tile.
 template <bool BATCHED, int CL = 1, int FE = 0>
 __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restrict__ jobs, const CUtensorMap* tmA,
                                          const CUtensorMap* tmB, int tile, int& jc, TileV& t, int rank = 0) {
@@ -317,7 +307,7 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
     } else {
       tile_coords(p, tile, t.b, t.tm, t.tn);
     }
-    if (CL >= 2) t.tm = 2 * t.tm + rank;
+    if (CL == 3) t.tm = 2 * t.tm + rank;
     t.ma = tmA;
     t.mb = tmB;
     t.arow = (int)(t.b * p.a_brows) + t.tm * 128;
@@ -363,11 +353,8 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
 // BATCHED: p.batch = number of jobs, p.tiles_m = total tiles, p.tiles_n = 1;
 // per-tile parameters come from jobs[].  NV (FP4 only): kind::mxf4nvf4 with
 // UE4M3 scales per 16 entries instead of kind::mxf4 with UE8M0 per 32.
-// CL = 2 (non-batched): clusters of two CTAs computing adjacent m-tiles of the
-// same n-tile; each CTA loads half of the B tile and multicasts it to both,
-// and each CTA's MMA commits release a stage in both CTAs (p.tiles_m counts
-// m-tile pairs, the B tensor map's box is half a tile).
-// CL = 3: 2-SM MMAs (cta_group::2).  The even CTA issues MMAs of M = 256 that
+// CL = 1: single CTAs, M = 128.
+// CL = 3 (non-batched): 2-SM MMAs (cta_group::2).  The even CTA issues MMAs of M = 256 that
 // read A's 128 rows and B's half tile from each CTA's shared memory and write
 // 128 accumulator rows into each CTA's tensor memory; each CTA holds only its
 // half of B, so a stage is 128 rows of A and half of B and more stages fit.
@@ -475,8 +462,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      // released by the MMA commits of every CTA of the cluster (CG2: the even CTA's, multicast)
-      mbar_init(empty0 + 8 * s, CG2 ? 1 : CL);
+      // released by the MMA commits (CG2: the even CTA's, signalled in both CTAs)
+      mbar_init(empty0 + 8 * s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
@@ -531,8 +518,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   const int total = BATCHED ? p.tiles_m : p.batch * p.tiles_m * p.tiles_n;
   const uint64_t lim = p.wait_limit_ns;
-  // tile loop: every CTA (CL = 1) or every cluster (CL = 2) takes every
-  // (gridDim.x / CL)-th tile
+  // tile loop: every CTA (CL = 1) or every CTA pair (CL = 3) takes every
+  // (gridDim.x / CLN)-th tile
   const int tfirst = blockIdx.x / CLN, tstep = gridDim.x / CLN;
   // everything above overlaps the previous kernel's tail; no role touches
   // global memory before that kernel (the operand planes' producer) is done
@@ -571,15 +558,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_expect_tx(fb, bytes);
             tma_load_2d(smem_u32(sA + stage * A_TILE), t.ma, fb, kb * 128, t.arow);
           }
-          if (CG2) {
-          } else if (CL == 2) {
-            // this CTA's half of the B tile, into both CTAs (the peer sends the other half)
-            const int half = t.BN / 2;
-            tma_load_2d_pair(smem_u32(sB + stage * B_SLOT + crank * half * 128), t.mb, fb, kb * 128,
-                             t.brow + (int)crank * half);
-          } else {
-            tma_load_2d(smem_u32(sB + stage * B_SLOT), t.mb, fb, kb * 128, t.brow);
-          }
+          if (!CG2) tma_load_2d(smem_u32(sB + stage * B_SLOT), t.mb, fb, kb * 128, t.brow);
           issued_mask |= 1u << stage;
           issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) {
@@ -650,7 +629,6 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
             }
             if (CG2) mma_commit_cg2(empty0 + 8 * stage);
-            else if (CL == 2) mma_commit_pair(empty0 + 8 * stage);
             else mma_commit(empty0 + 8 * stage);
             if (++stage == STAGES) {
               stage = 0;
@@ -896,17 +874,17 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
   if (p.BN % 16 != 0 || p.BN < 16 || p.BN > (fmt == kFmtNib ? SF_COL : 256) || ld_bytes % 16 != 0)
     return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
-  // 2-CTA clusters share B tiles when the m-tiles pair up (the caller pads the
-  // planes' rows to a multiple of 256 for that)
-  const bool pair = p.cluster >= 2 && p.tiles_m % 2 == 0 && num_sms >= 2;
+  // 2-SM pairs when the m-tiles pair up (the caller pads the planes' rows to
+  // a multiple of 256 for that); each CTA loads half of the B tile
+  const bool pair = p.cluster == 3 && p.tiles_m % 2 == 0 && num_sms >= 2;
   if (!tc_make_map(&ma, Aplanes, a_rows, ld_bytes, 128) ||
       !tc_make_map(&mb, Bplanes, b_rows, ld_bytes, pair ? p.BN / 2 : p.BN))
     return cudaErrorInvalidValue;
   // FP4 tiles of N <= 224 take the 5-stage ring
   const bool deep = fmt == kFmtNib && p.BN <= 224;
   const size_t smem = tc_smem_bytes(deep ? 5 : 4);
-  if (p.mode == 3 && !(pair && p.cluster == 3 && p.e <= 8)) return cudaErrorInvalidValue;
-  if (pair && p.cluster == 3) {
+  if (p.mode == 3 && !(pair && p.e <= 8)) return cudaErrorInvalidValue;
+  if (pair) {
     // 2-SM MMAs: the pair computes M = 256 rows per tile
     constexpr int S4 = cg2_stages(kFmtNib), S8 = cg2_stages(kFmtByte);
     auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S4> : tc_kernel<kFmtNib, false, false, 3, S4>)
@@ -933,38 +911,6 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
     cfg.gridDim = dim3(2 * clusters);
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = smem2;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = p.pdl ? 2 : 1;
-    err = cudaLaunchKernelEx(&cfg, kernel, ma, mb, q, (const TcJob*)nullptr);
-    if (launches) ++*launches;
-    return err != cudaSuccess ? err : cudaGetLastError();
-  }
-  if (pair) {
-    auto kernel = fmt == kFmtNib ? (deep ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 2, 5>
-                                                   : tc_kernel<kFmtNib, false, false, 2, 5>)
-                                         : (p.f4nv ? tc_kernel<kFmtNib, false, true, 2> : tc_kernel<kFmtNib, false, false, 2>))
-                                 : tc_kernel<kFmtByte, false, false, 2>;
-    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    TcParams q = p;
-    q.tiles_m = p.tiles_m / 2;  // tiles count m-tile pairs
-    q.group_m = std::max(1, std::min(q.tiles_m, p.group_m / 2));
-    const int64_t pairs = (int64_t)q.batch * q.tiles_m * q.tiles_n;
-    if (pairs > 0x7fffffffLL) return cudaErrorInvalidValue;
-    const int clusters = (int)std::min<int64_t>(pairs, num_sms / 2);
-    if (clusters <= 0) return cudaSuccess;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * clusters);
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
