@@ -338,20 +338,23 @@ m4rie_status m4rie_set_wait_limit_ns(m4rie_ctx *ctx, uint64_t ns);
  * No context is needed and the call allocates nothing.  Its operand planes
  * live in one statically allocated device array of 64 MiB that every GPU
  * loading this library holds until the process exits.  Problems whose planes
- * do not fit (roughly: Mp*e*Kp/8 + ceil(n/G)*G*e*e*Kp/8 + n*k*w bytes with
- * Kp = k rounded up to 128, Mp = m rounded up to 128, G = 64, 32 or 16 for
- * e = 2, 3-4, 5-10, w = element bytes; a 4096 x 4096 x 4096 product over
- * GF(2^4) fits) are rejected with M4RIE_ERR_SCRATCH before anything is
- * launched.
+ * do not fit (Mp*e*Kp/8 + ceil(n/G)*G*e*e*Kp/8 bytes, each rounded up to
+ * 1 KiB, plus 2 KiB, above 64 MiB - 256 bytes, with Kp = k rounded up to 128,
+ * Mp = m rounded up to 128, G = 64, 32 or 16 for e = 2, 3-4, 5-10; a
+ * 4096 x 4096 x 4096 product over GF(2^4) fits) are rejected with
+ * M4RIE_ERR_SCRATCH before anything is launched.
  *
  * A, B, C: device pointers as for m4rie_mul.  device_status: optional device
  * int that receives the status bits (1: an entry was >= 2^e, 2: a wait timed
- * out) OR-ed in; NULL discards them.  stream: cudaStream_t (NULL = legacy
+ * out) OR-ed in; with NULL they go to a word inside the scratch array that is
+ * never read, so they are lost (the product is computed all the same).  stream: cudaStream_t (NULL = legacy
  * default stream).  Asynchronous like m4rie_mul.
  *
  * The first call on each device looks up the device address of the scratch
- * array (cudaGetSymbolAddress); make that first call before any stream
- * capture on that device.  All calls share the scratch array, which keeps the
+ * array (cudaGetSymbolAddress) and caches it for the life of the process;
+ * make that first call before any stream capture on that device, and do not
+ * call this entry point on a device after cudaDeviceReset (the cached address
+ * is then stale).  All calls share the scratch array, which keeps the
  * previous call's contents (each call rewrites every word it reads), so calls
  * whose GPU work overlaps race on it: serialise them. */
 m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t n, int64_t k, const void *A, const void *B,

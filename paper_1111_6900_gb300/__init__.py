@@ -421,12 +421,30 @@ class Context:
 
 
 def mul_noalloc(e: int, f: int, A, B, C, accumulate: bool = False, device_status=None, stream=None) -> int:
-    """m4rie_mul_noalloc on CUDA tensors; returns the m4rie_status code."""
+    """m4rie_mul_noalloc on CUDA tensors; returns the m4rie_status code.
+
+    A (m x k), B (k x n) and C (m x n) are contiguous CUDA tensors of the
+    field's element type (uint8 for e <= 8, uint16 for e = 9, 10), checked here
+    because the entry point takes bare pointers and row strides equal to the
+    widths.  device_status: None or a CUDA int32 tensor of at least one element
+    (its first element receives the device-detected status bits)."""
     import torch
+    for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+        _check_dev(t, e, nm)
+    if A.dim() != 2 or B.dim() != 2 or C.dim() != 2:
+        raise ValueError("A, B and C must be 2-D")
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k or tuple(C.shape) != (m, n):
+        raise ValueError("shapes do not match: A m x k, B k x n, C m x n")
+    if device_status is not None:
+        if (not isinstance(device_status, torch.Tensor) or not device_status.is_cuda
+                or device_status.dtype != torch.int32):
+            raise TypeError("device_status must be a CUDA int32 tensor")
+        if device_status.numel() < 1:
+            raise ValueError("device_status must have at least one element")
     if stream is None:
         stream = torch.cuda.current_stream()
-    m, k = A.shape
-    n = B.shape[1]
     return int(lib.m4rie_mul_noalloc(e, f, m, n, k, _ptr(A), _ptr(B), _ptr(C), 1 if accumulate else 0,
                                      _ptr(device_status), ctypes.c_void_p(stream.cuda_stream)))
 

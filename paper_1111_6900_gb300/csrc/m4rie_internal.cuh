@@ -88,13 +88,11 @@ bool plane_offsets(PackParams& p);
 // Pack launchers (pack.cu).  launch_pack_planes: rows of X (rows x K, row
 // stride ldx) are the planes' rows.  launch_pack_cols: columns of X (K x rows,
 // row stride ldx) are the planes' rows, transposed on the way through shared
-// memory.  launch_transpose serves the entry point without allocation.
+// memory.
 cudaError_t launch_pack_planes(const PackParams& p, cudaStream_t s, int64_t* launches);
 cudaError_t launch_pack_cols(const PackParams& p, cudaStream_t s, int64_t* launches);
 // Both at once (A by rows, B by columns) in one launch.
 cudaError_t launch_pack_pair(const PackParams& a, const PackParams& b, cudaStream_t s, int64_t* launches);
-cudaError_t launch_transpose(const void* X, int64_t ldx, int64_t K, int64_t rows, int elem_bytes, void* Xt,
-                             cudaStream_t s, int64_t* launches);
 
 // Batched forms: job j owns blocks [start[j], start[j+1]) of one launch (all
 // jobs of a launch share the element width and the plane format).

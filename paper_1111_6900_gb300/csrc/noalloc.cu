@@ -14,8 +14,14 @@
 // which the library is loaded, for the life of the process.  Every call shares
 // it, so calls whose GPU work overlaps (two streams, two host threads) race on
 // it and must be serialised by the caller.  The array keeps the previous
-// call's contents: each call's pack kernels rewrite every plane word that its
-// GEMM reads, padding included, so nothing is cleared.
+// call's contents: each call's pack kernel rewrites every plane word that its
+// GEMM reads, padding included, so nothing is cleared.  The operand planes of
+// A are packed by rows and those of B by columns in one launch (B's columns
+// are transposed through shared memory on the way), as in the context path.
+//
+// The array's device address is looked up once per device and cached for the
+// life of the process; after cudaDeviceReset the cached address is stale, so
+// this entry point must not be called on a device that has been reset.
 #include <mutex>
 
 #include "../../include/m4rie_gpu.h"
@@ -70,8 +76,8 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   const int64_t Mp = round_up(m, 128);
   const int64_t groups = ceil_div(n, G);
   const int64_t brows = groups * e * G;
-  const double a_bytes_d = (double)Mp * ld / 8, b_bytes_d = (double)brows * ld / 8, t_bytes_d = (double)n * k * eb;
-  if (a_bytes_d + b_bytes_d + t_bytes_d + 2048.0 > (double)kStatusSlot) return M4RIE_ERR_SCRATCH;
+  const double a_bytes_d = (double)Mp * ld / 8, b_bytes_d = (double)brows * ld / 8;
+  if (a_bytes_d + b_bytes_d + 2048.0 > (double)kStatusSlot) return M4RIE_ERR_SCRATCH;
   const size_t a_bytes = (size_t)round_up(Mp * ld / 8, 1024);
   const size_t b_bytes = (size_t)round_up(brows * ld / 8, 1024);
 
@@ -81,7 +87,6 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   if (scratch_address(dev, &base) != cudaSuccess) return M4RIE_ERR_CUDA;
   uint8_t* Ap = static_cast<uint8_t*>(base);
   uint8_t* Bp = Ap + a_bytes;
-  uint8_t* Bt = Bp + b_bytes;  // B transposed (elements)
   int* status = device_status ? device_status : reinterpret_cast<int*>(static_cast<uint8_t*>(base) + kStatusSlot);
 
   uint16_t amask[10], bmask[100];
@@ -107,13 +112,9 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   pa.out = Ap;
   pa.status = status;
   for (int j = 0; j < e; ++j) pa.mask[j] = amask[j];
-  if (launch_pack_planes(pa, stream, nullptr) != cudaSuccess) return M4RIE_ERR_CUDA;
-  if (launch_transpose(B, n, k, n, eb, Bt, stream, nullptr) != cudaSuccess) return M4RIE_ERR_CUDA;
-
-  PackParams pb = pa;
-  pb.X = Bt;
-  pb.ldx = k;
-  pb.vec = (k * eb) % 16 == 0;
+  PackParams pb = pa;  // columns of B (k x n) are the planes' rows
+  pb.X = B;
+  pb.ldx = n;
   pb.rows = n;
   pb.rows_p = groups * G;
   pb.P = e * e;
@@ -122,7 +123,7 @@ extern "C" m4rie_status m4rie_mul_noalloc(int e, uint32_t f, int64_t m, int64_t 
   pb.G = G;
   pb.out = Bp;
   for (int q = 0; q < e * e; ++q) pb.mask[q] = bmask[q];
-  if (launch_pack_planes(pb, stream, nullptr) != cudaSuccess) return M4RIE_ERR_CUDA;
+  if (launch_pack_pair(pa, pb, stream, nullptr) != cudaSuccess) return M4RIE_ERR_CUDA;
 
   PopcParams pp{};
   pp.A = reinterpret_cast<const uint32_t*>(Ap);

@@ -442,67 +442,6 @@ __global__ void __launch_bounds__(256) pack_cols_batched(const PackParams* __res
   cols_body<T, FMT, E>(p, (uint32_t)(l % gx), (uint32_t)(l / gx), (uint32_t)gy, sm.mexp, tile);
 }
 
-// ---- Element transpose X (K x rows, row-major) -> Xt (rows x K), tiles of
-// 64 x 64 elements through shared memory (one 32-bit word per element).
-template <typename T>
-__device__ __forceinline__ void transpose_tiles(const T* __restrict__ X, int64_t ldx, int64_t K, int64_t rows,
-                                                T* __restrict__ Xt, int vec, int64_t c0, int64_t ty0, int64_t tystep,
-                                                uint32_t (*tile)[65]) {
-  for (int64_t t0 = ty0 * 64; t0 < K; t0 += tystep * 64) {
-    constexpr int CH = 64 * sizeof(T) / 16;  // 16-byte chunks per tile row
-    if (vec && c0 + 64 <= rows && t0 + 64 <= K) {
-      for (int idx = threadIdx.x; idx < 64 * CH; idx += 256) {
-        const int tt = idx / CH, ch = idx % CH;
-        const uint4 a = *reinterpret_cast<const uint4*>(X + (t0 + tt) * ldx + c0 + ch * (16 / sizeof(T)));
-        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-        for (int k = 0; k < 16 / (int)sizeof(T); ++k)
-          tile[tt][ch * (16 / sizeof(T)) + k] =
-              sizeof(T) == 1 ? (w[k >> 2] >> (8 * (k & 3))) & 0xFFu : (w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
-      }
-    } else {
-      for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
-        const int tt = idx >> 6, cc = idx & 63;
-        const int64_t t = t0 + tt, c = c0 + cc;
-        tile[tt][cc] = (t < K && c < rows) ? (uint32_t)X[t * ldx + c] : 0u;
-      }
-    }
-    __syncthreads();
-    // thread -> (column cl, 16 consecutive t)
-    const int cl = threadIdx.x >> 2, tq = (threadIdx.x & 3) * 16;
-    const int64_t c = c0 + cl;
-    if (c < rows) {
-      T* dst = Xt + c * K + t0 + tq;
-      if (vec && t0 + tq + 16 <= K) {
-        uint32_t w[16 * sizeof(T) / 4];
-#pragma unroll
-        for (int k = 0; k < 16 * (int)sizeof(T) / 4; ++k) {
-          if (sizeof(T) == 1)
-            w[k] = tile[tq + 4 * k][cl] | (tile[tq + 4 * k + 1][cl] << 8) | (tile[tq + 4 * k + 2][cl] << 16) |
-                   (tile[tq + 4 * k + 3][cl] << 24);
-          else
-            w[k] = tile[tq + 2 * k][cl] | (tile[tq + 2 * k + 1][cl] << 16);
-        }
-        uint4* d4 = reinterpret_cast<uint4*>(dst);
-#pragma unroll
-        for (int k = 0; k < (int)sizeof(T); ++k) d4[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
-      } else {
-        for (int u = 0; u < 16; ++u)
-          if (t0 + tq + u < K) dst[u] = (T)tile[tq + u][cl];
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ X, int64_t ldx, int64_t K, int64_t rows,
-                                                        T* __restrict__ Xt, int vec) {
-  __shared__ uint32_t tile[64][65];
-  transpose_tiles<T>(X, ldx, K, rows, Xt, vec, (int64_t)blockIdx.x * 64, blockIdx.y, gridDim.y, tile);
-}
-
-
 // ---- Public slice format: one warp per (row, 64-bit word).
 template <typename T>
 __global__ void __launch_bounds__(256) slice_kernel(int e, int64_t rows, int64_t cols, const T* __restrict__ X,
@@ -771,24 +710,6 @@ cudaError_t launch_pack_pair(const PackParams& a0, const PackParams& b0, cudaStr
   else if (a.fmt == kFmtByte)
     launch_pair_fmt<kFmtByte>(a, (int)tpr, (uint32_t)gxa, (uint32_t)gya, b, (uint32_t)gxb, (uint32_t)gyb, grid, s);
   else launch_pair_fmt<kFmtNib>(a, (int)tpr, (uint32_t)gxa, (uint32_t)gya, b, (uint32_t)gxb, (uint32_t)gyb, grid, s);
-  if (launches) ++*launches;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_transpose(const void* X, int64_t ldx, int64_t K, int64_t rows, int elem_bytes, void* Xt,
-                             cudaStream_t s, int64_t* launches) {
-  if (K <= 0 || rows <= 0) return cudaSuccess;
-  const int64_t gx = ceil_div(rows, 64), gy = std::min<int64_t>(ceil_div(K, 64), 65535);
-  if (gx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  const int vec = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Xt)) & 15u) == 0 &&
-                  (ldx * elem_bytes) % 16 == 0 && (K * elem_bytes) % 16 == 0;
-  const dim3 grid((unsigned)gx, (unsigned)gy);
-  if (elem_bytes == 2)
-    transpose_kernel<uint16_t><<<grid, 256, 0, s>>>(static_cast<const uint16_t*>(X), ldx, K, rows,
-                                                    static_cast<uint16_t*>(Xt), vec);
-  else
-    transpose_kernel<uint8_t><<<grid, 256, 0, s>>>(static_cast<const uint8_t*>(X), ldx, K, rows,
-                                                   static_cast<uint8_t*>(Xt), vec);
   if (launches) ++*launches;
   return cudaGetLastError();
 }

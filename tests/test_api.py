@@ -244,3 +244,32 @@ def test_binding_shape_checks(monkeypatch):
     assert [w for _, w in nc.seen[2:]] == ["m4rie_mul_batched", "m4rie_unpack", "m4rie_from_packed",
                                           "m4rie_mul_packed"]
     assert all(st == m4.ERR_ARG for st, _ in nc.seen)
+
+
+def test_noalloc_binding_checks(monkeypatch):
+    """mul_noalloc's argument checks, before the bare-pointer entry point is
+    reached: CUDA tensors of the field's element type, matching shapes, and a
+    CUDA int32 status tensor.  Matching arguments reach the C entry point,
+    which rejects an invalid field before any CUDA call."""
+    import torch
+    import paper_1111_6900_gb300 as m4
+
+    class Stream:
+        cuda_stream = 0
+
+    u8 = lambda *shape: torch.zeros(shape, dtype=torch.uint8)     # noqa: E731
+    # the real device check refuses host tensors and a wrong element type
+    with pytest.raises(TypeError):
+        m4.mul_noalloc(4, 0x13, u8(4, 3), u8(3, 5), u8(4, 5), stream=Stream())
+    monkeypatch.setattr(m4, "_check_dev", lambda *a, **k: None)
+    for bad in (lambda: m4.mul_noalloc(4, 0x13, u8(4, 3), u8(2, 5), u8(4, 5), stream=Stream()),
+                lambda: m4.mul_noalloc(4, 0x13, u8(4, 3), u8(3, 5), u8(5, 4), stream=Stream()),
+                lambda: m4.mul_noalloc(4, 0x13, u8(4, 3), u8(3, 5), u8(4, 6), stream=Stream()),
+                lambda: m4.mul_noalloc(4, 0x13, u8(4, 3, 1), u8(3, 5), u8(4, 5), stream=Stream())):
+        with pytest.raises(ValueError):
+            bad()
+    for status in (torch.zeros(1, dtype=torch.int32),            # host memory
+                   torch.zeros(1, dtype=torch.int64), [0]):
+        with pytest.raises(TypeError):
+            m4.mul_noalloc(4, 0x13, u8(4, 3), u8(3, 5), u8(4, 5), device_status=status, stream=Stream())
+    assert m4.mul_noalloc(11, 0x13, u8(4, 3), u8(3, 5), u8(4, 5), stream=Stream()) == m4.ERR_ARG

@@ -86,8 +86,10 @@ def test_batched_rejects_overlapping_outputs():
 
 def test_batched_workload_4096_instances():
     """The batched workload: 4096 instances, e in 2..8, m, n, k in 32..1024.
-    Every instance is checked on its first and last rows against the oracle;
-    64 instances are checked in full against the single-product popc form."""
+    Every instance is checked on its first and last rows against the oracle
+    and as a whole by Freivalds' test with 8 random columns (a wrong instance
+    passes with probability at most 2^-(8e)); 64 instances are compared with
+    the oracle's product element by element."""
     ctx = m4.Context()
     probs, host = [], []
     for j in range(workloads.BATCHED_COUNT):
@@ -100,14 +102,11 @@ def test_batched_workload_4096_instances():
     assert ctx.device_status() == m4.OK
     rng = np.random.default_rng(4)
     full = set(rng.choice(len(probs), size=64, replace=False).tolist())
-    chk = m4.Context()
-    chk.set_form("popc")
-    chk.set_schedule("alpha_b")
     for j, ((e, f, dA, dB, C, _), (A, B)) in enumerate(zip(probs, host)):
         got = C.cpu().numpy()
         rows = [0, A.shape[0] - 1]
         np.testing.assert_array_equal(got[rows], oracle.matmul(e, f, A[rows], B), err_msg=f"instance {j}")
+        assert oracle.freivalds(e, f, A, B, got, trials=8, seed=j), f"instance {j}: Freivalds' test failed"
         if j in full:
-            np.testing.assert_array_equal(got, chk.mul(e, f, dA, dB).cpu().numpy(), err_msg=f"instance {j}")
-    chk.close()
+            np.testing.assert_array_equal(got, oracle.matmul(e, f, A, B), err_msg=f"instance {j}")
     ctx.close()

@@ -299,8 +299,10 @@ def test_mul_packed_field_bits_above_e_are_flagged(ctx):
 
 @pytest.mark.parametrize("e,m,n,k", [(4, 4096, 4096, 4096), (2, 512, 512, 512), (8, 1024, 1024, 1024)])
 def test_newton_john_full_size_against_tensor_form(ctx, e, m, n, k):
-    """The Newton-John product equals the tcgen05 product (itself checked
-    against the oracle) bit for bit, and sampled rows equal the oracle."""
+    """The Newton-John product equals the tcgen05 product bit for bit, sampled
+    rows equal the oracle, and the whole product passes Freivalds' test against
+    the oracle with 8 random columns (a wrong product passes with probability
+    at most 2^-(8e))."""
     f = workloads.FIELD_POLY[e]
     A, B, _ = workloads.random_problem(e, m, n, k, seed=e + m)
     dA, dB = dev(A), dev(B)
@@ -311,7 +313,9 @@ def test_newton_john_full_size_against_tensor_form(ctx, e, m, n, k):
     ctx.set_form("auto")
     assert torch.equal(C1, C2)
     rows = np.random.default_rng(1).choice(m, size=8, replace=False)
-    np.testing.assert_array_equal(C1.cpu().numpy()[rows], oracle.matmul(e, f, A[rows], B))
+    got = C1.cpu().numpy()
+    np.testing.assert_array_equal(got[rows], oracle.matmul(e, f, A[rows], B))
+    assert oracle.freivalds(e, f, A, B, got, trials=8, seed=m + k), "Freivalds' test failed"
     assert ctx.device_status() == m4.OK
 
 
