@@ -19,9 +19,10 @@
 // MMAs into two TMEM accumulators, warps 2-5 drain TMEM.  The default runs
 // 2-SM pairs (cta_group::2, M = 256): each CTA of a 2-CTA cluster loads its
 // 128 rows of A and half of the B tile, the even CTA issues the MMAs for
-// both and its commits release stages and accumulators in both (7 stages of
-// FP4 or 6 of FP8 fit beside half a B tile).  Single-CTA tiles (M = 128,
-// 4 or 5 stages) serve small m and the batched launch.  No TMA load is
+// both and its commits release stages and accumulators in both (3 stages of
+// two k-blocks each: one barrier wait and one commit per 8 MMAs).
+// Single-CTA tiles (M = 128, 4 or 5 stages of one k-block) serve small m and
+// the batched launch.  No TMA load is
 // multicast: every CTA loads its own tiles.  Every wait is bounded by a
 // global-timer limit; on expiry the CTA sets the timeout status, stops
 // issuing, waits (bounded) for its copies in flight, frees TMEM and returns.
@@ -240,15 +241,6 @@ __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&v)[16
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tile_coords(const TcParams& p, int tile, int& b, int& tm, int& tn) {
   const int per = p.tiles_m * p.tiles_n;
   b = tile / per;
@@ -433,7 +425,7 @@ __device__ __forceinline__ bool store_slices(const TcParams& p, const TileV& t, 
   return bad;
 }
 
-template <int FMT, bool BATCHED, bool NV = false, int CL = 1, int STAGES = 4, int FE = 0>
+template <int FMT, bool BATCHED, bool NV = false, int CL = 1, int STAGES = 4, int FE = 0, int KPS = 1>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ TcParams p, const TcJob* __restrict__ jobs) {
@@ -445,9 +437,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // CG2 keeps the B slots first, so that every B-operand read of a stage,
   // even one past its half tile, stays inside this CTA's allocation
-  uint8_t* sA = CG2 ? smem + STAGES * B_SLOT : smem;
-  uint8_t* sB = CG2 ? smem : smem + STAGES * A_TILE;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * (A_TILE + B_SLOT));
+  // A stage holds KPS k-blocks: KPS A tiles and KPS B slots.
+  uint8_t* sA = CG2 ? smem + STAGES * KPS * B_SLOT : smem;
+  uint8_t* sB = CG2 ? smem : smem + STAGES * KPS * A_TILE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * KPS * (A_TILE + B_SLOT));
   // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain, never
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -541,29 +534,42 @@ __global__ void __launch_bounds__(THREADS, 1)
           asm volatile("prefetch.tensormap [%0];" ::"l"(&nj.ma) : "memory");
           asm volatile("prefetch.tensormap [%0];" ::"l"(&nj.mb) : "memory");
         }
-        // CG2: the even CTA's full barrier counts both CTAs' bytes
+        // bytes of one k-block (CG2: the even CTA's full barrier counts both CTAs' bytes)
         const uint32_t bytes = (CG2 ? 2 * A_TILE : A_TILE) + (uint32_t)t.BN * 128;
-        for (int kb = 0; kb < t.kblocks; ++kb) {
-          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status, lim)) {
-            ok = false;
-            break;
-          }
-          const uint32_t fb = full0 + 8 * stage;
-          if (CG2) {
-            const uint32_t fb_even = mapa_rank(fb, 0);
-            if (crank == 0) mbar_expect_tx(fb, bytes);
-            tma_load_2d_cg2(smem_u32(sA + stage * A_TILE), t.ma, fb_even, kb * 128, t.arow);
-            tma_load_2d_cg2(smem_u32(sB + stage * B_SLOT), t.mb, fb_even, kb * 128, t.brow + (int)crank * (t.BN / 2));
-          } else {
-            mbar_expect_tx(fb, bytes);
-            tma_load_2d(smem_u32(sA + stage * A_TILE), t.ma, fb, kb * 128, t.arow);
-          }
-          if (!CG2) tma_load_2d(smem_u32(sB + stage * B_SLOT), t.mb, fb, kb * 128, t.brow);
-          issued_mask |= 1u << stage;
-          issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
-          if (++stage == STAGES) {
-            stage = 0;
-            phase ^= 1;
+        // stages of up to KPS k-blocks, never across an accumulation chunk
+        // (the MMA warp walks the same steps)
+        for (int kb0 = 0; kb0 < t.kblocks && ok; kb0 += t.kc) {
+          const int kb1 = min(kb0 + t.kc, t.kblocks);
+          for (int kb = kb0; kb < kb1; kb += KPS) {
+            const int nk = min(KPS, kb1 - kb);
+            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status, lim)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fb = full0 + 8 * stage;
+            uint8_t* a_dst = sA + stage * KPS * A_TILE;
+            uint8_t* b_dst = sB + stage * KPS * B_SLOT;
+            if (CG2) {
+              const uint32_t fb_even = mapa_rank(fb, 0);
+              if (crank == 0) mbar_expect_tx(fb, bytes * nk);
+              for (int h = 0; h < nk; ++h) {
+                tma_load_2d_cg2(smem_u32(a_dst + h * A_TILE), t.ma, fb_even, (kb + h) * 128, t.arow);
+                tma_load_2d_cg2(smem_u32(b_dst + h * B_SLOT), t.mb, fb_even, (kb + h) * 128,
+                                t.brow + (int)crank * (t.BN / 2));
+              }
+            } else {
+              mbar_expect_tx(fb, bytes * nk);
+              for (int h = 0; h < nk; ++h) {
+                tma_load_2d(smem_u32(a_dst + h * A_TILE), t.ma, fb, (kb + h) * 128, t.arow);
+                tma_load_2d(smem_u32(b_dst + h * B_SLOT), t.mb, fb, (kb + h) * 128, t.brow);
+              }
+            }
+            issued_mask |= 1u << stage;
+            issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
           }
         }
       }
@@ -589,6 +595,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       // ---------------- MMA issuer
       const uint32_t sf = tmem + SF_COL;
+      const uint64_t sda0 = sdesc(smem_u32(sA)), sdb0 = sdesc(smem_u32(sB));
       int stage = 0, jc = 0;
       uint32_t phase = 0;
       int chunk = 0;
@@ -610,22 +617,34 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           fence_after();
           const uint32_t d = tmem + buf * ACC_COLS;
-          for (int kb = kb0; kb < kb1; ++kb) {
+          // One barrier wait and one commit per stage of KPS k-blocks: the
+          // single issuing thread needs the MMAs of about two k-blocks (8 MMAs)
+          // per wait-and-commit to keep the tensor pipe busy.
+          for (int kb = kb0; kb < kb1; kb += KPS) {
+            const int nk = min(KPS, kb1 - kb);
             if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.status, lim)) {
               ok = false;
               break;
             }
             fence_after();
-            const uint32_t a0 = smem_u32(sA + stage * A_TILE), b0 = smem_u32(sB + stage * B_SLOT);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA: 32 FP8 or 64 FP4 entries
-              const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
-              if (CG2) {
-                if (FMT == kFmtNib) mma_f4_cg2<NV>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, sf, acc);
-                else mma_f8_cg2(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, acc);
-              } else {
-                if (FMT == kFmtNib) mma_f4<NV>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, sf, acc);
-                else mma_f8(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, acc);
+            for (int h = 0; h < KPS; ++h) {
+              if (h < nk) {
+                // descriptors of this k-block's tiles; each MMA steps 32 bytes
+                // of K (32 FP8 or 64 FP4 entries; 2 in the address field)
+                const uint64_t da = sda0 + (uint64_t)((stage * KPS + h) * (A_TILE >> 4));
+                const uint64_t db = sdb0 + (uint64_t)((stage * KPS + h) * (B_SLOT >> 4));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                  const uint32_t acc = (kb + h > kb0 || k > 0) ? 1u : 0u;
+                  if (CG2) {
+                    if (FMT == kFmtNib) mma_f4_cg2<NV>(d, da + 2 * k, db + 2 * k, idesc, sf, acc);
+                    else mma_f8_cg2(d, da + 2 * k, db + 2 * k, idesc, acc);
+                  } else {
+                    if (FMT == kFmtNib) mma_f4<NV>(d, da + 2 * k, db + 2 * k, idesc, sf, acc);
+                    else mma_f8(d, da + 2 * k, db + 2 * k, idesc, acc);
+                  }
+                }
               }
             }
             if (CG2) mma_commit_cg2(empty0 + 8 * stage);
@@ -861,11 +880,15 @@ size_t tc_smem_bytes(int stages = STAGES) {
   return 1024 + (size_t)stages * (A_TILE + b_slot(stages)) + 16 * 8 + 16 + 128 * 9 * 4;
 }
 
-// 2-SM pairs: 7 stages of A + half of B for FP4, 6 for FP8.
-constexpr int cg2_stages(int fmt) { return fmt == kFmtNib ? 7 : 6; }
+// 2-SM pairs: 3 stages of two k-blocks each (A and half of B per k-block:
+// 62 KB for FP4, 64 KB for FP8).  Stages of one k-block (7 of FP4, 6 of FP8
+// fit) measured slower: the one issuing thread then waits on a barrier and
+// commits after every 4 MMAs, and that bookkeeping left the tensor pipe idle
+// about a quarter of the time; with 8 MMAs per wait and commit it stays busy.
+constexpr int CG2_STAGES = 3, CG2_KPS = 2;
 size_t tc_smem_bytes_cg2(int fmt) {
-  const int st = cg2_stages(fmt);
-  return 1024 + (size_t)st * (A_TILE + cg2_b_slot(fmt)) + (size_t)((2 * st + 6 + 1) & ~1) * 8 + 16 + 128 * 9 * 4;
+  return 1024 + (size_t)CG2_STAGES * CG2_KPS * (A_TILE + cg2_b_slot(fmt)) +
+         (size_t)((2 * CG2_STAGES + 6 + 1) & ~1) * 8 + 16 + 128 * 9 * 4;
 }
 
 cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* Bplanes, int64_t b_rows,
@@ -886,16 +909,17 @@ cudaError_t launch_tc(int fmt, const void* Aplanes, int64_t a_rows, const void* 
   if (p.mode == 3 && !(pair && p.e <= 8)) return cudaErrorInvalidValue;
   if (pair) {
     // 2-SM MMAs: the pair computes M = 256 rows per tile
-    constexpr int S4 = cg2_stages(kFmtNib), S8 = cg2_stages(kFmtByte);
-    auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S4> : tc_kernel<kFmtNib, false, false, 3, S4>)
-                                 : tc_kernel<kFmtByte, false, false, 3, S8>;
+    constexpr int S = CG2_STAGES, K2 = CG2_KPS;
+    auto kernel = fmt == kFmtNib ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S, 0, K2>
+                                           : tc_kernel<kFmtNib, false, false, 3, S, 0, K2>)
+                                 : tc_kernel<kFmtByte, false, false, 3, S, 0, K2>;
     if (p.mode == 3) {
       // Karatsuba with the recombination in the epilogue: output slices for e <= 4 or e <= 8
       if (fmt == kFmtNib)
-        kernel = p.e <= 4 ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S4, 4> : tc_kernel<kFmtNib, false, false, 3, S4, 4>)
-                          : (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S4, 8> : tc_kernel<kFmtNib, false, false, 3, S4, 8>);
+        kernel = p.e <= 4 ? (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S, 4, K2> : tc_kernel<kFmtNib, false, false, 3, S, 4, K2>)
+                          : (p.f4nv ? tc_kernel<kFmtNib, false, true, 3, S, 8, K2> : tc_kernel<kFmtNib, false, false, 3, S, 8, K2>);
       else
-        kernel = p.e <= 4 ? tc_kernel<kFmtByte, false, false, 3, S8, 4> : tc_kernel<kFmtByte, false, false, 3, S8, 8>;
+        kernel = p.e <= 4 ? tc_kernel<kFmtByte, false, false, 3, S, 4, K2> : tc_kernel<kFmtByte, false, false, 3, S, 8, K2>;
     }
     const size_t smem2 = tc_smem_bytes_cg2(fmt);
     cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
