@@ -329,13 +329,17 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   // keeps its scale factors in TMEM next to each accumulator)
   const int ntile = form == M4RIE_FORM_POPC ? 128 : (form == M4RIE_FORM_TC_F8 ? 256 : 224);
   const int64_t Np = round_up(n, ntile);
-  const int64_t ldp = round_up(Np / 32, 4);  // words per parity row (whole 16-byte groups)
+  // parity planes: popc, rows of ldp words (whole 16-byte groups); tcgen05,
+  // blocks of 128 rows x 8 words per output tile (TcParams)
+  const int64_t ldp = round_up(Np / 32, 4);
+  const bool blocked = form != M4RIE_FORM_POPC;
+  const int64_t p_plane = blocked ? (Mp / 128) * (Np / ntile) * 1024 : Mp * ldp;  // words per plane
   // tcgen05 on 2-SM pairs, e <= 8: the GEMM's epilogue recombines the products
   // of each output tile itself (no parity planes, no recombination kernel)
   const bool fused = form != M4RIE_FORM_POPC && pair && e <= 8 && ctx->fuse_recombine && r <= 64;
   const size_t a_bytes = round_up((int64_t)entries_bytes((int64_t)r * Mp * Kp, fi.bits), 1024);
   const size_t b_bytes = round_up((int64_t)entries_bytes((int64_t)r * Np * Kp, fi.bits), 1024);
-  const size_t p_bytes = fused ? 0 : round_up((int64_t)r * Mp * ldp * 4, 1024);
+  const size_t p_bytes = fused ? 0 : round_up((int64_t)r * p_plane * 4, 1024);
   m4rie_status st = ensure_ws(ctx, a_bytes + b_bytes + p_bytes);
   if (st != M4RIE_OK) return st;
   uint8_t* Bp = static_cast<uint8_t*>(ctx->ws);
@@ -416,8 +420,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
     tp.C = Pp;
     tp.status = ctx->d_status;
     tp.mode = 2;
-    tp.ldp = ldp;
-    tp.p_bstride = Mp * ldp;
+    tp.p_bstride = p_plane;
     tp.wait_limit_ns = ctx->wait_limit_ns;
     tp.f4nv = ctx->f4nv;
     tp.stall_test = ctx->stall_test;
@@ -447,6 +450,10 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   rc.P = Pp;
   rc.ldw = ldp;
   rc.rows_p = Mp;
+  rc.blocked = blocked ? 1 : 0;
+  rc.tw = ntile / 32;
+  rc.tiles_n = Np / ntile;
+  rc.bstride = p_plane;
   rc.r = r;
   rc.e = e;
   rc.m = m;

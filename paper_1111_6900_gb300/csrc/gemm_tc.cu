@@ -102,6 +102,18 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Bulk copy of `bytes` (a multiple of 16) from shared to global memory,
+// tracked by this thread's bulk-async group.
+__device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Wait until this thread's bulk copies have read their shared-memory sources.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Wait until this thread's bulk copies are complete.
+__device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -757,11 +769,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         continue;
       }
       if (p.mode == 2) {
-        // parity planes: row r0+row, columns tn*BN .. +BN
-        uint32_t* P = static_cast<uint32_t*>(t.C) + b * p.p_bstride + (r0 + row) * p.ldp + (int64_t)tn * t.BN / 32;
-#pragma unroll
-        for (int w = 0; w < 8; ++w)
-          if (w < t.BN / 32) P[w] = bits[w];
+        // Parity planes, blocked: this warp's 32 rows of the tile are 1 KB of
+        // contiguous words (8 per row).  The rows go to shared memory and one
+        // bulk copy writes them: scattered per-row global stores from the
+        // epilogue warps measurably slowed the MMAs of the same SM.
+        uint32_t* blk = static_cast<uint32_t*>(t.C) + (int64_t)b * p.p_bstride +
+                        ((int64_t)tm * p.tiles_n + tn) * 1024 + 32 * q * 8;
+        if (lane == 0) bulk_wait_read();  // the previous copy has read the staging rows
+        __syncwarp();
+        uint4* st = reinterpret_cast<uint4*>(wbits) + 2 * lane;
+        st[0] = make_uint4(bits[0], bits[1], bits[2], bits[3]);
+        st[1] = make_uint4(bits[4], bits[5], bits[6], bits[7]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the bulk copy
+        __syncwarp();
+        if (lane == 0) bulk_store(blk, smem_u32(wbits), 1024);
         continue;
       }
       // Assemble field elements.  The B planes are element-major: column
@@ -818,6 +839,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (bad) atomicOr(p.status, kStatusRange);
       __syncwarp();
     }
+    // the parity blocks' bulk copies are complete before the CTA leaves
+    if (lane == 0) bulk_wait();
+    __syncwarp();
   }
   fence_before();
   __syncthreads();

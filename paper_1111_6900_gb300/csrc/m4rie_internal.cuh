@@ -117,6 +117,10 @@ struct RecombineParams {
   const uint32_t* P;  // r bit planes, plane p row i at P + (p*rows_p + i)*ldw
   int64_t ldw;        // words per parity-plane row
   int64_t rows_p;
+  // blocked planes (the tcgen05 GEMM's layout, see TcParams): tw valid words
+  // of 8 per block row, tiles_n column tiles, bstride words between planes
+  int blocked, tw;
+  int64_t tiles_n, bstride;
   int r;
   int e;
   int64_t m, n;
@@ -176,13 +180,16 @@ struct TcParams {
   uint32_t emask;
   int* status;
   int mode;           // 0: elements, 1: raw counts of the first chunk (test hook), 2: parity planes
-  int64_t ldp;        // parity mode: words per plane row
+  // parity mode: the planes are stored in blocks of 128 rows x 8 words (256
+  // columns, the tile's BN / 32 <= 8 words and zeros), block (tm, tn) of
+  // product b at word b * p_bstride + (tm * tiles_n + tn) * 1024, row i of
+  // the block at 8 * i (tiles_n counts column tiles; tm counts 128-row tiles)
   int64_t p_bstride;  // parity mode: words between products
   uint64_t wait_limit_ns;
   const int* tile_job;  // batched launches: job of every global tile
   int f4nv;             // FP4: 1 = kind::mxf4nvf4 (UE4M3 scales per 16), 0 = kind::mxf4 (UE8M0 per 32)
   int stall_test;       // test hook: the epilogue first waits on a barrier that is never signalled
-  int cluster;          // 2: pairs of CTAs share B tiles (tiles_m must be even), 1: single CTAs
+  int cluster;          // 3: 2-SM pairs (tiles_m must be even), 1: single CTAs
   int pdl;              // launch with programmatic dependent launch
   // mode 3 (Karatsuba with the recombination in the epilogue; 2-SM pairs, e <= 8):
   // every product of an output tile runs on one pair, back to back

@@ -487,8 +487,9 @@ __global__ void __launch_bounds__(256) cling_kernel(int e, int64_t rows, int64_t
 
 // ---- Karatsuba recombination: bit s of C[r][c] is the parity of the
 // products selected by out_mask[s] (reduction mod f folded in).  One thread
-// per (row, 128 columns): it loads the r parity planes' 4 words with 16-byte
-// loads (rows of the planes are padded to whole 16-byte groups), XORs them
+// per (row, 4 words of 32 columns): it loads the r parity planes' 4 words with
+// 16-byte loads (row layout: rows padded to whole 16-byte groups; blocked
+// layout: half of a block row of 8 words), XORs them
 // into E output slice words each (which products feed which slices comes from
 // a per-block table), then transposes the bits into elements.
 template <typename T, int E>
@@ -558,18 +559,26 @@ __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ 
     qmask[q] = m;
   }
   __syncthreads();
-  const int64_t nw = (p.n + 31) / 32, ng = (nw + 3) / 4;
+  // A thread takes four consecutive words of one row of the planes: words
+  // w0 .. w0 + 3 of a row (row layout), or half a block row (blocked layout:
+  // the block's words 4h .. 4h + 3, output words tn * tw + 4h + u, u < 4,
+  // where 4h + u < tw).
+  const int64_t nw = (p.n + 31) / 32, ng = p.blocked ? 2 * p.tiles_n : (nw + 3) / 4;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = idx < p.m * ng;
-  const int64_t r = live ? idx / ng : 0, w0 = live ? (idx % ng) * 4 : 0;
+  const int64_t r = live ? idx / ng : 0, g = live ? idx % ng : 0;
+  const int64_t w0 = p.blocked ? (g >> 1) * p.tw + 4 * (g & 1) : 4 * g;  // output word of u = 0
+  const int uvalid = p.blocked ? min(4, p.tw - 4 * (int)(g & 1)) : 4;    // words of this thread that exist
   uint32_t out[4][E];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int s = 0; s < E; ++s) out[u][s] = 0;
   if (live) {
-    const uint4* src = reinterpret_cast<const uint4*>(p.P + r * p.ldw + w0);
-    const int64_t pstride = p.rows_p * p.ldw / 4;  // in 16-byte groups
+    const uint32_t* base = p.blocked ? p.P + ((r >> 7) * p.tiles_n + (g >> 1)) * 1024 + (r & 127) * 8 + 4 * (g & 1)
+                                     : p.P + r * p.ldw + w0;
+    const uint4* src = reinterpret_cast<const uint4*>(base);
+    const int64_t pstride = (p.blocked ? p.bstride : p.rows_p * p.ldw) / 4;  // in 16-byte groups
 #pragma unroll 4
     for (int q = 0; q < p.r; ++q) {
       const uint4 pw = __ldg(src + q * pstride);
@@ -588,7 +597,7 @@ __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ 
   if (live) {
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (w0 + u < nw) bad |= store_elements<T, E>(p, r, w0 + u, out[u]);
+      if (u < uvalid && w0 + u < nw) bad |= store_elements<T, E>(p, r, w0 + u, out[u]);
   }
   flag_range(p.status, bad);
 }
@@ -788,9 +797,11 @@ cudaError_t launch_cling(int e, int64_t rows, int64_t cols, const uint64_t* slic
 }
 
 cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches) {
-  const int64_t n = p.m * ceil_div(ceil_div(p.n, 32), 4);
+  const int64_t n = p.m * (p.blocked ? 2 * p.tiles_n : ceil_div(ceil_div(p.n, 32), 4));
   const int64_t g = ceil_div(n, 256);
-  if (p.r > 64 || p.ldw % 4 != 0 || (reinterpret_cast<uintptr_t>(p.P) & 15u) != 0) return cudaErrorInvalidValue;
+  if (p.r > 64 || (reinterpret_cast<uintptr_t>(p.P) & 15u) != 0) return cudaErrorInvalidValue;
+  if (p.blocked ? (p.tw < 1 || p.tw > 8 || p.bstride % 4 != 0 || p.tiles_n * p.tw * 32 < p.n) : p.ldw % 4 != 0)
+    return cudaErrorInvalidValue;
   switch (p.e) {
     case 2: return launch_pdl(recombine_kernel<uint8_t, 2>, g, 256, s, launches, p.pdl != 0, p);
     case 3: return launch_pdl(recombine_kernel<uint8_t, 3>, g, 256, s, launches, p.pdl != 0, p);
