@@ -36,6 +36,7 @@ def _sources():
 def _stamp() -> str:
     h = hashlib.sha256()
     for f in sorted(_sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+                    + glob.glob(os.path.join(CSRC, "*.inc"))
                     + glob.glob(os.path.join(INCLUDE, "*.h"))):
         h.update(f.encode())
         with open(f, "rb") as fh:

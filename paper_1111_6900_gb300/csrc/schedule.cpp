@@ -15,10 +15,21 @@
 //     (2 r(h) + r(n-h) products);
 //   * nesting n = u v: an outer schedule over blocks of u coefficients whose
 //     block products use an inner schedule (r(u) r(v) products).
+//
+// Shorter formulas for the field product itself (the product reduced modulo
+// f, whose bilinear rank can be below that of the polynomial product) come
+// from a flip-graph search (schedules/search.py) and are stored in
+// schedule_table.inc, one per e, each written for one field polynomial f_e.
+// A formula for f_e serves every irreducible f of degree e through the field
+// isomorphism x -> beta, beta a root of f in GF(2)[x]/f_e: with Phi the
+// matrix whose column i is beta^i, a *_f b = Phi^-1 (Phi a *_fe Phi b), so
+// L' = L Phi, R' = R Phi, W' = Phi^-1 W.  The shorter of the two schedules is
+// used, after the same symbolic check on every basis pair.
 #include "schedule.h"
 
 #include <algorithm>
 #include <map>
+#include <utility>
 
 namespace m4rie {
 
@@ -149,6 +160,96 @@ bool verify(const Bilinear& b) {
   return true;
 }
 
+// A field-product formula: r terms (L, R, W) for GF(2)[x]/f, W over the e
+// output coefficients.
+struct FieldFormula {
+  int e;
+  uint32_t f;
+  int r;
+  uint32_t t[3 * 64];
+};
+const FieldFormula kTable[] = {
+#include "schedule_table.inc"
+};
+
+// a * b in GF(2)[x]/f (degree e), by shift and add.
+uint32_t field_mul(int e, uint32_t f, uint32_t a, uint32_t b) {
+  uint32_t r = 0;
+  for (int i = e - 1; i >= 0; --i) {
+    r <<= 1;
+    if (r >> e & 1u) r ^= f;
+    if (b >> i & 1u) r ^= a;
+  }
+  return r;
+}
+
+int parity(uint32_t x) { return __builtin_parity(x); }
+
+// Columns of the inverse of the e x e GF(2) matrix with columns col[0..e-1]
+// (bit masks); false if it is singular.
+bool invert_cols(int e, const uint32_t* col, uint32_t* inv) {
+  // row i of [M | I]: bit j = M[i][j] for j < e, bit e + j = I[i][j]
+  uint32_t row[16];
+  for (int i = 0; i < e; ++i) {
+    row[i] = 1u << (e + i);
+    for (int j = 0; j < e; ++j)
+      if (col[j] >> i & 1u) row[i] |= 1u << j;
+  }
+  for (int c = 0; c < e; ++c) {
+    int piv = -1;
+    for (int i = c; i < e && piv < 0; ++i)
+      if (row[i] >> c & 1u) piv = i;
+    if (piv < 0) return false;
+    std::swap(row[c], row[piv]);
+    for (int i = 0; i < e; ++i)
+      if (i != c && (row[i] >> c & 1u)) row[i] ^= row[c];
+  }
+  // column j of M^-1: bit i = bit e + j of row i
+  for (int j = 0; j < e; ++j) {
+    inv[j] = 0;
+    for (int i = 0; i < e; ++i)
+      if (row[i] >> (e + j) & 1u) inv[j] |= 1u << i;
+  }
+  return true;
+}
+
+// The table's formula for degree e carried over to the field polynomial f;
+// false if there is none.
+bool field_formula(int e, uint32_t f, Bilinear* out) {
+  const FieldFormula* ff = nullptr;
+  for (const FieldFormula& x : kTable)
+    if (x.e == e) ff = &x;
+  if (!ff || ff->r < 1 || ff->r > 64) return false;
+  // beta: a root of f in GF(2)[x]/f_e (Horner on f's coefficients)
+  uint32_t beta = 0;
+  for (uint32_t c = 1; c < (1u << e) && !beta; ++c) {
+    uint32_t v = 0;
+    for (int d = e; d >= 0; --d) v = field_mul(e, ff->f, v, c) ^ ((f >> d) & 1u);
+    if (v == 0) beta = c;
+  }
+  if (!beta) return false;
+  uint32_t phi[16], inv[16];
+  phi[0] = 1;
+  for (int i = 1; i < e; ++i) phi[i] = field_mul(e, ff->f, phi[i - 1], beta);
+  if (!invert_cols(e, phi, inv)) return false;
+  out->n = e;
+  out->L.clear();
+  out->R.clear();
+  out->W.clear();
+  for (int p = 0; p < ff->r; ++p) {
+    uint32_t L = 0, R = 0, W = 0;
+    for (int i = 0; i < e; ++i) {
+      if (parity(ff->t[3 * p] & phi[i])) L |= 1u << i;
+      if (parity(ff->t[3 * p + 1] & phi[i])) R |= 1u << i;
+      if (ff->t[3 * p + 2] >> i & 1u) W ^= inv[i];
+    }
+    out->L.push_back(L);
+    out->R.push_back(R);
+    out->W.push_back(W);
+  }
+  return true;
+}
+
 const Bilinear& best(int n) {
   static std::map<int, Bilinear> memo;
   auto it = memo.find(n);
@@ -180,16 +281,22 @@ bool karatsuba_schedule(int e, uint32_t f, Schedule* out) {
   if (e < 1 || e > 10) return false;
   const Bilinear& b = best(e);
   if (!verify(b) || b.r() > 64) return false;
+  Bilinear fb;
+  const bool field = field_formula(e, f, &fb) && fb.r() < b.r();
+  const Bilinear& use = field ? fb : b;
   out->e = e;
-  out->r = b.r();
-  out->amask.assign(b.L.begin(), b.L.end());
-  out->bmask.assign(b.R.begin(), b.R.end());
+  out->r = use.r();
+  out->amask.assign(use.L.begin(), use.L.end());
+  out->bmask.assign(use.R.begin(), use.R.end());
   for (int s = 0; s < 10; ++s) out->out_mask[s] = 0;
+  // field formula: W_p are output coefficients already; polynomial formula:
   // C_s = sum_d [x^d mod f]_s c_d,  c_d = sum_p [d in W_p] P_p
-  for (int p = 0; p < b.r(); ++p) {
+  for (int p = 0; p < use.r(); ++p) {
     uint32_t red = 0;
-    for (int d = 0; d < 2 * e - 1; ++d)
-      if (b.W[p] >> d & 1u) red ^= x_pow_mod(e, f, d);
+    if (field) red = use.W[p];
+    else
+      for (int d = 0; d < 2 * e - 1; ++d)
+        if (use.W[p] >> d & 1u) red ^= x_pow_mod(e, f, d);
     for (int s = 0; s < e; ++s)
       if (red >> s & 1u) out->out_mask[s] |= 1ull << p;
   }
@@ -197,8 +304,8 @@ bool karatsuba_schedule(int e, uint32_t f, Schedule* out) {
   for (int i = 0; i < e; ++i)
     for (int j = 0; j < e; ++j) {
       uint32_t v = 0;
-      for (int p = 0; p < b.r(); ++p)
-        if ((b.L[p] >> i & 1u) && (b.R[p] >> j & 1u))
+      for (int p = 0; p < use.r(); ++p)
+        if ((use.L[p] >> i & 1u) && (use.R[p] >> j & 1u))
           for (int s = 0; s < e; ++s)
             if (out->out_mask[s] >> p & 1ull) v ^= 1u << s;
       if (v != x_pow_mod(e, f, i + j)) return false;

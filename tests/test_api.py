@@ -93,7 +93,7 @@ def test_schedule_is_the_field_product(e, sched):
             assert out == fr.x_power_mod(e, f, i + j), (i, j)
 
 
-@pytest.mark.parametrize("e", [2, 3, 5, 8, 10])
+@pytest.mark.parametrize("e", [2, 3, 5, 6, 7, 8, 9, 10])
 def test_karatsuba_schedule_on_matrices(e):
     """Run the Karatsuba schedule with numpy GF(2) products and compare with
     the oracle: the same recombination the GPU epilogue performs."""
@@ -122,8 +122,9 @@ def test_karatsuba_schedule_on_matrices(e):
 
 def test_product_counts():
     """alpha_b uses the schoolbook count e^2 (Table 3 'naive'); the
-    Karatsuba-like schedules use fewer, within the table's best-known counts
-    plus the gap of the recursive constructions for e = 5, 6, 7."""
+    Karatsuba-like schedules use fewer: Table 3's best-known polynomial counts
+    for e = 2..5 and 8 or below them (the field product modulo f needs only 15
+    and 24 products for e = 6 and 8, through GF(4)), one above them for e = 7."""
     import paper_1111_6900_gb300 as m4
     with open(os.path.join(ROOT, "tests", "golden", "table3_counts.txt")) as fh:
         rows = [l.split("#")[0].split() for l in fh]
@@ -135,8 +136,36 @@ def test_product_counts():
         assert got[e] < e * e
     for e, (naive, best) in table.items():
         assert naive == e * e
-        assert best <= got[e] <= best + 2, (e, got[e], best)
-    assert got == {2: 3, 3: 6, 4: 9, 5: 15, 6: 18, 7: 24, 8: 27, 9: 36, 10: 45}
+        assert got[e] <= best + (1 if e == 7 else 0), (e, got[e], best)
+    assert got == {2: 3, 3: 6, 4: 9, 5: 13, 6: 15, 7: 23, 8: 24, 9: 30, 10: 33}
+
+
+# irreducible polynomials other than the workloads' (some not primitive)
+OTHER_POLY = {5: [0x2F, 0x3D], 6: [0x5B, 0x49], 7: [0x89, 0xF7], 8: [0x11B, 0x187], 9: [0x221, 0x203],
+              10: [0x481, 0x46F]}
+
+
+@pytest.mark.parametrize("e", sorted(OTHER_POLY))
+def test_table_formulas_carried_to_other_polynomials(e):
+    """The searched formulas are written for one polynomial per e; for any
+    other irreducible f the library carries them over by a field isomorphism.
+    Checked here on every basis pair, with x^(i+j) mod f computed by the test,
+    and with the same number of products as for the workload polynomial."""
+    import paper_1111_6900_gb300 as m4
+    r0 = m4.schedule_products(e, workloads.FIELD_POLY[e], "karatsuba")
+    for f in OTHER_POLY[e]:
+        assert fr.is_irreducible(f) and fr.poly_deg(f) == e, hex(f)
+        am, bm, om = m4.schedule_masks(e, f, "karatsuba")
+        assert len(am) == r0
+        for i in range(e):
+            for j in range(e):
+                out = 0
+                for p in range(len(am)):
+                    if am[p] >> i & 1 and bm[p] >> j & 1:
+                        for s in range(e):
+                            if om[s] >> p & 1:
+                                out ^= 1 << s
+                assert out == fr.x_power_mod(e, f, i + j), (hex(f), i, j)
 
 
 def test_host_matrix_checks():
