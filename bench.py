@@ -557,22 +557,51 @@ def run_reference(args):
     return 0
 
 
+def batched_mma_flops(m4, probs, tuned):
+    """2 r m n k summed over the batch, r the GF(2) products of the schedule
+    each product takes: the measured one of its class (tuned), else the
+    library's rule (Karatsuba for e >= 3 when it needs fewer than e^2)."""
+    import math
+    total = 0.0
+    for e, f, A, B, C, _ in probs:
+        m, k = A.shape
+        n = B.shape[1]
+        if not (m and n and k):
+            continue
+        cls = min(63, int(math.floor(math.log2(max(1.0, float(m) * n * k)))))
+        rk = m4.schedule_products(e, f, "karatsuba")
+        sched = tuned.get((e, cls))
+        kara = rk < e * e and (sched == m4.SCHED_KARATSUBA if sched else e >= 3)
+        total += 2.0 * (rk if kara else e * e) * m * n * k
+    return total
+
+
 def run_batched_workload(args, m4, torch, world, rank, local):
     """4096 independent products (e in 2..8, m, n, k in 32..1024) replayed from
-    the CUDA graph of one persistent launch; value = sum of 2mnk / step time."""
-    probs, ops = [], 0.0
+    the CUDA graph of one persistent launch; value = sum of 2mnk / step time.
+    The schedule per (e, shape class) is measured first (m4rie_tune_batched)."""
+    import tempfile
+    probs, host, ops = [], [], 0.0
     for j in range(args.batched_count):
         e, f, m, n, k, A, B = workloads.batched_instance(j)
         C = torch.empty((m, n), dtype=m4.elem_dtype_torch(e), device="cuda")
         probs.append((e, f, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, False))
+        host.append((e, f, A, B))
         ops += 2.0 * m * n * k
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     ctx = m4.Context(stream)
     ctx.set_form(args.forms.split(",")[0] if args.forms not in ("popc,tc_f8,tc_f4,mma_s8,mma_b1,newton_john",)
                  else "auto")
+    t0 = time.time()
+    ctx.tune_batched(probs)
+    tune_s = time.time() - t0
+    with tempfile.NamedTemporaryFile("r", suffix=".txt", dir=ROOT, delete=True) as fh:
+        ctx.tune_save(fh.name)
+        tuned = {(int(w[1]), int(w[2])): int(w[4]) for w in (l.split() for l in open(fh.name)) if w and w[0] == "B"}
+    arr = m4.problem_array(probs)   # the descriptors, marshalled once
     for _ in range(args.warmup):
-        ctx.mul_batched(probs)
+        ctx.mul_batched(arr)
     torch.cuda.synchronize()
     launches0 = ctx.kernel_launches()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -584,22 +613,103 @@ def run_batched_workload(args, m4, torch, world, rank, local):
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
             starts[i].record(stream)
-            ctx.mul_batched(probs)
+            ctx.mul_batched(arr)
             stops[i].record(stream)
         torch.cuda.synchronize()
         clk.mark_end()
         time.sleep(0.1)
     ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops)) / args.steps
+    gpu_launches = (ctx.kernel_launches() - launches0) // max(args.steps, 1)
     if args.single:
         return 0
+    # phase pass: the graph's own events around the plane kernels, the GEMM and the recombination
+    ctx.enable_timing(True)
+    ctx.phase_times(reset=True)
+    nph = max(3, args.steps // 4)
+    for i in range(nph):
+        flush.fill_(i & 0xFF)
+        ctx.mul_batched(arr)
+        ctx.phase_times(reset=False)
+    pack_ms, gemm_ms, rec_ms, _ = ctx.phase_times(reset=True)
+    ctx.enable_timing(False)
+    pack_ms, gemm_ms, rec_ms = pack_ms / nph, gemm_ms / nph, rec_ms / nph
+    flops = batched_mma_flops(m4, probs, tuned)
+    pk = peaks() or {}
+    peak = pk.get("bf16_tflops", 1900.0) * 6.0
+    ceil = 2.0 * MMA_MAC_PER_CLK["tc_f4"] * 152 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (gemm_ms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": "measured bf16 burst x 6.0 (nominal f4/bf16 dense ratio)",
+            "instruction_ceiling": {"value": ceil, "frac": achieved / ceil,
+                                    "source": "tcgen05.mma issue-rate microbenchmark"},
+            "scope": f"the persistent batched GEMM ({gemm_ms:.3f} ms of the step; planes {pack_ms:.3f} ms, "
+                     f"recombination {rec_ms:.3f} ms; phases from CUDA events between the same launches issued without the graph)"}
+    # end to end: every input in one pinned host buffer, one copy in, the batch, one copy of every C out
+    # (each matrix starts on a 16-byte boundary, as separately allocated ones do)
+    r16 = lambda x: (x + 15) // 16 * 16  # noqa: E731
+    sizes = [(r16(A.numel() * A.element_size()) + r16(B.numel() * B.element_size()), r16(C.numel() * C.element_size()))
+             for _, _, A, B, C, _ in probs]
+    h_in8 = torch.empty(sum(a for a, _ in sizes), dtype=torch.uint8).pin_memory()
+    h_out8 = torch.empty(sum(c for _, c in sizes), dtype=torch.uint8).pin_memory()
+    d_in8 = torch.empty_like(h_in8, device="cuda")
+    d_out8 = torch.empty_like(h_out8, device="cuda")
+    eprobs, ia, ic = [], 0, 0
+    for (e, f, A, B, C, acc), (nin, nout) in zip(probs, sizes):
+        dt, w = A.dtype, A.element_size()
+        nA, nB, nC = A.numel() * w, B.numel() * w, C.numel() * w
+        oB = ia + r16(nA)
+        dA = d_in8[ia:ia + nA].view(dt).view(A.shape)
+        dB = d_in8[oB:oB + nB].view(dt).view(B.shape)
+        dC = d_out8[ic:ic + nC].view(dt).view(C.shape)
+        h_in8[ia:ia + nA].view(dt).view(A.shape).copy_(A.cpu())
+        h_in8[oB:oB + nB].view(dt).view(B.shape).copy_(B.cpu())
+        eprobs.append((e, f, dA, dB, dC, acc))
+        ia += nin
+        ic += nout
+    earr = m4.problem_array(eprobs)
+    ctx.mul_batched(earr)   # records the plan of these buffers
+    torch.cuda.synchronize()
+    e_steps = max(3, args.steps // 4)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(e_steps):
+        d_in8.copy_(h_in8, non_blocking=True)
+        ctx.mul_batched(earr)
+        h_out8.copy_(d_out8, non_blocking=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = ev0.elapsed_time(ev1) / e_steps
+    e2e_ok = all(torch.equal(ep[4].cpu(), p[4].cpu()) for ep, p in zip(eprobs[:8], probs[:8]))
     out = {"metric": "GF(2^e) batched matmul field-ops/s (sum of 2mnk)", "value": world * ops / (ms * 1e-3),
            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
            "config": {"workload": f"{args.batched_count} independent products, e uniform in 2..8, m, n, k uniform in {{32, ..., 1024}}",
                       "form": "tcgen05 persistent batched launch replayed from a CUDA graph",
+                      "schedules": {"karatsuba_classes": sum(1 for v in tuned.values() if v == m4.SCHED_KARATSUBA),
+                                    "alpha_b_classes": sum(1 for v in tuned.values() if v == m4.SCHED_ALPHA_B),
+                                    "tuning_s": round(tune_s, 2)},
                       "l2": "flushed between timed steps (512 MB write, not timed)"},
-           "clocks": clk.summary(), "gpu_launches": (ctx.kernel_launches() - launches0) // max(args.steps, 1),
+           "clocks": clk.summary(), "gpu_launches": gpu_launches, "roofline": roof,
+           "e2e": {"value": world * ops / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h_in8.numel()),
+                   "d2h_bytes_per_step": int(h_out8.numel()), "matches_device_run": e2e_ok},
            "device_status": ctx.device_status()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on a bounded sample: whole instances until about 10 s of host
+        # time; the GPU's products of those instances are compared with it
+        import oracle
+        t0, done, sops, equal = time.time(), 0, 0.0, True
+        for j, (e, f, A, B) in enumerate(host):
+            ref = oracle.matmul(e, f, A, B)
+            equal &= bool(np.array_equal(probs[j][4].cpu().numpy(), ref))
+            done += 1
+            sops += 2.0 * A.shape[0] * B.shape[1] * A.shape[1]
+            if time.time() - t0 > 10.0:
+                break
+        dt = time.time() - t0
+        out["cpu_baseline"] = {"value": sops / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                               "sample": f"the first {done} instances of the batch, whole products, {dt:.1f} s"}
+        out["bit_exact_vs_oracle"] = {"instances_checked": done, "equal": equal}
     if rank == 0:
         print(json.dumps(out))
     ctx.close()

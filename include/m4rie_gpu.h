@@ -287,6 +287,21 @@ int m4rie_schedule_masks(int e, uint32_t f, int schedule, int cap, uint16_t *ama
  * The context's explicit form and schedule settings are left unchanged. */
 m4rie_status m4rie_tune(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, int64_t k);
 
+/* Autotuner for batched products (m4rie_mul_batched; not in the paper, which
+ * multiplies one pair at a time): for every class (e, floor(log2(m n k))) of
+ * the given batch, up to 32 of its products (the same shapes, synthetic
+ * elements in scratch buffers this call allocates and frees; the batch's own
+ * A, B and C are not read or written) run in the persistent batched launch
+ * under the alpha^j-B and the Karatsuba-like schedule (Section 5), each
+ * recorded, warmed up and timed over five CUDA-graph replays on the context's
+ * stream; the faster schedule is kept for that class.  Later m4rie_mul_batched
+ * calls take the measured schedule per product; untuned classes keep the
+ * rule (Karatsuba for e >= 3).  m4rie_tune_save / m4rie_tune_load keep these
+ * choices too.  Synchronises the context's stream.  M4RIE_ERR_UNSUPPORTED if
+ * the context's form is not AUTO, TC_F4 or TC_F8 (the batched launch runs on
+ * tcgen05 only); argument errors as for m4rie_mul_batched. */
+m4rie_status m4rie_tune_batched(m4rie_ctx *ctx, int count, const m4rie_problem *problems);
+
 /* The autotuned choice for the shape class of (e, m, n, k): form and
  * schedule (0 when the class was not tuned) and its measured milliseconds. */
 m4rie_status m4rie_tuned_choice(m4rie_ctx *ctx, int e, int64_t m, int64_t n, int64_t k, int *form, int *schedule,

@@ -75,6 +75,7 @@ def _load() -> ctypes.CDLL:
         "m4rie_enable_timing": (i32, [vp, i32]),
         "m4rie_mul_noalloc": (i32, [i32, u32, i64, i64, i64, vp, vp, vp, i32, vp, vp]),
         "m4rie_tune": (i32, [vp, i32, u32, i64, i64, i64]),
+        "m4rie_tune_batched": (i32, [vp, i32, vp]),
         "m4rie_set_test_hook": (i32, [vp, i32]),
         "m4rie_tuned_choice": (i32, [vp, i32, i64, i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(ctypes.c_double)]),
@@ -174,6 +175,22 @@ def _check_dev(t, e, name, strided=False):
 def _ld(t):
     """Row stride of a 2-D window (elements); any value >= its width is valid for one row."""
     return max(int(t.stride(0)), int(t.shape[1])) if t.shape[0] > 1 else int(t.shape[1])
+
+
+def problem_array(problems):
+    """The m4rie_problem array of a list of (e, f, A, B, C, accumulate) with
+    CUDA tensors; mul_batched and tune_batched also take such an array, so
+    that a batch replayed many times is marshalled once."""
+    arr = (_Problem * len(problems))()
+    for i, (e, f, A, B, C, acc) in enumerate(problems):
+        for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+            _check_dev(t, e, f"{nm} of problem {i}")
+        m, k = A.shape
+        k2, n = B.shape
+        if k2 != k or tuple(C.shape) != (m, n):
+            raise ValueError(f"problem {i}: shapes do not match (A m x k, B k x n, C m x n)")
+        arr[i] = _Problem(e, f, m, n, k, A.data_ptr(), B.data_ptr(), C.data_ptr(), 1 if acc else 0, 0)
+    return arr
 
 
 class Context:
@@ -366,17 +383,16 @@ class Context:
         return C
 
     def mul_batched(self, problems):
-        """problems: list of (e, f, A, B, C, accumulate) with CUDA tensors."""
-        arr = (_Problem * len(problems))()
-        for i, (e, f, A, B, C, acc) in enumerate(problems):
-            for t, nm in ((A, "A"), (B, "B"), (C, "C")):
-                _check_dev(t, e, f"{nm} of problem {i}")
-            m, k = A.shape
-            k2, n = B.shape
-            if k2 != k or tuple(C.shape) != (m, n):
-                raise ValueError(f"problem {i}: shapes do not match (A m x k, B k x n, C m x n)")
-            arr[i] = _Problem(e, f, m, n, k, A.data_ptr(), B.data_ptr(), C.data_ptr(), 1 if acc else 0, 0)
+        """problems: list of (e, f, A, B, C, accumulate) with CUDA tensors, or
+        the array problem_array() made of one."""
+        arr = problems if isinstance(problems, ctypes.Array) else problem_array(problems)
         self._raise(lib.m4rie_mul_batched(self.handle, len(problems), arr), "m4rie_mul_batched")
+
+    def tune_batched(self, problems):
+        """m4rie_tune_batched: measure the schedule per (e, shape class) of this
+        batch for later mul_batched calls; the batch's tensors are not touched."""
+        arr = problems if isinstance(problems, ctypes.Array) else problem_array(problems)
+        self._raise(lib.m4rie_tune_batched(self.handle, len(problems), arr), "m4rie_tune_batched")
 
     def enable_timing(self, on: bool = True):
         self._raise(lib.m4rie_enable_timing(self.handle, 1 if on else 0), "m4rie_enable_timing")

@@ -576,6 +576,11 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
   if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) == 1 ? 1 : 3;
   if (const char* s = getenv("M4RIE_PDL")) ctx->pdl = atoi(s) != 0;
   if (const char* s = getenv("M4RIE_FUSE_RECOMBINE")) ctx->fuse_recombine = atoi(s) != 0;
+  if (const char* s = getenv("M4RIE_BATCHED_SCHED"))
+    ctx->batched_sched = strcmp(s, "alpha_b") == 0 ? M4RIE_SCHED_ALPHA_B
+                         : strcmp(s, "karatsuba") == 0 ? M4RIE_SCHED_KARATSUBA : M4RIE_SCHED_AUTO;
+  if (const char* s = getenv("M4RIE_BATCHED_KARA_MIN_E")) ctx->batched_kara_min_e = atoi(s);
+  if (const char* s = getenv("M4RIE_BATCHED_KARA_MIN_MNK")) ctx->batched_kara_min_mnk = atof(s);
   if (const char* s = getenv("M4RIE_ZERO_COPY")) ctx->zero_copy = atoi(s) != 0;
   if (const char* s = getenv("M4RIE_TUNE_CACHE")) m4rie_tune_load(ctx, s);  // a missing file is not an error
   *out = ctx;

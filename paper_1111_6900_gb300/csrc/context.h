@@ -58,6 +58,16 @@ struct m4rie_ctx {
   // of an output tile back to back, and that tile order costs the GEMM more
   // L2 misses than the recombination kernel costs.
   int fuse_recombine = 0;
+  // batched products: schedule per product (M4RIE_BATCHED_SCHED: alpha_b,
+  // karatsuba, or auto: Karatsuba for e >= batched_kara_min_e and m n k >=
+  // batched_kara_min_mnk, M4RIE_BATCHED_KARA_MIN_E / _MIN_MNK)
+  int batched_sched = M4RIE_SCHED_AUTO;
+  int batched_kara_min_e = 3;
+  double batched_kara_min_mnk = 0;
+  // m4rie_tune_batched: measured schedule per [e][floor(log2(m n k))] (sched
+  // 0: not tuned); batched_force: the schedule a tuning run imposes
+  m4rie::TuneEntry btuned[11][64];
+  int batched_force = 0;
   // m4rie_mul_host: kernels use pinned, device-mapped host buffers of small
   // products in place (M4RIE_ZERO_COPY=0: always staging copies)
   int zero_copy = 1;

@@ -294,6 +294,8 @@ struct TileV {
   int64_t m, n, ldc;
   int G, e, elem_bytes, add;
   uint32_t emask;
+  int mode, tiles_n;    // epilogue mode; column tiles (blocked parity layout)
+  int64_t p_bstride;    // parity mode: words between products
 };
 
 // Non-batched: one problem (or a batch of equally shaped parity products) in p.
@@ -328,17 +330,22 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
     t.elem_bytes = p.elem_bytes;
     t.add = p.add;
     t.emask = p.emask;
+    t.mode = p.mode;
+    t.tiles_n = p.tiles_n;
+    t.p_bstride = p.p_bstride;
   } else {
     jc = __ldg(p.tile_job + tile);
     const TcJob& j = jobs[jc];
     const int local = (int)(tile - j.tile_start);
-    t.b = 0;
-    t.tm = local % j.tiles_m;
-    t.tn = local / j.tiles_m;
+    const int per = j.tiles_m * j.tiles_n;
+    t.b = local / per;  // GF(2) product of the job (mode 2)
+    const int rem = local - t.b * per;
+    t.tm = rem % j.tiles_m;
+    t.tn = rem / j.tiles_m;
     t.ma = &j.ma;
     t.mb = &j.mb;
-    t.arow = t.tm * 128;
-    t.brow = t.tn * j.BN;
+    t.arow = (int)(t.b * j.a_brows) + t.tm * 128;
+    t.brow = (int)(t.b * j.b_brows) + t.tn * j.BN;
     t.BN = j.BN;
     t.kblocks = j.kblocks;
     t.kc = j.kc;
@@ -351,6 +358,9 @@ __device__ __forceinline__ void get_tile(const TcParams& p, const TcJob* __restr
     t.elem_bytes = j.elem_bytes;
     t.add = j.add;
     t.emask = j.emask;
+    t.mode = j.mode;
+    t.tiles_n = j.tiles_n;
+    t.p_bstride = j.p_bstride;
   }
 }
 
@@ -724,7 +734,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int h = 0; h < 4; ++h) {
             const int c16 = 4 * g + h;
             if (c16 < nc16) {
-              if (p.mode == 1) {
+              if (t.mode == 1) {
                 if (kb0 == 0) {
                   uint32_t* out = static_cast<uint32_t*>(t.C) + ((int64_t)tm * 128 + row) * t.ldc +
                                   (int64_t)tn * t.BN + 16 * c16;
@@ -748,7 +758,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         else mbar_arrive(tempty0 + 8 * buf);
         ++chunk;
       }
-      if (!ok || p.mode == 1) continue;
+      if (!ok || t.mode == 1) continue;
       const int64_t r0 = (int64_t)tm * 128;
       if constexpr (FE > 0) {
         // Karatsuba recombination (Section 5): output slice s is the XOR of
@@ -768,13 +778,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         continue;
       }
-      if (p.mode == 2) {
+      if (t.mode == 2) {
         // Parity planes, blocked: this warp's 32 rows of the tile are 1 KB of
         // contiguous words (8 per row).  The rows go to shared memory and one
         // bulk copy writes them: scattered per-row global stores from the
         // epilogue warps measurably slowed the MMAs of the same SM.
-        uint32_t* blk = static_cast<uint32_t*>(t.C) + (int64_t)b * p.p_bstride +
-                        ((int64_t)tm * p.tiles_n + tn) * 1024 + 32 * q * 8;
+        uint32_t* blk = static_cast<uint32_t*>(t.C) + (int64_t)b * t.p_bstride +
+                        ((int64_t)tm * t.tiles_n + tn) * 1024 + 32 * q * 8;
         if (lane == 0) bulk_wait_read();  // the previous copy has read the staging rows
         __syncwarp();
         uint4* st = reinterpret_cast<uint4*>(wbits) + 2 * lane;

@@ -134,6 +134,11 @@ struct RecombineParams {
   int pdl;                // launch with programmatic dependent launch
 };
 cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches);
+// Batched form: job j owns blocks [start[j], start[j + 1]) (all jobs of one
+// launch share the element width; e <= 8 for bytes, 9..10 for halfwords).
+int64_t recombine_job_blocks(const RecombineParams& p);
+cudaError_t launch_recombine_batched(const RecombineParams* d_jobs, const int64_t* d_start, int njobs,
+                                     int64_t blocks, int elem_bytes, cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------- popc form
 // Tile constants of the bit-packed GEMM (gemm_popc.cu).
@@ -210,6 +215,11 @@ struct alignas(alignof(CUtensorMap)) TcJob {
   int e, G, BN, kblocks, kc, tiles_m, tiles_n, elem_bytes, add;
   uint32_t emask;
   int64_t tile_start;
+  // mode 0: alpha^j-B product, elements into C (batch 1); mode 2: batch
+  // GF(2) products (Karatsuba), parity planes into C in the blocked layout of
+  // TcParams, product b's planes a_brows (b_brows) rows on in the A (B) map
+  int mode, batch;
+  int64_t a_brows, b_brows, p_bstride;
 };
 bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t ld_bytes, int box_rows);
 cudaError_t launch_tc_batched(int fmt, const TcJob* d_jobs, const int* d_tile_job, int njobs, int64_t total_tiles,

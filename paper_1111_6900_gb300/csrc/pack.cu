@@ -548,23 +548,12 @@ __device__ __forceinline__ bool store_elements(const RecombineParams& p, int64_t
   return bad;
 }
 
+// Recombination of the r parity planes of one product into its elements;
+// idx: this thread's index within the product, qmask: bit s of qmask[q] says
+// that product q feeds output slice s.
 template <typename T, int E>
-__global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecombineParams p) {
-  __shared__ uint32_t qmask[64];  // bit s: product q feeds output slice s
-  pdl_enter();
-  for (int q = threadIdx.x; q < p.r; q += blockDim.x) {
-    uint32_t m = 0;
-#pragma unroll
-    for (int s = 0; s < E; ++s) m |= (uint32_t)((p.out_mask[s] >> q) & 1ull) << s;
-    qmask[q] = m;
-  }
-  __syncthreads();
-  // A thread takes four consecutive words of one row of the planes: words
-  // w0 .. w0 + 3 of a row (row layout), or half a block row (blocked layout:
-  // the block's words 4h .. 4h + 3, output words tn * tw + 4h + u, u < 4,
-  // where 4h + u < tw).
+__device__ __forceinline__ void recombine_body(const RecombineParams& p, int64_t idx, const uint32_t* qmask) {
   const int64_t nw = (p.n + 31) / 32, ng = p.blocked ? 2 * p.tiles_n : (nw + 3) / 4;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = idx < p.m * ng;
   const int64_t r = live ? idx / ng : 0, g = live ? idx % ng : 0;
   const int64_t w0 = p.blocked ? (g >> 1) * p.tw + 4 * (g & 1) : 4 * g;  // output word of u = 0
@@ -600,6 +589,41 @@ __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ 
       if (u < uvalid && w0 + u < nw) bad |= store_elements<T, E>(p, r, w0 + u, out[u]);
   }
   flag_range(p.status, bad);
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecombineParams p) {
+  __shared__ uint32_t qmask[64];  // bit s: product q feeds output slice s
+  pdl_enter();
+  for (int q = threadIdx.x; q < p.r; q += blockDim.x) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int s = 0; s < E; ++s) m |= (uint32_t)((p.out_mask[s] >> q) & 1ull) << s;
+    qmask[q] = m;
+  }
+  __syncthreads();
+  recombine_body<T, E>(p, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, qmask);
+}
+
+// Many products' recombinations in one launch (the batched Karatsuba
+// products): block b serves job find_job(start, b).
+template <typename T>
+__global__ void __launch_bounds__(256) recombine_batched(const RecombineParams* __restrict__ jobs,
+                                                         const int64_t* __restrict__ start, int njobs) {
+  constexpr int E = sizeof(T) == 1 ? 8 : 10;
+  __shared__ uint32_t qmask[64];
+  __shared__ int sj;
+  if (threadIdx.x == 0) sj = find_job(start, njobs, blockIdx.x);
+  __syncthreads();
+  const RecombineParams& p = jobs[sj];
+  for (int q = threadIdx.x; q < p.r; q += blockDim.x) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int s = 0; s < E; ++s) m |= (uint32_t)((p.out_mask[s] >> q) & 1ull) << s;
+    qmask[q] = m;
+  }
+  __syncthreads();
+  recombine_body<T, E>(p, ((int64_t)blockIdx.x - start[sj]) * blockDim.x + threadIdx.x, qmask);
 }
 
 template <typename K, typename... Args>
@@ -794,6 +818,20 @@ cudaError_t launch_cling(int e, int64_t rows, int64_t cols, const uint64_t* slic
                   static_cast<uint16_t*>(elems));
   return launch(cling_kernel<uint8_t>, ceil_div(warps, 8), 256, s, launches, e, rows, cols, slices, ld_words,
                 static_cast<uint8_t*>(elems));
+}
+
+int64_t recombine_job_blocks(const RecombineParams& p) {
+  return ceil_div(p.m * (p.blocked ? 2 * p.tiles_n : ceil_div(ceil_div(p.n, 32), 4)), 256);
+}
+
+cudaError_t launch_recombine_batched(const RecombineParams* d_jobs, const int64_t* d_start, int njobs,
+                                     int64_t blocks, int elem_bytes, cudaStream_t s, int64_t* launches) {
+  if (njobs <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (elem_bytes == 2) recombine_batched<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(d_jobs, d_start, njobs);
+  else recombine_batched<uint8_t><<<(unsigned)blocks, 256, 0, s>>>(d_jobs, d_start, njobs);
+  if (launches) ++*launches;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches) {

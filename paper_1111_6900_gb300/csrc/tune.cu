@@ -41,6 +41,12 @@ __global__ void compare_bytes(const uint8_t* a, const uint8_t* b, int64_t n, int
 
 }  // namespace
 
+cudaError_t launch_fill_elements(void* X, int64_t count, int eb, uint32_t emask, uint64_t seed, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  fill_elements<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 4096), 256, 0, s>>>(X, count, eb, emask, seed);
+  return cudaGetLastError();
+}
+
 int shape_class(int64_t m, int64_t n, int64_t k) {
   const double v = std::max(1.0, (double)m * (double)n * (double)k);
   return std::min(63, (int)std::floor(std::log2(v)));
@@ -169,6 +175,12 @@ m4rie_status m4rie_tune_save(m4rie_ctx* ctx, const char* path) {
       const TuneEntry& t = ctx->tuned[e][c];
       if (t.form) fprintf(fp, "%d %d %d %d %d %.6f\n", e, c, t.form, t.sched, t.group_m, t.ms);
     }
+  // batched products (m4rie_tune_batched): "B e shape_class form schedule ms"
+  for (int e = 2; e <= 10; ++e)
+    for (int c = 0; c < 64; ++c) {
+      const TuneEntry& t = ctx->btuned[e][c];
+      if (t.sched) fprintf(fp, "B %d %d %d %d %.6f\n", e, c, t.form, t.sched, t.ms);
+    }
   fclose(fp);
   return M4RIE_OK;
 }
@@ -182,6 +194,13 @@ m4rie_status m4rie_tune_load(m4rie_ctx* ctx, const char* path) {
     if (line[0] == '#') continue;
     int e, c, form, sched, gm;
     double ms;
+    if (line[0] == 'B') {
+      if (sscanf(line + 1, "%d %d %d %d %lf", &e, &c, &form, &sched, &ms) == 5 && e >= 2 && e <= 10 && c >= 0 &&
+          c < 64 && (form == M4RIE_FORM_TC_F4 || form == M4RIE_FORM_TC_F8) && sched >= M4RIE_SCHED_ALPHA_B &&
+          sched <= M4RIE_SCHED_KARATSUBA)
+        ctx->btuned[e][c] = TuneEntry{form, sched, 0, ms};
+      continue;
+    }
     if (sscanf(line, "%d %d %d %d %d %lf", &e, &c, &form, &sched, &gm, &ms) != 6) continue;
     if (e < 2 || e > 10 || c < 0 || c > 63 || form < M4RIE_FORM_POPC || form > M4RIE_FORM_NEWTON_JOHN ||
         sched < M4RIE_SCHED_ALPHA_B || sched > M4RIE_SCHED_KARATSUBA || gm < 0)

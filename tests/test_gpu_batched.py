@@ -48,6 +48,86 @@ def test_batched_mixed_fields_and_shapes(form):
     ctx.close()
 
 
+KARA_SPECS = SPECS + [(5, 300, 20, 520, True), (6, 129, 33, 256, False), (8, 257, 229, 384, True),
+                      (7, 64, 448, 130, False), (10, 130, 224, 257, False), (3, 1, 600, 33, True)]
+
+
+@pytest.mark.parametrize("sched", ["karatsuba", "auto"])
+@pytest.mark.parametrize("form", ["tc_f4", "tc_f8"])
+def test_batched_karatsuba(monkeypatch, sched, form):
+    """Batched products on the Karatsuba-like schedule: r GF(2) products per
+    product written as blocked parity planes by the persistent GEMM, then one
+    batched recombination; narrow n takes narrower tiles.  Mixed fields,
+    ragged and degenerate shapes, accumulation; against the oracle."""
+    monkeypatch.setenv("M4RIE_BATCHED_SCHED", sched)
+    monkeypatch.setenv("M4RIE_BATCHED_KARA_MIN_MNK", "0")
+    ctx = m4.Context()
+    ctx.set_form(form)
+    probs, ref = _problems(KARA_SPECS, 5100)
+    ctx.mul_batched(probs)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == m4.OK
+    for (e, f, A, B, C, acc), r, spec in zip(probs, ref, KARA_SPECS):
+        np.testing.assert_array_equal(C.cpu().numpy(), r, err_msg=str(spec))
+    # a replay of the recorded graph gives the same products (accumulating ones again)
+    for (e, f, A, B, C, acc), (_, m, n, k, _) in zip(probs, KARA_SPECS):
+        if acc:
+            C.zero_()
+    ctx.mul_batched(probs)
+    torch.cuda.synchronize()
+    for (e, f, A, B, C, acc), spec in zip(probs, KARA_SPECS):
+        want = oracle.matmul(e, workloads.FIELD_POLY[e], A.cpu().numpy(), B.cpu().numpy()) if acc else None
+        if acc:
+            np.testing.assert_array_equal(C.cpu().numpy(), want, err_msg=str(spec))
+    assert ctx.device_status() == m4.OK
+    ctx.close()
+
+
+def _shape_class(m, n, k):
+    return min(63, int(np.floor(np.log2(max(1.0, float(m) * n * k)))))
+
+
+def test_tune_batched_then_mul(tmp_path):
+    """m4rie_tune_batched times every (e, shape class) of a batch under both
+    schedules on scratch inputs (the batch's tensors stay untouched), keeps
+    the faster, and later batches use the choices; the batch's products are
+    still equal to the oracle's.  With phase timing on, the replayed graph
+    reports its plane, GEMM and recombination phases."""
+    ctx = m4.Context()
+    specs = [s for s in KARA_SPECS if s[1] and s[2] and s[3]]
+    probs, ref = _problems(specs, 5200)
+    before = [p[4].clone() for p in probs]
+    ctx.tune_batched(probs)
+    torch.cuda.synchronize()
+    for p, c0 in zip(probs, before):
+        assert torch.equal(p[4], c0)
+    path = str(tmp_path / "tune.txt")
+    ctx.tune_save(path)
+    with open(path) as fh:
+        tuned = {(int(w[1]), int(w[2])): int(w[4]) for w in (l.split() for l in fh) if w and w[0] == "B"}
+    want = {(e, _shape_class(m, n, k)) for e, m, n, k, _ in specs}
+    assert set(tuned) == want
+    assert set(tuned.values()) <= {m4.SCHED_ALPHA_B, m4.SCHED_KARATSUBA}
+    ctx2 = m4.Context()                     # the cache file carries the choices
+    ctx2.tune_load(path)
+    for c in (ctx, ctx2):
+        for p in probs:
+            p[4].zero_()
+        c.enable_timing(True)
+        c.phase_times(reset=True)
+        c.mul_batched(probs)
+        torch.cuda.synchronize()
+        pack_ms, gemm_ms, rec_ms, nprod = c.phase_times(reset=True)
+        c.enable_timing(False)
+        assert pack_ms > 0 and gemm_ms > 0 and rec_ms >= 0 and nprod == len(specs)
+        for (e, f, A, B, C, acc), r, spec in zip(probs, ref, specs):
+            want_c = oracle.matmul(e, f, A.cpu().numpy(), B.cpu().numpy()) if acc else r
+            np.testing.assert_array_equal(C.cpu().numpy(), want_c, err_msg=str(spec))
+        assert c.device_status() == m4.OK
+    ctx2.close()
+    ctx.close()
+
+
 def test_batched_graph_replay_sees_new_inputs():
     ctx = m4.Context()
     specs = [(4, 100, 90, 80, False), (8, 50, 60, 70, False)]
