@@ -167,6 +167,26 @@ def replica_throughput(units: float, seconds: float, device=None):
     return world * units / seconds, seconds
 
 
+def link_rates(torch, h_in, h_out):
+    """Host-device link rates measured here: one pinned host tensor's copy in
+    and one's copy out (copy engines, CUDA events, best of three)."""
+    d_in = torch.empty_like(h_in, device="cuda")
+    d_out = torch.empty_like(h_out, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = {}
+    for name, dst, src in (("h2d_gbs", d_in, h_in), ("d2h_gbs", h_out, d_out)):
+        t = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+            t.append(a.elapsed_time(b))
+        best[name] = src.numel() * src.element_size() / (min(t) * 1e-3) / 1e9
+    return best
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -886,6 +906,7 @@ def main():
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     _, e2e_s = replica_throughput(w.field_ops, e2e_s, "cuda")
+    link = link_rates(torch, hA, hC)
 
     # roofline of the dominant kernel (the slice GEMM)
     pk = peaks() or {}
@@ -942,7 +963,9 @@ def main():
            "autotuned": {"form": tuned[0], "schedule": tuned[1], "ms": tuned[2]},
            "e2e": {"value": world * w.field_ops / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": A.nbytes + B.nbytes + (hC.numel() * hC.element_size() if add else 0),
-                   "d2h_bytes_per_step": hC.numel() * hC.element_size()},
+                   "d2h_bytes_per_step": hC.numel() * hC.element_size(), "link": link,
+                   "copy_floor_s": (A.nbytes + B.nbytes) / (link["h2d_gbs"] * 1e9)
+                                   + hC.numel() * hC.element_size() / (link["d2h_gbs"] * 1e9)},
            "roofline": roof,
            "forms": {k: ({"value": v["value"], "verified": v["verified"], "ms_per_step": v["ms_per_step"],
                           "gemm_ms": v["gemm_ms"],

@@ -576,6 +576,7 @@ m4rie_status m4rie_create(m4rie_ctx** out, void* stream) {
   if (const char* s = getenv("M4RIE_TC_CLUSTER")) ctx->cluster = atoi(s) == 1 ? 1 : 3;
   if (const char* s = getenv("M4RIE_PDL")) ctx->pdl = atoi(s) != 0;
   if (const char* s = getenv("M4RIE_FUSE_RECOMBINE")) ctx->fuse_recombine = atoi(s) != 0;
+  if (const char* s = getenv("M4RIE_IO_PANELS")) ctx->io_panels = std::min(std::max(1, atoi(s)), kIoPanelsMax);
   if (const char* s = getenv("M4RIE_BATCHED_SCHED"))
     ctx->batched_sched = strcmp(s, "alpha_b") == 0 ? M4RIE_SCHED_ALPHA_B
                          : strcmp(s, "karatsuba") == 0 ? M4RIE_SCHED_KARATSUBA : M4RIE_SCHED_AUTO;
@@ -659,7 +660,7 @@ m4rie_status io_streams(m4rie_ctx* ctx) {
   if (ctx->s_in) return M4RIE_OK;
   cudaError_t err = cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking);
   if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking);
-  for (int i = 0; i < 2 * kIoPanels && err == cudaSuccess; ++i)
+  for (int i = 0; i < 2 * kIoPanelsMax && err == cudaSuccess; ++i)
     err = cudaEventCreateWithFlags(&ctx->io_ev[i], cudaEventDisableTiming);
   return err == cudaSuccess ? M4RIE_OK : cuda_fail(ctx, err);
 }
@@ -712,7 +713,7 @@ m4rie_status m4rie_mul_host(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_
     // copied and sliced once; every panel takes the form and schedule chosen
     // for the whole product, so that the later panels reuse its planes.
     if ((st = io_streams(ctx)) != M4RIE_OK) return st;
-    constexpr int P = kIoPanels;
+    const int P = ctx->io_panels;
     const int64_t mp = round_up(ceil_div(m, P), 256);
     const int form = resolve_form(ctx, e, m, n, k), sched = resolve_schedule(ctx, e, m, n, k);
     const uint8_t* hA8 = static_cast<const uint8_t*>(hA);

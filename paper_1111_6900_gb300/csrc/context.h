@@ -18,7 +18,7 @@ struct TuneEntry {
 };
 int shape_class(int64_t m, int64_t n, int64_t k);  // floor(log2(m*n*k)), tune.cu
 // Operands of one product: A m x k, B k x n, C m x n, row strides in elements.
-constexpr int kIoPanels = 4;  // row panels of a pipelined host-buffer product
+constexpr int kIoPanelsMax = 8;  // row panels of a pipelined host-buffer product, at most
 
 struct Mats {
   const void* A;
@@ -77,7 +77,8 @@ struct m4rie_ctx {
   cudaStream_t ech_side = nullptr;
   cudaEvent_t ech_ev[2] = {};
   void* ech_po_host = nullptr;
-  cudaEvent_t io_ev[2 * m4rie::kIoPanels] = {};
+  cudaEvent_t io_ev[2 * m4rie::kIoPanelsMax] = {};
+  int io_panels = 4;  // row panels of a pipelined host-buffer product (M4RIE_IO_PANELS, 1..8)
   int group_m = 0;      // tcgen05 tile raster: m-tiles per column group (0: all m-tiles)
   m4rie::TuneEntry tuned[11][64];  // [e][floor(log2(m*n*k))] -> autotuned choice (form 0: none)
   // phase timing (m4rie_enable_timing)
