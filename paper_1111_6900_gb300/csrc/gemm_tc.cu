@@ -104,8 +104,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 
 // Bulk copy of `bytes` (a multiple of 16) from shared to global memory,
 // tracked by this thread's bulk-async group.
+// The parity planes are read back by the recombination right after the GEMM:
+// they are written with an L2 evict-last hint, so that the GEMM's own stream
+// of operand planes does not push them out to DRAM first.
 __device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
+  uint64_t policy;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(gdst),
+               "r"(ssrc), "r"(bytes), "l"(policy)
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
@@ -281,6 +287,24 @@ __device__ __forceinline__ int next_tile(const TcParams& p, int tile, int tstep)
 
 // FP4 only: TMEM columns [SF_COL, SF_COL + 16) hold the unit scale factors.
 constexpr int SF_COL = 240;
+// Every accumulator starts at 2^23 (the epilogue stores it into the columns
+// it has drained before releasing them, and into both buffers at the start):
+// an integer count x < 2^23 accumulated onto 2^23 in FP32 is exact and leaves
+// x in the low mantissa bits, so bit 0 of the raw word is x mod 2.
+constexpr uint32_t kBias = 0x4B000000u;  // 2^23 as FP32
+__host__ __device__ constexpr int bias_cols(int fmt) { return fmt == kFmtNib ? SF_COL : ACC_COLS; }
+
+// Store 2^23 into `cols` (a multiple of 16) accumulator columns from taddr on,
+// for this warp's 32 lanes, and wait for the stores.
+__device__ __forceinline__ void tmem_fill_bias(uint32_t taddr, int cols) {
+  for (int c = 0; c < cols; c += 16)
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
+            taddr + c),
+        "r"(kBias)
+        : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 
 // Everything a role needs to know about one output tile.
 struct TileV {
@@ -513,6 +537,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t crank = CLN == 2 ? cluster_rank() : 0;
   if (CLN == 2) cluster_sync();  // the peer's barriers are initialised before anything lands in them
   const uint32_t tmem = *tmem_slot;
+  if (warp >= 2) {  // both accumulators start at 2^23 (each epilogue warp owns 32 TMEM lanes)
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+    tmem_fill_bias(tmem + lanes, bias_cols(FMT));
+    tmem_fill_bias(tmem + lanes + ACC_COLS, bias_cols(FMT));
+  }
   if (FMT == kFmtNib) {
     // Unit block-scale factors (UE8M0 0x7F = 2^0) for every lane, written by
     // the four epilogue warps (each owns 32 TMEM lanes).
@@ -525,12 +554,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           : "memory");
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    // CG2: the even CTA's MMAs read the peer's scale factors too
-    if (CG2) cluster_sync();
   }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  // CG2: the even CTA's MMAs write the peer's accumulators (and read its scale factors)
+  if (CG2) cluster_sync();
   const int total = BATCHED ? p.tiles_m : p.batch * p.tiles_m * p.tiles_n;
   const uint64_t lim = p.wait_limit_ns;
   // tile loop: every CTA (CL = 1) or every CTA pair (CL = 3) takes every
@@ -658,7 +687,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint64_t db = sdb0 + (uint64_t)((stage * KPS + h) * (B_SLOT >> 4));
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                  const uint32_t acc = (kb + h > kb0 || k > 0) ? 1u : 0u;
+                  const uint32_t acc = 1u;  // onto the 2^23 bias
                   if (CG2) {
                     if (FMT == kFmtNib) mma_f4_cg2<NV>(d, da + 2 * k, db + 2 * k, idesc, sf, acc);
                     else mma_f8_cg2(d, da + 2 * k, db + 2 * k, idesc, acc);
@@ -734,31 +763,23 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int h = 0; h < 4; ++h) {
             const int c16 = 4 * g + h;
             if (c16 < nc16) {
-              if (t.mode == 1) {
-                if (kb0 == 0) {
-                  uint32_t* out = static_cast<uint32_t*>(t.C) + ((int64_t)tm * 128 + row) * t.ldc +
-                                  (int64_t)tn * t.BN + 16 * c16;
-#pragma unroll
-                  for (int j = 0; j < 16; ++j) out[j] = (uint32_t)__float2int_rz(__uint_as_float(v[h][j]));
-                }
-              } else {
+              {
                 uint32_t w = 0;
-                // parity of an integer count x < 2^23 held exactly in FP32: x + 2^23 is exact and
-                // leaves x in the low mantissa bits, so bit 0 of its encoding is x mod 2
+                // parity of the count: bit 0 of 2^23 + x (kBias)
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                  w |= (__float_as_uint(__uint_as_float(v[h][j]) + 8388608.0f) & 1u) << j;
+                for (int j = 0; j < 16; ++j) w |= (v[h][j] & 1u) << j;
                 bits[c16 >> 1] ^= w << (16 * (c16 & 1));
               }
             }
           }
         }
+        tmem_fill_bias(ta, bias_cols(FMT));  // the next chunk in this buffer starts at 2^23 again
         fence_before();
         if (CG2) mbar_arrive_cluster(mapa_rank(tempty0 + 8 * buf, 0));  // the even CTA's barrier
         else mbar_arrive(tempty0 + 8 * buf);
         ++chunk;
       }
-      if (!ok || t.mode == 1) continue;
+      if (!ok) continue;
       const int64_t r0 = (int64_t)tm * 128;
       if constexpr (FE > 0) {
         // Karatsuba recombination (Section 5): output slice s is the XOR of

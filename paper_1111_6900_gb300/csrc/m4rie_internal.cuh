@@ -184,7 +184,7 @@ struct TcParams {
   int add;
   uint32_t emask;
   int* status;
-  int mode;           // 0: elements, 1: raw counts of the first chunk (test hook), 2: parity planes
+  int mode;           // 0: elements, 2: parity planes, 3: Karatsuba recombined in the epilogue
   // parity mode: the planes are stored in blocks of 128 rows x 8 words (256
   // columns, the tile's BN / 32 <= 8 words and zeros), block (tm, tn) of
   // product b at word b * p_bstride + (tm * tiles_n + tn) * 1024, row i of

@@ -568,7 +568,7 @@ __device__ __forceinline__ void recombine_body(const RecombineParams& p, int64_t
                                      : p.P + r * p.ldw + w0;
     const uint4* src = reinterpret_cast<const uint4*>(base);
     const int64_t pstride = (p.blocked ? p.bstride : p.rows_p * p.ldw) / 4;  // in 16-byte groups
-#pragma unroll 4
+#pragma unroll 8
     for (int q = 0; q < p.r; ++q) {
       const uint4 pw = __ldg(src + q * pstride);
       const uint32_t m = qmask[q];

@@ -330,3 +330,25 @@ def test_host_buffers_pipelined_row_panels(pinned, accumulate):
         assert c.device_status() == m4.OK
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("form", ["tc_f4", "tc_f8"])
+@pytest.mark.parametrize("sched", ["alpha_b", "karatsuba"])
+def test_counts_at_the_chunk_limit(ctx, form, sched):
+    """Every entry of A and B has all its slice bits set, so the GF(2) counts
+    reach the largest value an accumulation chunk allows (the tensor forms
+    accumulate integer counts in FP32 on top of 2^23 and keep bit 0; a count
+    that lost a low bit would flip an output bit).  k spans several chunks."""
+    for e in (2, 4, 8):
+        f = workloads.FIELD_POLY[e]
+        m, n, k = 130, 70, 20000
+        A = np.full((m, k), (1 << e) - 1, dtype=np.uint8)
+        B = np.full((k, n), (1 << e) - 1, dtype=np.uint8)
+        B[::3] = 1
+        ctx.set_form(form)
+        ctx.set_schedule(sched)
+        got = ctx.mul(e, f, dev(A), dev(B)).cpu().numpy()
+        np.testing.assert_array_equal(got, oracle.matmul(e, f, A, B), err_msg=f"e={e}")
+    ctx.set_form("auto")
+    ctx.set_schedule("auto")
+    assert ctx.device_status() == m4.OK
