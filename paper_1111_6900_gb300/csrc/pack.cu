@@ -553,9 +553,23 @@ __device__ __forceinline__ bool store_elements(const RecombineParams& p, int64_t
 // that product q feeds output slice s.
 template <typename T, int E>
 __device__ __forceinline__ void recombine_body(const RecombineParams& p, int64_t idx, const uint32_t* qmask) {
+  // blocked layout: 256 consecutive threads take one block (128 rows of one
+  // column tile), thread 2 i + h row i's half h, so that their loads are
+  // contiguous; row layout: consecutive threads along a row
   const int64_t nw = (p.n + 31) / 32, ng = p.blocked ? 2 * p.tiles_n : (nw + 3) / 4;
-  const bool live = idx < p.m * ng;
-  const int64_t r = live ? idx / ng : 0, g = live ? idx % ng : 0;
+  int64_t r, g;
+  bool live;
+  if (p.blocked) {
+    const int64_t blk = idx >> 8;
+    r = (blk / p.tiles_n) * 128 + ((idx & 255) >> 1);
+    g = 2 * (blk % p.tiles_n) + (idx & 1);
+    live = r < p.m;
+  } else {
+    live = idx < p.m * ng;
+    r = live ? idx / ng : 0;
+    g = live ? idx % ng : 0;
+  }
+  if (!live) r = g = 0;
   const int64_t w0 = p.blocked ? (g >> 1) * p.tw + 4 * (g & 1) : 4 * g;  // output word of u = 0
   const int uvalid = p.blocked ? min(4, p.tw - 4 * (int)(g & 1)) : 4;    // words of this thread that exist
   uint32_t out[4][E];
@@ -821,7 +835,7 @@ cudaError_t launch_cling(int e, int64_t rows, int64_t cols, const uint64_t* slic
 }
 
 int64_t recombine_job_blocks(const RecombineParams& p) {
-  return ceil_div(p.m * (p.blocked ? 2 * p.tiles_n : ceil_div(ceil_div(p.n, 32), 4)), 256);
+  return p.blocked ? ceil_div(p.m, 128) * p.tiles_n : ceil_div(p.m * ceil_div(ceil_div(p.n, 32), 4), 256);
 }
 
 cudaError_t launch_recombine_batched(const RecombineParams* d_jobs, const int64_t* d_start, int njobs,
@@ -835,8 +849,7 @@ cudaError_t launch_recombine_batched(const RecombineParams* d_jobs, const int64_
 }
 
 cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches) {
-  const int64_t n = p.m * (p.blocked ? 2 * p.tiles_n : ceil_div(ceil_div(p.n, 32), 4));
-  const int64_t g = ceil_div(n, 256);
+  const int64_t g = recombine_job_blocks(p);
   if (p.r > 64 || (reinterpret_cast<uintptr_t>(p.P) & 15u) != 0) return cudaErrorInvalidValue;
   if (p.blocked ? (p.tw < 1 || p.tw > 8 || p.bstride % 4 != 0 || p.tiles_n * p.tw * 32 < p.n) : p.ldw % 4 != 0)
     return cudaErrorInvalidValue;
