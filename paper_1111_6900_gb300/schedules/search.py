@@ -209,11 +209,35 @@ def subfield_formulas(e, table):
     return out
 
 
+# Chinese remaindering over GF(2) itself, for e where no subfield helps: the
+# moduli (degrees adding up to 2e - 1) and their residue products' lengths
+GF2_CRT_MODULI = {
+    7: [("pt", 0, 2), ("pt", 1, 1), ("inf", 2), ("irr", [1, 1, 1]), ("irr", [1, 1, 0, 1]), ("irr", [1, 0, 1, 1])],
+}
+
+
+def gf2_crt_formulas(e, table):
+    if e not in GF2_CRT_MODULI:
+        return []
+
+    def ring(k, q):  # the shortest known formula for GF(2)[y]/(q), deg q = k
+        fk = FIELD_POLY[k]
+        base = [(a, b, reduce_poly(k, fk, w)) for a, b, w in recursive_formula(k)]
+        if table.get(k) and len(table[k]) < len(base):
+            base = table[k]
+        K = towers.GF(k, fk)
+        return towers.to_polynomial_basis(k, q, base, K.mul)
+
+    terms, tower_mul = towers.gf2_crt_formula(e, GF2_CRT_MODULI[e], ring)
+    pf = towers.to_polynomial_basis(e, FIELD_POLY[e], terms, tower_mul)
+    return [pf] if is_field_formula(e, FIELD_POLY[e], pf) else []
+
+
 def search(e, rounds, seeds, steps, plateau, known, table=None, verbose=True):
     f = FIELD_POLY[e]
     naive = [(1 << i, 1 << j, x_pow_mod(e, f, i + j)) for i in range(e) for j in range(e)]
     rec = [(a, b, reduce_poly(e, f, w)) for a, b, w in recursive_formula(e)]
-    pool = [t for t in [known, rec] + subfield_formulas(e, table or {}) if t]
+    pool = [t for t in [known, rec] + subfield_formulas(e, table or {}) + gf2_crt_formulas(e, table or {}) if t]
     best = min(pool, key=len)
     if verbose:
         print(f"e={e}: start formulas {sorted(len(t) for t in pool)}", flush=True)

@@ -1,19 +1,24 @@
-"""Bilinear formulas for GF(2^e) multiplication built through a subfield.
+"""Bilinear formulas for GF(2^e) multiplication by Chinese remaindering.
 
 For e = d * t, GF(2^e) is GF(2^d)[y] / (g) with g irreducible of degree t
-over GF(2^d).  Two elements are polynomials of degree < t over GF(2^d); their
-product (degree <= 2t - 2) is recovered from its residues modulo pairwise
-coprime moduli whose degrees add up to 2t - 1 (Chinese remaindering, the
-evaluation-interpolation of Toom and Cook): linear factors y - c for points c
-of GF(2^d), the point at infinity (the product's top coefficient), and monic
-irreducible quadratics over GF(2^d) when GF(2^d) has too few points.  Each
-residue product is one multiplication in GF(2^d) (linear moduli) or in
-GF(2^d)[y] / (q) ~ GF(2^2d) (quadratics, three GF(2^d) multiplications by
-Karatsuba), and each of those is a short GF(2) formula for GF(2^d).  Every
-map between them is GF(2)-linear, so the whole is a GF(2)-bilinear formula
-with (#linear moduli) * r(d) + (#quadratics) * 3 r(d) terms.  It is written in
-the tower basis and carried to the polynomial basis of GF(2)[x] / (f) through
-the isomorphism x -> tau, tau a root of f in the tower.
+over GF(2^d) (d = 1: GF(2)[y] / (g) itself).  Two elements are polynomials of
+degree < t over GF(2^d); their product (degree <= 2t - 2) is recovered from
+its residues modulo pairwise coprime moduli whose degrees add up to 2t - 1
+(the evaluation-interpolation of Toom and Cook): powers (y - c)^k of linear
+factors at points c of GF(2^d), the point at infinity (the product's top k
+coefficients), and monic irreducible polynomials over GF(2^d).  Each residue
+product is one multiplication in GF(2^d) (degree-1 moduli), a truncated
+product of two degree-1 polynomials (three GF(2^d) multiplications by
+Karatsuba, squared linear factors and infinity), or a multiplication in
+GF(2^d)[y] / (q) (a field of 2^(d deg q) elements).  Every map between them is
+GF(2)-linear, so the whole is a GF(2)-bilinear formula whose length is the
+sum of the residue products' lengths.  It is written in the tower basis and
+carried to the polynomial basis of GF(2)[x] / (f) through the isomorphism
+x -> tau, tau a root of f in the tower.
+
+Examples: e = 6 through GF(4) with its 4 points and infinity, 5 x 3 = 15
+products; e = 7 over GF(2) with x^2, x + 1, infinity^2, x^2 + x + 1 and the two
+irreducible cubics, 3 + 1 + 3 + 3 + 6 + 6 = 22.
 
 Only GF(2)-linear algebra on bit masks is used; the result is checked against
 the field product on every basis pair by the caller.
@@ -129,7 +134,7 @@ def monic_irreducibles(K: GF, t: int):
             yield m
 
 
-# ---------------------------------------------------------------- the tower construction
+# ---------------------------------------------------------------- Chinese remaindering
 
 def _block_bits(coeffs, d):
     return sum(c << (d * i) for i, c in enumerate(coeffs))
@@ -139,89 +144,137 @@ def _split(v: int, d: int, n: int):
     return [(v >> (d * i)) & ((1 << d) - 1) for i in range(n)]
 
 
-def subfield_formula(d: int, t: int, fd: int, small):
-    """The tower formula for GF(2^(d t)) = GF(2^d)[y] / (g): (terms, tower
-    multiplication), terms over the tower basis (bit d j + k = bit k of the
-    coefficient of y^j).  small: a formula for GF(2)[x] / (fd), terms
-    (L, R, W) over d bits.  None if GF(2^d) has too few moduli of degree <= 2."""
+def _deg2_formula(d, small, out_map):
+    """Formula for the product of two degree-1 polynomials over GF(2^d)
+    (2d bits each) by Karatsuba (three GF(2^d) products: u0 v0, u1 v1,
+    (u0 + u1)(v0 + v1)), the product's three coefficients (3d bits) sent
+    through the linear map out_map (columns: 3d masks)."""
+    lo = (1 << d) - 1
+    terms = []
+    for selu, blocks in ((1, (0, 1)), (2, (1, 2)), (3, (1,))):
+        for (l, r, w) in small:
+            L = (l if selu & 1 else 0) | ((l << d) if selu & 2 else 0)
+            R = (r if selu & 1 else 0) | ((r << d) if selu & 2 else 0)
+            W = 0
+            for b in blocks:
+                W ^= apply(out_map, (w & lo) << (d * b))
+            terms.append((L, R, W))
+    return terms
+
+
+def crt_formula(d: int, t: int, fd: int, small, g, moduli, ring_formula=None):
+    """GF(2)-bilinear formula for the product in GF(2^d)[y] / (g) (tower basis)
+    from residues modulo the given moduli, whose degrees add up to 2t - 1:
+      ("pt", c, k)   (y - c)^k, k = 1 or 2, residues in the basis 1, z (z = y - c);
+      ("inf", k)     the top k coefficients of the product (k = 1 or 2);
+      ("irr", q)     a monic irreducible q over GF(2^d) of degree >= 2 (coefficient list).
+    small: formula for GF(2^d) = GF(2)[x]/(fd).  ring_formula(q): formula for
+    GF(2^d)[y]/(q) in its basis 1, y, .. (default: Karatsuba for degree 2)."""
     K = GF(d, fd)
     e = d * t
-    g = next(monic_irreducibles(K, t))
     need = 2 * t - 1
-    # moduli: linear points first, then infinity, then quadratics
-    mods = [("lin", c) for c in range(K.q)][:need]
-    if len(mods) < need:
-        mods.append(("inf", None))
-    quads = []
-    if sum(1 for _ in mods) < need:
-        qs = monic_irreducibles(K, 2)
-        while len(mods) + 2 * len(quads) < need:
-            quads.append(next(qs))
-        if len(mods) + 2 * len(quads) != need:  # an odd remainder: drop one linear point
-            mods.pop(0 if mods[0][0] == "lin" else 1)
-    mods += [("quad", q) for q in quads]
-    assert sum(2 if k == "quad" else 1 for k, _ in mods) == need
 
-    def residue(coeffs, mod):
-        kind, v = mod
-        if kind == "lin":
-            acc = 0
-            for j in range(len(coeffs) - 1, -1, -1):
-                acc = K.mul(acc, v) ^ coeffs[j]
-            return acc
-        if kind == "inf":  # the coefficient of y^(2t-2) of a product, the top coefficient of a factor
-            return coeffs[-1] if len(coeffs) == need else coeffs[t - 1]
-        return _block_bits(pmod(K, coeffs, v), d)
+    def degree(mod):
+        return mod[2] if mod[0] == "pt" else mod[1] if mod[0] == "inf" else len(mod[1]) - 1
 
-    def res_bits(mod):
-        return 2 * d if mod[0] == "quad" else d
+    assert sum(degree(m) for m in moduli) == need, "moduli degrees must add up to 2t - 1"
 
-    # residue maps of a factor (tower, e bits) and the forward map of a product ((2t-1) d bits)
+    def shift_at(coeffs, c):
+        """Coefficients of a(z + c)."""
+        out = [0] * len(coeffs)
+        for i in range(len(coeffs) - 1, -1, -1):   # Horner: out = out * (z + c) + a_i
+            nxt = [0] * len(coeffs)
+            for j, x in enumerate(out):
+                if x:
+                    if j + 1 < len(nxt):
+                        nxt[j + 1] ^= x
+                    nxt[j] ^= K.mul(x, c)
+            nxt[0] ^= coeffs[i]
+            out = nxt
+        return out
+
+    def residue(coeffs, mod, product):
+        kind = mod[0]
+        if kind == "pt":
+            return _block_bits(shift_at(coeffs, mod[1])[:mod[2]], d)
+        if kind == "inf":  # reversed top coefficients: u0 = top, u1 = next
+            top = len(coeffs) - 1 if product else t - 1
+            return _block_bits([coeffs[top - i] if top - i >= 0 else 0 for i in range(mod[1])], d)
+        return _block_bits(pmod(K, coeffs, mod[1]), d)
+
+    def nbits(mod):
+        return degree(mod) * d
+
     fwd = []
     for i in range(need * d):
         P = _split(1 << i, d, need)
         v, off = 0, 0
-        for mod in mods:
-            v |= residue(P, mod) << off
-            off += res_bits(mod)
+        for mod in moduli:
+            v |= residue(P, mod, True) << off
+            off += nbits(mod)
         fwd.append(v)
     crt = invert(fwd, need * d)
     assert crt is not None, "moduli are not coprime"
     red = [_block_bits(pmod(K, _split(1 << i, d, need), g), d) for i in range(need * d)]
 
-    # multiplication formula of GF(2^d)[y] / (q) (2d bits) by Karatsuba over GF(2^d)
-    def quad_formula(q):
-        # output map (c0, c1, c2) in GF^3 (3d bits) -> GF[y]/q (2d bits)
-        out_map = [_block_bits(pmod(K, _split(1 << i, d, 3), q), d) for i in range(3 * d)]
-        lo = (1 << d) - 1
-        terms = []
-        for selu, selv, blocks in ((1, 1, (0, 1)), (2, 2, (1, 2)), (3, 3, (1,))):
-            for (l, r, w) in small:
-                L = (l if selu & 1 else 0) | ((l << d) if selu & 2 else 0)
-                R = (r if selv & 1 else 0) | ((r << d) if selv & 2 else 0)
-                W = 0
-                for b in blocks:
-                    W ^= apply(out_map, (w & lo) << (d * b))
-                terms.append((L, R, W))
-        return terms
+    def mod_formula(mod):
+        if degree(mod) == 1:
+            return small
+        if mod[0] in ("pt", "inf"):  # product mod z^2: keep c0, c1
+            trunc = [_block_bits(_split(1 << i, d, 3)[:2], d) for i in range(3 * d)]
+            return _deg2_formula(d, small, trunc)
+        if ring_formula is not None:
+            return ring_formula(mod[1])
+        assert len(mod[1]) == 3, "irreducible moduli of degree > 2 need ring_formula"
+        return _deg2_formula(d, small, [_block_bits(pmod(K, _split(1 << i, d, 3), mod[1]), d) for i in range(3 * d)])
 
     terms = []
     off = 0
-    for mod in mods:
-        nb = res_bits(mod)
-        rmap = [residue(_split(1 << i, d, t), mod) for i in range(e)]
-        formula = small if nb == d else quad_formula(mod[1])
-        for (l, r, w) in formula:
-            L = pull_back(l, rmap)
-            R = pull_back(r, rmap)
-            W = apply(red, apply(crt, w << off))
-            terms.append((L, R, W))
-        off += nb
+    for mod in moduli:
+        rmap = [residue(_split(1 << i, d, t), mod, False) for i in range(e)]
+        for (l, r, w) in mod_formula(mod):
+            terms.append((pull_back(l, rmap), pull_back(r, rmap), apply(red, apply(crt, w << off))))
+        off += nbits(mod)
 
     def tower_mul(a: int, b: int) -> int:
         return _block_bits(pmod(K, pmul(K, _split(a, d, t), _split(b, d, t)), g), d)
 
     return terms, tower_mul
+
+
+def subfield_formula(d: int, t: int, fd: int, small):
+    """The tower formula for GF(2^(d t)) = GF(2^d)[y] / (g): (terms, tower
+    multiplication), terms over the tower basis (bit d j + k = bit k of the
+    coefficient of y^j).  small: a formula for GF(2)[x] / (fd), terms
+    (L, R, W) over d bits.  Moduli: the points of GF(2^d), then infinity,
+    then monic irreducible quadratics."""
+    K = GF(d, fd)
+    g = next(monic_irreducibles(K, t))
+    need = 2 * t - 1
+    mods = [("pt", c, 1) for c in range(K.q)][:need]
+    if len(mods) < need:
+        mods.append(("inf", 1))
+    quads = []
+    if len(mods) < need:
+        qs = monic_irreducibles(K, 2)
+        while len(mods) + 2 * len(quads) < need:
+            quads.append(next(qs))
+        if len(mods) + 2 * len(quads) != need:  # an odd remainder: drop one linear point
+            mods.pop(0)
+    mods += [("irr", q) for q in quads]
+    return crt_formula(d, t, fd, small, g, mods)
+
+
+def gf2_crt_formula(e: int, moduli, field_formula):
+    """A formula for GF(2)[x]/(g) (g the first irreducible of degree e) from
+    residues over GF(2) itself; field_formula(k, q) gives a formula for
+    GF(2)[y]/(q) (q irreducible of degree k, as an integer bit mask)."""
+    K = GF(1, 0b10)
+    g = next(monic_irreducibles(K, e))
+    def ring(q):
+        qm = sum(c << i for i, c in enumerate(q))
+        return field_formula(len(q) - 1, qm)
+    return crt_formula(1, e, 0b10, [(1, 1, 1)], g, moduli, ring)
 
 
 def to_polynomial_basis(e: int, f: int, terms, tower_mul):
