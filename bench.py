@@ -618,7 +618,9 @@ def run_batched_workload(args, m4, torch, world, rank, local):
     tune_s = time.time() - t0
     with tempfile.NamedTemporaryFile("r", suffix=".txt", dir=ROOT, delete=True) as fh:
         ctx.tune_save(fh.name)
-        tuned = {(int(w[1]), int(w[2])): int(w[4]) for w in (l.split() for l in open(fh.name)) if w and w[0] == "B"}
+        lines = [w for w in (l.split() for l in open(fh.name)) if w and w[0] == "B"]
+        tuned = {(int(w[1]), int(w[2])): int(w[4]) for w in lines}
+        narrow = sum(1 for w in lines if int(w[5]) == 2)
     arr = m4.problem_array(probs)   # the descriptors, marshalled once
     for _ in range(args.warmup):
         ctx.mul_batched(arr)
@@ -708,6 +710,7 @@ def run_batched_workload(args, m4, torch, world, rank, local):
                       "form": "tcgen05 persistent batched launch replayed from a CUDA graph",
                       "schedules": {"karatsuba_classes": sum(1 for v in tuned.values() if v == m4.SCHED_KARATSUBA),
                                     "alpha_b_classes": sum(1 for v in tuned.values() if v == m4.SCHED_ALPHA_B),
+                                    "narrow_tile_classes": narrow,
                                     "tuning_s": round(tune_s, 2)},
                       "l2": "flushed between timed steps (512 MB write, not timed)"},
            "clocks": clk.summary(), "gpu_launches": gpu_launches, "roofline": roof,

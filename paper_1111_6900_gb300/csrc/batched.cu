@@ -123,6 +123,19 @@ bool use_karatsuba(const m4rie_ctx* ctx, const m4rie_problem& p, int r) {
   return p.e >= ctx->batched_kara_min_e && (double)p.m * p.n * p.k >= ctx->batched_kara_min_mnk;
 }
 
+// Tile width of one product of a batch: kTileWide, the widest tile of its
+// form (alpha^j-B: e G columns with G = tc_group(e); Karatsuba: 224 for FP4,
+// 256 for FP8), or kTileNarrow, the narrowest tile that still covers the
+// product's columns in one tile where they are fewer; the tuner's measured
+// choice for the class, else wide for alpha^j-B and narrow for Karatsuba.
+enum { kTileDefault = 0, kTileWide = 1, kTileNarrow = 2 };
+int tile_choice(const m4rie_ctx* ctx, const m4rie_problem& p, bool kara) {
+  if (ctx->batched_force_width) return ctx->batched_force_width;
+  const TuneEntry& t = ctx->btuned[p.e][shape_class(p.m, p.n, p.k)];
+  if (t.sched && t.group_m) return t.group_m;
+  return kara ? kTileNarrow : kTileWide;
+}
+
 }  // namespace
 
 namespace {
@@ -226,7 +239,8 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
       // 224 (FP4) or 256 (FP8), in whole 32-column words of the parity blocks
       L.kara = true;
       L.r = L.sc.r;
-      L.BN = (int)std::min<int64_t>(fmt == kFmtNib ? 224 : 256, round_up(p.n, 32));
+      const int wide = fmt == kFmtNib ? 224 : 256;
+      L.BN = tile_choice(ctx, p, true) == kTileNarrow ? (int)std::min<int64_t>(wide, round_up(p.n, 32)) : wide;
       L.G = L.BN;
       L.ld = L.Kp;
       L.ld_bytes = L.ld * bits / 8;
@@ -242,6 +256,11 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
       ws += round_up((int64_t)L.r * L.p_plane * 4, 1024);
     } else {
       L.G = tc_group(p.e, fmt);
+      if (tile_choice(ctx, p, false) == kTileNarrow) {
+        // the fewest elements per tile that cover n, with e G a multiple of 16
+        const int step = 16 / std::gcd(p.e, 16);
+        L.G = (int)std::min<int64_t>(L.G, round_up(p.n, step));
+      }
       L.BN = p.e * L.G;
       L.ld = (int64_t)p.e * L.Kp;
       L.ld_bytes = L.ld * bits / 8;
@@ -571,10 +590,20 @@ extern "C" m4rie_status m4rie_tune_batched(m4rie_ctx* ctx, int count, const m4ri
     Schedule sc;
     const bool kara_ok = karatsuba_schedule(e, problems[cls[key][0]].f, &sc) && sc.r < e * e;
     double best_ms = 0;
-    int best = 0;
-    for (int sched = M4RIE_SCHED_ALPHA_B; sched <= M4RIE_SCHED_KARATSUBA && err == cudaSuccess; ++sched) {
+    int best = 0, best_width = 0;
+    for (int cand = 0; cand < 4 && err == cudaSuccess; ++cand) {
+      const int sched = cand < 2 ? M4RIE_SCHED_ALPHA_B : M4RIE_SCHED_KARATSUBA;
+      const int width = cand % 2 ? kTileNarrow : kTileWide;
       if (sched == M4RIE_SCHED_KARATSUBA && !kara_ok) continue;
+      // the narrow tile is another candidate only where some product of the class has fewer columns
+      if (width == kTileNarrow) {
+        bool differs = false;
+        for (int t = 0; t < take; ++t) differs |= sub[t].n < (sched == M4RIE_SCHED_KARATSUBA ? (fmt == kFmtNib ? 224 : 256)
+                                                                                             : tc_group(e, fmt));
+        if (!differs) continue;
+      }
       ctx->batched_force = sched;
+      ctx->batched_force_width = width;
       m4rie_status st = run_batched(ctx, take, sub.data(), fmt);  // records the plan, runs once
       for (int w = 0; w < 2 && st == M4RIE_OK; ++w) st = run_batched(ctx, take, sub.data(), fmt);
       float ms = 0;
@@ -591,17 +620,20 @@ extern "C" m4rie_status m4rie_tune_batched(m4rie_ctx* ctx, int count, const m4ri
       }
       if (err == cudaSuccess && (!best || ms < best_ms)) {
         best = sched;
+        best_width = width;
         best_ms = ms;
       }
     }
     ctx->batched_force = 0;
+    ctx->batched_force_width = 0;
     cudaStreamSynchronize(ctx->stream);
     cudaFree(buf);
     if (err != cudaSuccess) result = M4RIE_ERR_CUDA;
-    if (result == M4RIE_OK && best) ctx->btuned[e][c] = TuneEntry{fmt == kFmtByte ? M4RIE_FORM_TC_F8 : M4RIE_FORM_TC_F4,
-                                                                 best, 0, best_ms / 5.0};
+    if (result == M4RIE_OK && best)
+      ctx->btuned[e][c] = TuneEntry{fmt == kFmtByte ? M4RIE_FORM_TC_F8 : M4RIE_FORM_TC_F4, best, best_width, best_ms / 5.0};
   }
   ctx->batched_force = 0;
+  ctx->batched_force_width = 0;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   // the choices may have changed: the next batched call records a new plan

@@ -64,10 +64,11 @@ struct m4rie_ctx {
   int batched_sched = M4RIE_SCHED_AUTO;
   int batched_kara_min_e = 3;
   double batched_kara_min_mnk = 0;
-  // m4rie_tune_batched: measured schedule per [e][floor(log2(m n k))] (sched
-  // 0: not tuned); batched_force: the schedule a tuning run imposes
+  // m4rie_tune_batched: measured schedule and tile width (group_m: 1 wide,
+  // 2 narrow) per [e][floor(log2(m n k))] (sched 0: not tuned);
+  // batched_force(_width): what a tuning run imposes
   m4rie::TuneEntry btuned[11][64];
-  int batched_force = 0;
+  int batched_force = 0, batched_force_width = 0;
   // m4rie_mul_host: kernels use pinned, device-mapped host buffers of small
   // products in place (M4RIE_ZERO_COPY=0: always staging copies)
   int zero_copy = 1;

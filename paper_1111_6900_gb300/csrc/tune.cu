@@ -175,11 +175,11 @@ m4rie_status m4rie_tune_save(m4rie_ctx* ctx, const char* path) {
       const TuneEntry& t = ctx->tuned[e][c];
       if (t.form) fprintf(fp, "%d %d %d %d %d %.6f\n", e, c, t.form, t.sched, t.group_m, t.ms);
     }
-  // batched products (m4rie_tune_batched): "B e shape_class form schedule ms"
+  // batched products (m4rie_tune_batched): "B e shape_class form schedule tile_width ms"
   for (int e = 2; e <= 10; ++e)
     for (int c = 0; c < 64; ++c) {
       const TuneEntry& t = ctx->btuned[e][c];
-      if (t.sched) fprintf(fp, "B %d %d %d %d %.6f\n", e, c, t.form, t.sched, t.ms);
+      if (t.sched) fprintf(fp, "B %d %d %d %d %d %.6f\n", e, c, t.form, t.sched, t.group_m, t.ms);
     }
   fclose(fp);
   return M4RIE_OK;
@@ -195,10 +195,11 @@ m4rie_status m4rie_tune_load(m4rie_ctx* ctx, const char* path) {
     int e, c, form, sched, gm;
     double ms;
     if (line[0] == 'B') {
-      if (sscanf(line + 1, "%d %d %d %d %lf", &e, &c, &form, &sched, &ms) == 5 && e >= 2 && e <= 10 && c >= 0 &&
-          c < 64 && (form == M4RIE_FORM_TC_F4 || form == M4RIE_FORM_TC_F8) && sched >= M4RIE_SCHED_ALPHA_B &&
-          sched <= M4RIE_SCHED_KARATSUBA)
-        ctx->btuned[e][c] = TuneEntry{form, sched, 0, ms};
+      int width = 0;
+      if (sscanf(line + 1, "%d %d %d %d %d %lf", &e, &c, &form, &sched, &width, &ms) == 6 && e >= 2 && e <= 10 &&
+          c >= 0 && c < 64 && (form == M4RIE_FORM_TC_F4 || form == M4RIE_FORM_TC_F8) &&
+          sched >= M4RIE_SCHED_ALPHA_B && sched <= M4RIE_SCHED_KARATSUBA && width >= 0 && width <= 2)
+        ctx->btuned[e][c] = TuneEntry{form, sched, width, ms};
       continue;
     }
     if (sscanf(line, "%d %d %d %d %d %lf", &e, &c, &form, &sched, &gm, &ms) != 6) continue;

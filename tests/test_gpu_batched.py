@@ -104,10 +104,12 @@ def test_tune_batched_then_mul(tmp_path):
     path = str(tmp_path / "tune.txt")
     ctx.tune_save(path)
     with open(path) as fh:
-        tuned = {(int(w[1]), int(w[2])): int(w[4]) for w in (l.split() for l in fh) if w and w[0] == "B"}
+        lines = [w for w in (l.split() for l in fh) if w and w[0] == "B"]
+    tuned = {(int(w[1]), int(w[2])): int(w[4]) for w in lines}
     want = {(e, _shape_class(m, n, k)) for e, m, n, k, _ in specs}
     assert set(tuned) == want
     assert set(tuned.values()) <= {m4.SCHED_ALPHA_B, m4.SCHED_KARATSUBA}
+    assert {int(w[5]) for w in lines} <= {1, 2}          # tile width: wide or narrow
     ctx2 = m4.Context()                     # the cache file carries the choices
     ctx2.tune_load(path)
     for c in (ctx, ctx2):
@@ -125,6 +127,27 @@ def test_tune_batched_then_mul(tmp_path):
             np.testing.assert_array_equal(C.cpu().numpy(), want_c, err_msg=str(spec))
         assert c.device_status() == m4.OK
     ctx2.close()
+    ctx.close()
+
+
+@pytest.mark.parametrize("width", [1, 2])
+@pytest.mark.parametrize("sched", [1, 2])
+def test_batched_tile_widths_from_the_tune_cache(tmp_path, sched, width):
+    """Every (schedule, tile width) the tuner can pick, imposed through a tune
+    cache, gives the oracle's products (narrow tiles cover few columns)."""
+    specs = [(e, m, n, k, acc) for e, m, n, k, acc in KARA_SPECS if m and n and k]
+    path = tmp_path / "cache.txt"
+    with open(path, "w") as fh:
+        for e, m, n, k, _ in specs:
+            fh.write(f"B {e} {_shape_class(m, n, k)} {m4.FORM_TC_F4} {sched} {width} 1.0\n")
+    ctx = m4.Context()
+    ctx.tune_load(str(path))
+    probs, ref = _problems(specs, 5300)
+    ctx.mul_batched(probs)
+    torch.cuda.synchronize()
+    for (e, f, A, B, C, acc), r, spec in zip(probs, ref, specs):
+        np.testing.assert_array_equal(C.cpu().numpy(), r, err_msg=str(spec))
+    assert ctx.device_status() == m4.OK
     ctx.close()
 
 
