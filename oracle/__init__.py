@@ -9,7 +9,7 @@ The arithmetic lives in ``oracle.c`` (plain C, OpenMP over rows): the field
 product of Section 2 (carry-less multiply, then reduction modulo f) and its
 inverse, the cubic matrix product of Algorithm 1, the triangular solve of
 Algorithm 5 (Section 4.3), the reduced row echelon form of Algorithm 4
-(Section 4.1), the packed representation of Section 3.1 and the slicing /
+(Section 4.1) and the PLE decomposition of Section 4.2, the packed representation of Section 3.1 and the slicing /
 clinging conversions of Section 3.2 and Figure 1.  This module only compiles that file with gcc and
 marshals numpy arrays to it.
 """
@@ -92,6 +92,8 @@ class OracleLib:
         L.oracle_trsm_lower_left.argtypes = [i32, u32, i64, i64, vp, vp]
         L.oracle_echelon.restype = i64
         L.oracle_echelon.argtypes = [i32, u32, i64, i64, vp, vp]
+        L.oracle_ple.restype = i64
+        L.oracle_ple.argtypes = [i32, u32, i64, i64, vp, vp, vp]
         self.L = L
         self.path = path
 
@@ -207,6 +209,19 @@ class OracleLib:
         r = int(self.L.oracle_echelon(e, f, m, n, A16.ctypes.data, piv.ctypes.data)) if m and n else 0
         return A16.astype(elem_dtype(e)), r, piv[:r].copy()
 
+    def ple(self, e: int, f: int, A):
+        """Section 4.2: (A overwritten with its PLE decomposition, as a new
+        array; rank r; P (m swap partners); Q (n entries, the pivot columns
+        first)).  Layout of the result: see oracle_ple in oracle.c."""
+        A16 = _as_u16(A, e, "A").copy()
+        if A16.ndim != 2:
+            raise ValueError("A must be 2-D")
+        m, n = A16.shape
+        P = np.arange(max(1, m), dtype=np.int64)
+        Q = np.arange(max(1, n), dtype=np.int64)
+        r = int(self.L.oracle_ple(e, f, m, n, A16.ctypes.data, P.ctypes.data, Q.ctypes.data)) if m and n else 0
+        return A16.astype(elem_dtype(e)), r, P[:m].copy(), Q[:n].copy()
+
     def freivalds(self, e: int, f: int, A, B, C, trials: int = 64, seed: int = 0) -> bool:
         """Randomised check that C == A * B: with X an n x trials matrix of
         uniform field elements, compare A(BX) with CX.  A wrong C passes one
@@ -273,6 +288,10 @@ def trsm(e, f, T, B, upper=True):
 
 def echelon(e, f, A):
     return default().echelon(e, f, A)
+
+
+def ple(e, f, A):
+    return default().ple(e, f, A)
 
 
 def packed_width(e):

@@ -31,6 +31,12 @@
  *     the first row at or below the current rank with a non-zero entry is
  *     scaled to a leading 1, swapped up, and its multiples are added to every
  *     other row to clear the column.
+ *   - PLE decomposition (Section 4.2, the library's variant of the
+ *     definition): Algorithm 4 with the changes Section 4.2 lists, that is
+ *     the swap partners and pivot columns recorded, only the rows below the
+ *     pivot cleared and from the column after the pivot on (the multipliers
+ *     stay in place as L), and L's columns moved next to the diagonal at the
+ *     end by column swaps on and below the diagonal.
  *   - Packed representation (Section 3.1 and Figure 1): each element is
  *     padded to the next field width that divides 64 (2, 4, 8 or 16 bits;
  *     F_32 elements take 8 bits, Figure 1's F_8 elements 4) and a row is a
@@ -313,6 +319,79 @@ int64_t oracle_echelon(int e, uint32_t f, int64_t m, int64_t n, uint16_t *A, int
         if (pivots)
             pivots[r] = j;
         r++;
+    }
+    return r;
+}
+
+/* Section 4.2, PLE decomposition in the library's variant: A = P L E with P a
+ * permutation, L (m x r) lower trapezoidal whose diagonal holds the pivots,
+ * and E (r x n) in row echelon form with leading entries 1.  A (m x n,
+ * row-major, leading dimension n) is overwritten in place; returns r.
+ *
+ * For every column j, as in Algorithm 4: the first row i >= r with
+ * A[i][j] != 0 is swapped with row r (whole rows), P[r] = i, Q[r] = j.  The
+ * entries of row r right of column j are multiplied by A[r][j]^{-1}, so that
+ * row r from column j + 1 on is E's row r; A[r][j] stays as L's diagonal
+ * entry.  Every row k > r with x = A[k][j] gets x times row r added from
+ * column j + 1 on; x stays at (k, j) as L[k][r].  Rows above r are not
+ * touched.  Then r grows by one.  At the end L's column t, held in column
+ * Q[t], is moved to column t: for t = 0 .. r-1 the columns t and Q[t] are
+ * swapped in rows t .. m-1.
+ *
+ * Result: A[i][t] = L[i][t] for t <= min(i, r - 1); for k < r, E[k][j] = 0
+ * for j < Q[k], 1 for j = Q[k] and A[k][j] for j > Q[k]; every other entry
+ * of A is 0.  P[i] = i for i >= r and Q[j] = j for j >= r (P has m entries,
+ * Q n).  A is recovered from L E by swapping rows t and P[t] for
+ * t = r-1 down to 0. */
+int64_t oracle_ple(int e, uint32_t f, int64_t m, int64_t n, uint16_t *A, int64_t *P, int64_t *Q)
+{
+    int nt = oracle_get_threads();
+    (void)nt;
+    for (int64_t i = 0; i < m; i++)
+        P[i] = i;
+    for (int64_t j = 0; j < n; j++)
+        Q[j] = j;
+    int64_t r = 0;
+    for (int64_t j = 0; j < n && r < m; j++) {
+        int64_t i = r;
+        while (i < m && A[i * n + j] == 0)
+            i++;
+        if (i == m)
+            continue;
+        if (i != r) {
+            uint16_t *ai = A + i * n, *ar = A + r * n;
+            for (int64_t c = 0; c < n; c++) {
+                uint16_t t = ar[c];
+                ar[c] = ai[c];
+                ai[c] = t;
+            }
+        }
+        P[r] = i;
+        Q[r] = j;
+        uint16_t *pr = A + r * n;
+        uint32_t inv = oracle_gf_inv(e, f, pr[j]);
+        for (int64_t c = j + 1; c < n; c++)
+            pr[c] = (uint16_t)oracle_gf_mul(e, f, inv, pr[c]);
+#pragma omp parallel for schedule(static) num_threads(nt) if ((m - r) * (n - j) > 65536)
+        for (int64_t k = r + 1; k < m; k++) {
+            uint32_t x = A[k * n + j];
+            if (x == 0)
+                continue;
+            uint16_t *ak = A + k * n;
+            for (int64_t c = j + 1; c < n; c++)
+                ak[c] ^= (uint16_t)oracle_gf_mul(e, f, x, pr[c]);
+        }
+        r++;
+    }
+    for (int64_t t = 0; t < r; t++) {
+        int64_t q = Q[t];
+        if (q == t)
+            continue;
+        for (int64_t k = t; k < m; k++) {
+            uint16_t v = A[k * n + t];
+            A[k * n + t] = A[k * n + q];
+            A[k * n + q] = v;
+        }
     }
     return r;
 }

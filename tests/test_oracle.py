@@ -15,6 +15,7 @@ import pytest
 import oracle
 import workloads
 from tests import fieldref as fr
+from tests import pleref
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -519,8 +520,8 @@ _MUTANTS = {
     # echelon form that clears only the rows below the pivot (not reduced)
     "echelon_below_only": ("for (int64_t k = 0; k < m; k++) {\n            if (k == r)", "for (int64_t k = r + 1; k < m; k++) {\n            if (k == r)"),
     # echelon form that searches for a pivot from the top instead of at or below the rank
-    "echelon_search_from_top": ("        int64_t i = r;\n        while (i < m && A[i * n + j] == 0)",
-                                "        int64_t i = 0;\n        while (i < m && A[i * n + j] == 0)"),
+    "echelon_search_from_top": ("        int64_t i = r;\n        while (i < m && A[i * n + j] == 0)\n            i++;\n        if (i == m)\n            continue;\n        uint32_t inv",
+                                "        int64_t i = 0;\n        while (i < m && A[i * n + j] == 0)\n            i++;\n        if (i == m)\n            continue;\n        uint32_t inv"),
     # echelon form that leaves the pivot row where it was found
     "echelon_no_swap": ("        if (i != r) {\n            uint16_t *ar = A + r * n;", "        if (0) {\n            uint16_t *ar = A + r * n;"),
     # echelon form that records the pivot's row instead of its column
@@ -539,6 +540,30 @@ _MUTANTS = {
     "unpack_keeps_padding": ("(uint16_t)((word >> (w * (c % per))) & ((1u << e) - 1u));",
                              "(uint16_t)((word >> (w * (c % per))) & ((1u << w) - 1u));"),
     # upper solve does not scale by the inverse diagonal entry
+    # PLE: the pivot row left where it was found
+    "ple_no_swap": ("        if (i != r) {\n            uint16_t *ai = A + i * n, *ar = A + r * n;",
+                    "        if (0) {\n            uint16_t *ai = A + i * n, *ar = A + r * n;"),
+    # PLE: the swap not recorded in P
+    "ple_p_not_recorded": ("        P[r] = i;", "        P[r] = r;"),
+    # PLE: Q records the pivot's row
+    "ple_q_records_row": ("        Q[r] = j;", "        Q[r] = i;"),
+    # PLE: the pivot row not scaled to a leading 1
+    "ple_no_scale": ("            pr[c] = (uint16_t)oracle_gf_mul(e, f, inv, pr[c]);\n#pragma omp parallel for schedule(static) num_threads(nt) if ((m - r) * (n - j) > 65536)",
+                     "            pr[c] = pr[c];\n#pragma omp parallel for schedule(static) num_threads(nt) if ((m - r) * (n - j) > 65536)"),
+    # PLE: the addition starts at the pivot column, so L is overwritten
+    "ple_clears_l": ("            for (int64_t c = j + 1; c < n; c++)\n                ak[c] ^= (uint16_t)oracle_gf_mul(e, f, x, pr[c]);\n        }\n        r++;",
+                     "            for (int64_t c = j; c < n; c++)\n                ak[c] ^= (uint16_t)oracle_gf_mul(e, f, x, pr[c]);\n        }\n        r++;"),
+    # PLE: the rows above the pivot cleared as well (reduced form)
+    "ple_clears_above": ("        for (int64_t k = r + 1; k < m; k++) {\n            uint32_t x = A[k * n + j];",
+                         "        for (int64_t k = 0; k < m; k++) {\n            uint32_t x = k == r ? 0 : A[k * n + j];"),
+    # PLE: L left in the pivot columns
+    "ple_no_compress": ("    for (int64_t t = 0; t < r; t++) {\n        int64_t q = Q[t];", "    for (int64_t t = 0; t < 0; t++) {\n        int64_t q = Q[t];"),
+    # PLE: the column swaps applied to every row, not only on and below the diagonal
+    "ple_compress_all_rows": ("        for (int64_t k = t; k < m; k++) {\n            uint16_t v = A[k * n + t];",
+                              "        for (int64_t k = 0; k < m; k++) {\n            uint16_t v = A[k * n + t];"),
+    # PLE: the last row with a non-zero entry becomes the pivot (a valid PLE, but not Algorithm 4's)
+    "ple_last_row": ("        int64_t i = r;\n        while (i < m && A[i * n + j] == 0)\n            i++;\n        if (i == m)\n            continue;\n        if (i != r) {",
+                     "        int64_t i = m - 1;\n        while (i >= r && A[i * n + j] == 0)\n            i--;\n        if (i < r)\n            continue;\n        if (i != r) {"),
     "trsm_no_scale": ("for (int64_t i = m - 1; i >= 0; i--) {\n        uint32_t d = U[i * m + i];\n        if (d == 0)\n            return -1;\n        uint32_t dinv = oracle_gf_inv(e, f, d);",
                       "for (int64_t i = m - 1; i >= 0; i--) {\n        uint32_t d = U[i * m + i];\n        if (d == 0)\n            return -1;\n        uint32_t dinv = 1;"),
 }
@@ -606,6 +631,22 @@ def _pins_pass(O: oracle.OracleLib) -> bool:
             E, r, p = O.echelon(e, f, A)
             if r != 6 or not np.array_equal(E.astype(np.int64), R) or not np.array_equal(p, piv):
                 return False
+            # PLE of the same S R and of a matrix with zero rows on top
+            Z = rng.integers(0, 1 << e, size=(9, 7))
+            Z[:4] = 0
+            for M in (A, Z):
+                out, r, P, Q = O.ple(e, f, M.astype(np.uint16))
+                _, rr, pv = O.echelon(e, f, M)
+                if not pleref.layout_ok(out, r, P, Q) or r != rr or list(Q[:r]) != list(pv):
+                    return False
+                if not np.array_equal(pleref.rebuild(e, f, out, r, P, Q, fr.slice_product), M.astype(np.int64)):
+                    return False
+        # the hand-worked PLE example
+        from tests.test_oracle_ple import read_hand_example
+        e, f, A, R, r, P, Q = read_hand_example()
+        out, rk, p, q = O.ple(e, f, A.astype(np.uint8))
+        if rk != r or not np.array_equal(out.astype(np.int64), R) or list(p) != P or list(q) != Q:
+            return False
         return True
     except Exception:
         return False
