@@ -176,6 +176,30 @@ m4rie_status m4rie_trsm_lower_left(m4rie_ctx *ctx, int e, uint32_t f, int64_t m,
 m4rie_status m4rie_echelonize(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, void *A, int64_t lda,
                               int64_t *rank, int64_t *pivots);
 
+/* PLE decomposition over GF(2^e) in place (Section 4.2, in the library's
+ * variant of the definition): A = P L E with P a permutation, L (m x r) lower
+ * trapezoidal holding the pivots on its diagonal and E (r x n) in row echelon
+ * form with leading entries 1.  Pivoting is Algorithm 4's (Section 4.1): for
+ * every column the first row at or below the current rank with a non-zero
+ * entry is swapped up, so the result is the one that algorithm with Section
+ * 4.2's changes gives.  A is m x n with row stride lda >= n.  On return, for
+ * rank r:
+ *   A[i][t] = L[i][t] for t <= min(i, r - 1);
+ *   for k < r: E[k][j] = 0 for j < Q[k], 1 for j = Q[k] (not stored),
+ *   A[k][j] for j > Q[k];
+ *   every other entry of A is 0.
+ * *rank (if rank != NULL) receives r; P (if not NULL, m entries) the swap
+ * partners: at step t rows t and P[t] were exchanged (P[t] >= t; P[i] = i for
+ * i >= r), so A is recovered from L E by swapping rows t and P[t] for
+ * t = r-1 down to 0; Q (if not NULL, n entries) the pivot column of step t
+ * in Q[t] for t < r (increasing) and Q[j] = j for j >= r.  P and Q are host
+ * arrays.  Runs by panels of 64 columns; synchronous (it reads each panel's
+ * pivot list back).  Entries >= 2^e set the sticky M4RIE_ERR_RANGE status.
+ * Uses the context-owned scratch of m4rie_echelonize (about 64 m + 256 n
+ * elements). */
+m4rie_status m4rie_ple(m4rie_ctx *ctx, int e, uint32_t f, int64_t m, int64_t n, void *A, int64_t lda, int64_t *rank,
+                       int64_t *P, int64_t *Q);
+
 /* m4rie_mul / m4rie_addmul (accumulate != 0) on HOST buffers: copies A, B
  * (and C when accumulating) to context-owned device memory, computes, copies
  * C back and waits for the stream.  Host buffers may be pageable or pinned.

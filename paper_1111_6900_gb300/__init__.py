@@ -55,6 +55,7 @@ def _load() -> ctypes.CDLL:
         "m4rie_trsm_upper_left": (i32, [vp, i32, u32, i64, i64, vp, i64, vp, i64]),
         "m4rie_trsm_lower_left": (i32, [vp, i32, u32, i64, i64, vp, i64, vp, i64]),
         "m4rie_echelonize": (i32, [vp, i32, u32, i64, i64, vp, i64, ctypes.POINTER(i64), vp]),
+        "m4rie_ple": (i32, [vp, i32, u32, i64, i64, vp, i64, ctypes.POINTER(i64), vp, vp]),
         "m4rie_mul_host": (i32, [vp, i32, u32, i64, i64, i64, vp, vp, vp, i32]),
         "m4rie_pack": (i32, [vp, i32, i64, i64, vp, vp, i64]),
         "m4rie_unpack": (i32, [vp, i32, i64, i64, vp, i64, vp]),
@@ -301,6 +302,21 @@ class Context:
         self._raise(lib.m4rie_echelonize(self.handle, e, f, m, n, _ptr(A), _ld(A) if m else n, ctypes.byref(rank),
                                          ctypes.c_void_p(piv.ctypes.data)), "m4rie_echelonize")
         return int(rank.value), [int(v) for v in piv[:rank.value]]
+
+    def ple(self, e: int, f: int, A):
+        """PLE decomposition of A in place (Section 4.2); returns (rank, P,
+        Q) with P (m swap partners) and Q (n entries, pivot columns first) as
+        int64 numpy arrays.  Layout of A afterwards: see m4rie_ple in the C
+        header.  Synchronous."""
+        import numpy as np
+        _check_dev(A, e, "A", strided=True)
+        m, n = A.shape
+        rank = ctypes.c_int64()
+        P = np.zeros(max(1, m), dtype=np.int64)
+        Q = np.zeros(max(1, n), dtype=np.int64)
+        self._raise(lib.m4rie_ple(self.handle, e, f, m, n, _ptr(A), _ld(A) if m else n, ctypes.byref(rank),
+                                  ctypes.c_void_p(P.ctypes.data), ctypes.c_void_p(Q.ctypes.data)), "m4rie_ple")
+        return int(rank.value), P[:m].copy(), Q[:n].copy()
 
     def mul_host(self, e: int, f: int, A, B, C, accumulate: bool = False):
         """Host-buffer product (torch CPU tensors or numpy arrays, row-major,

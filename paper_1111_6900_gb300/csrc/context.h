@@ -19,6 +19,7 @@ struct TuneEntry {
 int shape_class(int64_t m, int64_t n, int64_t k);  // floor(log2(m*n*k)), tune.cu
 // Operands of one product: A m x k, B k x n, C m x n, row strides in elements.
 constexpr int kIoPanelsMax = 8;  // row panels of a pipelined host-buffer product, at most
+constexpr size_t kPanelHostBytes = 1024;  // pinned pivot list of an echelon / PLE panel
 
 struct Mats {
   const void* A;
@@ -74,7 +75,8 @@ struct m4rie_ctx {
   int zero_copy = 1;
   // pipelined host-buffer products: copy streams and their events
   cudaStream_t s_in = nullptr, s_out = nullptr;
-  // echelon form look-ahead: side stream, its two events, pinned pivot list
+  // echelon form and PLE look-ahead: side stream, its two events, pinned
+  // pivot list of m4rie::kPanelHostBytes
   cudaStream_t ech_side = nullptr;
   cudaEvent_t ech_ev[2] = {};
   void* ech_po_host = nullptr;

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "context.h"
+#include "rowmove.cuh"
 
 namespace m4rie {
 
@@ -53,6 +54,7 @@ struct PanelOut {
   int rows[W];      // candidate index of pivot a
   int cols[W];      // panel column of pivot a
 };
+static_assert(sizeof(PanelOut) <= kPanelHostBytes, "pinned pivot list");
 
 // Rows i in [r, m) with a non-zero entry in a panel column not yet marked
 // done (done: bit j of done[j / 64]); the first R of them (in arrival order)
@@ -71,27 +73,6 @@ __global__ void select_rows(const T* __restrict__ A, int64_t lda, int64_t m, int
     const int idx = atomicAdd(count, 1);
     if (idx < R) cand[idx] = (int)i;
   }
-}
-
-// Row moves (columns c0 .. n-1): tmp[j] = A[src_j], then A[dst_j] = tmp[j].
-template <typename T>
-__global__ void gather_rows(const T* __restrict__ A, int64_t lda, int64_t c0, int64_t nt, const int* __restrict__ src,
-                            T* __restrict__ tmp) {
-  const int j = blockIdx.y;
-  const T* s = A + (int64_t)src[j] * lda + c0;
-  T* d = tmp + (int64_t)j * nt;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nt; c += (int64_t)gridDim.x * blockDim.x)
-    d[c] = s[c];
-}
-
-template <typename T>
-__global__ void scatter_rows(T* __restrict__ A, int64_t lda, int64_t c0, int64_t nt, const int* __restrict__ dst,
-                             const T* __restrict__ tmp) {
-  const int j = blockIdx.y;
-  T* d = A + (int64_t)dst[j] * lda + c0;
-  const T* s = tmp + (int64_t)j * nt;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nt; c += (int64_t)gridDim.x * blockDim.x)
-    d[c] = s[c];
 }
 
 // Step 2 on the candidate block A[r .. r+cnt)[c0 .. c0+wc) (cnt <= R): the
@@ -258,46 +239,20 @@ __global__ void gather_mult(const T* __restrict__ A, int64_t lda, int64_t m, int
   mult[i * W + a] = A[i * lda + c0 + po->cols[a]];
 }
 
-size_t ew(int e) { return e <= 8 ? 1 : 2; }
+size_t ew(int e) { return rowmove::elem_bytes(e); }
+using rowmove::fail;
+using rowmove::move_rows;
 
-constexpr int MOVE_SLOT = 4 * R;  // ints per pinned slot: up to 2R (src, dst) pairs
+constexpr int MOVE_SLOT = rowmove::kSlot;
+static_assert(R == rowmove::kRows, "candidate blocks and move lists have the same bound");
 
-struct Ews {
+struct Ews : rowmove::Bufs {
   int* cand = nullptr;      // [R] + count
-  int* moves = nullptr;     // device: two slots of [src | dst]
   PanelOut* po = nullptr;
   uint8_t* minv = nullptr;  // [W][W]
   uint8_t* mult = nullptr;  // [m][W]
   uint8_t* X = nullptr;     // [W][n]
-  uint8_t* tmp = nullptr;   // [2R][n]
-  int* host = nullptr;      // pinned: two slots of [src | dst]
 };
-
-m4rie_status fail(m4rie_ctx* ctx, cudaError_t err) {
-  ctx->last_error = cudaGetErrorString(err);
-  return M4RIE_ERR_CUDA;
-}
-
-// Row moves src[j] -> dst[j] of columns c0 .. n-1 through tmp, the lists
-// staged in pinned slot `slot`.  A slot is written again only after a later
-// read-back has synchronized the stream, so no wait is needed here.
-template <typename T>
-cudaError_t move_rows(m4rie_ctx* ctx, const Ews& w, int slot, T* A, int64_t lda, int64_t c0, int64_t nt,
-                      const std::vector<int>& src, const std::vector<int>& dst) {
-  const int nm = (int)src.size();
-  if (nm == 0 || nt == 0) return cudaSuccess;
-  int* h = w.host + slot * MOVE_SLOT;
-  int* d = w.moves + slot * MOVE_SLOT;
-  std::copy(src.begin(), src.end(), h);
-  std::copy(dst.begin(), dst.end(), h + nm);
-  cudaError_t err = cudaMemcpyAsync(d, h, sizeof(int) * 2 * nm, cudaMemcpyHostToDevice, ctx->stream);
-  if (err != cudaSuccess) return err;
-  const dim3 grid((unsigned)std::min<int64_t>(ceil_div(nt, 256), 64), (unsigned)nm);
-  gather_rows<T><<<grid, 256, 0, ctx->stream>>>(A, lda, c0, nt, d, reinterpret_cast<T*>(w.tmp));
-  scatter_rows<T><<<grid, 256, 0, ctx->stream>>>(A, lda, c0, nt, d + nm, reinterpret_cast<const T*>(w.tmp));
-  ctx->launches += 2;
-  return cudaGetLastError();
-}
 
 // Moves that bring rows want[0..] (sorted) to positions base, base+1, ...;
 // the rows they displace take the vacated positions.
@@ -370,7 +325,7 @@ m4rie_status echelon_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t 
     if ((err = cudaStreamCreateWithFlags(&ctx->ech_side, cudaStreamNonBlocking)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&ctx->ech_ev[0], cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&ctx->ech_ev[1], cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaMallocHost(&ctx->ech_po_host, sizeof(PanelOut))) != cudaSuccess)
+        (err = cudaMallocHost(&ctx->ech_po_host, kPanelHostBytes)) != cudaSuccess)
       return fail(ctx, err);
   }
   PanelOut* hpo_next = static_cast<PanelOut*>(ctx->ech_po_host);

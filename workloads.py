@@ -129,6 +129,14 @@ ECHELON_WORKLOADS = {
 }
 
 
+# PLE decompositions (Section 4.2) of random dense matrices: (e, m, n, seed)
+PLE_WORKLOADS = {
+    "ple_gf4_4000": (2, 4000, 4000, 1300),
+    "ple_gf256_1000": (8, 1000, 1000, 1301),
+    "ple_gf16_8192": (4, 8192, 8192, 1302),
+}
+
+
 def echelon_matrix(e: int, m: int, n: int, seed: int):
     """Seeded m x n matrix, entries uniform in [0, 2^e)."""
     return elements(np.random.default_rng(seed), e, (m, n))
