@@ -394,22 +394,34 @@ def run_trsm_workload(args, m4, torch, world, rank, local):
 PAPER_ECHELON_MS = {"rref_gf4_4000": 400.0, "rref_gf256_1000": 81.0}
 
 
+def is_ple(name):
+    return name in workloads.PLE_WORKLOADS
+
+
 def echelon_config(name):
-    e, m, n, seed = workloads.ECHELON_WORKLOADS[name]
+    """(e, m, n, seed, config) of a reduced echelon form or PLE workload."""
+    ple = is_ple(name)
+    e, m, n, seed = (workloads.PLE_WORKLOADS if ple else workloads.ECHELON_WORKLOADS)[name]
     ty = "uint8" if e <= 8 else "uint16"
+    what = "PLE decomposition (Section 4.2)" if ple else "reduced row echelon form"
     return e, m, n, seed, {
-        "workload": f"reduced row echelon form over GF(2^{e}), f = {hex(workloads.FIELD_POLY[e])}, random {m}x{n} {ty}",
-        "m": m, "n": n, "e": e, "op": "echelonize", "l2": "flushed between timed steps (512 MB write, not timed)"}
+        "workload": f"{what} over GF(2^{e}), f = {hex(workloads.FIELD_POLY[e])}, random {m}x{n} {ty}",
+        "m": m, "n": n, "e": e, "op": "ple" if ple else "echelonize",
+        "l2": "flushed between timed steps (512 MB write, not timed)"}
 
 
-def echelon_cpu_sample(e, f, A):
+def echelon_metric(name):
+    return f"GF(2^e) {'PLE decomposition' if is_ple(name) else 'reduced echelon form'} time, {name}"
+
+
+def echelon_cpu_sample(e, f, A, ple=False):
     """The oracle on the leading block of at most 1000 x 1000, scaled to the
     whole matrix by (rows x columns x rank), i.e. by (m n min(m, n)) / (s^2 min)."""
     import oracle
     m, n = A.shape
     s = min(1000, m, n)
     t0 = time.perf_counter()
-    oracle.echelon(e, f, np.ascontiguousarray(A[:s, :s]))
+    (oracle.ple if ple else oracle.echelon)(e, f, np.ascontiguousarray(A[:s, :s]))
     dt = time.perf_counter() - t0
     scale = (m * n * min(m, n)) / float(s * s * s)
     return dt * scale, f"leading {s}x{s} block ({dt:.2f} s), scaled by m n min(m,n) / {s}^3 = {scale:.1f} (extrapolated)"
@@ -419,16 +431,17 @@ def run_reference_echelon(args):
     e, m, n, seed, config = echelon_config(args.workload)
     f = workloads.FIELD_POLY[e]
     A = workloads.echelon_matrix(e, m, n, seed)
+    ple = is_ple(args.workload)
     for _ in range(min(args.warmup, 1)):
-        echelon_cpu_sample(e, f, A)
+        echelon_cpu_sample(e, f, A, ple)
     times = []
     for _ in range(args.steps):
-        t, sample = echelon_cpu_sample(e, f, A)
+        t, sample = echelon_cpu_sample(e, f, A, ple)
         times.append(t)
     ms = sum(times) / len(times) * 1e3
     import oracle
     base = PAPER_ECHELON_MS.get(args.workload)
-    out = {"impl": "reference", "metric": f"GF(2^e) reduced echelon form time, {args.workload}", "value": ms,
+    out = {"impl": "reference", "metric": echelon_metric(args.workload), "value": ms,
            "unit": "ms", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": ms / base if base else None,
            "dtype": "u8" if e <= 8 else "u16", "data": "synthetic", "config": config,
@@ -440,11 +453,19 @@ def run_reference_echelon(args):
 
 
 def run_echelon_workload(args, m4, torch, world, rank, local):
-    """Reduced row echelon form of a random dense matrix (Section 4.1,
-    Algorithm 4, by panels over the slice GEMM); value = ms per echelon form."""
+    """Reduced row echelon form (Section 4.1, Algorithm 4) or PLE
+    decomposition (Section 4.2) of a random dense matrix, by panels over the
+    slice GEMM; value = ms per decomposition."""
     e, m, n, seed, config = echelon_config(args.workload)
     f = workloads.FIELD_POLY[e]
     A = workloads.echelon_matrix(e, m, n, seed)
+    ple = is_ple(args.workload)
+
+    def decompose(d):
+        if ple:
+            r, _, _ = ctx.ple(e, f, d)
+            return r
+        return ctx.echelonize(e, f, d)[0]
     dA0 = torch.from_numpy(A).cuda()
     dA = dA0.clone()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -453,16 +474,16 @@ def run_echelon_workload(args, m4, torch, world, rank, local):
     if args.single:
         for _ in range(args.warmup + 1):
             dA.copy_(dA0)
-            ctx.echelonize(e, f, dA)
+            decompose(dA)
         torch.cuda.synchronize()
         status = ctx.device_status()
         ctx.close()
         return 0 if status == m4.OK else 1
-    rank0, piv0 = ctx.echelonize(e, f, dA)
+    rank0 = decompose(dA)
     E0 = dA.clone()
     for _ in range(args.warmup):
         dA.copy_(dA0)
-        ctx.echelonize(e, f, dA)
+        decompose(dA)
     torch.cuda.synchronize()
     launches0 = ctx.kernel_launches()
     ms_list = []
@@ -475,7 +496,7 @@ def run_echelon_workload(args, m4, torch, world, rank, local):
             flush.fill_(i & 0xFF)
             s, t = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s.record(stream)
-            rk, _ = ctx.echelonize(e, f, dA)
+            decompose(dA)
             t.record(stream)
             torch.cuda.synchronize()
             ms_list.append(s.elapsed_time(t))
@@ -491,19 +512,25 @@ def run_echelon_workload(args, m4, torch, world, rank, local):
     ctx.enable_timing(True)
     ctx.phase_times(reset=True)
     dA.copy_(dA0)
-    ctx.echelonize(e, f, dA)
+    decompose(dA)
     pack_ms, gemm_ms, rec_ms, nprod = ctx.phase_times(reset=True)
     ctx.enable_timing(False)
     w = 1 if e <= 8 else 2
-    # every panel reads and writes columns c0.. of all m rows (the update) and the pivot rows (X)
     W = 64
-    upd = sum(2.0 * m * (n - c0) * w + 2.0 * W * (n - c0) * w for c0 in range(0, min(n, rank0 + W), W))
+    if ple:
+        # every panel reads and writes the columns right of it of the rows below
+        # its pivots (the update) and of its pivot rows (G)
+        upd = sum(2.0 * max(0, m - min(c0, rank0) - W) * max(0, n - c0 - W) * w + 2.0 * W * max(0, n - c0 - W) * w
+                  for c0 in range(0, min(n, rank0 + W), W))
+    else:
+        # every panel reads and writes columns c0.. of all m rows (the update) and the pivot rows (X)
+        upd = sum(2.0 * m * (n - c0) * w + 2.0 * W * (n - c0) * w for c0 in range(0, min(n, rank0 + W), W))
     pk = peaks() or {}
     hbm = pk.get("hbm_gbs", 6800.0)
     achieved = upd / ((gemm_ms + pack_ms + rec_ms) * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
-            "scope": f"the {nprod} slice products of one echelon form (packing + GEMM + recombination: "
+            "scope": f"the {nprod} slice products of one decomposition (packing + GEMM + recombination: "
                      f"{pack_ms + gemm_ms + rec_ms:.2f} of {ms:.2f} ms); algorithmic bytes = read + write of the "
                      f"updated columns of every row per panel"}
 
@@ -515,14 +542,14 @@ def run_echelon_workload(args, m4, torch, world, rank, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         dA.copy_(hA, non_blocking=True)
-        ctx.echelonize(e, f, dA)
+        decompose(dA)
         hE.copy_(dA, non_blocking=True)
         torch.cuda.synchronize()
         if i:
             e2e.append(time.perf_counter() - t0)
     e2e_ms = sum(e2e) / len(e2e) * 1e3
     base = PAPER_ECHELON_MS.get(args.workload)
-    out = {"metric": f"GF(2^e) reduced echelon form time, {args.workload}; bit-exact", "value": ms, "unit": "ms",
+    out = {"metric": f"{echelon_metric(args.workload)}; bit-exact", "value": ms, "unit": "ms",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": ms / base if base else None,
            "dtype": "u8" if e <= 8 else "u16", "data": "synthetic",
@@ -532,13 +559,13 @@ def run_echelon_workload(args, m4, torch, world, rank, local):
            "roofline": roof, "repeatable": same}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        t, sample = echelon_cpu_sample(e, f, A)
+        t, sample = echelon_cpu_sample(e, f, A, ple)
         out["cpu_baseline"] = {"value": t * 1e3, "unit": "ms", "cores": oracle.get_threads(), "kind": "oracle",
                                "sample": sample}
         s = min(1000, m, n)
         if s == min(m, n) and m == n:
-            E_ref, r_ref, p_ref = oracle.echelon(e, f, A)
-            out["bit_exact_vs_oracle"] = {"equal": bool(np.array_equal(E0.cpu().numpy(), E_ref)), "rank": r_ref}
+            ref = (oracle.ple if ple else oracle.echelon)(e, f, A)
+            out["bit_exact_vs_oracle"] = {"equal": bool(np.array_equal(E0.cpu().numpy(), ref[0])), "rank": ref[1]}
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -551,7 +578,7 @@ def run_reference(args):
         return 0
     if args.workload in workloads.TRSM_WORKLOADS:
         return run_reference_trsm(args)
-    if args.workload in workloads.ECHELON_WORKLOADS:
+    if args.workload in workloads.ECHELON_WORKLOADS or is_ple(args.workload):
         return run_reference_echelon(args)
     import oracle
     w = WORKLOAD
@@ -752,7 +779,7 @@ def main():
     names = {w.name: i for i, w in workloads.WORKLOADS.items()}
     ap.add_argument("--workload", default="gf16_4096_mul",
                     choices=sorted(names) + ["batched"] + sorted(workloads.TRSM_WORKLOADS)
-                    + sorted(workloads.ECHELON_WORKLOADS),
+                    + sorted(workloads.ECHELON_WORKLOADS) + sorted(workloads.PLE_WORKLOADS),
                     help="gf16_4096_mul (default, the headline), another single-product workload, batched, "
                          "or a triangular solve (trsm_*)")
     ap.add_argument("--batched-count", type=int, default=workloads.BATCHED_COUNT,
@@ -783,7 +810,7 @@ def main():
         return run_batched_workload(args, m4, torch, world, rank, local)
     if args.workload in workloads.TRSM_WORKLOADS:
         return run_trsm_workload(args, m4, torch, world, rank, local)
-    if args.workload in workloads.ECHELON_WORKLOADS:
+    if args.workload in workloads.ECHELON_WORKLOADS or is_ple(args.workload):
         return run_echelon_workload(args, m4, torch, world, rank, local)
 
     metric = METRIC if WORKLOAD.name == "gf16_4096_mul" else f"GF(2^e) matmul field-ops/s, {WORKLOAD.name}; bit-exact"

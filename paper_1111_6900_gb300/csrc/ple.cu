@@ -117,29 +117,60 @@ __device__ __forceinline__ uint32_t element_at(const uint32_t (&sl)[E], int b) {
   return v;
 }
 
+// Loads 32 consecutive elements of a row (columns c0 .. c0+31 relative to
+// the panel, those outside [lo, hi) as 0) as E bit slices; all loads are
+// issued before any is used.  Returns whether an entry was >= 2^E.
+template <typename T, int E>
+__device__ __forceinline__ bool load_word(const T* __restrict__ src, int cbase, int lo, int hi, uint32_t (&sl)[E]) {
+  const uint32_t q = (1u << E) - 1;
+  uint32_t v[32];
+#pragma unroll
+  for (int b = 0; b < 32; ++b) {
+    const int c = cbase + b;
+    v[b] = (c >= lo && c < hi) ? (uint32_t)src[b] : 0u;
+  }
+  uint32_t any = 0;
+#pragma unroll
+  for (int t = 0; t < E; ++t) sl[t] = 0;
+#pragma unroll
+  for (int b = 0; b < 32; ++b) {
+    any |= v[b];
+#pragma unroll
+    for (int t = 0; t < E; ++t) sl[t] |= ((v[b] >> t) & 1u) << b;
+  }
+  return (any & ~q) != 0;
+}
+
 // Step 1 on the candidate block A[r .. r+cnt) over panel columns [js, wc)
 // (columns left of js are closed: they hold L entries or zeros).  Thread
 // (row, word): words 0 and 1 are the row's panel columns as E slices, words
 // 2 and 3 its combination of the original candidate rows, indexed by pivot
-// number (a pivot row gets coefficient 1 at its own number when chosen).
-// Only rows that are not pivots are eliminated, so pivot row a ends as
-// pv_a E_a with combination pv_a (Lp^{-1} row a): Lp^{-1}[a][b] = pv_a^{-1}
-// times the combination's entry b.  lrec keeps every candidate's multiplier
-// at every step it is eliminated in (L's entries of the later pivot rows).
+// number (a pivot row has coefficient 1 at its own number).  Only rows that
+// are not pivots are eliminated, so pivot row a ends as pv_a E_a with the
+// combination pv_a (Lp^{-1} row a): Lp^{-1}[a][b] = pv_a^{-1} times the
+// combination's entry b.  lrec keeps every candidate's multiplier at every
+// step it is eliminated in (L's entries of the later pivot rows).
+//
+// One barrier per column: before it, every thread stores its slices (a
+// snapshot, two buffers used alternately) and each warp offers its best
+// candidate, (position, row, entry) packed so that the minimum is the
+// candidate at the lowest current position; after it, the pivot's slices
+// are read from the snapshot.  The pivot's own coefficient bit is not in
+// the snapshot; the rows it eliminates add it themselves.  Positions live in
+// registers: the pivot takes position k, the row at position k the pivot's
+// old one (Algorithm 4's swap).
 template <typename T, int E>
 __global__ void __launch_bounds__(PT) ple_panel(T* __restrict__ A, int64_t lda, int64_t r, int64_t c0, int cnt,
                                                 int wc, int js, uint32_t flow, const uint16_t* __restrict__ gf,
                                                 PleOut* __restrict__ out, T* __restrict__ linv,
                                                 uint32_t* __restrict__ esl, int* status) {
+  extern __shared__ uint32_t snap[];  // [2][E][PT]
   __shared__ uint16_t lg[LOGW];
   __shared__ uint16_t ex[EXPW];
-  __shared__ uint32_t pivs[E][4];  // slices of the current pivot row
-  __shared__ unsigned cand[2];     // (position << 8 | row) of a column's pivot (two, used alternately)
-  __shared__ uint32_t pv_s;
-  __shared__ int posv[R], at[R];   // current window position of each candidate, and its inverse
+  __shared__ unsigned cand[3];      // a column's pivot key (three, used in turn)
   __shared__ int piv_col[W], piv_pos[W];
   __shared__ uint32_t piv_val[W];
-  __shared__ uint16_t lrec[R][W];
+  __shared__ T lrec[R][W];
   const uint32_t q = (1u << E) - 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = warp * 8 + (lane >> 2), word = lane & 3;
@@ -147,75 +178,66 @@ __global__ void __launch_bounds__(PT) ple_panel(T* __restrict__ A, int64_t lda, 
     if (i < (int)q) lg[i + 1] = gf[i + 1];
     else ex[i - q] = gf[LOGW + i - q];
   }
-  for (int i = tid; i < R; i += PT) {
-    posv[i] = i;
-    at[i] = i;
-  }
-  if (tid < 2) cand[tid] = ~0u;
+  if (tid < 3) cand[tid] = ~0u;
   uint32_t sl[E];
-#pragma unroll
-  for (int t = 0; t < E; ++t) sl[t] = 0;
   bool bad = false;
   if (word < 2 && row < cnt) {
-    const T* src = A + (r + row) * lda + c0 + 32 * word;
-    for (int b = 0; b < 32; ++b) {
-      const int c = 32 * word + b;
-      if (c >= wc) break;
-      if (c < js) continue;
-      uint32_t v = src[b];
-      bad |= v > q;
-      v &= q;
+    bad = load_word<T, E>(A + (r + row) * lda + c0 + 32 * word, 32 * word, js, wc, sl);
+  } else {
 #pragma unroll
-      for (int t = 0; t < E; ++t) sl[t] |= ((v >> t) & 1u) << b;
-    }
+    for (int t = 0; t < E; ++t) sl[t] = 0;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStatusRange);
   __syncthreads();
 
   int k = 0, my_a = -1, it = 0, j0 = wc;
+  int mypos = row;  // current window position of this row
   for (int j = js; j < wc; ++j) {
     const int wj = j >> 5, bj = j & 31;
     uint32_t x = word == wj ? element_at<E>(sl, bj) : 0u;
     x = __shfl_sync(0xffffffffu, x, (lane & ~3) | wj);  // the entry at column j, to the row's four lanes
+    uint32_t* sn = snap + (it & 1) * (E * PT);
+#pragma unroll
+    for (int t = 0; t < E; ++t) sn[t * PT + tid] = sl[t];
     const bool hit = word == wj && row < cnt && my_a < 0 && x != 0;
-    const unsigned key = hit ? ((unsigned)posv[row] << 8) | (unsigned)row : ~0u;
+    const unsigned key = hit ? ((unsigned)mypos << 17) | ((unsigned)row << 10) | x : ~0u;
     const unsigned wmin = __reduce_min_sync(0xffffffffu, key);
-    if (lane == 0 && wmin != ~0u) atomicMin(&cand[it & 1], wmin);
+    if (lane == 0 && wmin != ~0u) atomicMin(&cand[it % 3], wmin);
     __syncthreads();
-    const unsigned c = cand[it & 1];
-    // the other slot serves the next column: its last reads were before this
-    // column's barrier, its next writes come after the barrier below
-    if (tid == 0) cand[(it + 1) & 1] = ~0u;
+    const unsigned c = cand[it % 3];
+    // the slot of column it + 2: its last reads were before this barrier, its
+    // next writes come after the next one
+    if (tid == 0) cand[(it + 2) % 3] = ~0u;
     ++it;
     if (c == ~0u) {  // no candidate has a non-zero entry here (uniform): the round ends
       j0 = j;
       break;
     }
-    const int p = (int)(c & 0xffu);
+    const int p = (int)((c >> 10) & 127u), old = (int)(c >> 17);
+    const uint32_t pv = c & 1023u;
     if (row == p) {
       my_a = k;
+      mypos = k;
       if (word == 2 + (k >> 5)) sl[0] ^= 1u << (k & 31);  // coefficient 1 on its own original row
-#pragma unroll
-      for (int t = 0; t < E; ++t) pivs[t][word] = sl[t];
       if (word == 0) {
-        pv_s = x;
         piv_col[k] = j;
-        piv_val[k] = x;
+        piv_val[k] = pv;
+        piv_pos[k] = old;
       }
-    } else if (my_a < 0 && word == 0 && row < cnt) {
-      lrec[row][k] = (uint16_t)x;
+    } else {
+      if (mypos == k) mypos = old;
+      if (my_a < 0 && word == 0 && row < cnt) lrec[row][k] = (T)x;
     }
-    if (tid == 0) {  // Algorithm 4's swap: the pivot to position k, the row there to the pivot's place
-      const int old = posv[p], other = at[k];
-      posv[other] = old;
-      at[old] = other;
-      posv[p] = k;
-      at[k] = p;
-      piv_pos[k] = old;
+    if (my_a < 0 && row < cnt && x != 0) {
+      // row += (x / pv) * pivot row, slice by slice, and the pivot's own bit
+      const uint32_t s2 = ex[lg[x] + q - lg[pv]];
+      add_scaled<E>(sl, s2, &sn[p * 4 + word], PT, flow);
+      if (word == 2 + (k >> 5)) {
+#pragma unroll
+        for (int t = 0; t < E; ++t) sl[t] ^= ((s2 >> t) & 1u) << (k & 31);
+      }
     }
     ++k;
-    __syncthreads();
-    if (my_a < 0 && row < cnt && x != 0) add_scaled<E>(sl, ex[lg[x] + q - lg[pv_s]], &pivs[0][word], 4, flow);
   }
 
   if (my_a >= 0) {
@@ -239,7 +261,7 @@ __global__ void __launch_bounds__(PT) ple_panel(T* __restrict__ A, int64_t lda, 
     } else {
       const int b0 = 32 * (word - 2);
       // L's entries of the row: the multipliers, then the pivot on the diagonal
-      for (int s = b0; s < b0 + 32 && s <= my_a; ++s) dst[r + s] = (T)(s < my_a ? lrec[row][s] : pv);
+      for (int s = b0; s < b0 + 32 && s <= my_a; ++s) dst[r + s] = s < my_a ? lrec[row][s] : (T)pv;
       // Lp^{-1}: the combination scaled by pv^{-1}
       for (int bb = 0; bb < 32; ++bb) {
         const int b = b0 + bb;
@@ -273,7 +295,6 @@ __global__ void __launch_bounds__(AT) ple_apply(T* __restrict__ A, int64_t lda, 
                                                 int* __restrict__ first, int* status) {
   __shared__ uint32_t es[ESL_MAX];
   __shared__ int qc[W];
-  const uint32_t q = (1u << E) - 1;
   const int tid = threadIdx.x, lane = tid & 31;
   for (int i = tid; i < k * E * 2; i += AT) es[i] = esl[i];
   for (int i = tid; i < k; i += AT) qc[i] = po->cols[i];
@@ -286,19 +307,7 @@ __global__ void __launch_bounds__(AT) ple_apply(T* __restrict__ A, int64_t lda, 
   for (int t = 0; t < E; ++t) sl[t] = ls[t] = 0;
   bool bad = false;
   T* rowp = A + (live ? i : i_begin) * lda;
-  if (live) {
-    const T* src = rowp + c0 + 32 * word;
-    for (int b = 0; b < 32; ++b) {
-      const int c = 32 * word + b;
-      if (c >= wc) break;
-      if (c < js) continue;
-      uint32_t v = src[b];
-      bad |= v > q;
-      v &= q;
-#pragma unroll
-      for (int t = 0; t < E; ++t) sl[t] |= ((v >> t) & 1u) << b;
-    }
-  }
+  if (live) bad = load_word<T, E>(rowp + c0 + 32 * word, 32 * word, js, wc, sl);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStatusRange);
   for (int a = 0; a < k; ++a) {
     const int qa = qc[a], wq = qa >> 5;
@@ -329,14 +338,23 @@ __global__ void __launch_bounds__(AT) ple_apply(T* __restrict__ A, int64_t lda, 
   if (j0 < wc && word == (j0 >> 5) && element_at<E>(sl, j0 & 31) != 0) atomicMin(first, (int)i);
 }
 
+template <typename T, int E>
+cudaError_t launch_panel_e(T* A, int64_t lda, int64_t r, int64_t c0, int cnt, int wc, int js, uint32_t flow,
+                           const uint16_t* gf, PleOut* out, T* linv, uint32_t* esl, int* status, cudaStream_t s) {
+  constexpr int smem = 2 * E * PT * (int)sizeof(uint32_t);  // the two snapshots
+  const cudaError_t err = cudaFuncSetAttribute(ple_panel<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (err != cudaSuccess) return err;
+  ple_panel<T, E><<<1, PT, smem, s>>>(A, lda, r, c0, cnt, wc, js, flow, gf, out, linv, esl, status);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_panel(int e, T* A, int64_t lda, int64_t r, int64_t c0, int cnt, int wc, int js, uint32_t f,
                          const uint16_t* gf, PleOut* out, T* linv, uint32_t* esl, int* status, cudaStream_t s) {
   const uint32_t flow = f & ((1u << e) - 1u);
-#define M4RIE_PLE_CASE(EE)                                                                                     \
-  case EE:                                                                                                     \
-    ple_panel<T, EE><<<1, PT, 0, s>>>(A, lda, r, c0, cnt, wc, js, flow, gf, out, linv, esl, status); \
-    break;
+#define M4RIE_PLE_CASE(EE) \
+  case EE:                 \
+    return launch_panel_e<T, EE>(A, lda, r, c0, cnt, wc, js, flow, gf, out, linv, esl, status, s);
   switch (e) {
     M4RIE_PLE_CASE(2)
     M4RIE_PLE_CASE(3)
@@ -382,6 +400,14 @@ cudaError_t launch_apply(int e, T* A, int64_t lda, int64_t i_begin, int64_t m, i
 
 using rowmove::fail;
 using rowmove::move_rows;
+
+// The context's products on another stream for the lifetime of the object.
+struct OnStream {
+  m4rie_ctx* ctx;
+  cudaStream_t saved;
+  OnStream(m4rie_ctx* c, cudaStream_t s) : ctx(c), saved(c->stream) { c->stream = s; }
+  ~OnStream() { ctx->stream = saved; }
+};
 
 template <typename T>
 m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T* A, int64_t lda, int64_t* rank,
@@ -493,9 +519,24 @@ m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T
         if ((err = move_rows<T>(ctx, mv, 1, A, lda, 0, n, src, dst)) != cudaSuccess) return fail(ctx, err);
       }
       preswap = -1;
-      // 3. the other remaining rows over the panel; the pivot row of column j0
+      // 3. G = Lp^{-1} (pivot rows) right of the panel, on the side stream,
+      // beside the apply kernel on the other remaining rows (which also
+      // finds the pivot row of column j0)
       const int64_t rest = m - (r + k);
       const bool open = j0 < wc;
+      T* Ar = A + r * lda + cr;
+      const bool right = k > 0 && nb > 0;
+      if (right) {
+        if ((err = cudaEventRecord(ctx->ech_ev[0], ctx->stream)) != cudaSuccess ||
+            (err = cudaStreamWaitEvent(ctx->ech_side, ctx->ech_ev[0], 0)) != cudaSuccess)
+          return fail(ctx, err);
+        {
+          OnStream on(ctx, ctx->ech_side);
+          m4rie_status st = run_gemm(ctx, e, f, k, nb, k, Mats{linv, W, Ar, lda, X, nb}, 0);
+          if (st != M4RIE_OK) return st;
+        }
+        if ((err = cudaEventRecord(ctx->ech_ev[1], ctx->ech_side)) != cudaSuccess) return fail(ctx, err);
+      }
       if (rest > 0 && (k > 0 || open)) {
         if (open && (err = cudaMemsetAsync(d_first, 0x7f, sizeof(int), ctx->stream)) != cudaSuccess)
           return fail(ctx, err);
@@ -504,14 +545,13 @@ m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T
           return fail(ctx, err);
         ++ctx->launches;
       }
-      // 4. right of the panel: G = Lp^{-1} (pivot rows), then the other rows get L G
-      if (k > 0 && nb > 0) {
-        T* Ar = A + r * lda + cr;
-        m4rie_status st = run_gemm(ctx, e, f, k, nb, k, Mats{linv, W, Ar, lda, X, nb}, 0);
-        if (st != M4RIE_OK) return st;
+      // 4. the other remaining rows right of the panel get L G
+      if (right) {
+        if ((err = cudaStreamWaitEvent(ctx->stream, ctx->ech_ev[1], 0)) != cudaSuccess) return fail(ctx, err);
+        m4rie_status st;
         if (rest > 0) {
           const int64_t r_next = r + k;
-          const bool look = !open && cr < n && nb > 2 * W;
+          const bool look = !open && nb > 2 * W;
           const int64_t n1 = look ? W : nb;
           T* Ad = A + r_next * lda + cr;
           if ((st = run_gemm(ctx, e, f, rest, n1, k, Mats{lbuf, W, X, nb, Ad, lda}, 1)) != M4RIE_OK) return st;

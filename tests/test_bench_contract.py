@@ -76,3 +76,11 @@ def test_reference_arm_echelon_form():
     assert d["unit"] == "ms" and d["higher_is_better"] is False
     # the paper's own time for this workload (Table 2): value / 81 ms
     assert d["vs_baseline"] == pytest.approx(d["value"] / 81.0)
+
+
+def test_reference_arm_ple():
+    d = one_line(run_bench("--workload", "ple_gf256_1000", "--steps", "1", "--warmup", "0"))
+    check_common(d, 1)
+    assert "PLE" in d["metric"] and d["unit"] == "ms" and d["higher_is_better"] is False
+    assert d["config"]["op"] == "ple" and d["config"]["m"] == 1000
+    assert d["vs_baseline"] is None
