@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "context.h"
+#include "bitslice.cuh"
 #include "rowmove.cuh"
 
 namespace m4rie {
@@ -118,17 +119,7 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
 #pragma unroll
   for (int t = 0; t < E; ++t) sl[t] = 0;
   bool bad = false;
-  if (word < 2 && row < cnt) {
-    const T* src = A + (r + row) * lda + c0 + 32 * word;
-    for (int b = 0; b < 32; ++b) {
-      if (32 * word + b >= wc) break;
-      uint32_t v = src[b];
-      bad |= v > q;
-      v &= q;
-#pragma unroll
-      for (int t = 0; t < E; ++t) sl[t] |= ((v >> t) & 1u) << b;
-    }
-  }
+  if (word < 2 && row < cnt) bad = bitslice::load_word<T, E>(A + (r + row) * lda + c0 + 32 * word, 32 * word, 0, wc, sl);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStatusRange);
   __syncthreads();
 
@@ -321,13 +312,7 @@ m4rie_status echelon_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t 
 
   // look-ahead: the next panel's factorisation on a side stream (non-blocking,
   // ordered against ctx->stream by events), its pivot list into pinned memory
-  if (!ctx->ech_side) {
-    if ((err = cudaStreamCreateWithFlags(&ctx->ech_side, cudaStreamNonBlocking)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&ctx->ech_ev[0], cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&ctx->ech_ev[1], cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaMallocHost(&ctx->ech_po_host, kPanelHostBytes)) != cudaSuccess)
-      return fail(ctx, err);
-  }
+  if ((err = rowmove::ensure_side(ctx)) != cudaSuccess) return fail(ctx, err);
   PanelOut* hpo_next = static_cast<PanelOut*>(ctx->ech_po_host);
   bool ahead = false;  // the current panel's round-0 factorisation was launched by the previous panel
 

@@ -40,16 +40,18 @@
 //      of column j0) and another round starts at column j0; with none, column
 //      j0 has no pivot and the next round starts after it.
 //
-// Random dense input finds all 64 pivots of a panel in one round.  On a
-// panel's last round the update right of the panel first covers the next
-// panel's columns, and the next panel's kernel runs on a side stream while
-// the rest of the update runs (as in the echelon form).
+// Random dense input finds all 64 pivots of a panel in one round.  After a
+// panel's last round, the next panel's kernel starts on a side stream as
+// soon as L and G are known: it gives its own candidate block (96 rows x 64
+// columns) the update L G itself, and the products of step 4 skip that
+// block, so they run beside it.
 #include <algorithm>
 #include <climits>
 #include <numeric>
 #include <vector>
 
 #include "context.h"
+#include "bitslice.cuh"
 #include "rowmove.cuh"
 
 namespace m4rie {
@@ -60,6 +62,8 @@ m4rie_status ensure_field_tables(m4rie_ctx* ctx, int e, uint32_t f);
 
 namespace {
 
+using namespace bitslice;
+
 constexpr int W = 64;                // panel columns
 constexpr int R = rowmove::kRows;    // candidate rows per round
 constexpr int LOGW = 1024;           // log table entries
@@ -67,6 +71,9 @@ constexpr int EXPW = 4096;           // antilog entries (doubled, then zeros)
 constexpr int PT = 4 * R;            // panel kernel threads: (row, word) for 96 rows x 4 words
 constexpr int AT = 64;               // apply kernel threads: 32 rows x 2 words
 constexpr int ESL_MAX = W * 10 * 2;  // E's rows as slices: [pivot][slice][word]
+// Largest e for which the next panel's kernel applies the previous panel's
+// update to its candidate block itself (its cost grows as e^2 per step).
+constexpr int kPreUpdateMaxE = 4;
 
 struct PleOut {
   int k;        // pivots of the round
@@ -75,71 +82,6 @@ struct PleOut {
   int cols[W];  // panel column of pivot a
 };
 static_assert(sizeof(PleOut) <= kPanelHostBytes, "pinned pivot list");
-
-template <int E>
-__device__ __forceinline__ uint32_t times_x(uint32_t a, uint32_t flow) {
-  return (a << 1) ^ (((a >> (E - 1)) & 1u) ? (flow | (1u << E)) : 0u);
-}
-
-// sl += s * p on bit slices (s a field element; slice t of p at
-// p[t * stride]): slice t of p carries x^t, so it adds with the slices of
-// s x^t.
-template <int E>
-__device__ __forceinline__ void add_scaled(uint32_t (&sl)[E], uint32_t s, const uint32_t* p, int stride,
-                                           uint32_t flow) {
-#pragma unroll
-  for (int t = 0; t < E; ++t) {
-    const uint32_t pt = p[t * stride];
-#pragma unroll
-    for (int s2 = 0; s2 < E; ++s2) sl[s2] ^= pt & (0u - ((s >> s2) & 1u));
-    s = times_x<E>(s, flow);
-  }
-}
-
-// out = s * in on bit slices held in registers.
-template <int E>
-__device__ __forceinline__ void scaled(uint32_t (&out)[E], uint32_t s, const uint32_t (&in)[E], uint32_t flow) {
-#pragma unroll
-  for (int t = 0; t < E; ++t) out[t] = 0;
-#pragma unroll
-  for (int t = 0; t < E; ++t) {
-#pragma unroll
-    for (int s2 = 0; s2 < E; ++s2) out[s2] ^= in[t] & (0u - ((s >> s2) & 1u));
-    s = times_x<E>(s, flow);
-  }
-}
-
-template <int E>
-__device__ __forceinline__ uint32_t element_at(const uint32_t (&sl)[E], int b) {
-  uint32_t v = 0;
-#pragma unroll
-  for (int t = 0; t < E; ++t) v |= ((sl[t] >> b) & 1u) << t;
-  return v;
-}
-
-// Loads 32 consecutive elements of a row (columns c0 .. c0+31 relative to
-// the panel, those outside [lo, hi) as 0) as E bit slices; all loads are
-// issued before any is used.  Returns whether an entry was >= 2^E.
-template <typename T, int E>
-__device__ __forceinline__ bool load_word(const T* __restrict__ src, int cbase, int lo, int hi, uint32_t (&sl)[E]) {
-  const uint32_t q = (1u << E) - 1;
-  uint32_t v[32];
-#pragma unroll
-  for (int b = 0; b < 32; ++b) {
-    const int c = cbase + b;
-    v[b] = (c >= lo && c < hi) ? (uint32_t)src[b] : 0u;
-  }
-  uint32_t any = 0;
-#pragma unroll
-  for (int t = 0; t < E; ++t) sl[t] = 0;
-#pragma unroll
-  for (int b = 0; b < 32; ++b) {
-    any |= v[b];
-#pragma unroll
-    for (int t = 0; t < E; ++t) sl[t] |= ((v[b] >> t) & 1u) << b;
-  }
-  return (any & ~q) != 0;
-}
 
 // Step 1 on the candidate block A[r .. r+cnt) over panel columns [js, wc)
 // (columns left of js are closed: they hold L entries or zeros).  Thread
@@ -150,6 +92,12 @@ __device__ __forceinline__ bool load_word(const T* __restrict__ src, int cbase, 
 // combination pv_a (Lp^{-1} row a): Lp^{-1}[a][b] = pv_a^{-1} times the
 // combination's entry b.  lrec keeps every candidate's multiplier at every
 // step it is eliminated in (L's entries of the later pivot rows).
+//
+// With kp > 0 the candidate block first gets the previous panel's update:
+// block += pl[row][0 .. kp) times px's first wc columns (pl: the previous
+// panel's multipliers of these rows, stride W; px: its G, row stride ldx),
+// which is then written back to A (the update of the rest of the matrix
+// skips this block).
 //
 // One barrier per column: before it, every thread stores its slices (a
 // snapshot, two buffers used alternately) and each warp offers its best
@@ -163,14 +111,16 @@ template <typename T, int E>
 __global__ void __launch_bounds__(PT) ple_panel(T* __restrict__ A, int64_t lda, int64_t r, int64_t c0, int cnt,
                                                 int wc, int js, uint32_t flow, const uint16_t* __restrict__ gf,
                                                 PleOut* __restrict__ out, T* __restrict__ linv,
-                                                uint32_t* __restrict__ esl, int* status) {
-  extern __shared__ uint32_t snap[];  // [2][E][PT]
+                                                uint32_t* __restrict__ esl, int* status, const T* __restrict__ pl,
+                                                const T* __restrict__ px, int64_t ldx, int kp) {
+  extern __shared__ uint32_t snap[];  // [2][E][PT], then the previous G's slices [W][E][2]
+  uint32_t* xs = snap + 2 * E * PT;
   __shared__ uint16_t lg[LOGW];
   __shared__ uint16_t ex[EXPW];
   __shared__ unsigned cand[3];      // a column's pivot key (three, used in turn)
   __shared__ int piv_col[W], piv_pos[W];
   __shared__ uint32_t piv_val[W];
-  __shared__ T lrec[R][W];
+  __shared__ __align__(16) T lrec[R][W];
   const uint32_t q = (1u << E) - 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = warp * 8 + (lane >> 2), word = lane & 3;
@@ -188,49 +138,78 @@ __global__ void __launch_bounds__(PT) ple_panel(T* __restrict__ A, int64_t lda, 
     for (int t = 0; t < E; ++t) sl[t] = 0;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStatusRange);
+  if (kp > 0) {
+    // the previous panel's update of this block: its multipliers to lrec
+    // (overwritten later, each entry before it is read), its G as slices
+    constexpr int VPR = W * (int)sizeof(T) / 16;  // 16-byte vectors per row of pl and lrec
+    const uint4* src4 = reinterpret_cast<const uint4*>(pl);
+    uint4* dst4 = reinterpret_cast<uint4*>(&lrec[0][0]);
+    for (int i = tid; i < cnt * VPR; i += PT) dst4[i] = src4[i];
+    if (tid < 2 * kp) {
+      uint32_t gs[E];
+      load_word<T, E>(px + (int64_t)(tid >> 1) * ldx + 32 * (tid & 1), 32 * (tid & 1), 0, wc, gs);
+#pragma unroll
+      for (int t = 0; t < E; ++t) xs[((tid >> 1) * E + t) * 2 + (tid & 1)] = gs[t];
+    }
+    __syncthreads();
+    if (word < 2 && row < cnt) {
+      for (int a = 0; a < kp; ++a) {
+        const uint32_t sa = lrec[row][a];
+        if (sa) add_scaled<E>(sl, sa, &xs[a * E * 2 + word], 2, flow);
+      }
+      T* dst = A + (r + row) * lda + c0 + 32 * word;
+      for (int b = 0; b < 32 && 32 * word + b < wc; ++b) dst[b] = (T)element_at<E>(sl, b);
+    }
+  }
   __syncthreads();
 
-  int k = 0, my_a = -1, it = 0, j0 = wc;
-  int mypos = row;  // current window position of this row
+  // Rows at or past cnt hold zeros: they never offer a pivot and are never
+  // eliminated.
+  int k = 0, my_a = -1, j0 = wc;
+  int slot = 0;      // cand slot of this column (0, 1, 2 in turn)
+  int sbuf = 0;      // snapshot buffer of this column (0 or E PT, alternately)
+  int mypos = row;   // current window position of this row
   for (int j = js; j < wc; ++j) {
     const int wj = j >> 5, bj = j & 31;
     uint32_t x = word == wj ? element_at<E>(sl, bj) : 0u;
     x = __shfl_sync(0xffffffffu, x, (lane & ~3) | wj);  // the entry at column j, to the row's four lanes
-    uint32_t* sn = snap + (it & 1) * (E * PT);
+    const uint32_t lx = x ? lg[x] : 0u;                  // its logarithm, looked up before the barrier
+    uint32_t* sn = snap + sbuf;
 #pragma unroll
     for (int t = 0; t < E; ++t) sn[t * PT + tid] = sl[t];
-    const bool hit = word == wj && row < cnt && my_a < 0 && x != 0;
-    const unsigned key = hit ? ((unsigned)mypos << 17) | ((unsigned)row << 10) | x : ~0u;
+    const bool hit = word == wj && my_a < 0 && x != 0;
+    const unsigned key = hit ? ((unsigned)mypos << 17) | ((unsigned)row << 10) | lx : ~0u;
     const unsigned wmin = __reduce_min_sync(0xffffffffu, key);
-    if (lane == 0 && wmin != ~0u) atomicMin(&cand[it % 3], wmin);
+    if (lane == 0 && wmin != ~0u) atomicMin(&cand[slot], wmin);
     __syncthreads();
-    const unsigned c = cand[it % 3];
-    // the slot of column it + 2: its last reads were before this barrier, its
-    // next writes come after the next one
-    if (tid == 0) cand[(it + 2) % 3] = ~0u;
-    ++it;
+    const unsigned c = cand[slot];
+    // the slot of the column after next: its last reads were before this
+    // barrier, its next writes come after the next one
+    if (tid == 0) cand[slot == 0 ? 2 : slot - 1] = ~0u;
+    slot = slot == 2 ? 0 : slot + 1;
+    sbuf = sbuf ? 0 : E * PT;
     if (c == ~0u) {  // no candidate has a non-zero entry here (uniform): the round ends
       j0 = j;
       break;
     }
     const int p = (int)((c >> 10) & 127u), old = (int)(c >> 17);
-    const uint32_t pv = c & 1023u;
+    const uint32_t lpv = c & 1023u;  // log of the pivot
     if (row == p) {
       my_a = k;
       mypos = k;
       if (word == 2 + (k >> 5)) sl[0] ^= 1u << (k & 31);  // coefficient 1 on its own original row
       if (word == 0) {
         piv_col[k] = j;
-        piv_val[k] = pv;
+        piv_val[k] = x;
         piv_pos[k] = old;
       }
     } else {
       if (mypos == k) mypos = old;
-      if (my_a < 0 && word == 0 && row < cnt) lrec[row][k] = (T)x;
+      if (my_a < 0 && word == 0) lrec[row][k] = (T)x;
     }
-    if (my_a < 0 && row < cnt && x != 0) {
+    if (my_a < 0 && x != 0) {
       // row += (x / pv) * pivot row, slice by slice, and the pivot's own bit
-      const uint32_t s2 = ex[lg[x] + q - lg[pv]];
+      const uint32_t s2 = ex[lx + q - lpv];
       add_scaled<E>(sl, s2, &sn[p * 4 + word], PT, flow);
       if (word == 2 + (k >> 5)) {
 #pragma unroll
@@ -338,23 +317,36 @@ __global__ void __launch_bounds__(AT) ple_apply(T* __restrict__ A, int64_t lda, 
   if (j0 < wc && word == (j0 >> 5) && element_at<E>(sl, j0 & 31) != 0) atomicMin(first, (int)i);
 }
 
+// The previous panel's update of the candidate block (kp = 0: none).
+template <typename T>
+struct PreUpdate {
+  const T* pl = nullptr;
+  const T* px = nullptr;
+  int64_t ldx = 0;
+  int kp = 0;
+};
+
 template <typename T, int E>
 cudaError_t launch_panel_e(T* A, int64_t lda, int64_t r, int64_t c0, int cnt, int wc, int js, uint32_t flow,
-                           const uint16_t* gf, PleOut* out, T* linv, uint32_t* esl, int* status, cudaStream_t s) {
-  constexpr int smem = 2 * E * PT * (int)sizeof(uint32_t);  // the two snapshots
+                           const uint16_t* gf, PleOut* out, T* linv, uint32_t* esl, int* status,
+                           const PreUpdate<T>& pre, cudaStream_t s) {
+  // the two snapshots, then the previous G's slices
+  constexpr int smem = (2 * E * PT + W * E * 2) * (int)sizeof(uint32_t);
   const cudaError_t err = cudaFuncSetAttribute(ple_panel<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
-  ple_panel<T, E><<<1, PT, smem, s>>>(A, lda, r, c0, cnt, wc, js, flow, gf, out, linv, esl, status);
+  ple_panel<T, E><<<1, PT, smem, s>>>(A, lda, r, c0, cnt, wc, js, flow, gf, out, linv, esl, status, pre.pl, pre.px,
+                                      pre.ldx, pre.kp);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_panel(int e, T* A, int64_t lda, int64_t r, int64_t c0, int cnt, int wc, int js, uint32_t f,
-                         const uint16_t* gf, PleOut* out, T* linv, uint32_t* esl, int* status, cudaStream_t s) {
+                         const uint16_t* gf, PleOut* out, T* linv, uint32_t* esl, int* status, cudaStream_t s,
+                         const PreUpdate<T>& pre = PreUpdate<T>()) {
   const uint32_t flow = f & ((1u << e) - 1u);
 #define M4RIE_PLE_CASE(EE) \
   case EE:                 \
-    return launch_panel_e<T, EE>(A, lda, r, c0, cnt, wc, js, flow, gf, out, linv, esl, status, s);
+    return launch_panel_e<T, EE>(A, lda, r, c0, cnt, wc, js, flow, gf, out, linv, esl, status, pre, s);
   switch (e) {
     M4RIE_PLE_CASE(2)
     M4RIE_PLE_CASE(3)
@@ -441,13 +433,7 @@ m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T
     ctx->last_error = "pinned host buffer allocation failed";
     return M4RIE_ERR_NOMEM;
   }
-  if (!ctx->ech_side) {
-    if ((err = cudaStreamCreateWithFlags(&ctx->ech_side, cudaStreamNonBlocking)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&ctx->ech_ev[0], cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&ctx->ech_ev[1], cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaMallocHost(&ctx->ech_po_host, kPanelHostBytes)) != cudaSuccess)
-      return fail(ctx, err);
-  }
+  if ((err = rowmove::ensure_side(ctx)) != cudaSuccess) return fail(ctx, err);
   uint8_t* base = static_cast<uint8_t*>(ctx->ews);
   PleOut* d_po = reinterpret_cast<PleOut*>(base);
   int* d_first = reinterpret_cast<int*>(base + sizeof(PleOut));
@@ -551,18 +537,46 @@ m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T
         m4rie_status st;
         if (rest > 0) {
           const int64_t r_next = r + k;
-          const bool look = !open && nb > 2 * W;
-          const int64_t n1 = look ? W : nb;
           T* Ad = A + r_next * lda + cr;
-          if ((st = run_gemm(ctx, e, f, rest, n1, k, Mats{lbuf, W, X, nb, Ad, lda}, 1)) != M4RIE_OK) return st;
-          if (look) {
-            // the next panel's columns are final for rows r_next..: its first
-            // kernel runs beside the rest of this update
-            const int cnt_next = (int)std::min<int64_t>(R, m - r_next);
-            const int wc_next = (int)std::min<int64_t>(W, n - cr);
+          const bool look = !open && nb > 2 * W;
+          if (look && e <= kPreUpdateMaxE) {
+            // Look-ahead: the next panel's kernel gives its own candidate
+            // block (rows r_next.., the next W columns) this update and
+            // starts now, beside the update of the rest of the matrix.
+            const int cnt_next = (int)std::min<int64_t>(R, rest);
+            PreUpdate<T> pre;
+            pre.pl = lbuf;
+            pre.px = X;
+            pre.ldx = nb;
+            pre.kp = k;
             if ((err = cudaEventRecord(ctx->ech_ev[0], ctx->stream)) != cudaSuccess ||
                 (err = cudaStreamWaitEvent(ctx->ech_side, ctx->ech_ev[0], 0)) != cudaSuccess ||
-                (err = launch_panel<T>(e, A, lda, r_next, cr, cnt_next, wc_next, 0, f, ctx->d_gf, d_po, linv, esl,
+                (err = launch_panel<T>(e, A, lda, r_next, cr, cnt_next, W, 0, f, ctx->d_gf, d_po, linv, esl,
+                                       ctx->d_status, ctx->ech_side, pre)) != cudaSuccess ||
+                (err = cudaMemcpyAsync(hpo_next, d_po, sizeof(PleOut), cudaMemcpyDeviceToHost, ctx->ech_side)) !=
+                    cudaSuccess ||
+                (err = cudaEventRecord(ctx->ech_ev[1], ctx->ech_side)) != cudaSuccess)
+              return fail(ctx, err);
+            ++ctx->launches;
+            ahead = true;
+            // the candidate rows right of that block, then every row below them
+            if ((st = run_gemm(ctx, e, f, cnt_next, nb - W, k, Mats{lbuf, W, X + W, nb, Ad + W, lda}, 1)) !=
+                M4RIE_OK)
+              return st;
+            if (rest > cnt_next &&
+                (st = run_gemm(ctx, e, f, rest - cnt_next, nb, k,
+                               Mats{lbuf + (int64_t)cnt_next * W, W, X, nb, Ad + (int64_t)cnt_next * lda, lda}, 1)) !=
+                    M4RIE_OK)
+              return st;
+          } else if (look) {
+            // Look-ahead for larger fields, where the block's update costs the
+            // one-CTA kernel more than a product: the next panel's columns
+            // first, then its kernel beside the rest of the update.
+            const int cnt_next = (int)std::min<int64_t>(R, rest);
+            if ((st = run_gemm(ctx, e, f, rest, W, k, Mats{lbuf, W, X, nb, Ad, lda}, 1)) != M4RIE_OK) return st;
+            if ((err = cudaEventRecord(ctx->ech_ev[0], ctx->stream)) != cudaSuccess ||
+                (err = cudaStreamWaitEvent(ctx->ech_side, ctx->ech_ev[0], 0)) != cudaSuccess ||
+                (err = launch_panel<T>(e, A, lda, r_next, cr, cnt_next, W, 0, f, ctx->d_gf, d_po, linv, esl,
                                        ctx->d_status, ctx->ech_side)) != cudaSuccess ||
                 (err = cudaMemcpyAsync(hpo_next, d_po, sizeof(PleOut), cudaMemcpyDeviceToHost, ctx->ech_side)) !=
                     cudaSuccess ||
@@ -570,9 +584,10 @@ m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T
               return fail(ctx, err);
             ++ctx->launches;
             ahead = true;
-            if ((st = run_gemm(ctx, e, f, rest, nb - n1, k, Mats{lbuf, W, X + n1, nb, Ad + n1, lda}, 1)) !=
-                M4RIE_OK)
+            if ((st = run_gemm(ctx, e, f, rest, nb - W, k, Mats{lbuf, W, X + W, nb, Ad + W, lda}, 1)) != M4RIE_OK)
               return st;
+          } else if ((st = run_gemm(ctx, e, f, rest, nb, k, Mats{lbuf, W, X, nb, Ad, lda}, 1)) != M4RIE_OK) {
+            return st;
           }
         }
         if ((err = cudaMemcpy2DAsync(Ar, (size_t)lda * w, X, (size_t)nb * w, (size_t)nb * w, (size_t)k,

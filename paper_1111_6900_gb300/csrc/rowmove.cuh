@@ -27,6 +27,23 @@ inline m4rie_status fail(m4rie_ctx* ctx, cudaError_t err) {
   return M4RIE_ERR_CUDA;
 }
 
+// The look-ahead side stream of the echelon form and the PLE decomposition
+// (created at the highest priority, so that a panel kernel queued on it is
+// dispatched ahead of the products queued on the main stream), its two
+// events and the pinned pivot list.
+inline cudaError_t ensure_side(m4rie_ctx* ctx) {
+  if (ctx->ech_side) return cudaSuccess;
+  int lo = 0, hi = 0;
+  cudaError_t err = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (err != cudaSuccess) return err;
+  if ((err = cudaStreamCreateWithPriority(&ctx->ech_side, cudaStreamNonBlocking, hi)) != cudaSuccess ||
+      (err = cudaEventCreateWithFlags(&ctx->ech_ev[0], cudaEventDisableTiming)) != cudaSuccess ||
+      (err = cudaEventCreateWithFlags(&ctx->ech_ev[1], cudaEventDisableTiming)) != cudaSuccess ||
+      (err = cudaMallocHost(&ctx->ech_po_host, kPanelHostBytes)) != cudaSuccess)
+    return err;
+  return cudaSuccess;
+}
+
 template <typename T>
 __global__ void gather_rows(const T* __restrict__ A, int64_t lda, int64_t c0, int64_t nt, const int* __restrict__ src,
                             T* __restrict__ tmp) {
