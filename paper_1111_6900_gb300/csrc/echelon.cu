@@ -55,6 +55,20 @@ struct PanelOut {
   int rows[W];      // candidate index of pivot a
   int cols[W];      // panel column of pivot a
 };
+
+// Device-side bookkeeping of the pipelined form (see echelon_pipelined): the
+// panel kernel reads the rank before its panel from rr[0] and writes the rank
+// after it to rr[1], the panel's pivot columns to piv[rank ..], and the new
+// order of its candidate block to moves: moves[0] = cnt, moves[1 + x] = the
+// candidate that goes to row rank + x (the pivot rows first, in pivot order,
+// then the other candidates in order).
+struct DevPanel {
+  const int* rr_in = nullptr;
+  int* rr_out = nullptr;
+  int64_t* piv = nullptr;
+  int* moves = nullptr;
+  int64_t m = 0;
+};
 static_assert(sizeof(PanelOut) <= kPanelHostBytes, "pinned pivot list");
 
 // Rows i in [r, m) with a non-zero entry in a panel column not yet marked
@@ -97,7 +111,11 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
                                                               int64_t c0, int cnt, int wc, uint64_t done,
                                                               uint32_t flow, const uint16_t* __restrict__ gf,
                                                               PanelOut* __restrict__ out, T* __restrict__ minv,
-                                                              int* status) {
+                                                              int* status, DevPanel dev) {
+  if (dev.rr_in) {  // pipelined form: the rank before this panel from the device
+    r = *dev.rr_in;
+    cnt = (int)min((int64_t)R, dev.m - r);
+  }
   __shared__ uint16_t lg[LOGW];
   __shared__ uint16_t ex[EXPW];
   __shared__ uint32_t pivs[E][4];  // slices of the current pivot row
@@ -192,16 +210,41 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
     out->rows[a] = piv_row[a];
     out->cols[a] = piv_col[a];
   }
+  if (dev.rr_in) {
+    // M^{-1} as a W x W matrix: zeros outside its k x k block, so that the
+    // products can always take K = W
+    for (int i = tid; i < W * W; i += BS_THREADS)
+      if (i / W >= k || i % W >= k) minv[i] = (T)0;
+    for (int a = tid; a < k; a += BS_THREADS) dev.piv[r + a] = c0 + piv_col[a];
+    if (tid == 0) {
+      *dev.rr_out = (int)(r + k);
+      // pivot rows to r .. r+k-1 in pivot order, the other candidates after them in order
+      uint32_t used[(R + 31) / 32] = {};
+      for (int a = 0; a < k; ++a) used[piv_row[a] >> 5] |= 1u << (piv_row[a] & 31);
+      int next = 0;
+      for (int x = 0; x < cnt; ++x) {
+        int src;
+        if (x < k) {
+          src = piv_row[x];
+        } else {
+          while ((used[next >> 5] >> (next & 31)) & 1u) ++next;
+          src = next++;
+        }
+        dev.moves[1 + x] = src;
+      }
+      dev.moves[0] = cnt;
+    }
+  }
 }
 
 template <typename T>
 cudaError_t launch_panel_bitsliced(int e, const T* A, int64_t lda, int64_t r, int64_t c0, int cnt, int wc,
                                    uint64_t done, uint32_t f, const uint16_t* gf, PanelOut* out, T* minv, int* status,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const DevPanel& dev = DevPanel()) {
   const uint32_t flow = f & ((1u << e) - 1u);
-#define M4RIE_PANEL_CASE(EE)                                                                                       \
-  case EE:                                                                                                         \
-    panel_bitsliced<T, EE><<<1, BS_THREADS, 0, s>>>(A, lda, r, c0, cnt, wc, done, flow, gf, out, minv, status); \
+#define M4RIE_PANEL_CASE(EE)                                                                                        \
+  case EE:                                                                                                          \
+    panel_bitsliced<T, EE><<<1, BS_THREADS, 0, s>>>(A, lda, r, c0, cnt, wc, done, flow, gf, out, minv, status, dev); \
     break;
   switch (e) {
     M4RIE_PANEL_CASE(2)
@@ -228,6 +271,91 @@ __global__ void gather_mult(const T* __restrict__ A, int64_t lda, int64_t m, int
   const int64_t i = idx / k;
   const int a = (int)(idx % k);
   mult[i * W + a] = A[i * lda + c0 + po->cols[a]];
+}
+
+// ---------------------------------------------------------------- pipelined form
+// The kernels below read the rank before the panel (rr[0]) and after it
+// (rr[1]) from the device, so that every panel is queued without waiting for
+// the previous one's pivot list.
+
+// One launch prepares a panel's products, reading the rank before the panel
+// (rr[0]) and after it (rr[1]) and the candidate order `ord` (moves of the
+// panel kernel) from the device:
+//   * the candidate block's new row order, columns c0 .. c0+nt-1;
+//   * the pivot block pb (W x nt): row a < k is pivot row a, the rest zero;
+//   * the multipliers of every row, mult[i][a] = A[i][c0 + cols[a]] for
+//     a < k, 0 above; pivot row a also gets 1 added at a, so that the
+//     update A += mult X turns it into X's row a (P_a + (M_a + e_a) X = X_a
+//     in characteristic 2, X = M^{-1} P).
+// The first nchunks CTAs each take PREP_CW columns of the candidate block
+// through shared memory (chunk 0 holds the panel's columns and writes the
+// block's multipliers); the others write the multipliers of the rows
+// outside the block, which do not move.
+constexpr int PREP_CW = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(256) prep_panel_dev(T* __restrict__ A, int64_t lda, int64_t m, int64_t c0,
+                                                      int64_t nt, const int* __restrict__ rr,
+                                                      const PanelOut* __restrict__ po, const int* __restrict__ ord,
+                                                      T* __restrict__ mult, T* __restrict__ pb, int nchunks) {
+  __shared__ T stage[R][PREP_CW];
+  __shared__ int so[R];
+  __shared__ int scols[W];
+  const int64_t r = rr[0];
+  const int k = rr[1] - rr[0];
+  const int cnt = ord[0];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < k; i += 256) scols[i] = po->cols[i];
+  if ((int)blockIdx.x < nchunks) {
+    const int64_t cb = (int64_t)blockIdx.x * PREP_CW;
+    const int cw = (int)min((int64_t)PREP_CW, nt - cb);
+    for (int i = tid; i < cnt; i += 256) so[i] = ord[1 + i];
+    for (int idx = tid; idx < cnt * PREP_CW; idx += 256) {
+      const int x = idx / PREP_CW, c = idx % PREP_CW;
+      if (c < cw) stage[x][c] = A[(r + x) * lda + c0 + cb + c];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < cnt * PREP_CW; idx += 256) {
+      const int x = idx / PREP_CW, c = idx % PREP_CW;
+      if (c < cw) A[(r + x) * lda + c0 + cb + c] = stage[so[x]][c];
+    }
+    for (int idx = tid; idx < W * PREP_CW; idx += 256) {
+      const int a = idx / PREP_CW, c = idx % PREP_CW;
+      if (c < cw) pb[(int64_t)a * nt + cb + c] = a < k ? stage[so[a]][c] : (T)0;
+    }
+    if (blockIdx.x == 0) {
+      for (int idx = tid; idx < cnt * W; idx += 256) {
+        const int x = idx / W, a = idx % W;
+        T v = a < k ? stage[so[x]][scols[a]] : (T)0;
+        if (a == x && a < k) v ^= (T)1;
+        mult[(r + x) * W + a] = v;
+      }
+    }
+  } else {
+    __syncthreads();
+    const int64_t idx = ((int64_t)blockIdx.x - nchunks) * 256 + tid;
+    if (idx >= m * W) return;
+    const int64_t i = idx / W;
+    const int a = (int)(idx % W);
+    if (i >= r && i < r + cnt) return;
+    mult[idx] = a < k ? A[i * lda + c0 + scols[a]] : (T)0;
+  }
+}
+
+// *flag = 1 unless every row i < r is zero left of its pivot column piv[i]
+// and every row at or below r is zero (r = *rr): the pipelined pass missed
+// a pivot.  Every panel clears its pivot columns in all rows, so with this
+// the matrix is in reduced row echelon form.
+template <typename T>
+__global__ void check_echelon(const T* __restrict__ A, int64_t lda, int64_t n, const int* __restrict__ rr,
+                              const int64_t* __restrict__ piv, int* __restrict__ flag) {
+  const int64_t i = blockIdx.x;
+  const int64_t r = *rr;
+  const int64_t lim = i < r ? piv[i] : n;
+  const T* row = A + i * lda;
+  bool nz = false;
+  for (int64_t c = threadIdx.x; c < lim; c += blockDim.x) nz |= row[c] != 0;
+  if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
 size_t ew(int e) { return rowmove::elem_bytes(e); }
@@ -265,6 +393,130 @@ void placement(const std::vector<int>& want, int base, std::vector<int>& src, st
     src.push_back(displaced[i]);
     dst.push_back(vacated[i]);
   }
+}
+
+// The reduced row echelon form with every panel queued up front: the panel
+// kernels keep the rank and the candidate order on the device, and the
+// products always take K = W (M^{-1} is zero outside its k x k block, so the
+// unused multiplier columns add nothing).  Per panel: the panel kernel (the
+// next panel's on the side stream), one preparation kernel, the product X
+// and the update in two parts; the pivot list is read back once, at the end.  Each panel takes one round with the next
+// R rows as candidates, so a column whose only non-zero entries lie below
+// them gets no pivot.  A final check flags that case (*complete = false);
+// the matrix is then row-equivalent to the input, and the caller finishes
+// it with echelon_impl (the reduced form is unique).
+template <typename T>
+m4rie_status echelon_pipelined(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T* A, int64_t lda,
+                               int64_t* rank, int64_t* pivots, bool* complete) {
+  *complete = false;
+  const size_t w = ew(e);
+  const int P = (int)ceil_div(n, W);
+  const size_t sz_po = round_up((int64_t)sizeof(PanelOut), 256);
+  const size_t sz_minv = round_up((int64_t)((size_t)W * W * w), 256);
+  const size_t sz_mult = round_up((int64_t)((size_t)m * W * w), 256);
+  const size_t sz_X = round_up((int64_t)((size_t)W * n * w), 256);
+  const size_t sz_rr = round_up((int64_t)(sizeof(int) * (P + 2)), 256);
+  const size_t sz_piv = round_up((int64_t)(sizeof(int64_t) * std::min(m, n)), 256);
+  const size_t sz_mv = round_up((int64_t)(sizeof(int) * (1 + 2 * R) + 64), 256);
+  const size_t total = sz_po + sz_minv + sz_mult + 2 * sz_X + sz_rr + sz_piv + sz_mv;
+  cudaError_t err;
+  if (total > ctx->ews_bytes) {
+    if ((err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return fail(ctx, err);
+    if (ctx->ews) cudaFree(ctx->ews);
+    ctx->ews = nullptr;
+    ctx->ews_bytes = 0;
+    if (cudaMalloc(&ctx->ews, total) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->last_error = "echelon workspace allocation failed";
+      return M4RIE_ERR_NOMEM;
+    }
+    ctx->ews_bytes = total;
+  }
+  if ((err = rowmove::ensure_side(ctx)) != cudaSuccess) return fail(ctx, err);
+  uint8_t* base = static_cast<uint8_t*>(ctx->ews);
+  PanelOut* po = reinterpret_cast<PanelOut*>(base);
+  T* minv = reinterpret_cast<T*>(base + sz_po);
+  T* mult = reinterpret_cast<T*>(base + sz_po + sz_minv);
+  T* X = reinterpret_cast<T*>(base + sz_po + sz_minv + sz_mult);
+  T* pb = reinterpret_cast<T*>(base + sz_po + sz_minv + sz_mult + sz_X);
+  int* rr = reinterpret_cast<int*>(base + sz_po + sz_minv + sz_mult + 2 * sz_X);
+  int64_t* piv = reinterpret_cast<int64_t*>(base + sz_po + sz_minv + sz_mult + 2 * sz_X + sz_rr);
+  int* moves = reinterpret_cast<int*>(base + sz_po + sz_minv + sz_mult + 2 * sz_X + sz_rr + sz_piv);
+  int* flag = moves + 1 + 2 * R;
+  if ((err = cudaMemsetAsync(rr, 0, sizeof(int), ctx->stream)) != cudaSuccess ||
+      (err = cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream)) != cudaSuccess)
+    return fail(ctx, err);
+  cudaStream_t st = ctx->stream;
+  for (int p = 0; p < P; ++p) {
+    const int64_t c0 = (int64_t)p * W, nt = n - c0;
+    const int wc = (int)std::min<int64_t>(W, nt);
+    if (p == 0) {
+      DevPanel dv;
+      dv.rr_in = rr;
+      dv.rr_out = rr + 1;
+      dv.piv = piv;
+      dv.moves = moves;
+      dv.m = m;
+      if ((err = launch_panel_bitsliced<T>(e, A, lda, 0, c0, 0, wc, 0, f, ctx->d_gf, po, minv, ctx->d_status, st,
+                                           dv)) != cudaSuccess)
+        return fail(ctx, err);
+      ++ctx->launches;
+    } else if ((err = cudaStreamWaitEvent(st, ctx->ech_ev[1], 0)) != cudaSuccess) {
+      return fail(ctx, err);
+    }
+    // 1. the candidate block in its new order, the pivot block, the multipliers
+    const int nchunks = (int)ceil_div(nt, PREP_CW);
+    prep_panel_dev<T><<<(unsigned)(nchunks + ceil_div(m * W, 256)), 256, 0, st>>>(A, lda, m, c0, nt, rr + p, po,
+                                                                                  moves, mult, pb, nchunks);
+    ++ctx->launches;
+    // 2. X = M^{-1} (pivot rows); 3. A[:, c0..] += mult X (which also makes
+    // the pivot rows X's rows), the next panel's columns first, its kernel on
+    // the side stream beside the rest
+    m4rie_status s2 = run_gemm(ctx, e, f, W, nt, W, Mats{minv, W, pb, nt, X, nt}, 0);
+    if (s2 != M4RIE_OK) return s2;
+    const bool next = p + 1 < P;
+    const int64_t n1 = next && nt > 2 * W ? 2 * W : nt;
+    if ((s2 = run_gemm(ctx, e, f, m, n1, W, Mats{mult, W, X, nt, A + c0, lda}, 1)) != M4RIE_OK) return s2;
+    if (next) {
+      DevPanel dv;
+      dv.rr_in = rr + p + 1;
+      dv.rr_out = rr + p + 2;
+      dv.piv = piv;
+      dv.moves = moves;
+      dv.m = m;
+      const int wn = (int)std::min<int64_t>(W, n - c0 - W);
+      if ((err = cudaEventRecord(ctx->ech_ev[0], st)) != cudaSuccess ||
+          (err = cudaStreamWaitEvent(ctx->ech_side, ctx->ech_ev[0], 0)) != cudaSuccess ||
+          (err = launch_panel_bitsliced<T>(e, A, lda, 0, c0 + W, 0, wn, 0, f, ctx->d_gf, po, minv, ctx->d_status,
+                                           ctx->ech_side, dv)) != cudaSuccess ||
+          (err = cudaEventRecord(ctx->ech_ev[1], ctx->ech_side)) != cudaSuccess)
+        return fail(ctx, err);
+      ++ctx->launches;
+    }
+    if (n1 < nt &&
+        (s2 = run_gemm(ctx, e, f, m, nt - n1, W, Mats{mult, W, X + n1, nt, A + c0 + n1, lda}, 1)) != M4RIE_OK)
+      return s2;
+    if ((err = cudaGetLastError()) != cudaSuccess) return fail(ctx, err);
+  }
+  check_echelon<T><<<(unsigned)m, 256, 0, st>>>(A, lda, n, rr + P, piv, flag);
+  ++ctx->launches;
+  int h[2] = {0, 0};
+  if ((err = cudaMemcpyAsync(&h[0], flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(&h[1], rr + P, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (err = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(ctx, err);
+  if (h[0]) return M4RIE_OK;  // a pivot was missed: *complete stays false
+  const int64_t r = h[1];
+  if (r < 0 || r > std::min(m, n)) {
+    ctx->last_error = "echelon form: inconsistent rank on the device";
+    return M4RIE_ERR_CUDA;
+  }
+  if (pivots && r > 0 &&
+      (err = cudaMemcpy(pivots, piv, sizeof(int64_t) * (size_t)r, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return fail(ctx, err);
+  if (rank) *rank = r;
+  *complete = true;
+  return M4RIE_OK;
 }
 
 template <typename T>
@@ -483,6 +735,15 @@ m4rie_status m4rie_echelonize(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int6
   if (rank) *rank = 0;
   if (m == 0 || n == 0) return M4RIE_OK;
   if ((st = ensure_field_tables(ctx, e, f)) != M4RIE_OK) return st;
+  // The pipelined form when the rank cannot run out of rows long before the
+  // last panel; a missed pivot, or a wide matrix, takes the form that reads
+  // each panel's pivot list back.
+  if (n <= m + W) {
+    bool complete = false;
+    st = e <= 8 ? echelon_pipelined<uint8_t>(ctx, e, f, m, n, static_cast<uint8_t*>(A), lda, rank, pivots, &complete)
+                : echelon_pipelined<uint16_t>(ctx, e, f, m, n, static_cast<uint16_t*>(A), lda, rank, pivots, &complete);
+    if (st != M4RIE_OK || complete) return st;
+  }
   if (e <= 8) return echelon_impl<uint8_t>(ctx, e, f, m, n, static_cast<uint8_t*>(A), lda, rank, pivots);
   return echelon_impl<uint16_t>(ctx, e, f, m, n, static_cast<uint16_t*>(A), lda, rank, pivots);
 }
