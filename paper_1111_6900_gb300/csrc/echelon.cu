@@ -62,12 +62,24 @@ struct PanelOut {
 // order of its candidate block to moves: moves[0] = cnt, moves[1 + x] = the
 // candidate that goes to row rank + x (the pivot rows first, in pivot order,
 // then the other candidates in order).
+//
+// With blk set, the candidate block is not read from A: blk holds it (R rows
+// of W entries) before the previous panel's update, which the kernel applies
+// itself: X's rows over this panel's columns are M_prev^{-1} (mprev, W x W)
+// times the previous pivot rows there (pvn, row stride ldp), and candidate
+// row x gets multp[(r + x) W + a] times X's row a, a < the previous panel's
+// pivots (rr_in[0] - rr_in[-1]).
 struct DevPanel {
   const int* rr_in = nullptr;
   int* rr_out = nullptr;
   int64_t* piv = nullptr;
   int* moves = nullptr;
   int64_t m = 0;
+  const void* blk = nullptr;
+  const void* pvn = nullptr;
+  int64_t ldp = 0;
+  const void* mprev = nullptr;
+  const void* multp = nullptr;
 };
 static_assert(sizeof(PanelOut) <= kPanelHostBytes, "pinned pivot list");
 
@@ -123,6 +135,10 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
   __shared__ uint32_t pv_s;
   __shared__ int piv_row[W], piv_col[W];
   __shared__ uint32_t piv_val[W];
+  // the previous panel's update of the block (pipelined form with blk)
+  __shared__ T smv[W][W];
+  __shared__ __align__(16) T smult[R][W];
+  __shared__ uint32_t xsp[W * E * 2], xsx[W * E * 2];
   const uint32_t q = (1u << E) - 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = warp * 8 + (lane >> 2), word = lane & 3;
@@ -137,8 +153,49 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
 #pragma unroll
   for (int t = 0; t < E; ++t) sl[t] = 0;
   bool bad = false;
-  if (word < 2 && row < cnt) bad = bitslice::load_word<T, E>(A + (r + row) * lda + c0 + 32 * word, 32 * word, 0, wc, sl);
+  const T* blk = static_cast<const T*>(dev.blk);
+  if (word < 2 && row < cnt)
+    bad = bitslice::load_word<T, E>(blk ? blk + (int64_t)row * W + 32 * word : A + (r + row) * lda + c0 + 32 * word,
+                                    32 * word, 0, wc, sl);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStatusRange);
+  if (blk) {
+    const int kp = dev.rr_in[0] - dev.rr_in[-1];
+    const T* mprev = static_cast<const T*>(dev.mprev);
+    const T* pvn = static_cast<const T*>(dev.pvn);
+    for (int i = tid; i < kp * W; i += BS_THREADS) smv[i / W][i % W] = mprev[i];
+    if (tid < 2 * kp) {
+      uint32_t gs[E];
+      bitslice::load_word<T, E>(pvn + (int64_t)(tid >> 1) * dev.ldp + 32 * (tid & 1), 32 * (tid & 1), 0, wc, gs);
+#pragma unroll
+      for (int t = 0; t < E; ++t) xsp[((tid >> 1) * E + t) * 2 + (tid & 1)] = gs[t];
+    }
+    constexpr int VPR = W * (int)sizeof(T) / 16;  // 16-byte vectors per multiplier row
+    const uint4* m4 = reinterpret_cast<const uint4*>(static_cast<const T*>(dev.multp) + r * W);
+    uint4* d4 = reinterpret_cast<uint4*>(&smult[0][0]);
+    for (int i = tid; i < cnt * VPR; i += BS_THREADS) d4[i] = m4[i];
+    __syncthreads();
+    // X's rows over this panel's columns: X_a = sum_b M_prev^{-1}[a][b] P_b
+    if (tid < 2 * kp) {
+      const int a = tid >> 1, wd = tid & 1;
+      uint32_t acc[E];
+#pragma unroll
+      for (int t = 0; t < E; ++t) acc[t] = 0;
+      for (int b = 0; b < kp; ++b) {
+        const uint32_t sv = smv[a][b];
+        if (sv) bitslice::add_scaled<E>(acc, sv, &xsp[b * E * 2 + wd], 2, flow);
+      }
+#pragma unroll
+      for (int t = 0; t < E; ++t) xsx[(a * E + t) * 2 + wd] = acc[t];
+    }
+    __syncthreads();
+    // the block += its multipliers times X
+    if (word < 2 && row < cnt) {
+      for (int a = 0; a < kp; ++a) {
+        const uint32_t sv = smult[row][a];
+        if (sv) bitslice::add_scaled<E>(sl, sv, &xsx[a * E * 2 + word], 2, flow);
+      }
+    }
+  }
   __syncthreads();
 
   int k = 0, my_a = -1;  // pivots so far (uniform), this row's pivot number
@@ -292,12 +349,22 @@ __global__ void gather_mult(const T* __restrict__ A, int64_t lda, int64_t m, int
 // block's multipliers); the others write the multipliers of the rows
 // outside the block, which do not move.
 constexpr int PREP_CW = 128;
+// Largest e for which the next panel's kernel applies the previous panel's
+// update to its candidate block itself (its cost grows as e^2 per step).
+constexpr int kPreUpdateMaxE = 4;
 
+//
+// With wn > 0 it also writes blk, the next panel's candidate block (rows
+// r + k .., the next wn columns, in the new order), for the next panel
+// kernel, which applies this panel's update to it itself: CTAs past the
+// multiplier ones copy the rows outside this candidate block, chunk 0 the
+// rows inside it.
 template <typename T>
 __global__ void __launch_bounds__(256) prep_panel_dev(T* __restrict__ A, int64_t lda, int64_t m, int64_t c0,
                                                       int64_t nt, const int* __restrict__ rr,
                                                       const PanelOut* __restrict__ po, const int* __restrict__ ord,
-                                                      T* __restrict__ mult, T* __restrict__ pb, int nchunks) {
+                                                      T* __restrict__ mult, T* __restrict__ pb, int nchunks,
+                                                      int nmult, T* __restrict__ blk, int wn) {
   __shared__ T stage[R][PREP_CW];
   __shared__ int so[R];
   __shared__ int scols[W];
@@ -330,8 +397,15 @@ __global__ void __launch_bounds__(256) prep_panel_dev(T* __restrict__ A, int64_t
         if (a == x && a < k) v ^= (T)1;
         mult[(r + x) * W + a] = v;
       }
+      if (wn > 0) {
+        const int cn = (int)min((int64_t)R, m - r - k);
+        for (int idx = tid; idx < R * W; idx += 256) {
+          const int y = idx / W, c = idx % W;
+          if (y < cn && k + y < cnt) blk[idx] = c < wn ? stage[so[k + y]][W + c] : (T)0;
+        }
+      }
     }
-  } else {
+  } else if ((int)blockIdx.x < nchunks + nmult) {
     __syncthreads();
     const int64_t idx = ((int64_t)blockIdx.x - nchunks) * 256 + tid;
     if (idx >= m * W) return;
@@ -339,6 +413,12 @@ __global__ void __launch_bounds__(256) prep_panel_dev(T* __restrict__ A, int64_t
     const int a = (int)(idx % W);
     if (i >= r && i < r + cnt) return;
     mult[idx] = a < k ? A[i * lda + c0 + scols[a]] : (T)0;
+  } else {
+    const int idx = ((int)blockIdx.x - nchunks - nmult) * 256 + tid;
+    const int y = idx / W, c = idx % W;
+    const int cn = (int)min((int64_t)R, m - r - k);
+    if (wn <= 0 || y >= cn || k + y < cnt) return;
+    blk[idx] = c < wn ? A[(r + k + y) * lda + c0 + W + c] : (T)0;
   }
 }
 
@@ -398,11 +478,13 @@ void placement(const std::vector<int>& want, int base, std::vector<int>& src, st
 // The reduced row echelon form with every panel queued up front: the panel
 // kernels keep the rank and the candidate order on the device, and the
 // products always take K = W (M^{-1} is zero outside its k x k block, so the
-// unused multiplier columns add nothing).  Per panel: the panel kernel (the
-// next panel's on the side stream), one preparation kernel, the product X
-// and the update in two parts; the pivot list is read back once, at the end.  Each panel takes one round with the next
-// R rows as candidates, so a column whose only non-zero entries lie below
-// them gets no pivot.  A final check flags that case (*complete = false);
+// unused multiplier columns add nothing).  Per panel: one preparation
+// kernel; then the next panel's kernel on the side stream, from a snapshot of
+// its candidate block to which it applies this panel's update itself, beside
+// this panel's two products (X and the update).  The pivot list is read back
+// once, at the end.  Each panel takes one round with the next R rows as
+// candidates, so a column whose only non-zero entries lie below them gets no
+// pivot.  A final check flags that case (*complete = false);
 // the matrix is then row-equivalent to the input, and the caller finishes
 // it with echelon_impl (the reduced form is unique).
 template <typename T>
@@ -418,7 +500,8 @@ m4rie_status echelon_pipelined(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int
   const size_t sz_rr = round_up((int64_t)(sizeof(int) * (P + 2)), 256);
   const size_t sz_piv = round_up((int64_t)(sizeof(int64_t) * std::min(m, n)), 256);
   const size_t sz_mv = round_up((int64_t)(sizeof(int) * (1 + 2 * R) + 64), 256);
-  const size_t total = sz_po + sz_minv + sz_mult + 2 * sz_X + sz_rr + sz_piv + sz_mv;
+  const size_t sz_blk = round_up((int64_t)((size_t)R * W * w), 256);
+  const size_t total = sz_po + 2 * sz_minv + sz_mult + 2 * sz_X + sz_rr + sz_piv + sz_mv + sz_blk;
   cudaError_t err;
   if (total > ctx->ews_bytes) {
     if ((err = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return fail(ctx, err);
@@ -435,13 +518,15 @@ m4rie_status echelon_pipelined(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int
   if ((err = rowmove::ensure_side(ctx)) != cudaSuccess) return fail(ctx, err);
   uint8_t* base = static_cast<uint8_t*>(ctx->ews);
   PanelOut* po = reinterpret_cast<PanelOut*>(base);
-  T* minv = reinterpret_cast<T*>(base + sz_po);
-  T* mult = reinterpret_cast<T*>(base + sz_po + sz_minv);
-  T* X = reinterpret_cast<T*>(base + sz_po + sz_minv + sz_mult);
-  T* pb = reinterpret_cast<T*>(base + sz_po + sz_minv + sz_mult + sz_X);
-  int* rr = reinterpret_cast<int*>(base + sz_po + sz_minv + sz_mult + 2 * sz_X);
-  int64_t* piv = reinterpret_cast<int64_t*>(base + sz_po + sz_minv + sz_mult + 2 * sz_X + sz_rr);
-  int* moves = reinterpret_cast<int*>(base + sz_po + sz_minv + sz_mult + 2 * sz_X + sz_rr + sz_piv);
+  T* minv2[2] = {reinterpret_cast<T*>(base + sz_po), reinterpret_cast<T*>(base + sz_po + sz_minv)};
+  uint8_t* b2 = base + sz_po + 2 * sz_minv;
+  T* mult = reinterpret_cast<T*>(b2);
+  T* X = reinterpret_cast<T*>(b2 + sz_mult);
+  T* pb = reinterpret_cast<T*>(b2 + sz_mult + sz_X);
+  int* rr = reinterpret_cast<int*>(b2 + sz_mult + 2 * sz_X);
+  int64_t* piv = reinterpret_cast<int64_t*>(b2 + sz_mult + 2 * sz_X + sz_rr);
+  int* moves = reinterpret_cast<int*>(b2 + sz_mult + 2 * sz_X + sz_rr + sz_piv);
+  T* blk = reinterpret_cast<T*>(b2 + sz_mult + 2 * sz_X + sz_rr + sz_piv + sz_mv);
   int* flag = moves + 1 + 2 * R;
   if ((err = cudaMemsetAsync(rr, 0, sizeof(int), ctx->stream)) != cudaSuccess ||
       (err = cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream)) != cudaSuccess)
@@ -450,6 +535,10 @@ m4rie_status echelon_pipelined(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int
   for (int p = 0; p < P; ++p) {
     const int64_t c0 = (int64_t)p * W, nt = n - c0;
     const int wc = (int)std::min<int64_t>(W, nt);
+    const bool next = p + 1 < P;
+    const bool pre = next && e <= kPreUpdateMaxE;
+    const int wn = next ? (int)std::min<int64_t>(W, n - c0 - W) : 0;
+    T* minv = minv2[p & 1];  // this panel's M^{-1}; the next panel kernel writes the other one
     if (p == 0) {
       DevPanel dv;
       dv.rr_in = rr;
@@ -464,31 +553,51 @@ m4rie_status echelon_pipelined(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int
     } else if ((err = cudaStreamWaitEvent(st, ctx->ech_ev[1], 0)) != cudaSuccess) {
       return fail(ctx, err);
     }
-    // 1. the candidate block in its new order, the pivot block, the multipliers
+    // 1. the candidate block in its new order, the pivot block, the
+    // multipliers, the next panel's candidate block
     const int nchunks = (int)ceil_div(nt, PREP_CW);
-    prep_panel_dev<T><<<(unsigned)(nchunks + ceil_div(m * W, 256)), 256, 0, st>>>(A, lda, m, c0, nt, rr + p, po,
-                                                                                  moves, mult, pb, nchunks);
+    const int nmult = (int)ceil_div(m * W, 256);
+    const int nblk = pre ? (int)ceil_div(R * W, 256) : 0;
+    prep_panel_dev<T><<<(unsigned)(nchunks + nmult + nblk), 256, 0, st>>>(A, lda, m, c0, nt, rr + p, po, moves, mult,
+                                                                         pb, nchunks, nmult, blk, pre ? wn : 0);
     ++ctx->launches;
-    // 2. X = M^{-1} (pivot rows); 3. A[:, c0..] += mult X (which also makes
-    // the pivot rows X's rows), the next panel's columns first, its kernel on
-    // the side stream beside the rest
-    m4rie_status s2 = run_gemm(ctx, e, f, W, nt, W, Mats{minv, W, pb, nt, X, nt}, 0);
-    if (s2 != M4RIE_OK) return s2;
-    const bool next = p + 1 < P;
-    const int64_t n1 = next && nt > 2 * W ? 2 * W : nt;
-    if ((s2 = run_gemm(ctx, e, f, m, n1, W, Mats{mult, W, X, nt, A + c0, lda}, 1)) != M4RIE_OK) return s2;
-    if (next) {
-      DevPanel dv;
-      dv.rr_in = rr + p + 1;
-      dv.rr_out = rr + p + 2;
-      dv.piv = piv;
-      dv.moves = moves;
-      dv.m = m;
-      const int wn = (int)std::min<int64_t>(W, n - c0 - W);
+    DevPanel dn;  // the next panel's kernel
+    dn.rr_in = rr + p + 1;
+    dn.rr_out = rr + p + 2;
+    dn.piv = piv;
+    dn.moves = moves;
+    dn.m = m;
+    // 2. (e <= kPreUpdateMaxE) the next panel's kernel on the side stream: it
+    // applies this panel's update to its candidate block itself, so it
+    // waits for neither step 3 nor 4
+    if (pre) {
+      DevPanel dv = dn;
+      dv.blk = blk;
+      dv.pvn = pb + W;
+      dv.ldp = nt;
+      dv.mprev = minv;
+      dv.multp = mult;
       if ((err = cudaEventRecord(ctx->ech_ev[0], st)) != cudaSuccess ||
           (err = cudaStreamWaitEvent(ctx->ech_side, ctx->ech_ev[0], 0)) != cudaSuccess ||
-          (err = launch_panel_bitsliced<T>(e, A, lda, 0, c0 + W, 0, wn, 0, f, ctx->d_gf, po, minv, ctx->d_status,
-                                           ctx->ech_side, dv)) != cudaSuccess ||
+          (err = launch_panel_bitsliced<T>(e, A, lda, 0, c0 + W, 0, wn, 0, f, ctx->d_gf, po, minv2[(p + 1) & 1],
+                                           ctx->d_status, ctx->ech_side, dv)) != cudaSuccess ||
+          (err = cudaEventRecord(ctx->ech_ev[1], ctx->ech_side)) != cudaSuccess)
+        return fail(ctx, err);
+      ++ctx->launches;
+    }
+    // 3. X = M^{-1} (pivot rows); 4. A[:, c0..] += mult X, which also makes
+    // the pivot rows X's rows.  Larger fields, where the block's update costs
+    // the one-CTA kernel more than a product: the next panel's columns first,
+    // then its kernel on the side stream beside the rest.
+    m4rie_status s2 = run_gemm(ctx, e, f, W, nt, W, Mats{minv, W, pb, nt, X, nt}, 0);
+    if (s2 != M4RIE_OK) return s2;
+    const int64_t n1 = next && !pre && nt > 2 * W ? 2 * W : nt;
+    if ((s2 = run_gemm(ctx, e, f, m, n1, W, Mats{mult, W, X, nt, A + c0, lda}, 1)) != M4RIE_OK) return s2;
+    if (next && !pre) {
+      if ((err = cudaEventRecord(ctx->ech_ev[0], st)) != cudaSuccess ||
+          (err = cudaStreamWaitEvent(ctx->ech_side, ctx->ech_ev[0], 0)) != cudaSuccess ||
+          (err = launch_panel_bitsliced<T>(e, A, lda, 0, c0 + W, 0, wn, 0, f, ctx->d_gf, po, minv2[(p + 1) & 1],
+                                           ctx->d_status, ctx->ech_side, dn)) != cudaSuccess ||
           (err = cudaEventRecord(ctx->ech_ev[1], ctx->ech_side)) != cudaSuccess)
         return fail(ctx, err);
       ++ctx->launches;
