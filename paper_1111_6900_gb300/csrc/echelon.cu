@@ -136,8 +136,9 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
   __shared__ int piv_row[W], piv_col[W];
   __shared__ uint32_t piv_val[W];
   // the previous panel's update of the block (pipelined form with blk)
-  __shared__ T smv[W][W];
-  __shared__ __align__(16) T smult[R][W];
+  __shared__ T smv[W][W];  // M_prev^{-1}, transposed: a thread per row of X reads along a row here
+  constexpr int MP = W + 16 / (int)sizeof(T);  // padded multiplier rows: 16-byte aligned, no bank conflicts
+  __shared__ __align__(16) T smult[R][MP];
   __shared__ uint32_t xsp[W * E * 2], xsx[W * E * 2];
   const uint32_t q = (1u << E) - 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -162,7 +163,8 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
     const int kp = dev.rr_in[0] - dev.rr_in[-1];
     const T* mprev = static_cast<const T*>(dev.mprev);
     const T* pvn = static_cast<const T*>(dev.pvn);
-    for (int i = tid; i < kp * W; i += BS_THREADS) smv[i / W][i % W] = mprev[i];
+#pragma unroll 4
+    for (int i = tid; i < kp * W; i += BS_THREADS) smv[i % W][i / W] = mprev[i];
     if (tid < 2 * kp) {
       uint32_t gs[E];
       bitslice::load_word<T, E>(pvn + (int64_t)(tid >> 1) * dev.ldp + 32 * (tid & 1), 32 * (tid & 1), 0, wc, gs);
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
     constexpr int VPR = W * (int)sizeof(T) / 16;  // 16-byte vectors per multiplier row
     const uint4* m4 = reinterpret_cast<const uint4*>(static_cast<const T*>(dev.multp) + r * W);
     uint4* d4 = reinterpret_cast<uint4*>(&smult[0][0]);
-    for (int i = tid; i < cnt * VPR; i += BS_THREADS) d4[i] = m4[i];
+    for (int i = tid; i < cnt * VPR; i += BS_THREADS) d4[(i / VPR) * (MP * (int)sizeof(T) / 16) + i % VPR] = m4[i];
     __syncthreads();
     // X's rows over this panel's columns: X_a = sum_b M_prev^{-1}[a][b] P_b
     if (tid < 2 * kp) {
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(BS_THREADS) panel_bitsliced(const T* __restric
 #pragma unroll
       for (int t = 0; t < E; ++t) acc[t] = 0;
       for (int b = 0; b < kp; ++b) {
-        const uint32_t sv = smv[a][b];
+        const uint32_t sv = smv[b][a];
         if (sv) bitslice::add_scaled<E>(acc, sv, &xsp[b * E * 2 + wd], 2, flow);
       }
 #pragma unroll
@@ -335,7 +337,7 @@ __global__ void gather_mult(const T* __restrict__ A, int64_t lda, int64_t m, int
 // (rr[1]) from the device, so that every panel is queued without waiting for
 // the previous one's pivot list.
 
-// One launch prepares a panel's products, reading the rank before the panel
+// The preparation of a panel's products, reading the rank before the panel
 // (rr[0]) and after it (rr[1]) and the candidate order `ord` (moves of the
 // panel kernel) from the device:
 //   * the candidate block's new row order, columns c0 .. c0+nt-1;
@@ -343,40 +345,46 @@ __global__ void gather_mult(const T* __restrict__ A, int64_t lda, int64_t m, int
 //   * the multipliers of every row, mult[i][a] = A[i][c0 + cols[a]] for
 //     a < k, 0 above; pivot row a also gets 1 added at a, so that the
 //     update A += mult X turns it into X's row a (P_a + (M_a + e_a) X = X_a
-//     in characteristic 2, X = M^{-1} P).
-// The first nchunks CTAs each take PREP_CW columns of the candidate block
-// through shared memory (chunk 0 holds the panel's columns and writes the
-// block's multipliers); the others write the multipliers of the rows
-// outside the block, which do not move.
+//     in characteristic 2, X = M^{-1} P);
+//   * with wn > 0, blk: the next panel's candidate block (rows r + k .., the
+//     next wn columns, in the new order) for the next panel kernel, which
+//     applies this panel's update to it itself.
+// CTA roles, in grid order:
+//   * nch chunk CTAs, chunks ch0 .., each PREP_CW columns of the candidate
+//     block through shared memory (chunk 0 holds this panel's and the next
+//     panel's columns: it also writes the block's multipliers and blk's rows
+//     inside the block);
+//   * nmult CTAs of multipliers of the rows outside the block: next_only = 1,
+//     only those of the next candidate block; next_only = 2, all but those;
+//     0, all (these rows do not move);
+//   * nblk CTAs of blk's rows outside this candidate block.
 constexpr int PREP_CW = 128;
 // Largest e for which the next panel's kernel applies the previous panel's
 // update to its candidate block itself (its cost grows as e^2 per step).
 constexpr int kPreUpdateMaxE = 4;
 
-//
-// With wn > 0 it also writes blk, the next panel's candidate block (rows
-// r + k .., the next wn columns, in the new order), for the next panel
-// kernel, which applies this panel's update to it itself: CTAs past the
-// multiplier ones copy the rows outside this candidate block, chunk 0 the
-// rows inside it.
 template <typename T>
 __global__ void __launch_bounds__(256) prep_panel_dev(T* __restrict__ A, int64_t lda, int64_t m, int64_t c0,
                                                       int64_t nt, const int* __restrict__ rr,
                                                       const PanelOut* __restrict__ po, const int* __restrict__ ord,
-                                                      T* __restrict__ mult, T* __restrict__ pb, int nchunks,
-                                                      int nmult, T* __restrict__ blk, int wn) {
+                                                      T* __restrict__ mult, T* __restrict__ pb, int ch0, int nch,
+                                                      int nmult, int next_only, T* __restrict__ blk, int wn) {
   __shared__ T stage[R][PREP_CW];
   __shared__ int so[R];
   __shared__ int scols[W];
   const int64_t r = rr[0];
   const int k = rr[1] - rr[0];
   const int cnt = ord[0];
+  const int cn = (int)min((int64_t)R, m - r - k);  // rows of the next candidate block
   const int tid = threadIdx.x;
   for (int i = tid; i < k; i += 256) scols[i] = po->cols[i];
-  if ((int)blockIdx.x < nchunks) {
-    const int64_t cb = (int64_t)blockIdx.x * PREP_CW;
+  if ((int)blockIdx.x < nch) {
+    const int chunk = ch0 + (int)blockIdx.x;
+    const int64_t cb = (int64_t)chunk * PREP_CW;
     const int cw = (int)min((int64_t)PREP_CW, nt - cb);
     for (int i = tid; i < cnt; i += 256) so[i] = ord[1 + i];
+    // loads issued eight at a time (the loop has no dependence between iterations)
+#pragma unroll 8
     for (int idx = tid; idx < cnt * PREP_CW; idx += 256) {
       const int x = idx / PREP_CW, c = idx % PREP_CW;
       if (c < cw) stage[x][c] = A[(r + x) * lda + c0 + cb + c];
@@ -390,7 +398,7 @@ __global__ void __launch_bounds__(256) prep_panel_dev(T* __restrict__ A, int64_t
       const int a = idx / PREP_CW, c = idx % PREP_CW;
       if (c < cw) pb[(int64_t)a * nt + cb + c] = a < k ? stage[so[a]][c] : (T)0;
     }
-    if (blockIdx.x == 0) {
+    if (chunk == 0) {
       for (int idx = tid; idx < cnt * W; idx += 256) {
         const int x = idx / W, a = idx % W;
         T v = a < k ? stage[so[x]][scols[a]] : (T)0;
@@ -398,28 +406,34 @@ __global__ void __launch_bounds__(256) prep_panel_dev(T* __restrict__ A, int64_t
         mult[(r + x) * W + a] = v;
       }
       if (wn > 0) {
-        const int cn = (int)min((int64_t)R, m - r - k);
         for (int idx = tid; idx < R * W; idx += 256) {
           const int y = idx / W, c = idx % W;
           if (y < cn && k + y < cnt) blk[idx] = c < wn ? stage[so[k + y]][W + c] : (T)0;
         }
       }
     }
-  } else if ((int)blockIdx.x < nchunks + nmult) {
-    __syncthreads();
-    const int64_t idx = ((int64_t)blockIdx.x - nchunks) * 256 + tid;
-    if (idx >= m * W) return;
-    const int64_t i = idx / W;
-    const int a = (int)(idx % W);
-    if (i >= r && i < r + cnt) return;
-    mult[idx] = a < k ? A[i * lda + c0 + scols[a]] : (T)0;
-  } else {
-    const int idx = ((int)blockIdx.x - nchunks - nmult) * 256 + tid;
-    const int y = idx / W, c = idx % W;
-    const int cn = (int)min((int64_t)R, m - r - k);
-    if (wn <= 0 || y >= cn || k + y < cnt) return;
-    blk[idx] = c < wn ? A[(r + k + y) * lda + c0 + W + c] : (T)0;
+    return;
   }
+  __syncthreads();
+  if ((int)blockIdx.x < nch + nmult) {
+    const int64_t idx = ((int64_t)blockIdx.x - nch) * 256 + tid;
+    int64_t i;
+    if (next_only == 1) {  // the next candidate block's rows outside this one
+      i = r + cnt + idx / W;
+      if (i >= r + k + cn) return;
+    } else {
+      i = idx / W;
+      if (i >= m || (i >= r && i < r + cnt)) return;
+      if (next_only == 2 && i >= r + cnt && i < r + k + cn) return;
+    }
+    const int a = (int)(idx % W);
+    mult[i * W + a] = a < k ? A[i * lda + c0 + scols[a]] : (T)0;
+    return;
+  }
+  const int idx = ((int)blockIdx.x - nch - nmult) * 256 + tid;
+  const int y = idx / W, c = idx % W;
+  if (wn <= 0 || y >= cn || k + y < cnt) return;
+  blk[idx] = c < wn ? A[(r + k + y) * lda + c0 + W + c] : (T)0;
 }
 
 // *flag = 1 unless every row i < r is zero left of its pivot column piv[i]
@@ -554,12 +568,13 @@ m4rie_status echelon_pipelined(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int
       return fail(ctx, err);
     }
     // 1. the candidate block in its new order, the pivot block, the
-    // multipliers, the next panel's candidate block
+    // multipliers, the next panel's candidate block: with the look-ahead,
+    // what the next panel's kernel needs in a first small launch
     const int nchunks = (int)ceil_div(nt, PREP_CW);
-    const int nmult = (int)ceil_div(m * W, 256);
+    const int nmult_all = (int)ceil_div(m * W, 256);
     const int nblk = pre ? (int)ceil_div(R * W, 256) : 0;
-    prep_panel_dev<T><<<(unsigned)(nchunks + nmult + nblk), 256, 0, st>>>(A, lda, m, c0, nt, rr + p, po, moves, mult,
-                                                                         pb, nchunks, nmult, blk, pre ? wn : 0);
+    prep_panel_dev<T><<<(unsigned)(nchunks + nmult_all + nblk), 256, 0, st>>>(
+        A, lda, m, c0, nt, rr + p, po, moves, mult, pb, 0, nchunks, nmult_all, 0, blk, pre ? wn : 0);
     ++ctx->launches;
     DevPanel dn;  // the next panel's kernel
     dn.rr_in = rr + p + 1;
