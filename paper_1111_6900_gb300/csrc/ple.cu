@@ -22,7 +22,9 @@
 //      the next pivot and the row there takes its old one (Algorithm 4's
 //      swap); the candidates that are not yet pivots get the multiple of the
 //      pivot row that clears the column.  The round stops at the first column
-//      where no candidate has a non-zero entry (column j0).  Out: the pivots
+//      where no candidate has a non-zero entry (column j0), unless the
+//      candidates are all the remaining rows: then that column has no pivot
+//      and the round goes on.  Out: the pivots
 //      and their swaps, E's rows over the panel (the pivot rows scaled to a
 //      leading 1), Lp^{-1} (Lp: L's block of the round's pivot rows; the
 //      kernel tracks each pivot row's combination of the original rows), and
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(PT) ple_panel(T* __restrict__ A, int64_t lda, 
                                                 int wc, int js, uint32_t flow, const uint16_t* __restrict__ gf,
                                                 PleOut* __restrict__ out, T* __restrict__ linv,
                                                 uint32_t* __restrict__ esl, int* status, const T* __restrict__ pl,
-                                                const T* __restrict__ px, int64_t ldx, int kp) {
+                                                const T* __restrict__ px, int64_t ldx, int kp, int64_t m) {
   extern __shared__ uint32_t snap[];  // [2][E][PT], then the previous G's slices [W][E][2]
   uint32_t* xs = snap + 2 * E * PT;
   __shared__ uint16_t lg[LOGW];
@@ -188,8 +190,10 @@ __global__ void __launch_bounds__(PT) ple_panel(T* __restrict__ A, int64_t lda, 
     if (tid == 0) cand[slot == 0 ? 2 : slot - 1] = ~0u;
     slot = slot == 2 ? 0 : slot + 1;
     sbuf = sbuf ? 0 : E * PT;
-    if (c == ~0u) {  // no candidate has a non-zero entry here (uniform): the round ends
-      j0 = j;
+    if (c == ~0u) {  // no candidate has a non-zero entry here (uniform)
+      // with every remaining row a candidate, no row has one: no pivot here
+      if (cnt == m - r) continue;
+      j0 = j;  // a row below the candidates may have one: the round ends
       break;
     }
     const int p = (int)((c >> 10) & 127u), old = (int)(c >> 17);
@@ -318,12 +322,15 @@ __global__ void __launch_bounds__(AT) ple_apply(T* __restrict__ A, int64_t lda, 
 }
 
 // The previous panel's update of the candidate block (kp = 0: none).
+// m: the matrix's rows (the panel kernel needs them to know whether its
+// candidates are all the remaining rows).
 template <typename T>
 struct PreUpdate {
   const T* pl = nullptr;
   const T* px = nullptr;
   int64_t ldx = 0;
   int kp = 0;
+  int64_t m = 0;
 };
 
 template <typename T, int E>
@@ -335,14 +342,14 @@ cudaError_t launch_panel_e(T* A, int64_t lda, int64_t r, int64_t c0, int cnt, in
   const cudaError_t err = cudaFuncSetAttribute(ple_panel<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
   ple_panel<T, E><<<1, PT, smem, s>>>(A, lda, r, c0, cnt, wc, js, flow, gf, out, linv, esl, status, pre.pl, pre.px,
-                                      pre.ldx, pre.kp);
+                                      pre.ldx, pre.kp, pre.m);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_panel(int e, T* A, int64_t lda, int64_t r, int64_t c0, int cnt, int wc, int js, uint32_t f,
                          const uint16_t* gf, PleOut* out, T* linv, uint32_t* esl, int* status, cudaStream_t s,
-                         const PreUpdate<T>& pre = PreUpdate<T>()) {
+                         const PreUpdate<T>& pre) {
   const uint32_t flow = f & ((1u << e) - 1u);
 #define M4RIE_PLE_CASE(EE) \
   case EE:                 \
@@ -446,6 +453,8 @@ m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T
   T* X = reinterpret_cast<T*>(base + sz_small + sz_linv + sz_esl + sz_lbuf);
   mv.tmp = base + sz_small + sz_linv + sz_esl + sz_lbuf + sz_X;
   PleOut* hpo_next = static_cast<PleOut*>(ctx->ech_po_host);
+  PreUpdate<T> plain;  // no previous update to apply
+  plain.m = m;
 
   std::vector<int64_t> piv(std::min(m, n)), perm(std::min(m, n));
   std::vector<int> src, dst, win;
@@ -468,7 +477,7 @@ m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T
         ahead = false;
       } else {
         if ((err = launch_panel<T>(e, A, lda, r, c0, cnt, wc, js, f, ctx->d_gf, d_po, linv, esl, ctx->d_status,
-                                   ctx->stream)) != cudaSuccess)
+                                   ctx->stream, plain)) != cudaSuccess)
           return fail(ctx, err);
         ++ctx->launches;
         if ((err = cudaMemcpyAsync(&hpo, d_po, sizeof(PleOut), cudaMemcpyDeviceToHost, ctx->stream)) !=
@@ -549,6 +558,7 @@ m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T
             pre.px = X;
             pre.ldx = nb;
             pre.kp = k;
+            pre.m = m;
             if ((err = cudaEventRecord(ctx->ech_ev[0], ctx->stream)) != cudaSuccess ||
                 (err = cudaStreamWaitEvent(ctx->ech_side, ctx->ech_ev[0], 0)) != cudaSuccess ||
                 (err = launch_panel<T>(e, A, lda, r_next, cr, cnt_next, W, 0, f, ctx->d_gf, d_po, linv, esl,
@@ -577,7 +587,7 @@ m4rie_status ple_impl(m4rie_ctx* ctx, int e, uint32_t f, int64_t m, int64_t n, T
             if ((err = cudaEventRecord(ctx->ech_ev[0], ctx->stream)) != cudaSuccess ||
                 (err = cudaStreamWaitEvent(ctx->ech_side, ctx->ech_ev[0], 0)) != cudaSuccess ||
                 (err = launch_panel<T>(e, A, lda, r_next, cr, cnt_next, W, 0, f, ctx->d_gf, d_po, linv, esl,
-                                       ctx->d_status, ctx->ech_side)) != cudaSuccess ||
+                                       ctx->d_status, ctx->ech_side, plain)) != cudaSuccess ||
                 (err = cudaMemcpyAsync(hpo_next, d_po, sizeof(PleOut), cudaMemcpyDeviceToHost, ctx->ech_side)) !=
                     cudaSuccess ||
                 (err = cudaEventRecord(ctx->ech_ev[1], ctx->ech_side)) != cudaSuccess)
