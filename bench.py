@@ -55,11 +55,13 @@ CONFIG = config_of(WORKLOAD)
 # while the kernel source is the one that was profiled (sha256 below).
 TRAFFIC = {
     "tc_f4/karatsuba": {"bytes": 154.045440e6 + 3.784960e6, "source": "profiles/tc_f4_karatsuba_gf16_4096.md"},
+    "tc_f8/karatsuba": {"bytes": 302.094336e6 + 3.267328e6, "source": "profiles/tc_f8_karatsuba_gf16_4096.md"},
     "popc/alpha_b": {"bytes": 41.965824e6 + 0.164864e6, "source": "profiles/popc_alpha_b_gf16_4096.md"},
     "newton_john/alpha_b": {"bytes": 68.244224e6 + 6.878208e6, "source": "profiles/nj_rank64_gf256_8192.md",
                             "workload": "gf256_8192x64x8192_addmul"},
 }
 PROFILED_SOURCES = {"tc_f4/karatsuba": ("gemm_tc.cu", "f35ba7360a0e989d4bd923998564e9ff87d6429376d60caf295a78b1e925e70c"),
+                    "tc_f8/karatsuba": ("gemm_tc.cu", "f35ba7360a0e989d4bd923998564e9ff87d6429376d60caf295a78b1e925e70c"),
                     "popc/alpha_b": ("gemm_popc.cu", "6fc3d0a61765ce47396627acb19770a9ddecc498caad76ea310bae7c899f3a1b"),
                     "newton_john/alpha_b": ("nj_kernel.cuh",
                                             "401c1b6ee335e2c2bd6faefe5fa10256758b5175f58f22d194d82c5451a879dd")}
