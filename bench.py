@@ -54,17 +54,21 @@ CONFIG = config_of(WORKLOAD)
 # summaries (dram__bytes_read.sum + dram__bytes_write.sum).  It is reported only
 # while the kernel source is the one that was profiled (sha256 below).
 TRAFFIC = {
-    "tc_f4/karatsuba": {"bytes": 154.045440e6 + 3.784960e6, "source": "profiles/tc_f4_karatsuba_gf16_4096.md"},
+    "tc_f4/karatsuba": {"bytes": 155.226624e6 + 3.691008e6, "source": "profiles/tc_f4_karatsuba_gf16_4096.md"},
     "tc_f8/karatsuba": {"bytes": 302.094336e6 + 3.267328e6, "source": "profiles/tc_f8_karatsuba_gf16_4096.md"},
     "popc/alpha_b": {"bytes": 41.965824e6 + 0.164864e6, "source": "profiles/popc_alpha_b_gf16_4096.md"},
     "newton_john/alpha_b": {"bytes": 68.244224e6 + 6.878208e6, "source": "profiles/nj_rank64_gf256_8192.md",
                             "workload": "gf256_8192x64x8192_addmul"},
 }
-PROFILED_SOURCES = {"tc_f4/karatsuba": ("gemm_tc.cu", "f35ba7360a0e989d4bd923998564e9ff87d6429376d60caf295a78b1e925e70c"),
-                    "tc_f8/karatsuba": ("gemm_tc.cu", "f35ba7360a0e989d4bd923998564e9ff87d6429376d60caf295a78b1e925e70c"),
-                    "popc/alpha_b": ("gemm_popc.cu", "6fc3d0a61765ce47396627acb19770a9ddecc498caad76ea310bae7c899f3a1b"),
-                    "newton_john/alpha_b": ("nj_kernel.cuh",
-                                            "401c1b6ee335e2c2bd6faefe5fa10256758b5175f58f22d194d82c5451a879dd")}
+# sources each capture was taken on: the kernel's own and, where it sets the
+# kernel's tile shape, the host code that launches it
+_GEMM_TC = ("gemm_tc.cu", "f35ba7360a0e989d4bd923998564e9ff87d6429376d60caf295a78b1e925e70c")
+PROFILED_SOURCES = {"tc_f4/karatsuba": (_GEMM_TC,
+                                        ("api.cu", "efc4027a2353c9e7ff83ce40c9a65a4932aad1e1b94f1fba5f70e75b950fb0dc")),
+                    "tc_f8/karatsuba": (_GEMM_TC,),
+                    "popc/alpha_b": (("gemm_popc.cu", "6fc3d0a61765ce47396627acb19770a9ddecc498caad76ea310bae7c899f3a1b"),),
+                    "newton_john/alpha_b": (("nj_kernel.cuh",
+                                             "401c1b6ee335e2c2bd6faefe5fa10256758b5175f58f22d194d82c5451a879dd"),)}
 # tcgen05.mma issue rate measured on GB300 (one CTA per SM issuing MMAs on shared-memory
 # operands back to back), MAC per SM clock
 MMA_MAC_PER_CLK = {"tc_f8": 8192, "tc_f4": 16384}
@@ -77,11 +81,11 @@ def kernel_traffic(key):
     t = TRAFFIC.get(key)
     if not t or t.get("workload", "gf16_4096_mul") != WORKLOAD.name:
         return None
-    fname, sha = PROFILED_SOURCES[key]
-    path = os.path.join(ROOT, "paper_1111_6900_gb300", "csrc", fname)
-    with open(path, "rb") as fh:
-        cur = hashlib.sha256(fh.read()).hexdigest()
-    return t["bytes"] if sha is None or sha == cur else None
+    for fname, sha in PROFILED_SOURCES[key]:
+        with open(os.path.join(ROOT, "paper_1111_6900_gb300", "csrc", fname), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != sha:
+                return None
+    return t["bytes"]
 
 
 def peaks():

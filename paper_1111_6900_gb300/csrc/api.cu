@@ -325,18 +325,22 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   const int64_t Kp = round_up(k, 128);
   const bool pair = form != M4RIE_FORM_POPC && pair_m(ctx, m);
   const int64_t Mp = round_up(m, pair ? 256 : 128);
-  // popc parity tiles are 128 columns; tcgen05 tiles 256 (FP8) or 224 (FP4, which
-  // keeps its scale factors in TMEM next to each accumulator)
-  const int ntile = form == M4RIE_FORM_POPC ? 128 : (form == M4RIE_FORM_TC_F8 ? 256 : 224);
+  // tcgen05 on 2-SM pairs, e <= 8: the GEMM's epilogue recombines the products
+  // of each output tile itself (no parity planes, no recombination kernel)
+  const bool fused = form != M4RIE_FORM_POPC && pair && e <= 8 && ctx->fuse_recombine && r <= 64;
+  // popc parity tiles are 128 columns; tcgen05 tiles 256 (FP8) or 240 (FP4,
+  // which keeps its scale factors in TMEM columns 240..255 next to each
+  // accumulator; 224 with the recombination in the epilogue, whose output
+  // slices are whole 32-column words).  FP4 MMAs of N = 240 keep the tensor
+  // pipe busy with one barrier wait and commit per 8 of them, N = 224 ones
+  // leave it idle about 7% of the time.
+  const int ntile = form == M4RIE_FORM_POPC ? 128 : (form == M4RIE_FORM_TC_F8 ? 256 : (fused ? 224 : 240));
   const int64_t Np = round_up(n, ntile);
   // parity planes: popc, rows of ldp words (whole 16-byte groups); tcgen05,
   // blocks of 128 rows x 8 words per output tile (TcParams)
   const int64_t ldp = round_up(Np / 32, 4);
   const bool blocked = form != M4RIE_FORM_POPC;
   const int64_t p_plane = blocked ? (Mp / 128) * (Np / ntile) * 1024 : Mp * ldp;  // words per plane
-  // tcgen05 on 2-SM pairs, e <= 8: the GEMM's epilogue recombines the products
-  // of each output tile itself (no parity planes, no recombination kernel)
-  const bool fused = form != M4RIE_FORM_POPC && pair && e <= 8 && ctx->fuse_recombine && r <= 64;
   const size_t a_bytes = round_up((int64_t)entries_bytes((int64_t)r * Mp * Kp, fi.bits), 1024);
   const size_t b_bytes = round_up((int64_t)entries_bytes((int64_t)r * Np * Kp, fi.bits), 1024);
   const size_t p_bytes = fused ? 0 : round_up((int64_t)r * p_plane * 4, 1024);
@@ -451,7 +455,7 @@ m4rie_status run_karatsuba(m4rie_ctx* ctx, int form, int e, uint32_t f, int64_t 
   rc.ldw = ldp;
   rc.rows_p = Mp;
   rc.blocked = blocked ? 1 : 0;
-  rc.tw = ntile / 32;
+  rc.tcols = ntile;
   rc.tiles_n = Np / ntile;
   rc.bstride = p_plane;
   rc.r = r;

@@ -448,7 +448,7 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
       rc.P = reinterpret_cast<const uint32_t*>(wbase + L.p_off);
       rc.rows_p = L.Mp;
       rc.blocked = 1;
-      rc.tw = L.BN / 32;
+      rc.tcols = L.BN;
       rc.tiles_n = L.groups;
       rc.bstride = L.p_plane;
       rc.r = L.r;

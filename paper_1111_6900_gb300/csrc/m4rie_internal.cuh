@@ -117,9 +117,11 @@ struct RecombineParams {
   const uint32_t* P;  // r bit planes, plane p row i at P + (p*rows_p + i)*ldw
   int64_t ldw;        // words per parity-plane row
   int64_t rows_p;
-  // blocked planes (the tcgen05 GEMM's layout, see TcParams): tw valid words
-  // of 8 per block row, tiles_n column tiles, bstride words between planes
-  int blocked, tw;
+  // blocked planes (the tcgen05 GEMM's layout, see TcParams): tiles of tcols
+  // columns (a multiple of 16, at most 256) held in the first
+  // ceil(tcols / 32) of a block row's 8 words, tiles_n column tiles, bstride
+  // words between planes
+  int blocked, tcols;
   int64_t tiles_n, bstride;
   int r;
   int e;

@@ -493,8 +493,9 @@ __global__ void __launch_bounds__(256) cling_kernel(int e, int64_t rows, int64_t
 // into E output slice words each (which products feed which slices comes from
 // a per-block table), then transposes the bits into elements.
 template <typename T, int E>
-__device__ __forceinline__ bool store_elements(const RecombineParams& p, int64_t r, int64_t w, const uint32_t* out) {
-  // elements c = 32 w + b, packed 4 (u8) or 2 (u16) per 32-bit word
+__device__ __forceinline__ bool store_elements(const RecombineParams& p, int64_t r, int64_t cs, int nc,
+                                               const uint32_t* out) {
+  // elements c = cs + b for b < nc <= 32, packed 4 (u8) or 2 (u16) per 32-bit word
   constexpr int PER = 4 / sizeof(T);
   constexpr int NW = 32 / PER;
   uint32_t vals[NW];
@@ -510,38 +511,37 @@ __device__ __forceinline__ bool store_elements(const RecombineParams& p, int64_t
     vals[g] = v;
   }
   T* C = static_cast<T*>(p.C);
-  T* dst = C + r * p.ldc + 32 * w;
-  const bool full = 32 * w + 32 <= p.n;
-  const bool vec = full && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
+  T* dst = C + r * p.ldc + cs;
+  // 16-byte chunks of EPC elements: a whole chunk inside the word and the
+  // matrix goes out as one vector store, a ragged one element by element
+  constexpr int EPC = 16 / sizeof(T);
+  const bool al = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
+  const uint32_t rep = sizeof(T) == 1 ? p.emask * 0x01010101u : p.emask * 0x00010001u;
   bool bad = false;
-  if (vec) {
-    uint4* d4 = reinterpret_cast<uint4*>(dst);
-    uint4 old[NW / 4];
-    if (p.add) {
 #pragma unroll
-      for (int h = 0; h < NW / 4; ++h) old[h] = d4[h];
-    }
-#pragma unroll
-    for (int h = 0; h < NW / 4; ++h) {
+  for (int h = 0; h < NW / 4; ++h) {
+    const int b0 = h * EPC;
+    if (al && b0 + EPC <= nc && cs + b0 + EPC <= p.n) {
+      uint4* d4 = reinterpret_cast<uint4*>(dst + b0);
       uint4 o = make_uint4(vals[4 * h], vals[4 * h + 1], vals[4 * h + 2], vals[4 * h + 3]);
       if (p.add) {
-        const uint32_t rep = sizeof(T) == 1 ? p.emask * 0x01010101u : p.emask * 0x00010001u;
-        bad |= ((old[h].x | old[h].y | old[h].z | old[h].w) & ~rep) != 0;
-        o.x ^= old[h].x & rep, o.y ^= old[h].y & rep, o.z ^= old[h].z & rep, o.w ^= old[h].w & rep;
+        const uint4 old = *d4;
+        bad |= ((old.x | old.y | old.z | old.w) & ~rep) != 0;
+        o.x ^= old.x & rep, o.y ^= old.y & rep, o.z ^= old.z & rep, o.w ^= old.w & rep;
       }
-      d4[h] = o;
-    }
-  } else {
+      *d4 = o;
+    } else {
 #pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      if (32 * w + b < p.n) {
-        uint32_t v = (vals[b / PER] >> (8 * sizeof(T) * (b % PER))) & (sizeof(T) == 1 ? 0xFFu : 0xFFFFu);
-        if (p.add) {
-          const uint32_t old = dst[b];
-          bad |= old > p.emask;
-          v ^= old & p.emask;
+      for (int b = b0; b < b0 + EPC; ++b) {
+        if (b < nc && cs + b < p.n) {
+          uint32_t v = (vals[b / PER] >> (8 * sizeof(T) * (b % PER))) & (sizeof(T) == 1 ? 0xFFu : 0xFFFFu);
+          if (p.add) {
+            const uint32_t old = dst[b];
+            bad |= old > p.emask;
+            v ^= old & p.emask;
+          }
+          dst[b] = (T)v;
         }
-        dst[b] = (T)v;
       }
     }
   }
@@ -570,8 +570,9 @@ __device__ __forceinline__ void recombine_body(const RecombineParams& p, int64_t
     g = live ? idx % ng : 0;
   }
   if (!live) r = g = 0;
-  const int64_t w0 = p.blocked ? (g >> 1) * p.tw + 4 * (g & 1) : 4 * g;  // output word of u = 0
-  const int uvalid = p.blocked ? min(4, p.tw - 4 * (int)(g & 1)) : 4;    // words of this thread that exist
+  // output column of word u = 0, and this thread's columns within its tile
+  const int64_t cs0 = p.blocked ? (g >> 1) * p.tcols + 128 * (g & 1) : 128 * g;
+  const int tc = p.blocked ? p.tcols - 128 * (int)(g & 1) : 128;
   uint32_t out[4][E];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -579,7 +580,7 @@ __device__ __forceinline__ void recombine_body(const RecombineParams& p, int64_t
     for (int s = 0; s < E; ++s) out[u][s] = 0;
   if (live) {
     const uint32_t* base = p.blocked ? p.P + ((r >> 7) * p.tiles_n + (g >> 1)) * 1024 + (r & 127) * 8 + 4 * (g & 1)
-                                     : p.P + r * p.ldw + w0;
+                                     : p.P + r * p.ldw + 4 * g;
     const uint4* src = reinterpret_cast<const uint4*>(base);
     const int64_t pstride = (p.blocked ? p.bstride : p.rows_p * p.ldw) / 4;  // in 16-byte groups
 #pragma unroll 8
@@ -599,8 +600,10 @@ __device__ __forceinline__ void recombine_body(const RecombineParams& p, int64_t
   bool bad = false;
   if (live) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (u < uvalid && w0 + u < nw) bad |= store_elements<T, E>(p, r, w0 + u, out[u]);
+    for (int u = 0; u < 4; ++u) {
+      const int nc = min(32, tc - 32 * u);
+      if (nc > 0 && cs0 + 32 * u < p.n) bad |= store_elements<T, E>(p, r, cs0 + 32 * u, nc, out[u]);
+    }
   }
   flag_range(p.status, bad);
 }
@@ -851,7 +854,9 @@ cudaError_t launch_recombine_batched(const RecombineParams* d_jobs, const int64_
 cudaError_t launch_recombine(const RecombineParams& p, cudaStream_t s, int64_t* launches) {
   const int64_t g = recombine_job_blocks(p);
   if (p.r > 64 || (reinterpret_cast<uintptr_t>(p.P) & 15u) != 0) return cudaErrorInvalidValue;
-  if (p.blocked ? (p.tw < 1 || p.tw > 8 || p.bstride % 4 != 0 || p.tiles_n * p.tw * 32 < p.n) : p.ldw % 4 != 0)
+  if (p.blocked ? (p.tcols < 16 || p.tcols > 256 || p.tcols % 16 != 0 || p.bstride % 4 != 0 ||
+                   p.tiles_n * p.tcols < p.n)
+                : p.ldw % 4 != 0)
     return cudaErrorInvalidValue;
   switch (p.e) {
     case 2: return launch_pdl(recombine_kernel<uint8_t, 2>, g, 256, s, launches, p.pdl != 0, p);

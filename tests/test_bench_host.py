@@ -54,9 +54,12 @@ def test_traffic_pin_only_for_the_profiled_source_and_workload(monkeypatch):
     import hashlib
     by_name = {w.name: w for w in workloads.WORKLOADS.values()}
     # pin the recorded hashes to the sources as they stand, so that only the workload decides here
-    for key, (fname, _) in list(bench.PROFILED_SOURCES.items()):
+    def current(fname):
         with open(os.path.join(bench.ROOT, "paper_1111_6900_gb300", "csrc", fname), "rb") as fh:
-            monkeypatch.setitem(bench.PROFILED_SOURCES, key, (fname, hashlib.sha256(fh.read()).hexdigest()))
+            return fname, hashlib.sha256(fh.read()).hexdigest()
+
+    for key, pins in list(bench.PROFILED_SOURCES.items()):
+        monkeypatch.setitem(bench.PROFILED_SOURCES, key, tuple(current(f) for f, _ in pins))
     monkeypatch.setattr(bench, "WORKLOAD", by_name["gf16_4096_mul"])
     t = bench.TRAFFIC["tc_f4/karatsuba"]["bytes"]
     assert bench.kernel_traffic("tc_f4/karatsuba") == t
@@ -66,8 +69,13 @@ def test_traffic_pin_only_for_the_profiled_source_and_workload(monkeypatch):
     assert bench.kernel_traffic("newton_john/alpha_b") == bench.TRAFFIC["newton_john/alpha_b"]["bytes"]
     assert bench.kernel_traffic("tc_f4/karatsuba") is None
     # a changed source voids the pin
-    monkeypatch.setitem(bench.PROFILED_SOURCES, "newton_john/alpha_b", ("nj_kernel.cuh", "0" * 64))
+    monkeypatch.setitem(bench.PROFILED_SOURCES, "newton_john/alpha_b", (("nj_kernel.cuh", "0" * 64),))
     assert bench.kernel_traffic("newton_john/alpha_b") is None
+    # so does a change to any one of several pinned sources (the launching host code)
+    monkeypatch.setattr(bench, "WORKLOAD", by_name["gf16_4096_mul"])
+    monkeypatch.setitem(bench.PROFILED_SOURCES, "tc_f4/karatsuba",
+                        (current("gemm_tc.cu"), ("api.cu", "0" * 64)))
+    assert bench.kernel_traffic("tc_f4/karatsuba") is None
 
 
 def test_triangular_solve_multiply_adds():
