@@ -124,11 +124,14 @@ bool use_karatsuba(const m4rie_ctx* ctx, const m4rie_problem& p, int r) {
 }
 
 // Tile width of one product of a batch: kTileWide, the widest tile of its
-// form (alpha^j-B: e G columns with G = tc_group(e); Karatsuba: 224 for FP4,
+// form (alpha^j-B: e G columns with G = tc_group(e); Karatsuba: 240 for FP4,
 // 256 for FP8), or kTileNarrow, the narrowest tile that still covers the
 // product's columns in one tile where they are fewer; the tuner's measured
 // choice for the class, else wide for alpha^j-B and narrow for Karatsuba.
 enum { kTileDefault = 0, kTileWide = 1, kTileNarrow = 2 };
+// the wide Karatsuba tile: FP4 MMAs of N = 240 (its scale factors take TMEM
+// columns 240..255), FP8 ones of N = 256
+constexpr int kara_wide(int fmt) { return fmt == kFmtNib ? 240 : 256; }
 int tile_choice(const m4rie_ctx* ctx, const m4rie_problem& p, bool kara) {
   if (ctx->batched_force_width) return ctx->batched_force_width;
   const TuneEntry& t = ctx->btuned[p.e][shape_class(p.m, p.n, p.k)];
@@ -236,11 +239,11 @@ m4rie_status run_batched(m4rie_ctx* ctx, int count, const m4rie_problem* pr, int
     L.Mp = round_up(p.m, 128);
     if (karatsuba_schedule(p.e, p.f, &L.sc) && use_karatsuba(ctx, p, L.sc.r)) {
       // r products L_p(A) R_p(B); tiles as wide as the columns need, at most
-      // 224 (FP4) or 256 (FP8), in whole 32-column words of the parity blocks
+      // 240 (FP4) or 256 (FP8), in whole 16-column groups of the parity blocks
       L.kara = true;
       L.r = L.sc.r;
-      const int wide = fmt == kFmtNib ? 224 : 256;
-      L.BN = tile_choice(ctx, p, true) == kTileNarrow ? (int)std::min<int64_t>(wide, round_up(p.n, 32)) : wide;
+      const int wide = kara_wide(fmt);
+      L.BN = tile_choice(ctx, p, true) == kTileNarrow ? (int)std::min<int64_t>(wide, round_up(p.n, 16)) : wide;
       L.G = L.BN;
       L.ld = L.Kp;
       L.ld_bytes = L.ld * bits / 8;
@@ -598,8 +601,8 @@ extern "C" m4rie_status m4rie_tune_batched(m4rie_ctx* ctx, int count, const m4ri
       // the narrow tile is another candidate only where some product of the class has fewer columns
       if (width == kTileNarrow) {
         bool differs = false;
-        for (int t = 0; t < take; ++t) differs |= sub[t].n < (sched == M4RIE_SCHED_KARATSUBA ? (fmt == kFmtNib ? 224 : 256)
-                                                                                             : tc_group(e, fmt));
+        for (int t = 0; t < take; ++t)
+          differs |= sub[t].n < (sched == M4RIE_SCHED_KARATSUBA ? kara_wide(fmt) : tc_group(e, fmt));
         if (!differs) continue;
       }
       ctx->batched_force = sched;

@@ -78,6 +78,16 @@ def test_traffic_pin_only_for_the_profiled_source_and_workload(monkeypatch):
     assert bench.kernel_traffic("tc_f4/karatsuba") is None
 
 
+def test_recorded_traffic_pins_match_the_sources():
+    """The committed pins hold for the sources as committed: a kernel or
+    launch change without a new capture must show up here."""
+    import hashlib
+    for key, pins in bench.PROFILED_SOURCES.items():
+        for fname, sha in pins:
+            with open(os.path.join(bench.ROOT, "paper_1111_6900_gb300", "csrc", fname), "rb") as fh:
+                assert hashlib.sha256(fh.read()).hexdigest() == sha, (key, fname)
+
+
 def test_triangular_solve_multiply_adds():
     # one leaf: the whole triangle times n columns
     assert bench.trsm_macs(100, 7) == 100 * 100 * 7
