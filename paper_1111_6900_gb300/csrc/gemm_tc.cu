@@ -237,6 +237,15 @@ __device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
+// Arrive without release semantics: for a hand-over whose only hazard is on
+// tensor memory, whose accesses the arriving warp has already waited for
+// (tcgen05.wait::ld / wait::st) and ordered by tcgen05.fence::before_thread_sync.
+__device__ __forceinline__ void mbar_arrive_relaxed_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_relaxed(uint32_t bar) {
+  asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -506,7 +515,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, CG2 ? 256 : 128);  // CG2: both CTAs' epilogues
+      mbar_init(tempty0 + 8 * b, CG2 ? 8 : 4);  // one arrival per epilogue warp (CG2: of both CTAs)
     }
     mbar_init(drain, 1);
     mbar_init(never, 1);
@@ -774,9 +783,16 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
         tmem_fill_bias(ta, bias_cols(FMT));  // the next chunk in this buffer starts at 2^23 again
+        // The warp's TMEM loads and stores are complete (wait::ld, wait::st)
+        // and ordered before the arrive by the tcgen05 fence, which is all the
+        // MMAs that next write this buffer depend on: one lane of the warp
+        // arrives, without release semantics.
         fence_before();
-        if (CG2) mbar_arrive_cluster(mapa_rank(tempty0 + 8 * buf, 0));  // the even CTA's barrier
-        else mbar_arrive(tempty0 + 8 * buf);
+        __syncwarp();
+        if (lane == 0) {
+          if (CG2) mbar_arrive_relaxed_cluster(mapa_rank(tempty0 + 8 * buf, 0));  // the even CTA's barrier
+          else mbar_arrive_relaxed(tempty0 + 8 * buf);
+        }
         ++chunk;
       }
       if (!ok) continue;
