@@ -257,14 +257,14 @@ __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// 16 consecutive accumulator columns of this thread's lane, without waiting
-// (tmem_wait_ld waits for every load issued before it).
-__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
+// 16 consecutive accumulator columns of this thread's lane, the low 16 bits
+// of each (which hold a count's parity bit), two columns to a register:
+// register i holds column 2i in bits 0..15 and column 2i + 1 in bits 16..31.
+// Does not wait (tmem_wait_ld waits for every load issued before it).
+__device__ __forceinline__ void tmem_ld16_packed(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.pack::16b.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -760,25 +760,27 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         fence_after();
         const uint32_t ta = tmem + lane_base + buf * ACC_COLS;
-        // 64 columns per round: four loads in flight, then one wait
+        // 128 columns per round: eight packed loads in flight (each round
+        // trip to tensor memory costs several hundred clocks), then one wait
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          uint32_t v[4][16];
+        for (int g = 0; g < 2; ++g) {
+          uint32_t v[8][8];
 #pragma unroll
-          for (int h = 0; h < 4; ++h)
-            if (4 * g + h < nc16) tmem_ld16_async(ta + 16 * (4 * g + h), v[h]);
-          if (4 * g < nc16) tmem_wait_ld();
+          for (int h = 0; h < 8; ++h)
+            if (8 * g + h < nc16) tmem_ld16_packed(ta + 16 * (8 * g + h), v[h]);
+          if (8 * g < nc16) tmem_wait_ld();
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const int c16 = 4 * g + h;
+          for (int h = 0; h < 8; ++h) {
+            const int c16 = 8 * g + h;
             if (c16 < nc16) {
-              {
-                uint32_t w = 0;
-                // parity of the count: bit 0 of 2^23 + x (kBias)
+              // parity of the count: bit 0 of 2^23 + x (kBias), i.e. bits 0
+              // and 16 of a packed register; t gathers column 2i's at bit 2i
+              // and column 2i + 1's at bit 16 + 2i
+              uint32_t t = 0;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) w |= (v[h][j] & 1u) << j;
-                bits[c16 >> 1] ^= w << (16 * (c16 & 1));
-              }
+              for (int i = 0; i < 8; ++i) t |= (v[h][i] & 0x00010001u) << (2 * i);
+              const uint32_t w = (t & 0x5555u) | ((t >> 15) & 0xAAAAu);
+              bits[c16 >> 1] ^= w << (16 * (c16 & 1));
             }
           }
         }
